@@ -1,0 +1,135 @@
+/*
+ * smg.h -- C ABI of libsmg: SMG-preconditioned PCG / flexible PCG / PSD and LOBPCG for the
+ * 7-point 3D Dirichlet Laplacian, on one GB300 GPU (sm_103a).
+ *
+ * Method: Bouwmeester, Dougherty, Knyazev, "Nonsymmetric multigrid preconditioning for
+ * conjugate gradient methods", arXiv:1212.6680.
+ *   - Algorithm 1 (section "PSD and PCG methods"), beta from eq. (1) (standard PCG),
+ *     eq. (2) (flexible PCG) or beta = 0 (PSD).
+ *   - SMG preconditioner T with -v npre npost relaxation (section "Preconditioning with SMG").
+ *   - LOBPCG preconditioned by SMG (section "Preconditioning of LOBPCG with SMG").
+ * The model problem (section "PSD and PCG methods"): negative Laplacian, 7-point stencil,
+ * grid spacing one, homogeneous Dirichlet boundary, on the interior points of an
+ * nx x ny x nz brick.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Layout.  A grid vector holds N = nx*ny*nz doubles, index (z*ny + y)*nx + x (x fastest).
+ *           A block of m vectors is column-major N x m: vector j starts at element j*N.
+ *  Memory.  Vector pointers are caller-owned.  Unless an entry point says otherwise they are
+ *           device pointers (e.g. PyTorch CUDA tensors) on the current device.  The handle owns
+ *           the hierarchy and all scratch space; smg_setup allocates them and smg_destroy
+ *           frees them.
+ *  Streams. `stream` is a cudaStream_t (NULL = the legacy default stream).  Work on one handle
+ *           is stream-ordered.  A handle is not thread-safe: one host thread at a time.
+ *  Errors.  Every entry point returns SMG_OK (0) or a negative SMG_ERR_* code.  Invalid
+ *           arguments return SMG_ERR_ARG before anything is launched or written.
+ *           smg_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef SMG_H
+#define SMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smg_ctx *smg_handle; /* opaque; owns the hierarchy and workspace */
+
+enum {
+    SMG_OK = 0,
+    SMG_ERR_ARG = -1,       /* invalid argument; nothing was launched */
+    SMG_ERR_CUDA = -2,      /* a CUDA call failed (message in smg_last_error) */
+    SMG_ERR_NOCONV = -3,    /* maxit reached; the last iterate is returned */
+    SMG_ERR_BREAKDOWN = -4, /* (p, Ap) <= 0 or (s_{k-1}, r_{k-1}) = 0 in Algorithm 1 */
+    SMG_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+    SMG_ERR_NAN = -6        /* NaN or Inf met in a residual norm or inner product */
+};
+
+enum { SMG_PCG = 0, SMG_FPCG = 1, SMG_PSD = 2 };       /* eq. (1), eq. (2), beta = 0 */
+enum { SMG_FP64 = 0, SMG_FP32 = 1, SMG_BF16 = 2 };     /* V-cycle storage precision */
+
+/* Options for smg_set_option. */
+enum {
+    SMG_OPT_COARSE_ITERS = 0, /* plane-cycle steps on the one-plane coarsest level (>= 1, default 1) */
+    SMG_OPT_THREADS = 1,      /* threads per CTA of the plane-relaxation kernel: 256 or 512 */
+    SMG_OPT_PROFILE = 2       /* 1: time every plane-relaxation launch with CUDA events */
+};
+
+/*
+ * smg_setup -- build the SMG hierarchy for the nx x ny x nz brick (section "Preconditioning
+ * with SMG": -v npre npost).  npre >= 1 pre-relaxation sweeps, npost >= 0 post-relaxation
+ * sweeps (npost = 0 is the paper's nonsymmetric "no post-relaxation" cycle).  The hierarchy
+ * is computed on the host in FP64 (z-semicoarsening, Galerkin coarse operators, per-plane
+ * y-hierarchies) and copied to the current device; work vectors for one right-hand side are
+ * allocated.  Sizes: 1 <= nx <= 512, 1 <= ny <= 512, 1 <= nz <= 4096.  *out receives the handle.
+ * The cycle precision starts as SMG_FP64.
+ */
+int smg_setup(int nx, int ny, int nz, int npre, int npost, smg_handle *out);
+
+/* smg_set_precision -- storage precision of the V-cycle: SMG_FP64, SMG_FP32 or SMG_BF16.
+ * FP32 computes in FP32; BF16 stores level vectors in bfloat16 and computes in FP32.  The
+ * one-plane coarsest level always computes in FP64.  Krylov recurrences, inner products and
+ * norms stay FP64. */
+int smg_set_precision(smg_handle h, int prec);
+
+/* smg_set_option -- set one SMG_OPT_* option (see the enum). */
+int smg_set_option(smg_handle h, int option, int value);
+
+/*
+ * smg_apply -- s = T r, one V-cycle with zero initial guess (the preconditioner of
+ * Algorithm 1).  r and s: device, N doubles each, must not overlap.
+ */
+int smg_apply(smg_handle h, const double *r, double *s, void *stream);
+
+/*
+ * smg_apply_batched -- S = T R for nb right-hand sides at once (R, S: device, N x nb
+ * column-major).  All nb cycles run in the same launches.  1 <= nb <= 64.
+ */
+int smg_apply_batched(smg_handle h, int nb, const double *R, double *S, void *stream);
+
+/* smg_apply_A -- out = A u, the 7-point operator in FP64 (device, N doubles each). */
+int smg_apply_A(smg_handle h, const double *u, double *out, void *stream);
+
+/*
+ * krylov_solve -- Algorithm 1 with T = SMG: variant SMG_PCG (eq. (1)), SMG_FPCG (eq. (2)) or
+ * SMG_PSD (beta = 0).  x holds x0 on entry and the solution on exit.  Stops when the FP64 true
+ * residual satisfies ||b - A x||_2 <= tol ||b||_2 (the recurrence residual is tested first;
+ * if the true residual then fails, the solver continues from it with beta = 0).
+ * b and x may be device pointers or host pointers (pageable or pinned); for host pointers
+ * the library copies b and x0 to the device and x back, inside the call, and returns after
+ * the copy back.  *iters (preconditioner applications) and *relres (true relative residual)
+ * are always written.  Returns SMG_ERR_NOCONV after maxit iterations (last iterate in x).
+ * tol > 0, maxit >= 0.  Synchronises `stream` once per iteration (8-byte residual readback).
+ */
+int krylov_solve(smg_handle h, int variant, const double *b, double *x, double tol, int maxit,
+                 int *iters, double *relres, void *stream);
+
+/*
+ * lobpcg_solve -- the m smallest eigenpairs of A by LOBPCG preconditioned with T (section
+ * "Preconditioning of LOBPCG with SMG"; m = 1 in the paper).  X (device, N x m column-major)
+ * holds the initial block on entry and the eigenvector approximations on exit; lambda (host,
+ * m doubles) receives the Ritz values in ascending order.  Converged when every column has
+ * ||A x_i - lambda_i x_i||_2 <= tol * lambda_i * ||x_i||_2.  1 <= m <= 64, 3m <= N.
+ */
+int lobpcg_solve(smg_handle h, int m, double *X, double *lambda, double tol, int maxit,
+                 int *iters, void *stream);
+
+/* smg_destroy -- free the handle and everything it owns (NULL is accepted). */
+int smg_destroy(smg_handle h);
+
+/* smg_last_error -- message of the calling thread's last failed call ("" if none). */
+const char *smg_last_error(void);
+
+/*
+ * smg_profile_read -- when SMG_OPT_PROFILE is on, the plane-relaxation launches timed so far
+ * on this handle: launches, total device milliseconds (CUDA events on the launch stream) and
+ * algorithmic bytes (vector elements the launches must read and write), split by level:
+ * level 0 (the finest) and all coarser levels together (which = 0 or 1).  Reading resets
+ * the counters of that class.  Synchronises the device.
+ */
+int smg_profile_read(smg_handle h, int which, long long *launches, double *ms, double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,528 @@
+// api.cpp -- the C ABI of libsmg (include/smg.h): handle lifetime, argument checks, the SMG
+// V-cycle launch sequence and the Krylov driver of Algorithm 1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/smg.h"
+#include "krylov.h"
+#include "lobpcg.h"
+#include "smg_internal.h"
+
+using namespace smg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define SMG_CUDA(call)                                                                               \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(SMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+constexpr size_t kSmemBudget = 200 * 1024;
+
+struct ProfClass {
+    long long launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
+
+struct PendingEvent {
+    cudaEvent_t a, b;
+    int cls;
+    double bytes;
+};
+
+}  // namespace
+
+struct smg_ctx {
+    int nx = 0, ny = 0, nz = 0, npre = 1, npost = 1, coarse_iters = 1, threads = 512;
+    Prec prec = Prec::F64;
+    HostHierarchy H;
+    double *d_zcoef = nullptr, *d_pcoef = nullptr;
+    // level storage (current precision) for nb_alloc right-hand sides
+    int nb_alloc = 0;
+    Prec alloc_prec = Prec::F64;
+    std::vector<void *> d_f, d_u;   // [L]; level 0 entries used only when the caller's buffers are not
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    PlaneLayout lay_c, lay_d;       // compute type = storage compute (float/double) and double (coarsest)
+    // Krylov vectors (one right-hand side)
+    double *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_dr = nullptr;
+    double *d_bh = nullptr, *d_xh = nullptr;  // device copies for host-pointer calls
+    KrylovWork kw;
+    KrylovScalars *h_sc = nullptr;  // pinned host mirror
+    // profiling
+    bool profile = false;
+    ProfClass prof[2];
+    std::vector<PendingEvent> pending;
+    std::vector<cudaEvent_t> event_pool;
+    // LOBPCG state
+    LobpcgWork lw;
+
+    long long N() const { return static_cast<long long>(nx) * ny * nz; }
+    long long Nl(int l) const { return static_cast<long long>(nx) * ny * H.nz_l[l]; }
+};
+
+namespace {
+
+void free_levels(smg_ctx *h) {
+    for (void *p : h->d_f) cudaFree(p);
+    for (void *p : h->d_u) cudaFree(p);
+    h->d_f.clear();
+    h->d_u.clear();
+    cudaFree(h->d_ws);
+    h->d_ws = nullptr;
+    h->ws_bytes = 0;
+    h->nb_alloc = 0;
+}
+
+size_t compute_bytes(Prec p) { return p == Prec::F64 ? 8 : 4; }
+
+int instantiated_K(int nx) {
+    const int k = (nx + 31) / 32;
+    if (k <= 4) return k;
+    if (k <= 6) return 6;
+    if (k <= 8) return 8;
+    return 16;
+}
+
+// Allocate level vectors for nb right-hand sides in the current precision, and the plane
+// workspace; configure the kernels' dynamic shared memory.
+int ensure_levels(smg_ctx *h, int nb) {
+    if (h->nb_alloc >= nb && h->alloc_prec == h->prec) return SMG_OK;
+    free_levels(h);
+    const HostHierarchy &H = h->H;
+    const size_t sb = storage_bytes(h->prec);
+    h->d_f.assign(H.L, nullptr);
+    h->d_u.assign(H.L, nullptr);
+    for (int l = 0; l < H.L; ++l) {
+        const size_t bytes = static_cast<size_t>(h->Nl(l)) * nb * sb;
+        SMG_CUDA(cudaMalloc(&h->d_f[l], bytes));
+        SMG_CUDA(cudaMalloc(&h->d_u[l], bytes));
+    }
+    h->lay_c = plan_plane_layout(H, compute_bytes(h->prec), kSmemBudget);
+    h->lay_d = plan_plane_layout(H, 8, kSmemBudget);
+    const long long slots = static_cast<long long>((H.nz + 1) / 2) * nb;
+    const size_t per = std::max(static_cast<size_t>(h->lay_c.ws_per_plane) * compute_bytes(h->prec),
+                                static_cast<size_t>(h->lay_d.ws_per_plane) * 8);
+    h->ws_bytes = std::max<size_t>(per * slots, 256);
+    SMG_CUDA(cudaMalloc(&h->d_ws, h->ws_bytes));
+    const bool f64c = (h->prec == Prec::F64);
+    const int K = instantiated_K(h->nx);
+    if (set_plane_relax_smem(h->prec, f64c, K, h->threads, h->lay_c.smem_bytes) != 0)
+        return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, level precision) failed");
+    if (set_plane_relax_smem(h->prec, true, K, h->threads, h->lay_d.smem_bytes) != 0)
+        return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, FP64 coarsest) failed");
+    h->nb_alloc = nb;
+    h->alloc_prec = h->prec;
+    return SMG_OK;
+}
+
+cudaEvent_t take_event(smg_ctx *h) {
+    if (h->event_pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+}
+
+// One plane-relaxation launch: colour c of level l, all nb right-hand sides.
+int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, const void *f, void *u, int nb,
+          cudaStream_t st) {
+    const HostHierarchy &H = h->H;
+    const int nzl = H.nz_l[l];
+    const int nplanes = colour == 0 ? (nzl + 1) / 2 : nzl / 2;
+    if (nplanes == 0) return SMG_OK;
+    const bool f64c = coarsest || h->prec == Prec::F64;
+    const PlaneLayout &lay = (f64c && h->prec != Prec::F64) ? h->lay_d : h->lay_c;
+    PlaneRelaxArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.nz = nzl;
+    a.colour = colour;
+    a.mode = mode;
+    a.iters = iters;
+    a.f = f;
+    a.u = u;
+    a.vstride = h->Nl(l);
+    a.zcoef = h->d_zcoef + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane;
+    a.pcoef = h->d_pcoef + static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine;
+    a.gws = h->d_ws;
+    a.ws_per_plane = lay.ws_per_plane;
+    a.P = H.P;
+    a.sum_ny = H.sum_ny;
+    for (int m = 0; m < H.P; ++m) {
+        a.ny_m[m] = H.ny_m[m];
+        a.line_base[m] = H.line_base[m];
+        a.off_u[m] = lay.off_u[m];
+        a.off_g[m] = lay.off_g[m];
+    }
+    a.smem_u_mask = lay.smem_u_mask;
+    a.smem_g_mask = lay.smem_g_mask;
+    const int K = instantiated_K(h->nx);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profile) {
+        e0 = take_event(h);
+        e1 = take_event(h);
+        cudaEventRecord(e0, st);
+    }
+    cudaError_t err = launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
+    if (err != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("plane relaxation launch: ") + cudaGetErrorString(err));
+    if (h->profile) {
+        cudaEventRecord(e1, st);
+        // algorithmic traffic: read f_z, write u_z (+ read u_z in correction form) for every
+        // relaxed plane, and read each opposite-colour plane once when it can be nonzero
+        const double np = static_cast<double>(h->nx) * h->ny;
+        const int nother = nzl - nplanes;
+        double planes = nplanes * (2.0 + (mode == 2 ? 1.0 : 0.0)) + (mode >= 1 ? nother : 0);
+        planes *= iters;
+        const double bytes = planes * np * nb * static_cast<double>(storage_bytes(h->prec));
+        h->pending.push_back(PendingEvent{e0, e1, l == 0 ? 0 : 1, bytes});
+    }
+    return SMG_OK;
+}
+
+// u0 = T f0 for nb right-hand sides; f0, u0 in storage precision, level-0 layout.
+int run_cycle(smg_ctx *h, int nb, const void *f0, void *u0, cudaStream_t st) {
+    const HostHierarchy &H = h->H;
+    const int L = H.L;
+    int rc;
+    auto F = [&](int l) -> const void * { return l == 0 ? f0 : h->d_f[l]; };
+    auto U = [&](int l) -> void * { return l == 0 ? u0 : h->d_u[l]; };
+    for (int l = 0; l + 1 < L; ++l) {
+        for (int s = 0; s < h->npre; ++s) {
+            if ((rc = relax(h, l, 0, s == 0 ? 0 : 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
+            if ((rc = relax(h, l, 1, s == 0 ? 1 : 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
+        }
+        cudaError_t e = launch_restrict(h->prec, h->nx, h->ny, H.nz_l[l], nb, F(l), U(l), h->d_f[l + 1],
+                                        h->d_zcoef + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
+                                        h->Nl(l), h->Nl(l + 1), st);
+        if (e != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("restriction launch: ") + cudaGetErrorString(e));
+    }
+    if ((rc = relax(h, L - 1, 0, 0, h->coarse_iters, true, F(L - 1), U(L - 1), nb, st)) != SMG_OK) return rc;
+    for (int l = L - 2; l >= 0; --l) {
+        cudaError_t e = launch_prolong(h->prec, h->nx, h->ny, H.nz_l[l], nb, U(l), U(l + 1),
+                                       h->d_zcoef + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
+                                       h->Nl(l), h->Nl(l + 1), st);
+        if (e != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("prolongation launch: ") + cudaGetErrorString(e));
+        for (int s = 0; s < h->npost; ++s) {
+            if ((rc = relax(h, l, 1, 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
+            if ((rc = relax(h, l, 0, 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
+        }
+    }
+    return SMG_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_handle(smg_handle h) {
+    if (h == nullptr) return fail(SMG_ERR_ARG, "null handle");
+    return SMG_OK;
+}
+
+int ensure_krylov(smg_ctx *h) {
+    if (h->d_r) return SMG_OK;
+    const size_t b = static_cast<size_t>(h->N()) * sizeof(double);
+    SMG_CUDA(cudaMalloc(&h->d_r, b));
+    SMG_CUDA(cudaMalloc(&h->d_p, b));
+    SMG_CUDA(cudaMalloc(&h->d_q, b));
+    SMG_CUDA(cudaMalloc(&h->d_dr, b));
+    SMG_CUDA(cudaMalloc(&h->kw.sc, sizeof(KrylovScalars)));
+    SMG_CUDA(cudaMalloc(&h->kw.part, sizeof(double) * 2 * 2 * kMaxReduceBlocks));
+    SMG_CUDA(cudaMalloc(&h->kw.counter, sizeof(unsigned)));
+    SMG_CUDA(cudaMemset(h->kw.counter, 0, sizeof(unsigned)));
+    SMG_CUDA(cudaMemset(h->kw.sc, 0, sizeof(KrylovScalars)));
+    SMG_CUDA(cudaMallocHost(&h->h_sc, sizeof(KrylovScalars)));
+    return SMG_OK;
+}
+
+int read_scalars(smg_ctx *h, cudaStream_t st) {
+    SMG_CUDA(cudaMemcpyAsync(h->h_sc, h->kw.sc, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st));
+    SMG_CUDA(cudaStreamSynchronize(st));
+    return SMG_OK;
+}
+
+int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double tol, int maxit, int *iters,
+                  double *relres, cudaStream_t st) {
+    int rc;
+    if ((rc = ensure_levels(h, 1)) != SMG_OK) return rc;
+    if ((rc = ensure_krylov(h)) != SMG_OK) return rc;
+    const bool f64 = (h->prec == Prec::F64);
+    void *f0 = f64 ? static_cast<void *>(h->d_r) : h->d_f[0];     // cycle input  = (S) r
+    void *u0 = h->d_u[0];                                           // cycle output s = T r
+    void *f0k = f64 ? nullptr : f0;                                 // what the Krylov kernels write
+    KrylovScalars init;
+    std::memset(&init, 0, sizeof(init));
+    init.variant = variant;
+    SMG_CUDA(cudaMemcpyAsync(h->kw.sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+    SMG_CUDA(kry_init_residual(h->prec, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+    const double tol2 = tol * tol;
+    int k = 0, status = SMG_ERR_NOCONV;
+    double tt = -1.0;
+    for (k = 0;; ++k) {
+        if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
+        const KrylovScalars &s = *h->h_sc;
+        if (s.status != 0) {
+            status = s.status;
+            break;
+        }
+        const double bb = s.bb > 0.0 ? s.bb : 1.0;
+        if (s.rr <= tol2 * bb) {
+            SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, st));
+            if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
+            tt = h->h_sc->tt;
+            if (tt <= tol2 * bb) {
+                status = SMG_OK;
+                break;
+            }
+            // continue from the true residual, with beta = 0 on the next step
+            SMG_CUDA(kry_init_residual(h->prec, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+            tt = -1.0;
+        }
+        if (k >= maxit) {
+            status = SMG_ERR_NOCONV;
+            break;
+        }
+        if ((rc = run_cycle(h, 1, f0, u0, st)) != SMG_OK) return rc;
+        SMG_CUDA(kry_iteration_tail(h->prec, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, st));
+    }
+    if (tt < 0.0) {
+        SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, st));
+        if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
+        tt = h->h_sc->tt;
+    }
+    const double bb = h->h_sc->bb > 0.0 ? h->h_sc->bb : 1.0;
+    *iters = k;
+    *relres = std::sqrt(tt / bb);
+    if (status == SMG_ERR_NOCONV) return fail(SMG_ERR_NOCONV, "maximum number of iterations reached");
+    if (status == SMG_ERR_BREAKDOWN) return fail(status, "breakdown: (p, Ap) <= 0 or (s_{k-1}, r_{k-1}) = 0");
+    if (status == SMG_ERR_NAN) return fail(status, "NaN or Inf in a residual norm or inner product");
+    return status;
+}
+
+}  // namespace
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+extern "C" {
+
+const char *smg_last_error(void) { return g_last_error.c_str(); }
+
+int smg_setup(int nx, int ny, int nz, int npre, int npost, smg_handle *out) {
+    if (out == nullptr) return fail(SMG_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(SMG_ERR_ARG, "grid sizes must be >= 1");
+    if (nx > kMaxNx) return fail(SMG_ERR_ARG, "nx must be <= 512");
+    if (ny > kMaxNy) return fail(SMG_ERR_ARG, "ny must be <= 512");
+    if (nz > kMaxNz) return fail(SMG_ERR_ARG, "nz must be <= 4096");
+    if (npre < 1) return fail(SMG_ERR_ARG, "npre must be >= 1");
+    if (npost < 0) return fail(SMG_ERR_ARG, "npost must be >= 0");
+    smg_ctx *h = new smg_ctx();
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->npre = npre;
+    h->npost = npost;
+    build_hierarchy(nx, ny, nz, h->H);
+    const size_t zb = h->H.zcoef.size() * sizeof(double), pb = h->H.pcoef.size() * sizeof(double);
+    cudaError_t e = cudaMalloc(&h->d_zcoef, zb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_pcoef, pb);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_zcoef, h->H.zcoef.data(), zb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_pcoef, h->H.pcoef.data(), pb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        smg_destroy(h);
+        return fail(SMG_ERR_CUDA, std::string("smg_setup: ") + cudaGetErrorString(e));
+    }
+    int rc = ensure_levels(h, 1);
+    if (rc != SMG_OK) {
+        smg_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return SMG_OK;
+}
+
+int smg_set_precision(smg_handle h, int prec) {
+    if (int rc = check_handle(h)) return rc;
+    if (prec != SMG_FP64 && prec != SMG_FP32 && prec != SMG_BF16) return fail(SMG_ERR_ARG, "unknown precision");
+    h->prec = static_cast<Prec>(prec);
+    return SMG_OK;
+}
+
+int smg_set_option(smg_handle h, int option, int value) {
+    if (int rc = check_handle(h)) return rc;
+    switch (option) {
+    case SMG_OPT_COARSE_ITERS:
+        if (value < 1 || value > 64) return fail(SMG_ERR_ARG, "coarse_iters must be in [1, 64]");
+        h->coarse_iters = value;
+        return SMG_OK;
+    case SMG_OPT_THREADS:
+        if (value != 256 && value != 512) return fail(SMG_ERR_ARG, "threads must be 256 or 512");
+        h->threads = value;
+        return SMG_OK;
+    case SMG_OPT_PROFILE:
+        h->profile = (value != 0);
+        return SMG_OK;
+    }
+    return fail(SMG_ERR_ARG, "unknown option");
+}
+
+int smg_apply_batched(smg_handle h, int nb, const double *R, double *S, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (nb < 1 || nb > 64) return fail(SMG_ERR_ARG, "nb must be in [1, 64]");
+    if (R == nullptr || S == nullptr) return fail(SMG_ERR_ARG, "null vector");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc;
+    if ((rc = ensure_levels(h, nb)) != SMG_OK) return rc;
+    const long long n = h->N() * nb;
+    if (h->prec == Prec::F64) return run_cycle(h, nb, R, S, st);
+    SMG_CUDA(launch_convert_to(h->prec, n, R, h->d_f[0], st));
+    if ((rc = run_cycle(h, nb, h->d_f[0], h->d_u[0], st)) != SMG_OK) return rc;
+    SMG_CUDA(launch_convert_from(h->prec, n, h->d_u[0], S, st));
+    return SMG_OK;
+}
+
+int smg_apply(smg_handle h, const double *r, double *s, void *stream) {
+    return smg_apply_batched(h, 1, r, s, stream);
+}
+
+int smg_apply_A(smg_handle h, const double *u, double *out, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (u == nullptr || out == nullptr) return fail(SMG_ERR_ARG, "null vector");
+    SMG_CUDA(launch_apply_A(h->nx, h->ny, h->nz, 1, u, out, static_cast<cudaStream_t>(stream)));
+    return SMG_OK;
+}
+
+int krylov_solve(smg_handle h, int variant, const double *b, double *x, double tol, int maxit, int *iters,
+                 double *relres, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    if (variant != SMG_PCG && variant != SMG_FPCG && variant != SMG_PSD) return fail(SMG_ERR_ARG, "unknown variant");
+    if (b == nullptr || x == nullptr || iters == nullptr || relres == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SMG_ERR_ARG, "tol must be > 0");
+    if (maxit < 0) return fail(SMG_ERR_ARG, "maxit must be >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    if (bdev && xdev) return krylov_device(h, variant, b, x, tol, maxit, iters, relres, st);
+    // host buffers: copy in, solve, copy out
+    const size_t bytes = static_cast<size_t>(h->N()) * sizeof(double);
+    if (h->d_bh == nullptr) {
+        SMG_CUDA(cudaMalloc(&h->d_bh, bytes));
+        SMG_CUDA(cudaMalloc(&h->d_xh, bytes));
+    }
+    const double *bd = b;
+    double *xd = x;
+    if (!bdev) {
+        SMG_CUDA(cudaMemcpyAsync(h->d_bh, b, bytes, cudaMemcpyHostToDevice, st));
+        bd = h->d_bh;
+    }
+    if (!xdev) {
+        SMG_CUDA(cudaMemcpyAsync(h->d_xh, x, bytes, cudaMemcpyHostToDevice, st));
+        xd = h->d_xh;
+    }
+    int rc = krylov_device(h, variant, bd, xd, tol, maxit, iters, relres, st);
+    if (rc != SMG_OK && rc != SMG_ERR_NOCONV) return rc;
+    if (!xdev) {
+        SMG_CUDA(cudaMemcpyAsync(x, h->d_xh, bytes, cudaMemcpyDeviceToHost, st));
+        SMG_CUDA(cudaStreamSynchronize(st));
+    }
+    return rc;
+}
+
+int lobpcg_solve(smg_handle h, int m, double *X, double *lambda, double tol, int maxit, int *iters, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (iters) *iters = 0;
+    if (X == nullptr || lambda == nullptr || iters == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    if (m < 1 || m > 64 || 3LL * m > h->N()) return fail(SMG_ERR_ARG, "m must satisfy 1 <= m <= 64 and 3m <= N");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SMG_ERR_ARG, "tol must be > 0");
+    if (maxit < 0) return fail(SMG_ERR_ARG, "maxit must be >= 0");
+    int rc;
+    if ((rc = ensure_levels(h, m)) != SMG_OK) return rc;
+    LobpcgOps ops;
+    ops.n = h->N();
+    ops.apply_A = [h](int nb, const double *u, double *out, cudaStream_t st) -> int {
+        cudaError_t e = launch_apply_A(h->nx, h->ny, h->nz, nb, u, out, st);
+        return e == cudaSuccess ? SMG_OK : fail(SMG_ERR_CUDA, std::string("apply_A: ") + cudaGetErrorString(e));
+    };
+    ops.apply_T = [h](int nb, const double *r, double *s, cudaStream_t st) -> int {
+        return smg_apply_batched(h, nb, r, s, st);
+    };
+    std::string msg;
+    rc = lobpcg_run(ops, h->lw, m, X, lambda, tol, maxit, iters, static_cast<cudaStream_t>(stream), msg);
+    if (rc != SMG_OK) return fail(rc, msg);
+    return SMG_OK;
+}
+
+int smg_profile_read(smg_handle h, int which, long long *launches, double *ms, double *bytes) {
+    if (int rc = check_handle(h)) return rc;
+    if (which < 0 || which > 1 || !launches || !ms || !bytes) return fail(SMG_ERR_ARG, "bad arguments");
+    SMG_CUDA(cudaDeviceSynchronize());
+    for (auto &p : h->pending) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, p.a, p.b);
+        h->prof[p.cls].launches += 1;
+        h->prof[p.cls].ms += t;
+        h->prof[p.cls].bytes += p.bytes;
+        h->event_pool.push_back(p.a);
+        h->event_pool.push_back(p.b);
+    }
+    h->pending.clear();
+    *launches = h->prof[which].launches;
+    *ms = h->prof[which].ms;
+    *bytes = h->prof[which].bytes;
+    h->prof[which] = ProfClass();
+    return SMG_OK;
+}
+
+int smg_destroy(smg_handle h) {
+    if (h == nullptr) return SMG_OK;
+    free_levels(h);
+    cudaFree(h->d_zcoef);
+    cudaFree(h->d_pcoef);
+    cudaFree(h->d_r);
+    cudaFree(h->d_p);
+    cudaFree(h->d_q);
+    cudaFree(h->d_dr);
+    cudaFree(h->d_bh);
+    cudaFree(h->d_xh);
+    cudaFree(h->kw.sc);
+    cudaFree(h->kw.part);
+    cudaFree(h->kw.counter);
+    if (h->h_sc) cudaFreeHost(h->h_sc);
+    for (auto &p : h->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    lobpcg_free(h->lw);
+    delete h;
+    return SMG_OK;
+}
+
+}  // extern "C"

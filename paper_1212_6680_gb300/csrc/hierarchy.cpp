@@ -1,0 +1,229 @@
+// hierarchy.cpp -- host construction of the SMG hierarchy in FP64 (setup, done once).
+//
+// SMG (section "Preconditioning with SMG" of arXiv:1212.6680) coarsens in z; each plane is
+// relaxed by a 2D cycle that coarsens in y with exact x-line solves.  The paper leaves the
+// internals open; the library uses this semicoarsening reading:
+//   * coarse points are the odd 0-based indices, n_{l+1} = floor(n_l / 2), down to 1;
+//   * interpolation injects coarse points and gives each even fine point the weights
+//     -X(i, i+-1) / X(i, i) of the coupling matrix X obtained by collapsing the interior
+//     stencil across the non-coarsened directions (for z: X = K_l; for y: X = T_m);
+//   * restriction is the transpose and coarse operators are Galerkin products P^T A P.
+// Operators keep the Kronecker form
+//   (A_l u)_z = sum_dz M_l(z,z+dz) L2D u_{z+dz} + K_l(z,z+dz) u_{z+dz},   M_0 = I, K_0 = tridiag(-1,2,-1)
+//   (B_m u)_y = sum_dy S_m(y,y+dy) Lx u_{y+dy} + T_m(y,y+dy) u_{y+dy},   S_0 = c I, T_0 = c Ly + d I
+// with c = M_l(z,z), d = K_l(z,z) for the plane operator B = c L2D + d I of plane z.
+#include <algorithm>
+#include <array>
+#include <cstdio>
+
+#include "smg_internal.h"
+
+namespace smg {
+namespace {
+
+// Tridiagonal matrix as three diagonals: lo[i] = X(i,i-1), di[i] = X(i,i), up[i] = X(i,i+1).
+struct Tridiag {
+    std::vector<double> lo, di, up;
+    explicit Tridiag(int n = 0) : lo(n, 0.0), di(n, 0.0), up(n, 0.0) {}
+    int size() const { return static_cast<int>(di.size()); }
+};
+
+struct Weights {
+    std::vector<double> wm, wp;  // per fine point; zero for coarse (odd) points
+};
+
+Weights collapse_weights(const Tridiag &X) {
+    const int n = X.size();
+    Weights w{std::vector<double>(n, 0.0), std::vector<double>(n, 0.0)};
+    for (int i = 0; i < n; i += 2) {
+        if (i > 0) w.wm[i] = -X.lo[i] / X.di[i];
+        if (i + 1 < n) w.wp[i] = -X.up[i] / X.di[i];
+    }
+    return w;
+}
+
+// Galerkin product P^T X P for the interpolation given by w.  P has, in column j (coarse
+// point j <-> fine 2j+1): 1 at row 2j+1, wp(2j) at row 2j, wm(2j+2) at row 2j+2.
+Tridiag galerkin(const Tridiag &X, const Weights &w) {
+    const int n = X.size(), nc = n / 2;
+    Tridiag C(nc);
+    // column j of P as (row, weight) triples
+    auto col = [&](int j, std::array<std::pair<int, double>, 3> &out) {
+        int cnt = 0;
+        out[cnt++] = {2 * j + 1, 1.0};
+        out[cnt++] = {2 * j, w.wp[2 * j]};
+        if (2 * j + 2 < n) out[cnt++] = {2 * j + 2, w.wm[2 * j + 2]};
+        else out[cnt++] = {-1, 0.0};
+        return cnt;
+    };
+    auto xget = [&](int i, int k) -> double {
+        if (i < 0 || k < 0 || i >= n || k >= n) return 0.0;
+        if (k == i) return X.di[i];
+        if (k == i - 1) return X.lo[i];
+        if (k == i + 1) return X.up[i];
+        return 0.0;
+    };
+    for (int i = 0; i < nc; ++i) {
+        std::array<std::pair<int, double>, 3> ci, cj;
+        col(i, ci);
+        for (int j = std::max(0, i - 1); j <= std::min(nc - 1, i + 1); ++j) {
+            col(j, cj);
+            double v = 0.0;
+            for (auto &a : ci) {
+                if (a.first < 0) continue;
+                for (auto &b : cj) {
+                    if (b.first < 0) continue;
+                    v += a.second * xget(a.first, b.first) * b.second;
+                }
+            }
+            if (j == i) C.di[i] = v;
+            else if (j == i - 1) C.lo[i] = v;
+            else C.up[i] = v;
+        }
+    }
+    return C;
+}
+
+int num_levels(int n) {
+    int c = 1;
+    while (n > 1) {
+        n /= 2;
+        ++c;
+    }
+    return c;
+}
+
+}  // namespace
+
+void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H) {
+    H = HostHierarchy();
+    H.nx = nx;
+    H.ny = ny;
+    H.nz = nz;
+    H.L = num_levels(nz);
+    H.P = num_levels(ny);
+    H.nz_l.resize(H.L);
+    H.plane_base.resize(H.L);
+    H.ny_m.resize(H.P);
+    H.line_base.resize(H.P);
+    {
+        int n = ny, base = 0;
+        for (int m = 0; m < H.P; ++m) {
+            H.ny_m[m] = n;
+            H.line_base[m] = base;
+            base += n;
+            n /= 2;
+        }
+        H.sum_ny = base;
+    }
+    {
+        int n = nz, base = 0;
+        for (int l = 0; l < H.L; ++l) {
+            H.nz_l[l] = n;
+            H.plane_base[l] = base;
+            base += n;
+            n /= 2;
+        }
+        H.nplanes_total = base;
+    }
+    H.zcoef.assign(static_cast<size_t>(H.nplanes_total) * kCoefPerPlane, 0.0);
+    H.pcoef.assign(static_cast<size_t>(H.nplanes_total) * H.sum_ny * kCoefPerLine, 0.0);
+
+    Tridiag M(nz), K(nz);
+    for (int z = 0; z < nz; ++z) {
+        M.di[z] = 1.0;
+        K.di[z] = 2.0;
+        if (z > 0) K.lo[z] = -1.0;
+        if (z + 1 < nz) K.up[z] = -1.0;
+    }
+    for (int l = 0; l < H.L; ++l) {
+        const int n = M.size();
+        Weights w = (l + 1 < H.L) ? collapse_weights(K)
+                                  : Weights{std::vector<double>(n, 0.0), std::vector<double>(n, 0.0)};
+        for (int z = 0; z < n; ++z) {
+            double *zc = &H.zcoef[static_cast<size_t>(H.plane_base[l] + z) * kCoefPerPlane];
+            zc[0] = M.lo[z];
+            zc[1] = M.di[z];
+            zc[2] = M.up[z];
+            zc[3] = K.lo[z];
+            zc[4] = K.di[z];
+            zc[5] = K.up[z];
+            zc[6] = w.wm[z];
+            zc[7] = w.wp[z];
+            // the plane's 2D hierarchy for B = c L2D + d I
+            const double c = M.di[z], d = K.di[z];
+            Tridiag S(ny), T(ny);
+            for (int y = 0; y < ny; ++y) {
+                S.di[y] = c;
+                T.di[y] = 2.0 * c + d;
+                if (y > 0) T.lo[y] = -c;
+                if (y + 1 < ny) T.up[y] = -c;
+            }
+            double *pc = &H.pcoef[static_cast<size_t>(H.plane_base[l] + z) * H.sum_ny * kCoefPerLine];
+            for (int m = 0; m < H.P; ++m) {
+                const int nym = S.size();
+                Weights wy = (m + 1 < H.P) ? collapse_weights(T)
+                                           : Weights{std::vector<double>(nym, 0.0), std::vector<double>(nym, 0.0)};
+                for (int y = 0; y < nym; ++y) {
+                    double *lc = pc + static_cast<size_t>(H.line_base[m] + y) * kCoefPerLine;
+                    lc[0] = S.lo[y];
+                    lc[1] = S.di[y];
+                    lc[2] = S.up[y];
+                    lc[3] = T.lo[y];
+                    lc[4] = T.di[y];
+                    lc[5] = T.up[y];
+                    lc[6] = wy.wm[y];
+                    lc[7] = wy.wp[y];
+                }
+                if (m + 1 < H.P) {
+                    Tridiag Sc = galerkin(S, wy), Tc = galerkin(T, wy);
+                    S = Sc;
+                    T = Tc;
+                }
+            }
+        }
+        if (l + 1 < H.L) {
+            Tridiag Mc = galerkin(M, w), Kc = galerkin(K, w);
+            M = Mc;
+            K = Kc;
+        }
+    }
+}
+
+// Greedy placement of the 2D-cycle arrays: the coefficient table first, then the coarsest
+// levels (latency-bound, few lines) and finally the finest; u_m before g_m at each level
+// (the iterate is touched more often than the right-hand side).  What does not fit in
+// `smem_budget` goes to a global slot per CTA (L2-resident for the sizes of interest).
+PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget) {
+    PlaneLayout P;
+    P.K = (H.nx + 31) / 32;
+    size_t smem_elems = static_cast<size_t>(H.sum_ny) * kCoefPerLine;  // coefficient table
+    long long gl = 0;
+    auto align4 = [](size_t v) { return (v + 3) & ~static_cast<size_t>(3); };
+    smem_elems = align4(smem_elems);
+    const size_t budget_elems = smem_budget / elem_bytes;
+    for (int m = H.P - 1; m >= 0; --m) {
+        const size_t sz = align4(static_cast<size_t>(H.nx) * H.ny_m[m]);
+        for (int which = 0; which < 2; ++which) {
+            if (smem_elems + sz <= budget_elems) {
+                if (which == 0) {
+                    P.off_u[m] = static_cast<int>(smem_elems);
+                    P.smem_u_mask |= 1u << m;
+                } else {
+                    P.off_g[m] = static_cast<int>(smem_elems);
+                    P.smem_g_mask |= 1u << m;
+                }
+                smem_elems += sz;
+            } else {
+                if (which == 0) P.off_u[m] = static_cast<int>(gl);
+                else P.off_g[m] = static_cast<int>(gl);
+                gl += static_cast<long long>(sz);
+            }
+        }
+    }
+    P.smem_bytes = smem_elems * elem_bytes;
+    P.ws_per_plane = gl;
+    return P;
+}
+
+}  // namespace smg

@@ -1,0 +1,297 @@
+// krylov_kernels.cu -- FP64 kernels of Algorithm 1 (section "PSD and PCG methods" of
+// arXiv:1212.6680): s_k = T r_k, p_k = s_k + beta_k p_{k-1}, alpha_k = (s_k, r_k)/(p_k, A p_k),
+// x_{k+1} = x_k + alpha_k p_k, r_{k+1} = r_k - alpha_k A p_k, with beta_k from eq. (1)
+// (standard PCG), eq. (2) (flexible PCG, extra vector r_k - r_{k-1}) or 0 (PSD).
+//
+// The scalars live on the device (KrylovScalars); the last CTA of each reduction kernel
+// combines the per-CTA partial sums and computes the scalar the next kernel needs, so one
+// iteration runs without the host.  Inner products: each thread accumulates its products
+// with FMA, then partials are combined with error-free TwoSum (compensated summation).
+// The preconditioned residual s is read straight from the V-cycle's level-0 storage
+// (FP64, FP32 or BF16): widening it to FP64 is exact, so no FP64 copy of s is made.
+#include <cuda_bf16.h>
+
+#include "krylov.h"
+#include "plane_relax.cuh"
+
+namespace smg {
+
+struct DSum {
+    double s, c;
+};
+
+__device__ __forceinline__ void two_sum_acc(DSum &a, double b) {
+    const double t = a.s + b;
+    const double bp = t - a.s;
+    const double err = (a.s - (t - bp)) + (b - bp);
+    a.s = t;
+    a.c += err;
+}
+__device__ __forceinline__ DSum dsum_combine(DSum a, const DSum &b) {
+    two_sum_acc(a, b.s);
+    a.c += b.c;
+    return a;
+}
+__device__ __forceinline__ DSum shfl_down_dsum(const DSum &v, int o) {
+    return DSum{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+}
+
+// Block-reduce NV compensated sums; on return thread 0 holds the block totals.
+template <int NV>
+__device__ __forceinline__ void block_reduce(DSum (&v)[NV]) {
+    __shared__ DSum sh[NV][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] = dsum_combine(v[k], shfl_down_dsum(v[k], o));
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            v[k] = (lane < nw) ? sh[k][lane] : DSum{0.0, 0.0};
+            for (int o = 16; o > 0; o >>= 1) v[k] = dsum_combine(v[k], shfl_down_dsum(v[k], o));
+        }
+    }
+    __syncthreads();
+}
+
+// Write this block's partials; the last block to finish reduces all of them into tot[].
+// Returns true in every thread of the last block.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(DSum (&v)[NV], DSum *part, unsigned *counter, double (&tot)[NV]) {
+    __shared__ bool last;
+    block_reduce<NV>(v);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) part[static_cast<size_t>(blockIdx.x) * NV + k] = v[k];
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    DSum w[NV];
+    for (int k = 0; k < NV; ++k) w[k] = DSum{0.0, 0.0};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+        for (int k = 0; k < NV; ++k) {
+            const volatile DSum *vp = &part[static_cast<size_t>(b) * NV + k];
+            const DSum pb{vp->s, vp->c};
+            w[k] = dsum_combine(w[k], pb);
+        }
+    block_reduce<NV>(w);
+    __shared__ double res[NV];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) res[k] = w[k].s + w[k].c;
+        *counter = 0u;
+    }
+    __syncthreads();
+    for (int k = 0; k < NV; ++k) tot[k] = res[k];
+    return true;
+}
+
+__device__ __forceinline__ double stencil7(const double *__restrict__ u, long long i, int x, int y, int z, int nx,
+                                           int ny, int nz, long long np) {
+    double nb = 0.0;
+    if (x > 0) nb += u[i - 1];
+    if (x < nx - 1) nb += u[i + 1];
+    if (y > 0) nb += u[i - nx];
+    if (y < ny - 1) nb += u[i + nx];
+    if (z > 0) nb += u[i - np];
+    if (z < nz - 1) nb += u[i + np];
+    return 6.0 * u[i] - nb;
+}
+
+// r = b - A x ; f0 = (S) r ; rr = ||r||^2 ; bb = ||b||^2 ; restart = 1.
+template <class S>
+__global__ void k_init_residual(int nx, int ny, int nz, const double *__restrict__ b, const double *__restrict__ x,
+                                double *__restrict__ r, S *__restrict__ f0, KrylovScalars *sc, DSum *part,
+                                unsigned *counter) {
+    const long long np = static_cast<long long>(nx) * ny, n = np * nz;
+    DSum v[2] = {{0.0, 0.0}, {0.0, 0.0}};
+    double a0 = 0.0, a1 = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int xx = static_cast<int>(i % nx), yy = static_cast<int>((i / nx) % ny), zz = static_cast<int>(i / np);
+        const double bi = b[i];
+        const double ri = bi - stencil7(x, i, xx, yy, zz, nx, ny, nz, np);
+        r[i] = ri;
+        if (f0 != nullptr) stv<S, double>(f0 + i, ri);
+        a0 = fma(ri, ri, a0);
+        a1 = fma(bi, bi, a1);
+    }
+    v[0].s = a0;
+    v[1].s = a1;
+    double tot[2];
+    if (grid_reduce<2>(v, part, counter, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->bb = tot[1];
+        sc->restart = 1;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) sc->status = -6;
+    }
+}
+
+// tt = ||b - A x||^2 (true residual).
+__global__ void k_true_residual(int nx, int ny, int nz, const double *__restrict__ b, const double *__restrict__ x,
+                                KrylovScalars *sc, DSum *part, unsigned *counter) {
+    const long long np = static_cast<long long>(nx) * ny, n = np * nz;
+    DSum v[1] = {{0.0, 0.0}};
+    double a0 = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int xx = static_cast<int>(i % nx), yy = static_cast<int>((i / nx) % ny), zz = static_cast<int>(i / np);
+        const double ri = b[i] - stencil7(x, i, xx, yy, zz, nx, ny, nz, np);
+        a0 = fma(ri, ri, a0);
+    }
+    v[0].s = a0;
+    double tot[1];
+    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) sc->tt = tot[0];
+}
+
+// rho = (s, r), sdr = (s, r_k - r_{k-1}); beta by eq. (1), eq. (2) or 0.
+template <class S>
+__global__ void k_dots_beta(long long n, const S *__restrict__ s, const double *__restrict__ r,
+                            const double *__restrict__ dr, KrylovScalars *sc, DSum *part, unsigned *counter) {
+    const int variant = sc->variant;
+    const bool need_sdr = (variant == 1) && (sc->restart == 0);
+    DSum v[2] = {{0.0, 0.0}, {0.0, 0.0}};
+    double a0 = 0.0, a1 = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double si = ldv<double>(s + i);
+        a0 = fma(si, r[i], a0);
+        if (need_sdr) a1 = fma(si, dr[i], a1);
+    }
+    v[0].s = a0;
+    v[1].s = a1;
+    double tot[2];
+    if (grid_reduce<2>(v, part, counter, tot) && threadIdx.x == 0) {
+        const double rho = tot[0];
+        double beta = 0.0;
+        if (sc->restart == 0 && variant != 2) {
+            if (sc->rho_prev == 0.0) {
+                sc->status = -4;
+            } else {
+                beta = (variant == 0) ? rho / sc->rho_prev : tot[1] / sc->rho_prev;
+            }
+        }
+        if (!isfinite(rho) || !isfinite(beta)) sc->status = -6;
+        sc->rho = rho;
+        sc->sdr = tot[1];
+        sc->beta = beta;
+    }
+}
+
+// p = s + beta p
+template <class S>
+__global__ void k_update_p(long long n, const S *__restrict__ s, double *__restrict__ p, const KrylovScalars *sc) {
+    const double beta = sc->beta;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double si = ldv<double>(s + i);
+        p[i] = (beta == 0.0) ? si : fma(beta, p[i], si);
+    }
+}
+
+// q = A p ; pq = (p, q) ; alpha = rho / pq
+__global__ void k_spmv_alpha(int nx, int ny, int nz, const double *__restrict__ p, double *__restrict__ q,
+                             KrylovScalars *sc, DSum *part, unsigned *counter) {
+    const long long np = static_cast<long long>(nx) * ny, n = np * nz;
+    DSum v[1] = {{0.0, 0.0}};
+    double a0 = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int xx = static_cast<int>(i % nx), yy = static_cast<int>((i / nx) % ny), zz = static_cast<int>(i / np);
+        const double qi = stencil7(p, i, xx, yy, zz, nx, ny, nz, np);
+        q[i] = qi;
+        a0 = fma(p[i], qi, a0);
+    }
+    v[0].s = a0;
+    double tot[1];
+    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        sc->pq = pq;
+        if (!(pq > 0.0)) {
+            sc->status = (pq == pq) ? -4 : -6;
+            sc->alpha = 0.0;
+        } else {
+            sc->alpha = sc->rho / pq;
+        }
+    }
+}
+
+// x += alpha p ; r_new = r - alpha q ; dr = r_new - r ; r = r_new ; f0 = (S) r_new ; rr = ||r_new||^2
+template <class S>
+__global__ void k_update_xr(long long n, double *__restrict__ x, const double *__restrict__ p, double *__restrict__ r,
+                            const double *__restrict__ q, double *__restrict__ dr, S *__restrict__ f0,
+                            KrylovScalars *sc, DSum *part, unsigned *counter) {
+    const double alpha = sc->alpha;
+    const bool want_dr = (sc->variant == 1);
+    DSum v[1] = {{0.0, 0.0}};
+    double a0 = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ro = r[i];
+        const double rn = fma(-alpha, q[i], ro);
+        if (want_dr) dr[i] = rn - ro;
+        r[i] = rn;
+        if (f0 != nullptr) stv<S, double>(f0 + i, rn);
+        a0 = fma(rn, rn, a0);
+    }
+    v[0].s = a0;
+    double tot[1];
+    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->rho_prev = sc->rho;
+        sc->restart = 0;
+        if (!isfinite(tot[0])) sc->status = -6;
+    }
+}
+
+// ---- launchers --------------------------------------------------------------------------------
+int reduction_blocks(long long n) {
+    long long b = (n + 256LL * 8 - 1) / (256LL * 8);
+    if (b < 1) b = 1;
+    if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+    return static_cast<int>(b);
+}
+
+#define SMG_PREC_SWITCH(storage, ...)                               \
+    switch (storage) {                                              \
+    case Prec::F64: { using S = double; __VA_ARGS__; break; }       \
+    case Prec::F32: { using S = float; __VA_ARGS__; break; }        \
+    case Prec::BF16: { using S = __nv_bfloat16; __VA_ARGS__; break; } \
+    }
+
+cudaError_t kry_init_residual(Prec st_prec, int nx, int ny, int nz, const double *b, const double *x, double *r,
+                              void *f0, KrylovWork &w, cudaStream_t st) {
+    const long long n = static_cast<long long>(nx) * ny * nz;
+    const int nb = reduction_blocks(n);
+    SMG_PREC_SWITCH(st_prec, k_init_residual<S><<<nb, 256, 0, st>>>(nx, ny, nz, b, x, r, static_cast<S *>(f0),
+                                                                      w.sc, w.part, w.counter));
+    return cudaGetLastError();
+}
+
+cudaError_t kry_true_residual(int nx, int ny, int nz, const double *b, const double *x, KrylovWork &w,
+                              cudaStream_t st) {
+    const long long n = static_cast<long long>(nx) * ny * nz;
+    k_true_residual<<<reduction_blocks(n), 256, 0, st>>>(nx, ny, nz, b, x, w.sc, w.part, w.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void *s, double *x, double *r, double *p,
+                               double *q, double *dr, void *f0, KrylovWork &w, cudaStream_t st) {
+    const long long n = static_cast<long long>(nx) * ny * nz;
+    const int nb = reduction_blocks(n);
+    SMG_PREC_SWITCH(st_prec, {
+        k_dots_beta<S><<<nb, 256, 0, st>>>(n, static_cast<const S *>(s), r, dr, w.sc, w.part, w.counter);
+        k_update_p<S><<<nb, 256, 0, st>>>(n, static_cast<const S *>(s), p, w.sc);
+        k_spmv_alpha<<<nb, 256, 0, st>>>(nx, ny, nz, p, q, w.sc, w.part, w.counter);
+        k_update_xr<S><<<nb, 256, 0, st>>>(n, x, p, r, q, dr, static_cast<S *>(f0), w.sc, w.part, w.counter);
+    });
+    return cudaGetLastError();
+}
+
+}  // namespace smg

@@ -1,0 +1,486 @@
+// lobpcg.cu -- block LOBPCG with SMG preconditioning.
+//
+// Locally optimal block preconditioned conjugate gradient (Knyazev's LOBPCG, which the paper
+// runs through BLOPEX, section "Preconditioning of LOBPCG with SMG" of arXiv:1212.6680) for
+// the m smallest eigenpairs of A:
+//   R = A X - X Lambda;  W = T R (one batched V-cycle over the active columns);
+//   Rayleigh-Ritz on span[X, W, P]:  (S^T A S) C = (S^T S) C Theta, S = [X W P];
+//   X = S C_m, P = [W P] C_{WP,m}.
+// Columns whose residual meets the tolerance are soft-locked (kept in X, dropped from W, P).
+// W is orthogonalised against X and W, P are orthonormalised (Cholesky QR) before the
+// Rayleigh-Ritz step, so S^T S stays well conditioned.
+// Device: FP64 block kernels (Gram products with split-K partial sums, tall-skinny block
+// updates).  Host: the k x k (k <= 3m) FP64 generalized eigenproblem by Cholesky reduction
+// and cyclic Jacobi.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "../../include/smg.h"
+#include "lobpcg.h"
+
+namespace smg {
+
+namespace {
+
+constexpr int kGT = 48;          // Gram output tile (kGT x kGT per CTA)
+constexpr int kGRows = 32;       // rows staged per step
+constexpr int kGChunk = 8192;    // rows per CTA (split-K)
+constexpr int kMulCols = 16;     // output columns per block_mul thread
+
+// Partial Gram: part[chunk][ti][tj] tile of U^T V over rows [chunk*kGChunk, ...).
+__global__ void gram_partial_kernel(long long n, int k1, int k2, const double *__restrict__ U,
+                                    const double *__restrict__ V, double *__restrict__ part, int ntj) {
+    __shared__ double su[kGRows][kGT + 1];
+    __shared__ double sv[kGRows][kGT + 1];
+    const int tile = blockIdx.y, ti = tile / ntj, tj = tile % ntj;
+    const int i0 = ti * kGT, j0 = tj * kGT;
+    const long long r0 = static_cast<long long>(blockIdx.x) * kGChunk;
+    const long long r1 = min(n, r0 + kGChunk);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 3 x 3 outputs each
+    double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (long long rb = r0; rb < r1; rb += kGRows) {
+        for (int t = threadIdx.x; t < kGRows * kGT; t += blockDim.x) {
+            const int rr = t % kGRows, cc = t / kGRows;
+            const long long r = rb + rr;
+            su[rr][cc] = (r < r1 && i0 + cc < k1) ? U[static_cast<long long>(i0 + cc) * n + r] : 0.0;
+            sv[rr][cc] = (r < r1 && j0 + cc < k2) ? V[static_cast<long long>(j0 + cc) * n + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kGRows; ++rr) {
+            const double a0 = su[rr][ty], a1 = su[rr][ty + 16], a2 = su[rr][ty + 32];
+            const double b0 = sv[rr][tx], b1 = sv[rr][tx + 16], b2 = sv[rr][tx + 32];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[0][2] = fma(a0, b2, acc[0][2]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+            acc[1][2] = fma(a1, b2, acc[1][2]);
+            acc[2][0] = fma(a2, b0, acc[2][0]);
+            acc[2][1] = fma(a2, b1, acc[2][1]);
+            acc[2][2] = fma(a2, b2, acc[2][2]);
+        }
+        __syncthreads();
+    }
+    double *out = part + (static_cast<long long>(blockIdx.x) * gridDim.y + tile) * kGT * kGT;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) out[(ty + 16 * a) * kGT + tx + 16 * b] = acc[a][b];
+}
+
+// G[i][j] (k1 x k2 row-major) = sum over chunks of the partial tiles (compensated summation).
+__global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int ntiles, const double *__restrict__ part,
+                                   double *__restrict__ G) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= k1 * k2) return;
+    const int i = idx / k2, j = idx % k2;
+    const int ti = i / kGT, tj = j / kGT, tile = ti * ntj + tj;
+    double s = 0.0, c = 0.0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const double v = part[(static_cast<long long>(ch) * ntiles + tile) * kGT * kGT + (i - ti * kGT) * kGT + (j - tj * kGT)];
+        const double t = s + v;
+        const double bp = t - s;
+        c += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+    G[idx] = s + c;
+}
+
+// Y = alpha * U C + beta * Y  (U: n x k, C: k x m2 row-major, Y: n x m2, column stride n)
+__global__ void block_mul_kernel(long long n, int k, int m2, const double *__restrict__ U,
+                                 const double *__restrict__ C, double alpha, double beta, double *__restrict__ Y) {
+    extern __shared__ double sc[];
+    const int j0 = blockIdx.y * kMulCols;
+    const int nc = min(kMulCols, m2 - j0);
+    for (int t = threadIdx.x; t < k * kMulCols; t += blockDim.x) {
+        const int i = t / kMulCols, j = t % kMulCols;
+        sc[t] = (j < nc) ? C[i * m2 + j0 + j] : 0.0;
+    }
+    __syncthreads();
+    const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double acc[kMulCols];
+#pragma unroll
+    for (int j = 0; j < kMulCols; ++j) acc[j] = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double u = U[static_cast<long long>(i) * n + r];
+#pragma unroll
+        for (int j = 0; j < kMulCols; ++j) acc[j] = fma(u, sc[i * kMulCols + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kMulCols; ++j) {
+        if (j < nc) {
+            double *y = Y + static_cast<long long>(j0 + j) * n + r;
+            *y = (beta == 0.0) ? alpha * acc[j] : fma(alpha, acc[j], beta * *y);
+        }
+    }
+}
+
+// R = AX - X diag(lambda)
+__global__ void residual_kernel(long long n, int m, const double *__restrict__ X, const double *__restrict__ AX,
+                                const double *__restrict__ lam, double *__restrict__ R) {
+    const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= n * m) return;
+    const int j = static_cast<int>(t / n);
+    R[t] = fma(-lam[j], X[t], AX[t]);
+}
+
+int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
+
+// ---- dense FP64 helpers ---------------------------------------------------------------------
+// Forward substitution helpers for L (lower, row-major).
+void lower_inverse_transpose(int k, const double *L, double *Z) {
+    // Z = L^{-T} (upper triangular), column by column: L^T Z = I
+    std::fill(Z, Z + static_cast<size_t>(k) * k, 0.0);
+    for (int c = 0; c < k; ++c) {
+        for (int i = k - 1; i >= 0; --i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int j = i + 1; j < k; ++j) v -= L[j * k + i] * Z[j * k + c];
+            Z[i * k + c] = v / L[i * k + i];
+        }
+    }
+}
+
+}  // namespace
+
+bool cholesky(int k, const double *A, double *L) {
+    std::fill(L, L + static_cast<size_t>(k) * k, 0.0);
+    for (int j = 0; j < k; ++j) {
+        double d = A[j * k + j];
+        for (int p = 0; p < j; ++p) d -= L[j * k + p] * L[j * k + p];
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        const double ljj = std::sqrt(d);
+        L[j * k + j] = ljj;
+        for (int i = j + 1; i < k; ++i) {
+            double v = A[i * k + j];
+            for (int p = 0; p < j; ++p) v -= L[i * k + p] * L[j * k + p];
+            L[i * k + j] = v / ljj;
+        }
+    }
+    return true;
+}
+
+void jacobi_eigh(int k, const double *Ain, double *w, double *V) {
+    std::vector<double> A(Ain, Ain + static_cast<size_t>(k) * k);
+    std::fill(V, V + static_cast<size_t>(k) * k, 0.0);
+    for (int i = 0; i < k; ++i) V[i * k + i] = 1.0;
+    double norm = 0.0;
+    for (double v : A) norm += v * v;
+    norm = std::sqrt(norm);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) off += A[p * k + q] * A[p * k + q];
+        if (std::sqrt(off) <= 1e-17 * norm || off == 0.0) break;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                const double apq = A[p * k + q];
+                if (apq == 0.0) continue;
+                const double app = A[p * k + p], aqq = A[q * k + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < k; ++r) {  // A <- A J
+                    const double arp = A[r * k + p], arq = A[r * k + q];
+                    A[r * k + p] = c * arp - s * arq;
+                    A[r * k + q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < k; ++r) {  // A <- J^T A
+                    const double apr = A[p * k + r], aqr = A[q * k + r];
+                    A[p * k + r] = c * apr - s * aqr;
+                    A[q * k + r] = s * apr + c * aqr;
+                }
+                A[p * k + q] = A[q * k + p] = 0.0;
+                for (int r = 0; r < k; ++r) {  // V <- V J
+                    const double vrp = V[r * k + p], vrq = V[r * k + q];
+                    V[r * k + p] = c * vrp - s * vrq;
+                    V[r * k + q] = s * vrp + c * vrq;
+                }
+            }
+    }
+    std::vector<int> idx(k);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A[a * k + a] < A[b * k + b]; });
+    std::vector<double> Vs(static_cast<size_t>(k) * k);
+    for (int c = 0; c < k; ++c) {
+        w[c] = A[idx[c] * k + idx[c]];
+        for (int r = 0; r < k; ++r) Vs[r * k + c] = V[r * k + idx[c]];
+    }
+    std::copy(Vs.begin(), Vs.end(), V);
+}
+
+namespace {
+
+struct Ctx {
+    const LobpcgOps &ops;
+    LobpcgWork &w;
+    cudaStream_t st;
+    std::string &msg;
+    long long n;
+};
+
+#define LCHK(call)                                                                 \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            c.msg = std::string("lobpcg: ") + #call + ": " + cudaGetErrorString(e_); \
+            return SMG_ERR_CUDA;                                                   \
+        }                                                                          \
+    } while (0)
+
+// G (k1 x k2, host row-major) = U^T V
+int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G) {
+    const int nti = cdiv(k1, kGT), ntj = cdiv(k2, kGT);
+    const int nch = cdiv(c.n, kGChunk);
+    dim3 grid(nch, nti * ntj);
+    gram_partial_kernel<<<grid, 256, 0, c.st>>>(c.n, k1, k2, U, V, c.w.part, ntj);
+    LCHK(cudaGetLastError());
+    gram_reduce_kernel<<<cdiv(static_cast<long long>(k1) * k2, 256), 256, 0, c.st>>>(nch, k1, k2, ntj, nti * ntj,
+                                                                                      c.w.part, c.w.gram);
+    LCHK(cudaGetLastError());
+    G.resize(static_cast<size_t>(k1) * k2);
+    LCHK(cudaMemcpyAsync(c.w.h_buf, c.w.gram, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c.st));
+    LCHK(cudaStreamSynchronize(c.st));
+    std::memcpy(G.data(), c.w.h_buf, sizeof(double) * G.size());
+    return SMG_OK;
+}
+
+// Y = alpha U C + beta Y with C (k x m2, host row-major)
+int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, double alpha, double beta, double *Y) {
+    LCHK(cudaMemcpyAsync(c.w.coef, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, c.st));
+    dim3 grid(cdiv(c.n, 256), cdiv(m2, kMulCols));
+    block_mul_kernel<<<grid, 256, sizeof(double) * k * kMulCols, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y);
+    LCHK(cudaGetLastError());
+    // the host vector C may be reused right after; the copy above is stream-ordered but reads
+    // host memory asynchronously only for pinned memory, so pageable C is safe here
+    return SMG_OK;
+}
+
+// Orthonormalize the q columns of Y in place (Cholesky QR), applying the same transform to AY
+// when given.  Returns false when Y^T Y is numerically singular.
+int ortho(Ctx &c, int q, double *Y, double *AY, double *tmp, bool &ok) {
+    std::vector<double> G, L(static_cast<size_t>(q) * q), Z(static_cast<size_t>(q) * q);
+    int rc = gram(c, q, Y, q, Y, G);
+    if (rc) return rc;
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < i; ++j) G[i * q + j] = G[j * q + i] = 0.5 * (G[i * q + j] + G[j * q + i]);
+    ok = cholesky(q, G.data(), L.data());
+    if (!ok) return SMG_OK;
+    lower_inverse_transpose(q, L.data(), Z.data());
+    const size_t bytes = sizeof(double) * static_cast<size_t>(q) * c.n;
+    if ((rc = bmul(c, q, Y, q, Z, 1.0, 0.0, tmp))) return rc;
+    LCHK(cudaMemcpyAsync(Y, tmp, bytes, cudaMemcpyDeviceToDevice, c.st));
+    if (AY) {
+        if ((rc = bmul(c, q, AY, q, Z, 1.0, 0.0, tmp))) return rc;
+        LCHK(cudaMemcpyAsync(AY, tmp, bytes, cudaMemcpyDeviceToDevice, c.st));
+    }
+    return SMG_OK;
+}
+
+// Generalized symmetric eigenproblem GA C = GB C Theta via GB = L L^T.
+bool rayleigh_ritz(int k, std::vector<double> GA, const std::vector<double> &GB, std::vector<double> &theta,
+                   std::vector<double> &C) {
+    std::vector<double> L(static_cast<size_t>(k) * k), Z(static_cast<size_t>(k) * k), H(static_cast<size_t>(k) * k),
+        T(static_cast<size_t>(k) * k), V(static_cast<size_t>(k) * k);
+    std::vector<double> GBs(GB);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < i; ++j) {
+            GA[i * k + j] = GA[j * k + i] = 0.5 * (GA[i * k + j] + GA[j * k + i]);
+            GBs[i * k + j] = GBs[j * k + i] = 0.5 * (GBs[i * k + j] + GBs[j * k + i]);
+        }
+    if (!cholesky(k, GBs.data(), L.data())) return false;
+    lower_inverse_transpose(k, L.data(), Z.data());  // Z = L^{-T}
+    // H = Z^T GA Z
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            double v = 0.0;
+            for (int p = 0; p < k; ++p) v += GA[i * k + p] * Z[p * k + j];
+            T[i * k + j] = v;
+        }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            double v = 0.0;
+            for (int p = 0; p < k; ++p) v += Z[p * k + i] * T[p * k + j];
+            H[i * k + j] = v;
+        }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < i; ++j) H[i * k + j] = H[j * k + i] = 0.5 * (H[i * k + j] + H[j * k + i]);
+    theta.resize(k);
+    jacobi_eigh(k, H.data(), theta.data(), V.data());
+    C.assign(static_cast<size_t>(k) * k, 0.0);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            double v = 0.0;
+            for (int p = 0; p < k; ++p) v += Z[i * k + p] * V[p * k + j];
+            C[i * k + j] = v;
+        }
+    return true;
+}
+
+}  // namespace
+
+void lobpcg_free(LobpcgWork &w) {
+    cudaFree(w.S);
+    cudaFree(w.AS);
+    cudaFree(w.T1);
+    cudaFree(w.T2);
+    cudaFree(w.part);
+    cudaFree(w.gram);
+    cudaFree(w.coef);
+    if (w.h_buf) cudaFreeHost(w.h_buf);
+    w = LobpcgWork();
+}
+
+int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double *lambda, double tol, int maxit,
+               int *iters, cudaStream_t st, std::string &msg) {
+    const long long n = ops.n;
+    Ctx c{ops, w, st, msg, n};
+    if (w.n != n || w.m < m) {
+        lobpcg_free(w);
+        w.n = n;
+        w.m = m;
+        const size_t blk = sizeof(double) * static_cast<size_t>(n) * 3 * m;
+        LCHK(cudaMalloc(&w.S, blk));
+        LCHK(cudaMalloc(&w.AS, blk));
+        LCHK(cudaMalloc(&w.T1, blk));
+        LCHK(cudaMalloc(&w.T2, blk));
+        const int k = 3 * m, nt = cdiv(k, kGT);
+        LCHK(cudaMalloc(&w.part, sizeof(double) * static_cast<size_t>(cdiv(n, kGChunk)) * nt * nt * kGT * kGT));
+        LCHK(cudaMalloc(&w.gram, sizeof(double) * k * k));
+        LCHK(cudaMalloc(&w.coef, sizeof(double) * k * k));
+        LCHK(cudaMallocHost(&w.h_buf, sizeof(double) * k * k));
+    }
+    const size_t col = sizeof(double) * static_cast<size_t>(n);
+    double *X = w.S, *AX = w.AS;
+    // P and AP for all m columns live in T2 (columns [0, m) and [m, 2m))
+    double *Pf = w.T2, *APf = w.T2 + static_cast<size_t>(n) * m;
+    int rc;
+    LCHK(cudaMemcpyAsync(X, Xuser, col * m, cudaMemcpyDeviceToDevice, st));
+    bool ok = false;
+    if ((rc = ortho(c, m, X, nullptr, w.T1, ok))) return rc;
+    if (!ok) {
+        msg = "lobpcg: the initial block is rank deficient";
+        return SMG_ERR_BREAKDOWN;
+    }
+    if ((rc = ops.apply_A(m, X, AX, st))) return rc;
+    // Rayleigh-Ritz on X alone
+    std::vector<double> GA, GB, theta, C;
+    if ((rc = gram(c, m, X, m, AX, GA))) return rc;
+    if ((rc = gram(c, m, X, m, X, GB))) return rc;
+    if (!rayleigh_ritz(m, GA, GB, theta, C)) {
+        msg = "lobpcg: Rayleigh-Ritz on the initial block failed";
+        return SMG_ERR_BREAKDOWN;
+    }
+    if ((rc = bmul(c, m, X, m, C, 1.0, 0.0, w.T1))) return rc;
+    LCHK(cudaMemcpyAsync(X, w.T1, col * m, cudaMemcpyDeviceToDevice, st));
+    if ((rc = bmul(c, m, AX, m, C, 1.0, 0.0, w.T1))) return rc;
+    LCHK(cudaMemcpyAsync(AX, w.T1, col * m, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> lam(theta.begin(), theta.begin() + m);
+    bool haveP = false;
+    int it = 0, status = SMG_ERR_NOCONV;
+    double *d_lam = w.coef;  // reused for lambda right before the residual kernel
+    for (it = 0;; ++it) {
+        // residuals R = AX - X Lambda into T1[:, 0:m]
+        double *R = w.T1;
+        LCHK(cudaMemcpyAsync(d_lam, lam.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        residual_kernel<<<cdiv(n * m, 256), 256, 0, st>>>(n, m, X, AX, d_lam, R);
+        LCHK(cudaGetLastError());
+        std::vector<double> GR;
+        if ((rc = gram(c, m, R, m, R, GR))) return rc;
+        std::vector<int> active;
+        for (int j = 0; j < m; ++j) {
+            const double rn = std::sqrt(std::max(0.0, GR[j * m + j]));
+            if (!std::isfinite(rn)) {
+                msg = "lobpcg: NaN in a residual";
+                return SMG_ERR_NAN;
+            }
+            if (rn > tol * std::fabs(lam[j])) active.push_back(j);
+        }
+        if (active.empty()) {
+            status = SMG_OK;
+            break;
+        }
+        if (it >= maxit) break;
+        const int na = static_cast<int>(active.size());
+        double *W = w.S + static_cast<size_t>(n) * m, *AW = w.AS + static_cast<size_t>(n) * m;
+        // gather the active residuals and precondition them: W = T R_active
+        for (int a = 0; a < na; ++a)
+            LCHK(cudaMemcpyAsync(AW + static_cast<size_t>(n) * a, R + static_cast<size_t>(n) * active[a], col,
+                                 cudaMemcpyDeviceToDevice, st));
+        if ((rc = ops.apply_T(na, AW, W, st))) return rc;
+        // W -= X (X^T W)
+        std::vector<double> XW;
+        if ((rc = gram(c, m, X, na, W, XW))) return rc;
+        if ((rc = bmul(c, m, X, na, XW, -1.0, 1.0, W))) return rc;
+        if ((rc = ortho(c, na, W, nullptr, R, ok))) return rc;
+        if (!ok) {
+            msg = "lobpcg: the preconditioned residual block is rank deficient";
+            return SMG_ERR_BREAKDOWN;
+        }
+        if ((rc = ops.apply_A(na, W, AW, st))) return rc;
+        // P block: active columns of the last direction, orthonormalized
+        int np = 0;
+        double *Pa = w.S + static_cast<size_t>(n) * (m + na), *APa = w.AS + static_cast<size_t>(n) * (m + na);
+        if (haveP) {
+            for (int a = 0; a < na; ++a) {
+                LCHK(cudaMemcpyAsync(Pa + static_cast<size_t>(n) * a, Pf + static_cast<size_t>(n) * active[a], col,
+                                     cudaMemcpyDeviceToDevice, st));
+                LCHK(cudaMemcpyAsync(APa + static_cast<size_t>(n) * a, APf + static_cast<size_t>(n) * active[a], col,
+                                     cudaMemcpyDeviceToDevice, st));
+            }
+            if ((rc = ortho(c, na, Pa, APa, R, ok))) return rc;
+            np = ok ? na : 0;
+        }
+        // Rayleigh-Ritz on S = [X W P]
+        int k = m + na + np;
+        if ((rc = gram(c, k, w.S, k, w.AS, GA))) return rc;
+        if ((rc = gram(c, k, w.S, k, w.S, GB))) return rc;
+        if (!rayleigh_ritz(k, GA, GB, theta, C)) {
+            if (np == 0) {
+                msg = "lobpcg: Gram matrix of [X W] is not positive definite";
+                return SMG_ERR_BREAKDOWN;
+            }
+            // drop P and retry
+            np = 0;
+            k = m + na;
+            std::vector<double> GA2(static_cast<size_t>(k) * k), GB2(static_cast<size_t>(k) * k);
+            const int kf = m + 2 * na;
+            for (int i = 0; i < k; ++i)
+                for (int j = 0; j < k; ++j) {
+                    GA2[i * k + j] = GA[i * kf + j];
+                    GB2[i * k + j] = GB[i * kf + j];
+                }
+            if (!rayleigh_ritz(k, GA2, GB2, theta, C)) {
+                msg = "lobpcg: Gram matrix of [X W] is not positive definite";
+                return SMG_ERR_BREAKDOWN;
+            }
+        }
+        // C_m = C[:, 0:m]; X = S C_m, AX = AS C_m; P = S_WP C_WP,m, AP = AS_WP C_WP,m
+        std::vector<double> Cm(static_cast<size_t>(k) * m), Cwp(static_cast<size_t>(k - m) * m);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < m; ++j) {
+                Cm[i * m + j] = C[i * k + j];
+                if (i >= m) Cwp[(i - m) * m + j] = C[i * k + j];
+            }
+        double *Xn = w.T1;  // T1 is free again (R no longer needed)
+        double *AXn = w.T1 + static_cast<size_t>(n) * m;
+        if ((rc = bmul(c, k, w.S, m, Cm, 1.0, 0.0, Xn))) return rc;
+        if ((rc = bmul(c, k, w.AS, m, Cm, 1.0, 0.0, AXn))) return rc;
+        if ((rc = bmul(c, k - m, W, m, Cwp, 1.0, 0.0, Pf))) return rc;
+        if ((rc = bmul(c, k - m, AW, m, Cwp, 1.0, 0.0, APf))) return rc;
+        LCHK(cudaMemcpyAsync(X, Xn, col * m, cudaMemcpyDeviceToDevice, st));
+        LCHK(cudaMemcpyAsync(AX, AXn, col * m, cudaMemcpyDeviceToDevice, st));
+        haveP = true;
+        for (int j = 0; j < m; ++j) lam[j] = theta[j];
+    }
+    LCHK(cudaMemcpyAsync(Xuser, X, col * m, cudaMemcpyDeviceToDevice, st));
+    LCHK(cudaStreamSynchronize(st));
+    for (int j = 0; j < m; ++j) lambda[j] = lam[j];
+    *iters = it;
+    if (status == SMG_ERR_NOCONV) msg = "lobpcg: maximum number of iterations reached";
+    return status;
+}
+
+}  // namespace smg

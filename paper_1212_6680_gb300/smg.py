@@ -1,0 +1,185 @@
+"""Thin ctypes binding of libsmg's C ABI (include/smg.h), with the same names.
+
+Argument marshalling only: every step of the method runs in libsmg's CUDA kernels.  Vectors
+are passed as raw pointers: a torch CUDA tensor (its data_ptr), a numpy array (host memory,
+accepted where the C ABI accepts host pointers), or an int address.  Streams are torch
+streams or raw cudaStream_t handles.  Importing this module loads libsmg.so and fails loudly
+when it is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsmg.so")
+
+SMG_OK, SMG_ERR_ARG, SMG_ERR_CUDA, SMG_ERR_NOCONV, SMG_ERR_BREAKDOWN, SMG_ERR_TIMEOUT, SMG_ERR_NAN = 0, -1, -2, -3, -4, -5, -6
+SMG_PCG, SMG_FPCG, SMG_PSD = 0, 1, 2
+SMG_FP64, SMG_FP32, SMG_BF16 = 0, 1, 2
+SMG_OPT_COARSE_ITERS, SMG_OPT_THREADS, SMG_OPT_PROFILE = 0, 1, 2
+
+VARIANTS = {"pcg": SMG_PCG, "fpcg": SMG_FPCG, "psd": SMG_PSD}
+PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}
+
+# every symbol include/smg.h declares
+EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg_apply_batched",
+           "smg_apply_A", "krylov_solve", "lobpcg_solve", "smg_destroy", "smg_last_error",
+           "smg_profile_read")
+
+
+class SMGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libsmg error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsmg.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double
+    L.smg_setup.argtypes = [i, i, i, i, i, ctypes.POINTER(vp)]
+    L.smg_set_precision.argtypes = [vp, i]
+    L.smg_set_option.argtypes = [vp, i, i]
+    L.smg_apply.argtypes = [vp, vp, vp, vp]
+    L.smg_apply_batched.argtypes = [vp, i, vp, vp, vp]
+    L.smg_apply_A.argtypes = [vp, vp, vp, vp]
+    L.krylov_solve.argtypes = [vp, i, vp, vp, d, i, ip, dp, vp]
+    L.lobpcg_solve.argtypes = [vp, i, vp, dp, d, i, ip, vp]
+    L.smg_destroy.argtypes = [vp]
+    L.smg_last_error.restype = ctypes.c_char_p
+    L.smg_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp]
+    for name in EXPORTS:
+        getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def smg_last_error() -> str:
+    return _lib.smg_last_error().decode()
+
+
+def _check(rc: int, allow=()):
+    if rc != SMG_OK and rc not in allow:
+        raise SMGError(rc, smg_last_error())
+    return rc
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _stream(s) -> int:
+    if s is None:
+        try:
+            import torch
+
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return 0
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def smg_setup(nx: int, ny: int, nz: int, npre: int = 1, npost: int = 1) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.smg_setup(nx, ny, nz, npre, npost, ctypes.byref(h)))
+    return h.value
+
+
+def smg_set_precision(h: int, prec) -> None:
+    _check(_lib.smg_set_precision(h, PRECISIONS.get(prec, prec)))
+
+
+def smg_set_option(h: int, option: int, value: int) -> None:
+    _check(_lib.smg_set_option(h, option, value))
+
+
+def smg_apply(h: int, r, s, stream=None) -> None:
+    _check(_lib.smg_apply(h, _ptr(r), _ptr(s), _stream(stream)))
+
+
+def smg_apply_batched(h: int, nb: int, R, S, stream=None) -> None:
+    _check(_lib.smg_apply_batched(h, nb, _ptr(R), _ptr(S), _stream(stream)))
+
+
+def smg_apply_A(h: int, u, out, stream=None) -> None:
+    _check(_lib.smg_apply_A(h, _ptr(u), _ptr(out), _stream(stream)))
+
+
+def krylov_solve(h: int, variant, b, x, tol: float = 1e-8, maxit: int = 100, stream=None, check=True):
+    """Returns (status, iters, relres); raises on errors other than SMG_ERR_NOCONV when check."""
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    rc = _lib.krylov_solve(h, VARIANTS.get(variant, variant), _ptr(b), _ptr(x), tol, maxit, ctypes.byref(it),
+                           ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(rc, allow=(SMG_ERR_NOCONV,))
+    return rc, it.value, rr.value
+
+
+def lobpcg_solve(h: int, m: int, X, tol: float = 1e-8, maxit: int = 100, stream=None, check=True):
+    """Returns (status, iters, lambdas as a numpy array)."""
+    lam = np.zeros(m)
+    it = ctypes.c_int(0)
+    rc = _lib.lobpcg_solve(h, m, _ptr(X), lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), tol, maxit,
+                           ctypes.byref(it), _stream(stream))
+    if check:
+        _check(rc, allow=(SMG_ERR_NOCONV,))
+    return rc, it.value, lam
+
+
+def smg_profile_read(h: int, which: int):
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    by = ctypes.c_double(0.0)
+    _check(_lib.smg_profile_read(h, which, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return n.value, ms.value, by.value
+
+
+def smg_destroy(h: int) -> None:
+    _check(_lib.smg_destroy(h))
+
+
+class Handle:
+    """Owns one smg_handle (context manager); attribute access only marshals arguments."""
+
+    def __init__(self, nx, ny, nz, npre=1, npost=1, precision="fp64"):
+        self.h = smg_setup(nx, ny, nz, npre, npost)
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        if precision != "fp64":
+            smg_set_precision(self.h, precision)
+
+    def close(self):
+        if self.h:
+            smg_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

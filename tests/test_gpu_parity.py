@@ -1,0 +1,190 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 cycle: relative 1e-12 per V-cycle (both sides follow the same sequence of exact
+    line solves; they differ only in summation order and in the line-solve algorithm
+    (partition + cyclic reduction vs Thomas), whose rounding differences are amplified at
+    most by the line systems' condition number, below ~1e4 here).
+  * FP32 cycle: relative 2e-5 per V-cycle (unit roundoff 6e-8 times the same amplification);
+    BF16 storage: relative 3e-2 (storage roundoff 4e-3 per level vector, a few levels deep).
+  * Krylov solves: true relative residual <= tol, checked independently with the oracle's
+    operator, and iteration counts within +-1 of the oracle's FP64 run.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1212_6680_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def smg():
+    from paper_1212_6680_gb300 import build
+
+    build.build()
+    from paper_1212_6680_gb300 import smg as m
+
+    assert torch.cuda.is_available()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+SHAPES = [(32, 32, 32), (33, 17, 20), (7, 5, 3), (1, 1, 8), (8, 1, 1), (5, 6, 1), (64, 48, 40), (130, 9, 6),
+          (257, 4, 5), (96, 96, 9), (2, 3, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("npre,npost", [(1, 1), (1, 0), (2, 1)])
+def test_apply_fp64_matches_oracle(smg, orc, shape, npre, npost):
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=11)
+    ref = orc.SMG(nx, ny, nz, npre, npost).apply(r)
+    with smg.Handle(nx, ny, nz, npre, npost) as h:
+        rd, sd = dev(r), torch.empty(nz * ny * nx, dtype=torch.float64, device="cuda")
+        smg.smg_apply(h.h, rd, sd)
+        torch.cuda.synchronize()
+        s = sd.cpu().numpy()
+        # applying twice gives identical results (fixed, linear preconditioner)
+        smg.smg_apply(h.h, rd, sd)
+        assert np.array_equal(sd.cpu().numpy(), s)
+    assert rel(s, ref) <= 1e-12, rel(s, ref)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("bf16", 3e-2)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 20), (96, 96, 9)])
+@pytest.mark.parametrize("npost", [1, 0])
+def test_apply_mixed_precision_close_to_oracle(smg, orc, prec, tol, shape, npost):
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=12)
+    ref = orc.SMG(nx, ny, nz, 1, npost).apply(r)
+    with smg.Handle(nx, ny, nz, 1, npost, precision=prec) as h:
+        sd = torch.empty(r.size, dtype=torch.float64, device="cuda")
+        smg.smg_apply(h.h, dev(r), sd)
+        s = sd.cpu().numpy()
+    assert rel(s, ref) <= tol, rel(s, ref)
+
+
+def test_apply_batched_matches_columns(smg, orc):
+    nx, ny, nz, nb = 24, 20, 18, 3
+    R = np.stack([inputs.rhs(nx, ny, nz, seed=20 + j).ravel() for j in range(nb)])
+    T = orc.SMG(nx, ny, nz, 1, 0)
+    with smg.Handle(nx, ny, nz, 1, 0) as h:
+        Sd = torch.empty(nb * R.shape[1], dtype=torch.float64, device="cuda")
+        smg.smg_apply_batched(h.h, nb, dev(R), Sd)
+        S = Sd.cpu().numpy().reshape(nb, -1)
+    for j in range(nb):
+        assert rel(S[j], T.apply(R[j].reshape(nz, ny, nx))) <= 1e-12
+
+
+def test_apply_A_matches_oracle(smg, orc):
+    nx, ny, nz = 37, 21, 13
+    u = inputs.rhs(nx, ny, nz, seed=3)
+    with smg.Handle(nx, ny, nz) as h:
+        o = torch.empty(u.size, dtype=torch.float64, device="cuda")
+        smg.smg_apply_A(h.h, dev(u), o)
+        assert rel(o.cpu().numpy(), orc.apply_A(u)) <= 1e-15
+
+
+@pytest.mark.parametrize("variant", ["pcg", "fpcg", "psd"])
+@pytest.mark.parametrize("npost", [1, 0])
+def test_krylov_32cube_matches_oracle(smg, orc, variant, npost):
+    n = 32
+    b = inputs.rhs(n, n, n, seed=0)
+    maxit = 100 if not (variant == "pcg" and npost == 0) else 25
+    ref = orc.krylov(b, variant, orc.SMG(n, n, n, 1, npost), tol=1e-8, maxit=maxit)
+    with smg.Handle(n, n, n, 1, npost) as h:
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        rc, it, relres = smg.krylov_solve(h.h, variant, dev(b), x, tol=1e-8, maxit=maxit)
+        xh = x.cpu().numpy().reshape(b.shape)
+    true = np.linalg.norm(b - orc.apply_A(xh)) / np.linalg.norm(b)
+    assert abs(true - relres) <= 1e-3 * relres + 1e-15
+    if ref["status"] == 0:
+        assert rc == smg.SMG_OK
+        assert true <= 1e-8
+        assert abs(it - ref["iters"]) <= 1, (it, ref["iters"])
+    else:  # eq. (1) with the nonsymmetric cycle stalls on both sides
+        assert rc == smg.SMG_ERR_NOCONV and it == maxit
+        assert true > 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("variant", ["fpcg", "psd"])
+def test_krylov_mixed_precision_reaches_tolerance(smg, orc, prec, variant):
+    nx, ny, nz = 40, 33, 29
+    b = inputs.rhs(nx, ny, nz, seed=1)
+    ref = orc.krylov(b, variant, orc.SMG(nx, ny, nz, 1, 0), tol=1e-8, maxit=100)
+    with smg.Handle(nx, ny, nz, 1, 0, precision=prec) as h:
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        rc, it, relres = smg.krylov_solve(h.h, variant, dev(b), x, tol=1e-8, maxit=100)
+        xh = x.cpu().numpy().reshape(b.shape)
+    assert rc == smg.SMG_OK
+    assert np.linalg.norm(b - orc.apply_A(xh)) / np.linalg.norm(b) <= 1e-8
+    # FP64 solution error of the mixed path vs the oracle's FP64 solve: both within tol of A^{-1} b
+    assert rel(xh, ref["x"]) <= 1e-5
+    assert it <= ref["iters"] + (2 if prec == "fp32" else 6)
+
+
+def test_krylov_host_pointers(smg, orc):
+    nx, ny, nz = 20, 18, 16
+    b = inputs.rhs(nx, ny, nz, seed=5).ravel().copy()
+    x = np.zeros_like(b)
+    with smg.Handle(nx, ny, nz, 1, 0, precision="fp32") as h:
+        rc, it, relres = smg.krylov_solve(h.h, "fpcg", b, x, tol=1e-8, maxit=100)
+    assert rc == smg.SMG_OK and relres <= 1e-8
+    assert np.linalg.norm(b - orc.apply_A(x.reshape(nz, ny, nx)).ravel()) / np.linalg.norm(b) <= 1e-8
+
+
+def test_krylov_maxit_zero_and_nan(smg):
+    n = 8
+    b = inputs.rhs(n, n, n, seed=2).ravel().copy()
+    with smg.Handle(n, n, n) as h:
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        rc, it, relres = smg.krylov_solve(h.h, "fpcg", dev(b), x, maxit=0)
+        assert rc == smg.SMG_ERR_NOCONV and it == 0 and abs(relres - 1.0) < 1e-12
+        b[5] = np.nan
+        rc, it, relres = smg.krylov_solve(h.h, "fpcg", dev(b), torch.zeros_like(x), maxit=10, check=False)
+        assert rc == smg.SMG_ERR_NAN
+
+
+def test_krylov_nonzero_initial_guess(smg, orc):
+    n = 16
+    b = inputs.rhs(n, n, n, seed=8)
+    x0 = inputs.rhs(n, n, n, seed=9)
+    with smg.Handle(n, n, n, 1, 1) as h:
+        x = dev(x0)
+        rc, it, relres = smg.krylov_solve(h.h, "pcg", dev(b), x, tol=1e-10, maxit=50)
+        xh = x.cpu().numpy().reshape(b.shape)
+    assert rc == smg.SMG_OK
+    assert np.linalg.norm(b - orc.apply_A(xh)) / np.linalg.norm(b) <= 1e-10
+
+
+def closed_form_smallest(nx, ny, nz, m):
+    lx = 4 * np.sin(np.pi * np.arange(1, nx + 1) / (2 * (nx + 1))) ** 2
+    ly = 4 * np.sin(np.pi * np.arange(1, ny + 1) / (2 * (ny + 1))) ** 2
+    lz = 4 * np.sin(np.pi * np.arange(1, nz + 1) / (2 * (nz + 1))) ** 2
+    return np.sort((lz[:, None, None] + ly[None, :, None] + lx[None, None, :]).ravel())[:m]
+
+
+@pytest.mark.parametrize("shape,m,npost", [((16, 16, 16), 4, 0), ((12, 10, 14), 6, 1), ((20, 20, 20), 16, 0)])
+def test_lobpcg_matches_closed_form(smg, shape, m, npost):
+    nx, ny, nz = shape
+    X0 = inputs.initial_block(nx, ny, nz, m, seed=7)
+    with smg.Handle(nx, ny, nz, 1, npost) as h:
+        X = dev(X0)
+        rc, it, lam = smg.lobpcg_solve(h.h, m, X, tol=1e-8, maxit=200)
+        Xh = X.cpu().numpy().reshape(m, -1)
+    assert rc == smg.SMG_OK, smg.smg_last_error()
+    ref = closed_form_smallest(nx, ny, nz, m)
+    assert np.all(np.abs(lam - ref) <= 1e-10 * ref), (lam, ref)
+    G = Xh @ Xh.T
+    assert np.abs(G - np.eye(m)).max() <= 1e-10
