@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Benchmark: seconds to a 1e-8 relative residual for flexible PCG preconditioned by SMG with
+post-smoothing off (-v 1 0) on the 128^3 7-point Dirichlet Laplacian, with the V-cycle in FP32
+(outer Krylov recurrences, inner products and norms in FP64), on one GB300.
+
+One step = one complete solve (x0 = 0, seeded U[-1,1) right-hand side) through the C ABI:
+every kernel of the path (plane relaxation with the 2D plane cycle and x-line solves,
+residual + restriction, prolongation, the FP64 Krylov kernels) runs in the timed region.
+The same solve with an FP64 cycle and with a BF16-storage cycle is timed beside it.
+
+Prints one JSON line.  `--impl reference` times the plain FP64 CPU oracle on the same
+workload instead (the reference arm; rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s to 1e-8 rel. residual, 3D Laplacian FPCG-SMG: mixed/learned vs FP64"
+NX = NY = NZ = 128
+TOL = 1e-8
+WORKLOAD = "FPCG-SMG(1,0) 128^3 7-point Dirichlet Laplacian, V-cycle FP32, Krylov FP64, tol 1e-8"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1212_6680_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.startswith("plane_relax"):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per level-0 launch of the plane-relaxation kernel from the committed ncu
+    summary, if it was captured from the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "plane_relax_traffic.json")
+    try:
+        d = json.load(open(p))
+        if d.get("source_hash") == source_hash():
+            return d
+    except Exception:
+        pass
+    return None
+
+
+def run_reference(args):
+    import oracle
+    from paper_1212_6680_gb300 import inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle.build()
+    b = inputs.rhs(NX, NY, NZ, seed=0)
+    T = oracle.SMG(NX, NY, NZ, 1, 0)
+    for _ in range(args.warmup):  # warm-up: one V-cycle each
+        T.apply(b)
+    times, iters = [], None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = oracle.krylov(b, "fpcg", T, tol=TOL, maxit=100)
+        times.append(time.perf_counter() - t0)
+        iters = out["iters"]
+        assert out["status"] == 0 and out["relres"] <= TOL
+    v = statistics.mean(times)
+    sample = f"full FPCG-SMG(1,0) solve, 128^3, FP64, {iters} iterations, single thread"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("V-cycle FP32", "V-cycle FP64 (CPU oracle)"),
+                       "grid": [NX, NY, NZ], "iters": iters},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1212_6680_gb300 import build as _build
+    from paper_1212_6680_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    from paper_1212_6680_gb300 import smg
+
+    b_np = inputs.rhs(NX, NY, NZ, seed=0).ravel().copy()
+    n = b_np.size
+    b = torch.from_numpy(b_np).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed_solves(h, steps, warmup, host=False):
+        """Per-step device time (events) of `steps` solves, L2 flushed before each."""
+        bh = torch.from_numpy(b_np).pin_memory() if host else None
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory() if host else None
+        for _ in range(warmup):
+            x.zero_()
+            smg.krylov_solve(h, "fpcg", b, x, TOL, 100)
+        times, its, res = [], None, None
+        for _ in range(steps):
+            flush.zero_()
+            if host:
+                xh.zero_()
+            else:
+                x.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if host:
+                rc, its, res = smg.krylov_solve(h, "fpcg", bh.numpy(), xh.numpy(), TOL, 100)
+            else:
+                rc, its, res = smg.krylov_solve(h, "fpcg", b, x, TOL, 100)
+            e1.record(stream)
+            barrier()
+            assert rc == smg.SMG_OK and res <= TOL, (rc, res)
+            times.append(e0.elapsed_time(e1) / 1e3)
+        return times, its, res
+
+    handles = {}
+    for prec in ("fp32", "fp64", "bf16"):
+        h = smg.smg_setup(NX, NY, NZ, 1, 0)
+        smg.smg_set_precision(h, prec)
+        handles[prec] = h
+    h32 = handles["fp32"]
+
+    # ---- main arm: FP32 cycle, device buffers; level-0 plane-relaxation launches timed ----
+    for _ in range(args.warmup):
+        x.zero_()
+        smg.krylov_solve(h32, "fpcg", b, x, TOL, 100)
+    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 1)
+    smg.smg_profile_read(h32, 0)
+    l0 = smg.smg_launch_count(h32)
+    barrier()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        times, iters, relres = timed_solves(h32, args.steps, 0)
+    wall = time.perf_counter() - wall0
+    launches = smg.smg_launch_count(h32) - l0
+    pl, pms, pbytes = smg.smg_profile_read(h32, 0)
+    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 0)
+    t_step = statistics.mean(times)
+    t_max = t_step
+    if dist is not None:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    # ---- comparison arms on the same GPU: FP64 and BF16 cycles ----
+    k2 = max(1, min(args.steps, 3))
+    t64, it64, _ = timed_solves(handles["fp64"], k2, 1)
+    t16, it16, _ = timed_solves(handles["bf16"], k2, 1)
+    # ---- end to end: host buffers, copies inside the call ----
+    te, _, _ = timed_solves(h32, max(1, min(args.steps, 3)), 1, host=True)
+
+    for h in handles.values():
+        smg.smg_destroy(h)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = (pbytes / 1e9) / (pms / 1e3) if pms > 0 else None
+    tr = ncu_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "kernel": "plane_relax_kernel<float,float,4> (finest level)",
+                "launches": pl, "avg_launch_us": (pms * 1e3 / pl) if pl else None,
+                "algorithmic_bytes_per_launch": (pbytes / pl) if pl else None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
+                "fallback 6.8 TB/s"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        bo = inputs.rhs(NX, NY, NZ, seed=0)
+        T = oracle.SMG(NX, NY, NZ, 1, 0)
+        t0 = time.perf_counter()
+        out = oracle.krylov(bo, "fpcg", T, tol=TOL, maxit=100)
+        tc = time.perf_counter() - t0
+        cpu = {"value": tc, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"one full FPCG-SMG(1,0) solve at 128^3 in FP64 ({out['iters']} iterations), single thread"}
+    line = {
+        "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "variant": "fpcg", "npre": 1, "npost": 0,
+                   "cycle_precision": "fp32", "iters": iters, "true_relres": relres,
+                   "l2": "256 MB buffer written before every timed solve", "parallelism": "replicas" if world > 1 else "single GPU",
+                   "fp64_cycle_s": statistics.mean(t64), "fp64_cycle_iters": it64,
+                   "bf16_cycle_s": statistics.mean(t16), "bf16_cycle_iters": it16,
+                   "speedup_fp32_vs_fp64": statistics.mean(t64) / t_step},
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": statistics.mean(te), "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -52,7 +52,12 @@ enum { SMG_FP64 = 0, SMG_FP32 = 1, SMG_BF16 = 2 };     /* V-cycle storage precis
 enum {
     SMG_OPT_COARSE_ITERS = 0, /* plane-cycle steps on the one-plane coarsest level (>= 1, default 1) */
     SMG_OPT_THREADS = 1,      /* threads per CTA of the plane-relaxation kernel: 256 or 512 */
-    SMG_OPT_PROFILE = 2       /* 1: time every plane-relaxation launch with CUDA events */
+    SMG_OPT_PROFILE = 2,      /* time plane-relaxation launches with CUDA events: 0 off,
+                                 1 the finest level's launches only, 2 every launch */
+    SMG_OPT_CLUSTER_MAX = 3,  /* largest thread-block cluster (CTAs per plane) for the FP64
+                                 plane relaxations: 1, 2, 4, 8 or 16 (default 16) */
+    SMG_OPT_CLUSTER_MAX32 = 4 /* the same for the FP32-compute plane relaxations of the FP32 and
+                                 BF16 cycles (default 1: off) */
 };
 
 /*
@@ -123,11 +128,26 @@ const char *smg_last_error(void);
 /*
  * smg_profile_read -- when SMG_OPT_PROFILE is on, the plane-relaxation launches timed so far
  * on this handle: launches, total device milliseconds (CUDA events on the launch stream) and
- * algorithmic bytes (vector elements the launches must read and write), split by level:
- * level 0 (the finest) and all coarser levels together (which = 0 or 1).  Reading resets
- * the counters of that class.  Synchronises the device.
+ * algorithmic bytes (vector elements the launches must read and write), by class `which`:
+ * 0 plane relaxation on the finest level, 1 plane relaxation on the other levels except the
+ * coarsest, 2 the one-plane coarsest solve, 3 restriction and prolongation, 4 the Krylov
+ * kernels of each iteration (classes 1-4 are timed only with SMG_OPT_PROFILE = 2).
+ * Reading resets the counters of that class.  Synchronises the device.
  */
 int smg_profile_read(smg_handle h, int which, long long *launches, double *ms, double *bytes);
+
+/*
+ * smg_check_conversions -- diagnostic for the library's own FP32 <-> FP64 conversions (the
+ * paper has no counterpart; the conversions are the ones the mixed-precision cycle and the
+ * Krylov kernels use).  For each of the n device doubles in src it compares the integer-pipe
+ * narrowing (round to nearest even) with the hardware conversion, and the widening of the
+ * rounded value with the hardware widening, bit for bit.  mismatches: device int[2], set to the
+ * narrowing and widening mismatch counts.  Asynchronous on `stream`.
+ */
+int smg_check_conversions(long long n, const double *src, int *mismatches, void *stream);
+
+/* smg_launch_count -- number of CUDA kernel launches this handle has issued so far. */
+int smg_launch_count(smg_handle h, long long *count);
 
 #ifdef __cplusplus
 }

@@ -42,9 +42,10 @@ def _units():
         lang = ["-x", "cu"] if s.endswith(".cu") else ["-x", "c++"]
         units.append((src, obj, lang, []))
     for k in KS:
-        src = os.path.join(CSRC, "plane_relax_inst.cu")
-        obj = os.path.join(BUILD, f"plane_relax_k{k}.o")
-        units.append((src, obj, ["-x", "cu"], [f"-DSMG_K={k}"]))
+        for prec in (0, 1, 2):
+            src = os.path.join(CSRC, "plane_relax_inst.cu")
+            obj = os.path.join(BUILD, f"plane_relax_k{k}_p{prec}.o")
+            units.append((src, obj, ["-x", "cu"], [f"-DSMG_K={k}", f"-DSMG_PREC={prec}"]))
     return units
 
 

@@ -32,7 +32,12 @@ int fail(int code, const std::string &msg) {
             return fail(SMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
     } while (0)
 
-constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kSmemBudget = 224 * 1024;  // of the 227 KB a CTA may use
+
+// profiling classes: 0 plane relaxation on the finest level, 1 plane relaxation on the other
+// levels (all but the coarsest), 2 the one-plane coarsest solve, 3 restriction + prolongation,
+// 4 the Krylov kernels of one iteration
+constexpr int kProfClasses = 5;
 
 struct ProfClass {
     long long launches = 0;
@@ -52,6 +57,7 @@ struct smg_ctx {
     Prec prec = Prec::F64;
     HostHierarchy H;
     double *d_zcoef = nullptr, *d_pcoef = nullptr;
+    float *d_zcoef32 = nullptr, *d_pcoef32 = nullptr;  // the same tables rounded to FP32
     // level storage (current precision) for nb_alloc right-hand sides
     int nb_alloc = 0;
     Prec alloc_prec = Prec::F64;
@@ -59,14 +65,23 @@ struct smg_ctx {
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
     PlaneLayout lay_c, lay_d;       // compute type = storage compute (float/double) and double (coarsest)
+    PlaneLayout lay_cl[5];          // FP64-compute cluster layouts for R = 2, 4, 8, 16 (index log2 R)
+    bool cl_ok[5] = {false, false, false, false, false};
+    PlaneLayout lay_cl32[5];        // FP32-compute cluster layouts
+    bool cl32_ok[5] = {false, false, false, false, false};
+    int cluster_max = 16;           // largest cluster for FP64-compute plane relaxations (1 = none)
+    int cluster_max32 = 1;          // largest cluster for FP32-compute plane relaxations (measured: the
+                                    // FP32 plane cycle is latency-bound, clusters only add barrier cost)
+    int num_sms = 0;
     // Krylov vectors (one right-hand side)
     double *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_dr = nullptr;
     double *d_bh = nullptr, *d_xh = nullptr;  // device copies for host-pointer calls
     KrylovWork kw;
     KrylovScalars *h_sc = nullptr;  // pinned host mirror
     // profiling
-    bool profile = false;
-    ProfClass prof[2];
+    int profile = 0;                // 0 off, 1 level-0 launches, 2 every launch
+    long long launches = 0;         // kernel launches issued by this handle
+    ProfClass prof[kProfClasses];
     std::vector<PendingEvent> pending;
     std::vector<cudaEvent_t> event_pool;
     // LOBPCG state
@@ -122,10 +137,39 @@ int ensure_levels(smg_ctx *h, int nb) {
     SMG_CUDA(cudaMalloc(&h->d_ws, h->ws_bytes));
     const bool f64c = (h->prec == Prec::F64);
     const int K = instantiated_K(h->nx);
-    if (set_plane_relax_smem(h->prec, f64c, K, h->threads, h->lay_c.smem_bytes) != 0)
+    if (set_plane_relax_smem(h->prec, f64c, false, K, h->lay_c.smem_bytes) != 0)
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, level precision) failed");
-    if (set_plane_relax_smem(h->prec, true, K, h->threads, h->lay_d.smem_bytes) != 0)
+    if (set_plane_relax_smem(h->prec, true, false, K, h->lay_d.smem_bytes) != 0)
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, FP64 coarsest) failed");
+    if (h->num_sms == 0) {
+        int dev = 0;
+        SMG_CUDA(cudaGetDevice(&dev));
+        SMG_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    // Cluster layouts (FP64 compute, and FP32 compute for the FP32/BF16 cycles): usable when
+    // they fit in shared memory and the cluster can be resident; the kernels' shared-memory
+    // limit is then set to the largest usable layout.
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool cf64 = (pass == 0);
+        if (!cf64 && h->prec == Prec::F64) break;
+        PlaneLayout *lays = cf64 ? h->lay_cl : h->lay_cl32;
+        bool *ok = cf64 ? h->cl_ok : h->cl32_ok;
+        size_t cl_smem = 0;
+        for (int lr = 1; lr <= 4; ++lr) {
+            const int R = 1 << lr;
+            ok[lr] = false;
+            lays[lr] = plan_plane_layout_cluster(H, cf64 ? 8 : 4, kSmemBudget, R);
+            if (lays[lr].smem_bytes == 0) continue;
+            if (set_plane_relax_smem(h->prec, cf64, true, K, lays[lr].smem_bytes) != 0) {
+                cudaGetLastError();
+                continue;
+            }
+            ok[lr] = cluster_resident(h->prec, cf64, K, R, h->threads, lays[lr].smem_bytes);
+            if (ok[lr]) cl_smem = std::max(cl_smem, lays[lr].smem_bytes);
+        }
+        if (cl_smem > 0 && set_plane_relax_smem(h->prec, cf64, true, K, cl_smem) != 0)
+            return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, cluster) failed");
+    }
     h->nb_alloc = nb;
     h->alloc_prec = h->prec;
     return SMG_OK;
@@ -142,6 +186,28 @@ cudaEvent_t take_event(smg_ctx *h) {
     return e;
 }
 
+// Event pair around a non-relaxation region (profile mode 2 only).
+struct RegionTimer {
+    smg_ctx *h;
+    cudaStream_t st;
+    int cls;
+    double bytes;
+    cudaEvent_t e0 = nullptr;
+    RegionTimer(smg_ctx *h_, cudaStream_t st_, int cls_, double bytes_) : h(h_), st(st_), cls(cls_), bytes(bytes_) {
+        if (h->profile == 2) {
+            e0 = take_event(h);
+            cudaEventRecord(e0, st);
+        }
+    }
+    ~RegionTimer() {
+        if (e0) {
+            cudaEvent_t e1 = take_event(h);
+            cudaEventRecord(e1, st);
+            h->pending.push_back(PendingEvent{e0, e1, cls, bytes});
+        }
+    }
+};
+
 // One plane-relaxation launch: colour c of level l, all nb right-hand sides.
 int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, const void *f, void *u, int nb,
           cudaStream_t st) {
@@ -150,7 +216,16 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     const int nplanes = colour == 0 ? (nzl + 1) / 2 : nzl / 2;
     if (nplanes == 0) return SMG_OK;
     const bool f64c = coarsest || h->prec == Prec::F64;
-    const PlaneLayout &lay = (f64c && h->prec != Prec::F64) ? h->lay_d : h->lay_c;
+    // FP64-bound relaxations spread each plane over a cluster of R CTAs while the grid still
+    // fits on the SMs at once
+    // Each plane is spread over a cluster of R CTAs while the grid still fits on the SMs at once
+    int R = 1;
+    const bool *ok = f64c ? h->cl_ok : h->cl32_ok;
+    const int rmax = f64c ? h->cluster_max : h->cluster_max32;
+    for (int cand = 2; cand <= rmax && cand <= 16; cand *= 2)
+        if (ok[__builtin_ctz(cand)] && static_cast<long long>(nplanes) * nb * cand <= h->num_sms) R = cand;
+    const PlaneLayout &lay = (R > 1) ? (f64c ? h->lay_cl[__builtin_ctz(R)] : h->lay_cl32[__builtin_ctz(R)])
+                                     : ((f64c && h->prec != Prec::F64) ? h->lay_d : h->lay_c);
     PlaneRelaxArgs a;
     std::memset(&a, 0, sizeof(a));
     a.nx = h->nx;
@@ -163,6 +238,8 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     a.u = u;
     a.vstride = h->Nl(l);
     a.zcoef = h->d_zcoef + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane;
+    a.zcoef32 = h->d_zcoef32 + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane;
+    a.pcoef32 = h->d_pcoef32 + static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine;
     a.pcoef = h->d_pcoef + static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine;
     a.gws = h->d_ws;
     a.ws_per_plane = lay.ws_per_plane;
@@ -176,16 +253,22 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     }
     a.smem_u_mask = lay.smem_u_mask;
     a.smem_g_mask = lay.smem_g_mask;
+    a.R = R;
+    a.MF = lay.MF;
+    a.off_fs = lay.off_fs;
     const int K = instantiated_K(h->nx);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->profile) {
+    const bool timed = (h->profile == 2) || (h->profile == 1 && l == 0);
+    const int cls = coarsest ? 2 : (l == 0 ? 0 : 1);
+    if (timed) {
         e0 = take_event(h);
         e1 = take_event(h);
         cudaEventRecord(e0, st);
     }
     cudaError_t err = launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
     if (err != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("plane relaxation launch: ") + cudaGetErrorString(err));
-    if (h->profile) {
+    h->launches += 1;
+    if (timed) {
         cudaEventRecord(e1, st);
         // algorithmic traffic: read f_z, write u_z (+ read u_z in correction form) for every
         // relaxed plane, and read each opposite-colour plane once when it can be nonzero
@@ -194,7 +277,7 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
         double planes = nplanes * (2.0 + (mode == 2 ? 1.0 : 0.0)) + (mode >= 1 ? nother : 0);
         planes *= iters;
         const double bytes = planes * np * nb * static_cast<double>(storage_bytes(h->prec));
-        h->pending.push_back(PendingEvent{e0, e1, l == 0 ? 0 : 1, bytes});
+        h->pending.push_back(PendingEvent{e0, e1, cls, bytes});
     }
     return SMG_OK;
 }
@@ -211,17 +294,23 @@ int run_cycle(smg_ctx *h, int nb, const void *f0, void *u0, cudaStream_t st) {
             if ((rc = relax(h, l, 0, s == 0 ? 0 : 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
             if ((rc = relax(h, l, 1, s == 0 ? 1 : 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
         }
+        RegionTimer rt(h, st, 3, 2.5 * h->Nl(l) * nb * storage_bytes(h->prec));
         cudaError_t e = launch_restrict(h->prec, h->nx, h->ny, H.nz_l[l], nb, F(l), U(l), h->d_f[l + 1],
                                         h->d_zcoef + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
+                                        h->d_zcoef32 + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
                                         h->Nl(l), h->Nl(l + 1), st);
         if (e != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("restriction launch: ") + cudaGetErrorString(e));
+        h->launches += 1;
     }
     if ((rc = relax(h, L - 1, 0, 0, h->coarse_iters, true, F(L - 1), U(L - 1), nb, st)) != SMG_OK) return rc;
     for (int l = L - 2; l >= 0; --l) {
+        RegionTimer rt(h, st, 3, 2.5 * h->Nl(l) * nb * storage_bytes(h->prec));
         cudaError_t e = launch_prolong(h->prec, h->nx, h->ny, H.nz_l[l], nb, U(l), U(l + 1),
                                        h->d_zcoef + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
+                                       h->d_zcoef32 + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
                                        h->Nl(l), h->Nl(l + 1), st);
         if (e != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("prolongation launch: ") + cudaGetErrorString(e));
+        h->launches += 1;
         for (int s = 0; s < h->npost; ++s) {
             if ((rc = relax(h, l, 1, 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
             if ((rc = relax(h, l, 0, 2, 1, false, F(l), U(l), nb, st)) != SMG_OK) return rc;
@@ -280,6 +369,7 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
     init.variant = variant;
     SMG_CUDA(cudaMemcpyAsync(h->kw.sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
     SMG_CUDA(kry_init_residual(h->prec, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+    h->launches += 1;
     const double tol2 = tol * tol;
     int k = 0, status = SMG_ERR_NOCONV;
     double tt = -1.0;
@@ -293,6 +383,7 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
         const double bb = s.bb > 0.0 ? s.bb : 1.0;
         if (s.rr <= tol2 * bb) {
             SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, st));
+            h->launches += 1;
             if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
             tt = h->h_sc->tt;
             if (tt <= tol2 * bb) {
@@ -301,6 +392,7 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
             }
             // continue from the true residual, with beta = 0 on the next step
             SMG_CUDA(kry_init_residual(h->prec, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+            h->launches += 1;
             tt = -1.0;
         }
         if (k >= maxit) {
@@ -308,10 +400,15 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
             break;
         }
         if ((rc = run_cycle(h, 1, f0, u0, st)) != SMG_OK) return rc;
-        SMG_CUDA(kry_iteration_tail(h->prec, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, st));
+        {
+            RegionTimer rt(h, st, 4, 0.0);
+            SMG_CUDA(kry_iteration_tail(h->prec, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, st));
+        }
+        h->launches += 4;
     }
     if (tt < 0.0) {
         SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, st));
+        h->launches += 1;
         if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
         tt = h->h_sc->tt;
     }
@@ -354,6 +451,13 @@ int smg_setup(int nx, int ny, int nz, int npre, int npost, smg_handle *out) {
     if (e == cudaSuccess) e = cudaMalloc(&h->d_pcoef, pb);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_zcoef, h->H.zcoef.data(), zb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_pcoef, h->H.pcoef.data(), pb, cudaMemcpyHostToDevice);
+    {
+        std::vector<float> z32(h->H.zcoef.begin(), h->H.zcoef.end()), p32(h->H.pcoef.begin(), h->H.pcoef.end());
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_zcoef32, z32.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_pcoef32, p32.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_zcoef32, z32.data(), z32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_pcoef32, p32.data(), p32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         smg_destroy(h);
         return fail(SMG_ERR_CUDA, std::string("smg_setup: ") + cudaGetErrorString(e));
@@ -385,8 +489,19 @@ int smg_set_option(smg_handle h, int option, int value) {
         if (value != 256 && value != 512) return fail(SMG_ERR_ARG, "threads must be 256 or 512");
         h->threads = value;
         return SMG_OK;
+    case SMG_OPT_CLUSTER_MAX:
+        if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(SMG_ERR_ARG, "cluster_max must be 1, 2, 4, 8 or 16");
+        h->cluster_max = value;
+        return SMG_OK;
+    case SMG_OPT_CLUSTER_MAX32:
+        if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(SMG_ERR_ARG, "cluster_max must be 1, 2, 4, 8 or 16");
+        h->cluster_max32 = value;
+        return SMG_OK;
     case SMG_OPT_PROFILE:
-        h->profile = (value != 0);
+        if (value < 0 || value > 2) return fail(SMG_ERR_ARG, "profile must be 0, 1 or 2");
+        h->profile = value;
         return SMG_OK;
     }
     return fail(SMG_ERR_ARG, "unknown option");
@@ -404,6 +519,7 @@ int smg_apply_batched(smg_handle h, int nb, const double *R, double *S, void *st
     SMG_CUDA(launch_convert_to(h->prec, n, R, h->d_f[0], st));
     if ((rc = run_cycle(h, nb, h->d_f[0], h->d_u[0], st)) != SMG_OK) return rc;
     SMG_CUDA(launch_convert_from(h->prec, n, h->d_u[0], S, st));
+    h->launches += 2;
     return SMG_OK;
 }
 
@@ -481,7 +597,7 @@ int lobpcg_solve(smg_handle h, int m, double *X, double *lambda, double tol, int
 
 int smg_profile_read(smg_handle h, int which, long long *launches, double *ms, double *bytes) {
     if (int rc = check_handle(h)) return rc;
-    if (which < 0 || which > 1 || !launches || !ms || !bytes) return fail(SMG_ERR_ARG, "bad arguments");
+    if (which < 0 || which >= kProfClasses || !launches || !ms || !bytes) return fail(SMG_ERR_ARG, "bad arguments");
     SMG_CUDA(cudaDeviceSynchronize());
     for (auto &p : h->pending) {
         float t = 0.0f;
@@ -500,11 +616,28 @@ int smg_profile_read(smg_handle h, int which, long long *launches, double *ms, d
     return SMG_OK;
 }
 
+int smg_check_conversions(long long n, const double *src, int *mismatches, void *stream) {
+    if (n < 0 || (n > 0 && (src == nullptr || mismatches == nullptr))) return fail(SMG_ERR_ARG, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SMG_CUDA(cudaMemsetAsync(mismatches, 0, 2 * sizeof(int), st));
+    SMG_CUDA(launch_check_conversions(n, src, mismatches, st));
+    return SMG_OK;
+}
+
+int smg_launch_count(smg_handle h, long long *count) {
+    if (int rc = check_handle(h)) return rc;
+    if (count == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    *count = h->launches;
+    return SMG_OK;
+}
+
 int smg_destroy(smg_handle h) {
     if (h == nullptr) return SMG_OK;
     free_levels(h);
     cudaFree(h->d_zcoef);
     cudaFree(h->d_pcoef);
+    cudaFree(h->d_zcoef32);
+    cudaFree(h->d_pcoef32);
     cudaFree(h->d_r);
     cudaFree(h->d_p);
     cudaFree(h->d_q);

@@ -16,11 +16,13 @@ namespace smg {
 
 size_t storage_bytes(Prec p) { return p == Prec::F64 ? 8 : (p == Prec::F32 ? 4 : 2); }
 
-// ---- plane-relaxation dispatch over K ---------------------------------------------------------
-#define SMG_DECL_K(k)                                                                                 \
-    cudaError_t launch_plane_relax_k##k(Prec, bool, int, int, int, const PlaneRelaxArgs &, size_t,    \
-                                        cudaStream_t);                                                \
-    int set_plane_relax_smem_k##k(Prec, bool, size_t);
+// ---- plane-relaxation dispatch over (K, storage precision) -------------------------------------
+#define SMG_DECL_KP(k, p)                                                                             \
+    cudaError_t launch_plane_relax_k##k##_p##p(bool, int, int, int, const PlaneRelaxArgs &, size_t,   \
+                                               cudaStream_t);                                         \
+    int set_plane_relax_smem_k##k##_p##p(bool, bool, size_t);                                         \
+    bool cluster_resident_k##k##_p##p(bool, int, int, size_t);
+#define SMG_DECL_K(k) SMG_DECL_KP(k, 0) SMG_DECL_KP(k, 1) SMG_DECL_KP(k, 2)
 SMG_DECL_K(1)
 SMG_DECL_K(2)
 SMG_DECL_K(3)
@@ -29,63 +31,73 @@ SMG_DECL_K(6)
 SMG_DECL_K(8)
 SMG_DECL_K(16)
 
+#define SMG_SWITCH_KP(K, storage, CALL)                                                               \
+    switch (K) {                                                                                      \
+    case 1: SMG_SWITCH_P(1, storage, CALL)                                                            \
+    case 2: SMG_SWITCH_P(2, storage, CALL)                                                            \
+    case 3: SMG_SWITCH_P(3, storage, CALL)                                                            \
+    case 4: SMG_SWITCH_P(4, storage, CALL)                                                            \
+    case 6: SMG_SWITCH_P(6, storage, CALL)                                                            \
+    case 8: SMG_SWITCH_P(8, storage, CALL)                                                            \
+    case 16: SMG_SWITCH_P(16, storage, CALL)                                                          \
+    }
+#define SMG_SWITCH_P(k, storage, CALL)                                                                \
+    switch (storage) {                                                                                \
+    case Prec::F64: return CALL(k, 0);                                                                \
+    case Prec::F32: return CALL(k, 1);                                                                \
+    case Prec::BF16: return CALL(k, 2);                                                               \
+    }                                                                                                 \
+    break;
+
 cudaError_t launch_plane_relax(Prec storage, bool f64, int K, int nplanes, int nb, int threads,
                                const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
-    switch (K) {
-    case 1: return launch_plane_relax_k1(storage, f64, nplanes, nb, threads, a, smem, st);
-    case 2: return launch_plane_relax_k2(storage, f64, nplanes, nb, threads, a, smem, st);
-    case 3: return launch_plane_relax_k3(storage, f64, nplanes, nb, threads, a, smem, st);
-    case 4: return launch_plane_relax_k4(storage, f64, nplanes, nb, threads, a, smem, st);
-    case 6: return launch_plane_relax_k6(storage, f64, nplanes, nb, threads, a, smem, st);
-    case 8: return launch_plane_relax_k8(storage, f64, nplanes, nb, threads, a, smem, st);
-    case 16: return launch_plane_relax_k16(storage, f64, nplanes, nb, threads, a, smem, st);
-    }
+#define SMG_CALL_LAUNCH(k, p) launch_plane_relax_k##k##_p##p(f64, nplanes, nb, threads, a, smem, st)
+    SMG_SWITCH_KP(K, storage, SMG_CALL_LAUNCH)
     return cudaErrorInvalidValue;
 }
 
-int set_plane_relax_smem(Prec storage, bool f64, int K, int, size_t smem) {
-    switch (K) {
-    case 1: return set_plane_relax_smem_k1(storage, f64, smem);
-    case 2: return set_plane_relax_smem_k2(storage, f64, smem);
-    case 3: return set_plane_relax_smem_k3(storage, f64, smem);
-    case 4: return set_plane_relax_smem_k4(storage, f64, smem);
-    case 6: return set_plane_relax_smem_k6(storage, f64, smem);
-    case 8: return set_plane_relax_smem_k8(storage, f64, smem);
-    case 16: return set_plane_relax_smem_k16(storage, f64, smem);
-    }
+int set_plane_relax_smem(Prec storage, bool f64, bool cl, int K, size_t smem) {
+#define SMG_CALL_SMEM(k, p) set_plane_relax_smem_k##k##_p##p(f64, cl, smem)
+    SMG_SWITCH_KP(K, storage, SMG_CALL_SMEM)
     return static_cast<int>(cudaErrorInvalidValue);
+}
+
+bool cluster_resident(Prec storage, bool f64, int K, int R, int threads, size_t smem) {
+#define SMG_CALL_RES(k, p) cluster_resident_k##k##_p##p(f64, R, threads, smem)
+    SMG_SWITCH_KP(K, storage, SMG_CALL_RES)
+    return false;
 }
 
 // ---- residual + restriction -------------------------------------------------------------------
 template <class S, class C>
 __global__ void restrict_kernel(int nx, int ny, int nzf, int nzc, long long total, const S *__restrict__ f,
-                                const S *__restrict__ u, S *__restrict__ fc, const double *__restrict__ zcoef,
-                                long long vsf, long long vsc) {
-    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const long long np = static_cast<long long>(nx) * ny;
-    const int x = static_cast<int>(idx % nx);
-    long long t = idx / nx;
-    const int y = static_cast<int>(t % ny);
-    t /= ny;
-    const int j = static_cast<int>(t % nzc);
-    const int b = static_cast<int>(t / nzc);
+                                const S *__restrict__ u, S *__restrict__ fc, const double *__restrict__ zcoef64,
+                                const float *__restrict__ zcoef32, long long vsf, long long vsc) {
+    const C *zcoef = coef_table<C>(zcoef64, zcoef32);
+    // blockIdx.y: one coarse plane of one batch entry; x-y plane covered by the x-dimension
+    const int ip32 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npi = nx * ny;
+    if (ip32 >= npi) return;
+    const long long np = npi;
+    const int y = ip32 / nx, x = ip32 - y * nx;
+    const int j = blockIdx.y;
+    const int b = blockIdx.z;
     const S *fb = f + b * vsf;
     const S *ub = u + b * vsf;
-    const long long ip = static_cast<long long>(y) * nx + x;
+    const long long ip = ip32;
     C acc = C(0);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int zf = 2 * j + k;
         if (zf >= nzf) break;
-        const double *zc = zcoef + static_cast<long long>(zf) * kCoefPerPlane;
-        const C w = (k == 1) ? C(1) : static_cast<C>(k == 0 ? zc[7] : zc[6]);
+        const C *zc = zcoef + static_cast<long long>(zf) * kCoefPerPlane;
+        const C w = (k == 1) ? C(1) : (k == 0 ? zc[7] : zc[6]);
         C r = ldv<C>(fb + zf * np + ip);
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
             const int zz = zf + dz;
             if (zz < 0 || zz >= nzf) continue;
-            r -= plane_term<C>(ub + zz * np, x, y, nx, ny, static_cast<C>(zc[1 + dz]), static_cast<C>(zc[4 + dz]));
+            r -= plane_term<C>(ub + zz * np, x, y, nx, ny, zc[1 + dz], zc[4 + dz]);
         }
         acc += w * r;
     }
@@ -95,25 +107,26 @@ __global__ void restrict_kernel(int nx, int ny, int nzf, int nzc, long long tota
 // ---- prolongation + correction ----------------------------------------------------------------
 template <class S, class C>
 __global__ void prolong_kernel(int nx, int ny, int nzf, int nzc, long long total, S *__restrict__ u,
-                               const S *__restrict__ uc, const double *__restrict__ zcoef, long long vsf,
-                               long long vsc) {
-    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const long long np = static_cast<long long>(nx) * ny;
-    const long long ip = idx % np;
-    long long t = idx / np;
-    const int z = static_cast<int>(t % nzf);
-    const int b = static_cast<int>(t / nzf);
+                               const S *__restrict__ uc, const double *__restrict__ zcoef64,
+                               const float *__restrict__ zcoef32, long long vsf, long long vsc) {
+    const C *zcoef = coef_table<C>(zcoef64, zcoef32);
+    const int ip32 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npi = nx * ny;
+    if (ip32 >= npi) return;
+    const long long np = npi;
+    const long long ip = ip32;
+    const int z = blockIdx.y;
+    const int b = blockIdx.z;
     const S *cb = uc + b * vsc;
     C e;
     if (z & 1) {
         e = ldv<C>(cb + static_cast<long long>((z - 1) / 2) * np + ip);
     } else {
-        const double *zc = zcoef + static_cast<long long>(z) * kCoefPerPlane;
+        const C *zc = zcoef + static_cast<long long>(z) * kCoefPerPlane;
         e = C(0);
         const int jl = z / 2 - 1, jh = z / 2;
-        if (jl >= 0) e += static_cast<C>(zc[6]) * ldv<C>(cb + static_cast<long long>(jl) * np + ip);
-        if (jh < nzc) e += static_cast<C>(zc[7]) * ldv<C>(cb + static_cast<long long>(jh) * np + ip);
+        if (jl >= 0) e += zc[6] * ldv<C>(cb + static_cast<long long>(jl) * np + ip);
+        if (jh < nzc) e += zc[7] * ldv<C>(cb + static_cast<long long>(jh) * np + ip);
     }
     S *p = u + b * vsf + static_cast<long long>(z) * np + ip;
     stv<S, C>(p, ldv<C>(p) + e);
@@ -124,49 +137,51 @@ static inline unsigned nblocks(long long total, int threads) {
 }
 
 cudaError_t launch_restrict(Prec storage, int nx, int ny, int nzf, int nb, const void *f, const void *u, void *fc,
-                            const double *zcoef, long long vsf, long long vsc, cudaStream_t st) {
+                            const double *zcoef, const float *zcoef32, long long vsf, long long vsc, cudaStream_t st) {
     const int nzc = nzf / 2;
     const long long total = static_cast<long long>(nx) * ny * nzc * nb;
     if (total == 0) return cudaSuccess;
     const int T = 256;
+    const dim3 grid(nblocks(static_cast<long long>(nx) * ny, T), nzc, nb);
     switch (storage) {
     case Prec::F64:
-        restrict_kernel<double, double><<<nblocks(total, T), T, 0, st>>>(
+        restrict_kernel<double, double><<<grid, T, 0, st>>>(
             nx, ny, nzf, nzc, total, static_cast<const double *>(f), static_cast<const double *>(u),
-            static_cast<double *>(fc), zcoef, vsf, vsc);
+            static_cast<double *>(fc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::F32:
-        restrict_kernel<float, float><<<nblocks(total, T), T, 0, st>>>(
+        restrict_kernel<float, float><<<grid, T, 0, st>>>(
             nx, ny, nzf, nzc, total, static_cast<const float *>(f), static_cast<const float *>(u),
-            static_cast<float *>(fc), zcoef, vsf, vsc);
+            static_cast<float *>(fc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::BF16:
-        restrict_kernel<__nv_bfloat16, float><<<nblocks(total, T), T, 0, st>>>(
+        restrict_kernel<__nv_bfloat16, float><<<grid, T, 0, st>>>(
             nx, ny, nzf, nzc, total, static_cast<const __nv_bfloat16 *>(f), static_cast<const __nv_bfloat16 *>(u),
-            static_cast<__nv_bfloat16 *>(fc), zcoef, vsf, vsc);
+            static_cast<__nv_bfloat16 *>(fc), zcoef, zcoef32, vsf, vsc);
         break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(Prec storage, int nx, int ny, int nzf, int nb, void *u, const void *uc,
-                           const double *zcoef, long long vsf, long long vsc, cudaStream_t st) {
+                           const double *zcoef, const float *zcoef32, long long vsf, long long vsc, cudaStream_t st) {
     const int nzc = nzf / 2;
     const long long total = static_cast<long long>(nx) * ny * nzf * nb;
     const int T = 256;
+    const dim3 grid(nblocks(static_cast<long long>(nx) * ny, T), nzf, nb);
     switch (storage) {
     case Prec::F64:
-        prolong_kernel<double, double><<<nblocks(total, T), T, 0, st>>>(
-            nx, ny, nzf, nzc, total, static_cast<double *>(u), static_cast<const double *>(uc), zcoef, vsf, vsc);
+        prolong_kernel<double, double><<<grid, T, 0, st>>>(
+            nx, ny, nzf, nzc, total, static_cast<double *>(u), static_cast<const double *>(uc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::F32:
-        prolong_kernel<float, float><<<nblocks(total, T), T, 0, st>>>(
-            nx, ny, nzf, nzc, total, static_cast<float *>(u), static_cast<const float *>(uc), zcoef, vsf, vsc);
+        prolong_kernel<float, float><<<grid, T, 0, st>>>(
+            nx, ny, nzf, nzc, total, static_cast<float *>(u), static_cast<const float *>(uc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::BF16:
-        prolong_kernel<__nv_bfloat16, float><<<nblocks(total, T), T, 0, st>>>(
+        prolong_kernel<__nv_bfloat16, float><<<grid, T, 0, st>>>(
             nx, ny, nzf, nzc, total, static_cast<__nv_bfloat16 *>(u), static_cast<const __nv_bfloat16 *>(uc), zcoef,
-            vsf, vsc);
+            zcoef32, vsf, vsc);
         break;
     }
     return cudaGetLastError();
@@ -212,16 +227,33 @@ cudaError_t launch_convert_from(Prec storage, long long n, const void *src, doub
     return cudaGetLastError();
 }
 
+// ---- conversion self-check -------------------------------------------------------------------
+__global__ void check_conversions_kernel(long long n, const double *__restrict__ src, int *mism) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double d = src[i];
+    const float hw = __double2float_rn(d), sw = narrow_f64(d);
+    if (__float_as_uint(hw) != __float_as_uint(sw)) atomicAdd(&mism[0], 1);
+    const double wh = static_cast<double>(hw), ws = widen_f32(hw);
+    if (__double_as_longlong(wh) != __double_as_longlong(ws)) atomicAdd(&mism[1], 1);
+}
+
+cudaError_t launch_check_conversions(long long n, const double *src, int *mism, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    check_conversions_kernel<<<nblocks(n, 256), 256, 0, st>>>(n, src, mism);
+    return cudaGetLastError();
+}
+
 // ---- the 7-point operator in FP64 -------------------------------------------------------------
 __global__ void apply_A_kernel(int nx, int ny, int nz, long long total, const double *__restrict__ u,
                                double *__restrict__ out) {
-    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    const long long np = static_cast<long long>(nx) * ny, nn = np * nz;
-    const long long iv = i % nn;
-    const int x = static_cast<int>(iv % nx);
-    const int y = static_cast<int>((iv / nx) % ny);
-    const int z = static_cast<int>(iv / np);
+    // blockIdx.y: plane z, blockIdx.z: batch entry
+    const int ip32 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip32 >= nx * ny) return;
+    const long long np = static_cast<long long>(nx) * ny;
+    const int y = ip32 / nx, x = ip32 - y * nx;
+    const int z = blockIdx.y;
+    const long long i = (static_cast<long long>(blockIdx.z) * nz + z) * np + ip32;
     double s = u[i - 0] * 6.0;
     double nb = 0.0;
     if (x > 0) nb += u[i - 1];
@@ -237,7 +269,7 @@ cudaError_t launch_apply_A(int nx, int ny, int nz, int nb, const double *u, doub
     const long long total = static_cast<long long>(nx) * ny * nz * nb;
     const int T = 256;
     if (total == 0) return cudaSuccess;
-    apply_A_kernel<<<nblocks(total, T), T, 0, st>>>(nx, ny, nz, total, u, out);
+    apply_A_kernel<<<dim3(nblocks(static_cast<long long>(nx) * ny, T), nz, nb), T, 0, st>>>(nx, ny, nz, total, u, out);
     return cudaGetLastError();
 }
 

@@ -194,13 +194,40 @@ void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H) {
 // levels (latency-bound, few lines) and finally the finest; u_m before g_m at each level
 // (the iterate is touched more often than the right-hand side).  What does not fit in
 // `smem_budget` goes to a global slot per CTA (L2-resident for the sizes of interest).
+// Instantiated x-line chunk size for nx (rows per lane): 1, 2, 3, 4, 6, 8 or 16.
+// Factor sets worth keeping: 2D levels with at least 16 lines (at least 8 per colour, so
+// several warps would factor the same matrix), using at most a quarter of the budget.
+static int factor_levels(const HostHierarchy &H, int K, size_t elem_bytes, size_t smem_budget) {
+    int mf = 0;
+    while (mf < H.P - 1 && mf < kMaxFactorLevels && H.ny_m[mf] >= 16) ++mf;
+    const size_t set_bytes = static_cast<size_t>(trifac_set_elems(K)) * elem_bytes;
+    while (mf > 0 && static_cast<size_t>(mf) * set_bytes > smem_budget / 4) --mf;
+    return mf;
+}
+
+static int chunk_K(int nx) {
+    const int k = (nx + 31) / 32;
+    if (k <= 4) return k;
+    if (k <= 6) return 6;
+    if (k <= 8) return 8;
+    return 16;
+}
+
+// Shared memory starts with the plane's coefficient table and the factor sets of the interior
+// line matrices of the first MF 2D levels (the levels with many lines; the others factor on
+// the fly), then the 2D-cycle arrays, placed greedily: the coarsest levels first (latency-bound,
+// few lines) and finally the finest; u_m before g_m at each level (the iterate is touched more
+// often).  What does not fit in `smem_budget` goes to a global slot per CTA (L2-resident for
+// the sizes of interest).
 PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget) {
     PlaneLayout P;
-    P.K = (H.nx + 31) / 32;
-    size_t smem_elems = static_cast<size_t>(H.sum_ny) * kCoefPerLine;  // coefficient table
-    long long gl = 0;
+    P.K = chunk_K(H.nx);
     auto align4 = [](size_t v) { return (v + 3) & ~static_cast<size_t>(3); };
-    smem_elems = align4(smem_elems);
+    size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
+    P.MF = factor_levels(H, P.K, elem_bytes, smem_budget);
+    P.off_fs = static_cast<int>(smem_elems);
+    smem_elems += static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
+    long long gl = 0;
     const size_t budget_elems = smem_budget / elem_bytes;
     for (int m = H.P - 1; m >= 0; --m) {
         const size_t sz = align4(static_cast<size_t>(H.nx) * H.ny_m[m]);
@@ -223,6 +250,31 @@ PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t 
     }
     P.smem_bytes = smem_elems * elem_bytes;
     P.ws_per_plane = gl;
+    return P;
+}
+
+PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R) {
+    PlaneLayout P;
+    P.K = chunk_K(H.nx);
+    auto align4 = [](size_t v) { return (v + 3) & ~static_cast<size_t>(3); };
+    size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
+    P.MF = factor_levels(H, P.K, elem_bytes, smem_budget);
+    P.off_fs = static_cast<int>(smem_elems);
+    smem_elems += static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
+    for (int m = H.P - 1; m >= 0; --m) {
+        const int pairs = (H.ny_m[m] + 1) / 2;
+        const size_t nloc = 2 * static_cast<size_t>((pairs + R - 1) / R);
+        const size_t sz = align4(static_cast<size_t>(H.nx) * nloc);
+        P.off_u[m] = static_cast<int>(smem_elems);
+        P.smem_u_mask |= 1u << m;
+        smem_elems += sz;
+        P.off_g[m] = static_cast<int>(smem_elems);
+        P.smem_g_mask |= 1u << m;
+        smem_elems += sz;
+    }
+    P.smem_bytes = smem_elems * elem_bytes;
+    if (P.smem_bytes > smem_budget) P.smem_bytes = 0;
+    P.ws_per_plane = 0;
     return P;
 }
 

@@ -36,35 +36,40 @@ __device__ __forceinline__ DSum shfl_down_dsum(const DSum &v, int o) {
     return DSum{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
 }
 
-// Block-reduce NV compensated sums; on return thread 0 holds the block totals.
+// Inner products: every thread accumulates its (about 2N / (threads in the grid)) products with
+// FMA, the block adds the thread partials pairwise (warp shuffles, then one warp over the warp
+// sums), and the last block to finish combines the block partials with error-free TwoSum
+// (compensated summation).  FP64 work per element stays at one FMA, which matters on GB300
+// where an FP64 operation costs as much SM time as dozens of FP32 ones.
 template <int NV>
-__device__ __forceinline__ void block_reduce(DSum (&v)[NV]) {
-    __shared__ DSum sh[NV][32];
+__device__ __forceinline__ void block_reduce_plain(double (&v)[NV]) {
+    __shared__ double sh[NV][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] = dsum_combine(v[k], shfl_down_dsum(v[k], o));
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (lane == 0)
         for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
     __syncthreads();
     if (w == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            v[k] = (lane < nw) ? sh[k][lane] : DSum{0.0, 0.0};
-            for (int o = 16; o > 0; o >>= 1) v[k] = dsum_combine(v[k], shfl_down_dsum(v[k], o));
+            v[k] = (lane < nw) ? sh[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
         }
     }
     __syncthreads();
 }
 
-// Write this block's partials; the last block to finish reduces all of them into tot[].
-// Returns true in every thread of the last block.
+// Write this block's partials; the last block to finish sums all of them (compensated) into
+// tot[].  Returns true in every thread of the last block.
 template <int NV>
-__device__ __forceinline__ bool grid_reduce(DSum (&v)[NV], DSum *part, unsigned *counter, double (&tot)[NV]) {
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], DSum *part, unsigned *counter, double (&tot)[NV]) {
     __shared__ bool last;
-    block_reduce<NV>(v);
+    __shared__ double res[NV];
+    block_reduce_plain<NV>(v);
     if (threadIdx.x == 0) {
-        for (int k = 0; k < NV; ++k) part[static_cast<size_t>(blockIdx.x) * NV + k] = v[k];
+        for (int k = 0; k < NV; ++k) part[static_cast<size_t>(blockIdx.x) * NV + k] = DSum{v[k], 0.0};
         __threadfence();
         const unsigned t = atomicAdd(counter, 1u);
         last = (t == gridDim.x - 1);
@@ -72,19 +77,18 @@ __device__ __forceinline__ bool grid_reduce(DSum (&v)[NV], DSum *part, unsigned 
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    DSum w[NV];
-    for (int k = 0; k < NV; ++k) w[k] = DSum{0.0, 0.0};
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         for (int k = 0; k < NV; ++k) {
-            const volatile DSum *vp = &part[static_cast<size_t>(b) * NV + k];
-            const DSum pb{vp->s, vp->c};
-            w[k] = dsum_combine(w[k], pb);
+            DSum w{0.0, 0.0};
+            for (unsigned b = lane; b < gridDim.x; b += 32) {
+                const volatile DSum *vp = &part[static_cast<size_t>(b) * NV + k];
+                two_sum_acc(w, vp->s);
+            }
+            for (int o = 16; o > 0; o >>= 1) w = dsum_combine(w, shfl_down_dsum(w, o));
+            if (lane == 0) res[k] = w.s + w.c;
         }
-    block_reduce<NV>(w);
-    __shared__ double res[NV];
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < NV; ++k) res[k] = w[k].s + w[k].c;
-        *counter = 0u;
+        if (lane == 0) *counter = 0u;
     }
     __syncthreads();
     for (int k = 0; k < NV; ++k) tot[k] = res[k];
@@ -109,11 +113,10 @@ __global__ void k_init_residual(int nx, int ny, int nz, const double *__restrict
                                 double *__restrict__ r, S *__restrict__ f0, KrylovScalars *sc, DSum *part,
                                 unsigned *counter) {
     const long long np = static_cast<long long>(nx) * ny, n = np * nz;
-    DSum v[2] = {{0.0, 0.0}, {0.0, 0.0}};
     double a0 = 0.0, a1 = 0.0;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int xx = static_cast<int>(i % nx), yy = static_cast<int>((i / nx) % ny), zz = static_cast<int>(i / np);
+    const int npi = nx * ny, n32 = npi * nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
+        const int zz = i / npi, ip = i - zz * npi, yy = ip / nx, xx = ip - yy * nx;
         const double bi = b[i];
         const double ri = bi - stencil7(x, i, xx, yy, zz, nx, ny, nz, np);
         r[i] = ri;
@@ -121,8 +124,7 @@ __global__ void k_init_residual(int nx, int ny, int nz, const double *__restrict
         a0 = fma(ri, ri, a0);
         a1 = fma(bi, bi, a1);
     }
-    v[0].s = a0;
-    v[1].s = a1;
+    double v[2] = {a0, a1};
     double tot[2];
     if (grid_reduce<2>(v, part, counter, tot) && threadIdx.x == 0) {
         sc->rr = tot[0];
@@ -136,15 +138,14 @@ __global__ void k_init_residual(int nx, int ny, int nz, const double *__restrict
 __global__ void k_true_residual(int nx, int ny, int nz, const double *__restrict__ b, const double *__restrict__ x,
                                 KrylovScalars *sc, DSum *part, unsigned *counter) {
     const long long np = static_cast<long long>(nx) * ny, n = np * nz;
-    DSum v[1] = {{0.0, 0.0}};
     double a0 = 0.0;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int xx = static_cast<int>(i % nx), yy = static_cast<int>((i / nx) % ny), zz = static_cast<int>(i / np);
+    const int npi = nx * ny, n32 = npi * nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
+        const int zz = i / npi, ip = i - zz * npi, yy = ip / nx, xx = ip - yy * nx;
         const double ri = b[i] - stencil7(x, i, xx, yy, zz, nx, ny, nz, np);
         a0 = fma(ri, ri, a0);
     }
-    v[0].s = a0;
+    double v[1] = {a0};
     double tot[1];
     if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) sc->tt = tot[0];
 }
@@ -155,16 +156,14 @@ __global__ void k_dots_beta(long long n, const S *__restrict__ s, const double *
                             const double *__restrict__ dr, KrylovScalars *sc, DSum *part, unsigned *counter) {
     const int variant = sc->variant;
     const bool need_sdr = (variant == 1) && (sc->restart == 0);
-    DSum v[2] = {{0.0, 0.0}, {0.0, 0.0}};
     double a0 = 0.0, a1 = 0.0;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int n32 = static_cast<int>(n);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
         const double si = ldv<double>(s + i);
         a0 = fma(si, r[i], a0);
         if (need_sdr) a1 = fma(si, dr[i], a1);
     }
-    v[0].s = a0;
-    v[1].s = a1;
+    double v[2] = {a0, a1};
     double tot[2];
     if (grid_reduce<2>(v, part, counter, tot) && threadIdx.x == 0) {
         const double rho = tot[0];
@@ -187,8 +186,8 @@ __global__ void k_dots_beta(long long n, const S *__restrict__ s, const double *
 template <class S>
 __global__ void k_update_p(long long n, const S *__restrict__ s, double *__restrict__ p, const KrylovScalars *sc) {
     const double beta = sc->beta;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int n32 = static_cast<int>(n);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
         const double si = ldv<double>(s + i);
         p[i] = (beta == 0.0) ? si : fma(beta, p[i], si);
     }
@@ -198,16 +197,15 @@ __global__ void k_update_p(long long n, const S *__restrict__ s, double *__restr
 __global__ void k_spmv_alpha(int nx, int ny, int nz, const double *__restrict__ p, double *__restrict__ q,
                              KrylovScalars *sc, DSum *part, unsigned *counter) {
     const long long np = static_cast<long long>(nx) * ny, n = np * nz;
-    DSum v[1] = {{0.0, 0.0}};
     double a0 = 0.0;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int xx = static_cast<int>(i % nx), yy = static_cast<int>((i / nx) % ny), zz = static_cast<int>(i / np);
+    const int npi = nx * ny, n32 = npi * nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
+        const int zz = i / npi, ip = i - zz * npi, yy = ip / nx, xx = ip - yy * nx;
         const double qi = stencil7(p, i, xx, yy, zz, nx, ny, nz, np);
         q[i] = qi;
         a0 = fma(p[i], qi, a0);
     }
-    v[0].s = a0;
+    double v[1] = {a0};
     double tot[1];
     if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
         const double pq = tot[0];
@@ -228,10 +226,9 @@ __global__ void k_update_xr(long long n, double *__restrict__ x, const double *_
                             KrylovScalars *sc, DSum *part, unsigned *counter) {
     const double alpha = sc->alpha;
     const bool want_dr = (sc->variant == 1);
-    DSum v[1] = {{0.0, 0.0}};
     double a0 = 0.0;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int n32 = static_cast<int>(n);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
         x[i] = fma(alpha, p[i], x[i]);
         const double ro = r[i];
         const double rn = fma(-alpha, q[i], ro);
@@ -240,7 +237,7 @@ __global__ void k_update_xr(long long n, double *__restrict__ x, const double *_
         if (f0 != nullptr) stv<S, double>(f0 + i, rn);
         a0 = fma(rn, rn, a0);
     }
-    v[0].s = a0;
+    double v[1] = {a0};
     double tot[1];
     if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
         sc->rr = tot[0];
@@ -251,10 +248,12 @@ __global__ void k_update_xr(long long n, double *__restrict__ x, const double *_
 }
 
 // ---- launchers --------------------------------------------------------------------------------
+// Two 256-thread CTAs per SM of a 152-SM GB300 at most: each thread then sums tens of
+// products, and the block and grid reductions stay a small fraction of the kernel.
 int reduction_blocks(long long n) {
-    long long b = (n + 256LL * 8 - 1) / (256LL * 8);
+    long long b = (n + 256LL * 16 - 1) / (256LL * 16);
     if (b < 1) b = 1;
-    if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+    if (b > kReduceBlocks) b = kReduceBlocks;
     return static_cast<int>(b);
 }
 

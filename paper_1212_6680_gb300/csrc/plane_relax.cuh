@@ -26,100 +26,241 @@
 
 #include <cuda_bf16.h>
 
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
 #include "smg_internal.h"
 
 namespace smg {
 
+namespace cg = cooperative_groups;
+
 // ---- storage <-> compute conversion -------------------------------------------------------
+// FP32 <-> FP64 conversions written out on the integer pipe from the IEEE-754 binary32 and
+// binary64 formats (GB300's conversion instruction runs at a small fraction of even its FP64
+// rate).  Widening a normal or zero float is exact: rebias the exponent (1023 - 127 = 896) and
+// shift the 23-bit fraction into the top of the 52-bit one.  Narrowing a double whose result
+// is a normal float rounds the 52-bit fraction to 23 bits to nearest, ties to even; a carry out
+// of the fraction increments the exponent (and gives infinity past the largest float).
+// Denormals, infinities and NaNs go through the hardware instruction.
+__device__ __forceinline__ double widen_f32(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double(static_cast<long long>(static_cast<unsigned long long>(u) << 32));
+    if (e == 0u || e == 0xffu) return static_cast<double>(f);
+    const unsigned long long bits = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
+                                    (static_cast<unsigned long long>(e + 896u) << 52) |
+                                    (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ __forceinline__ float narrow_f64(double d) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+    const unsigned hi = static_cast<unsigned>(b >> 32);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e < 897u || e > 1150u) return __double2float_rn(d);  // not a normal float (or zero)
+    const unsigned long long m = b & 0xfffffffffffffull;
+    unsigned mant = static_cast<unsigned>(m >> 29);
+    const unsigned rem = static_cast<unsigned>(m & 0x1fffffffull);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) mant += 1u;
+    return __uint_as_float((hi & 0x80000000u) | (((e - 896u) << 23) + mant));
+}
+
 template <class C, class S> __device__ __forceinline__ C ldv(const S *p);
 template <> __device__ __forceinline__ float ldv<float, float>(const float *p) { return *p; }
 template <> __device__ __forceinline__ float ldv<float, __nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 template <> __device__ __forceinline__ double ldv<double, double>(const double *p) { return *p; }
-template <> __device__ __forceinline__ double ldv<double, float>(const float *p) { return static_cast<double>(*p); }
-template <> __device__ __forceinline__ double ldv<double, __nv_bfloat16>(const __nv_bfloat16 *p) { return static_cast<double>(__bfloat162float(*p)); }
+template <> __device__ __forceinline__ double ldv<double, float>(const float *p) { return widen_f32(*p); }
+template <> __device__ __forceinline__ double ldv<double, __nv_bfloat16>(const __nv_bfloat16 *p) { return widen_f32(__bfloat162float(*p)); }
 
 template <class S, class C> __device__ __forceinline__ void stv(S *p, C v);
 template <> __device__ __forceinline__ void stv<float, float>(float *p, float v) { *p = v; }
 template <> __device__ __forceinline__ void stv<__nv_bfloat16, float>(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ void stv<double, double>(double *p, double v) { *p = v; }
-template <> __device__ __forceinline__ void stv<float, double>(float *p, double v) { *p = static_cast<float>(v); }
-template <> __device__ __forceinline__ void stv<__nv_bfloat16, double>(__nv_bfloat16 *p, double v) { *p = __float2bfloat16_rn(static_cast<float>(v)); }
+template <> __device__ __forceinline__ void stv<float, double>(float *p, double v) { *p = narrow_f64(v); }
+template <> __device__ __forceinline__ void stv<__nv_bfloat16, double>(__nv_bfloat16 *p, double v) { *p = __float2bfloat16_rn(narrow_f64(v)); }
+
+// Coefficient tables are stored in both precisions; each kernel reads the one it computes in.
+template <class C> __device__ __forceinline__ const C *coef_table(const double *d64, const float *d32);
+template <> __device__ __forceinline__ const double *coef_table<double>(const double *d64, const float *) { return d64; }
+template <> __device__ __forceinline__ const float *coef_table<float>(const double *, const float *d32) { return d32; }
 
 // ---- warp tridiagonal solver ---------------------------------------------------------------
 // Solves the n x n system  of*x[i-1] + dg*x[i] + of*x[i+1] = d[i]  (Dirichlet ends) held by a
-// warp: lane l owns rows lK .. lK+K-1 in d[]; rows >= n are identity rows with d = 0.  On
-// return d holds x.  dg > 2|of| (strict diagonal dominance) keeps every pivot away from 0.
+// warp: lane l owns rows lK .. lK+K-1; rows >= n are identity rows with d = 0.  dg > 2|of|
+// (strict diagonal dominance) keeps every pivot away from 0.
+// Partition method + parallel cyclic reduction, split in two parts:
+//   tri_factor : everything that depends only on (dg, of, n) -- all divisions and the
+//                coefficient shuffles -- computed once and reused for every line of a level
+//                that has the same matrix (all interior lines do);
+//   tri_apply  : the right-hand-side sweeps (FMAs and two shuffles per reduction step), for NL
+//                lines at once so that their dependency chains interleave.
 template <class C, int K>
-__device__ __forceinline__ void warp_tridiag(const C dg, const C of, C (&d)[K], const int n, const int lane) {
+struct TriFac {
+    C dg, of;                  // the matrix these factors belong to
+    C inv[K], cbf[K];          // forward pivots (reciprocal) and forward upper coefficients
+    C ab[K], cb[K];            // x_j = d_j - ab_j F - cb_j G after the backward sweep
+    C a0, c0, rbf;             // the lane's first row and the final pivot (reciprocal)
+    C k1[5], k2[5];            // cyclic-reduction multipliers
+};
+
+template <class C, int K>
+__device__ __noinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of, const int n, const int lane) {
     const int i0 = lane * K;
     auto A = [&](int j) -> C { const int i = i0 + j; return (i > 0 && i < n) ? of : C(0); };
     auto B = [&](int j) -> C { const int i = i0 + j; return (i < n) ? dg : C(1); };
     auto Cu = [&](int j) -> C { const int i = i0 + j; return (i < n - 1) ? of : C(0); };
-    C RA, RB, RC, RD;  // reduced row of the lane's first unknown F:  RA F_prev + RB F + RC F_next = RD
-    C ab[K > 1 ? K : 1], cb[K > 1 ? K : 1];
+    f.dg = dg;
+    f.of = of;
+    C RA, RB, RC;
+    f.a0 = A(0);
+    f.c0 = Cu(0);
     if constexpr (K == 1) {
-        RA = A(0);
+        RA = f.a0;
         RB = B(0);
-        RC = Cu(0);
-        RD = d[0];
+        RC = f.c0;
     } else {
-        // forward: rows j >= 1 as  ab[j] F + x_j + cb[j] x_{j+1} = d[j]
-        {
-            const C inv = C(1) / B(1);
-            ab[1] = A(1) * inv;
-            cb[1] = Cu(1) * inv;
-            d[1] *= inv;
-        }
+        f.inv[1] = C(1) / B(1);
+        f.ab[1] = A(1) * f.inv[1];
+        f.cb[1] = Cu(1) * f.inv[1];
 #pragma unroll
         for (int j = 2; j < K; ++j) {
             const C aj = A(j);
-            const C inv = C(1) / (B(j) - aj * cb[j - 1]);
-            ab[j] = -aj * ab[j - 1] * inv;
-            cb[j] = Cu(j) * inv;
-            d[j] = (d[j] - aj * d[j - 1]) * inv;
+            f.inv[j] = C(1) / (B(j) - aj * f.cb[j - 1]);
+            f.ab[j] = -aj * f.ab[j - 1] * f.inv[j];
+            f.cb[j] = Cu(j) * f.inv[j];
         }
-        // backward: rows j >= 1 as  x_j = d[j] - ab[j] F - cb[j] G   (G = next lane's F)
+#pragma unroll
+        for (int j = 1; j < K; ++j) f.cbf[j] = f.cb[j];
 #pragma unroll
         for (int j = K - 2; j >= 1; --j) {
-            const C c = cb[j];
-            d[j] -= c * d[j + 1];
-            ab[j] -= c * ab[j + 1];
-            cb[j] = -c * cb[j + 1];
+            const C c = f.cb[j];
+            f.ab[j] -= c * f.ab[j + 1];
+            f.cb[j] = -c * f.cb[j + 1];
         }
-        // previous lane's last row gives x_{i0-1} = pd - pa F_prev - pc F
-        C pd = __shfl_up_sync(0xffffffffu, d[K - 1], 1);
-        C pa = __shfl_up_sync(0xffffffffu, ab[K - 1], 1);
-        C pc = __shfl_up_sync(0xffffffffu, cb[K - 1], 1);
-        if (lane == 0) { pd = C(0); pa = C(0); pc = C(0); }
-        const C a0 = A(0), c0 = Cu(0);
-        RA = -a0 * pa;
-        RB = B(0) - a0 * pc - c0 * ab[1];
-        RC = -c0 * cb[1];
-        RD = d[0] - a0 * pd - c0 * d[1];
+        C pa = __shfl_up_sync(0xffffffffu, f.ab[K - 1], 1);
+        C pc = __shfl_up_sync(0xffffffffu, f.cb[K - 1], 1);
+        if (lane == 0) { pa = C(0); pc = C(0); }
+        RA = -f.a0 * pa;
+        RB = B(0) - f.a0 * pc - f.c0 * f.ab[1];
+        RC = -f.c0 * f.cb[1];
     }
-    // parallel cyclic reduction of the 32 interface rows
 #pragma unroll
-    for (int s = 1; s < 32; s <<= 1) {
+    for (int t = 0; t < 5; ++t) {
+        const int s = 1 << t;
         const C rb = C(1) / RB;
         C am = __shfl_up_sync(0xffffffffu, RA, s), rbm = __shfl_up_sync(0xffffffffu, rb, s);
-        C cm = __shfl_up_sync(0xffffffffu, RC, s), dm = __shfl_up_sync(0xffffffffu, RD, s);
+        C cm = __shfl_up_sync(0xffffffffu, RC, s);
         C ap = __shfl_down_sync(0xffffffffu, RA, s), rbp = __shfl_down_sync(0xffffffffu, rb, s);
-        C cp = __shfl_down_sync(0xffffffffu, RC, s), dp = __shfl_down_sync(0xffffffffu, RD, s);
-        if (lane < s) { am = C(0); rbm = C(0); cm = C(0); dm = C(0); }
-        if (lane + s >= 32) { ap = C(0); rbp = C(0); cp = C(0); dp = C(0); }
+        C cp = __shfl_down_sync(0xffffffffu, RC, s);
+        if (lane < s) { am = C(0); rbm = C(0); cm = C(0); }
+        if (lane + s >= 32) { ap = C(0); rbp = C(0); cp = C(0); }
         const C k1 = RA * rbm, k2 = RC * rbp;
         RB = RB - k1 * cm - k2 * ap;
-        RD = RD - k1 * dm - k2 * dp;
         RA = -k1 * am;
         RC = -k2 * cp;
+        f.k1[t] = k1;
+        f.k2[t] = k2;
     }
-    const C F = RD / RB;
-    d[0] = F;
-    if constexpr (K > 1) {
-        C G = __shfl_down_sync(0xffffffffu, F, 1);
-        if (lane == 31) G = C(0);
+    f.rbf = C(1) / RB;
+}
+
+// A factor set in shared memory: field k of lane l at fs[k * 32 + l].
+template <class C, int K>
+constexpr int trifac_fields() { return 4 * K + 15; }
+
+template <class C, int K>
+__device__ __forceinline__ void trifac_store(C *fs, const TriFac<C, K> &f, int lane) {
+    int k = 0;
+    fs[(k++) * 32 + lane] = f.dg;
+    fs[(k++) * 32 + lane] = f.of;
 #pragma unroll
-        for (int j = 1; j < K; ++j) d[j] = d[j] - ab[j] * F - cb[j] * G;
+    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.inv[j];
+#pragma unroll
+    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.cbf[j];
+#pragma unroll
+    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.ab[j];
+#pragma unroll
+    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.cb[j];
+    fs[(k++) * 32 + lane] = f.a0;
+    fs[(k++) * 32 + lane] = f.c0;
+    fs[(k++) * 32 + lane] = f.rbf;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) fs[(k++) * 32 + lane] = f.k1[t];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) fs[(k++) * 32 + lane] = f.k2[t];
+}
+
+template <class C, int K>
+__device__ __forceinline__ void trifac_load(TriFac<C, K> &f, const C *fs, int lane) {
+    int k = 0;
+    f.dg = fs[(k++) * 32 + lane];
+    f.of = fs[(k++) * 32 + lane];
+#pragma unroll
+    for (int j = 0; j < K; ++j) f.inv[j] = fs[(k++) * 32 + lane];
+#pragma unroll
+    for (int j = 0; j < K; ++j) f.cbf[j] = fs[(k++) * 32 + lane];
+#pragma unroll
+    for (int j = 0; j < K; ++j) f.ab[j] = fs[(k++) * 32 + lane];
+#pragma unroll
+    for (int j = 0; j < K; ++j) f.cb[j] = fs[(k++) * 32 + lane];
+    f.a0 = fs[(k++) * 32 + lane];
+    f.c0 = fs[(k++) * 32 + lane];
+    f.rbf = fs[(k++) * 32 + lane];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) f.k1[t] = fs[(k++) * 32 + lane];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) f.k2[t] = fs[(k++) * 32 + lane];
+}
+
+template <class C, int K, int NL>
+__device__ __forceinline__ void tri_apply(const TriFac<C, K> &f, C (&d)[NL][K], const int n, const int lane) {
+    const int i0 = lane * K;
+    C RD[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        if constexpr (K == 1) {
+            RD[l] = d[l][0];
+        } else {
+            d[l][1] *= f.inv[1];
+#pragma unroll
+            for (int j = 2; j < K; ++j) {
+                const C aj = (i0 + j < n) ? f.of : C(0);
+                d[l][j] = (d[l][j] - aj * d[l][j - 1]) * f.inv[j];
+            }
+#pragma unroll
+            for (int j = K - 2; j >= 1; --j) d[l][j] -= f.cbf[j] * d[l][j + 1];
+        }
+    }
+    if constexpr (K > 1) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            C pd = __shfl_up_sync(0xffffffffu, d[l][K - 1], 1);
+            if (lane == 0) pd = C(0);
+            RD[l] = d[l][0] - f.a0 * pd - f.c0 * d[l][1];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int s = 1 << t;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const C dm = __shfl_up_sync(0xffffffffu, RD[l], s);
+            const C dp = __shfl_down_sync(0xffffffffu, RD[l], s);
+            RD[l] = RD[l] - f.k1[t] * dm - f.k2[t] * dp;   // k1 = 0 / k2 = 0 where the partner is absent
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const C F = RD[l] * f.rbf;
+        if constexpr (K > 1) {
+            C G = __shfl_down_sync(0xffffffffu, F, 1);
+            if (lane == 31) G = C(0);
+#pragma unroll
+            for (int j = 1; j < K; ++j) d[l][j] = d[l][j] - f.ab[j] * F - f.cb[j] * G;
+        }
+        d[l][0] = F;
     }
 }
 
@@ -139,11 +280,21 @@ __device__ __forceinline__ C plane_term(const S *u, int x, int y, int nx, int ny
 enum : int { NB_NONE = 0, NB_PLAIN = 1, NB_CORR = 2 };
 enum : int { OUT_U = 0, OUT_U_AND_PLANE = 1, OUT_PLANE = 2 };
 
+// Where the 2D-cycle arrays live.  CL = false: one CTA owns the plane; every array is either
+// in its shared memory or in its global slot.  CL = true: a thread-block cluster of R CTAs
+// shares the plane; line y of every 2D level belongs to CTA ((y/2) mod R), which keeps it in
+// its shared memory at local line ((y/2) div R)*2 + (y mod 2); other CTAs read it through
+// distributed shared memory.  Lines are owned in pairs so both colours are spread over all
+// CTAs.
 template <class C>
 struct PlaneCtx {
     C *sm;       // shared memory base (coefficient table first)
-    C *gw;       // this CTA's global slot
+    C *gw;       // this CTA's global slot (CL = false only)
+    C *g0;       // when set: the level-0 right-hand side lives here (the plane of f itself)
     int nx;
+    int R, rank; // cluster size and this CTA's rank in it (1, 0 without a cluster)
+    C *fs;       // shared-memory factor sets of the interior line matrix of 2D levels 0..MF-1
+    int MF;
 };
 
 template <class C>
@@ -151,144 +302,385 @@ __device__ __forceinline__ C *arr_u(const PlaneRelaxArgs &a, const PlaneCtx<C> &
     return (((a.smem_u_mask >> m) & 1u) ? c.sm : c.gw) + a.off_u[m];
 }
 template <class C>
-__device__ __forceinline__ C *arr_g(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m) {
+__device__ __forceinline__ C *arr_g_local(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m) {
     return (((a.smem_g_mask >> m) & 1u) ? c.sm : c.gw) + a.off_g[m];
 }
 
-// Relax line y of 2D level m exactly (one warp).
-template <class S, class C, int K>
-__device__ __forceinline__ void relax_line(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int y,
-                                           int nbmode, int out, S *plane, bool accumulate, int lane) {
-    const int nx = c.nx, nym = a.ny_m[m];
-    const C *lc = c.sm + (a.line_base[m] + y) * kCoefPerLine;
-    const C *g = arr_g(a, c, m) + static_cast<long long>(y) * nx;
-    C d[K];
+template <class C, bool CL>
+__device__ __forceinline__ C *line_at(const PlaneCtx<C> &c, C *base, int y) {
+    if constexpr (!CL) {
+        return base + y * c.nx;
+    } else {
+        const int k = y >> 1;
+        const int owner = k % c.R;
+        const int local = (k / c.R) * 2 + (y & 1);
+        return cg::this_cluster().map_shared_rank(base + local * c.nx, owner);
+    }
+}
+template <class C, bool CL>
+__device__ __forceinline__ C *line_u(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int y) {
+    return line_at<C, CL>(c, arr_u(a, c, m), y);
+}
+template <class C, bool CL>
+__device__ __forceinline__ C *line_g(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int y) {
+    if (m == 0 && c.g0 != nullptr) return c.g0 + y * c.nx;  // f itself, in global memory
+    return line_at<C, CL>(c, arr_g_local(a, c, m), y);
+}
+
+template <bool CL>
+__device__ __forceinline__ void plane_sync() {
+    if constexpr (CL) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+// The t-th line of a level that this CTA owns, counting lines in owned pairs (all lines).
+template <class C>
+__device__ __forceinline__ int owned_line(const PlaneCtx<C> &c, int t) {
+    return 2 * (c.rank + c.R * (t >> 1)) + (t & 1);
+}
+
+// Load a line (K registers per lane, 0 beyond nx).
+template <class C, int K>
+__device__ __forceinline__ void load_line(C (&v)[K], const C *line, int nx, int lane) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int x = lane * K + j;
-        d[j] = (x < nx) ? g[x] : C(0);
+        v[j] = (x < nx) ? line[x] : C(0);
     }
-    if (nbmode != NB_NONE) {
-        const C *um = arr_u(a, c, m);
-        const C *uc = (nbmode == NB_CORR) ? arr_u(a, c, m + 1) : nullptr;
-        const int nyc = (nbmode == NB_CORR) ? a.ny_m[m + 1] : 0;
+}
+template <class C, int K>
+__device__ __forceinline__ void store_line(C *line, const C (&v)[K], int nx, int lane) {
 #pragma unroll
-        for (int s = -1; s <= 1; s += 2) {
-            const int yy = y + s;
-            if (yy < 0 || yy >= nym) continue;
-            const C sc = lc[1 + s], tc = lc[4 + s];
-            C v[K];
+    for (int j = 0; j < K; ++j) {
+        const int x = lane * K + j;
+        if (x < nx) line[x] = v[j];
+    }
+}
+
+// d -= sc * Lx v + tc * v  for one neighbouring line v (x-halo through shuffles).
+template <class C, int K>
+__device__ __forceinline__ void sub_coupling(C (&d)[K], const C (&v)[K], C sc, C tc, int lane) {
+    C vl = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
+    C vr = __shfl_down_sync(0xffffffffu, v[0], 1);
+    if (lane == 0) vl = C(0);
+    if (lane == 31) vr = C(0);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const C left = (j == 0) ? vl : v[j - 1];
+        const C right = (j == K - 1) ? vr : v[j + 1];
+        d[j] -= sc * (C(2) * v[j] - left - right) + tc * v[j];
+    }
+}
+
+// Make `fac` hold the factors of the line matrix (dg, of) of 2D level m: keep it when it
+// already does, else copy the level's shared factor set when the matrix is that level's
+// interior one, else factor (rare: lines next to the last boundary of a level).
+template <class C, int K>
+__device__ __forceinline__ void ensure_fac(const PlaneCtx<C> &c, TriFac<C, K> &fac, int m, C dg, C of, int lane) {
+    if (fac.dg == dg && fac.of == of) return;
+    if (m < c.MF) {
+        const C *fs = c.fs + m * trifac_fields<C, K>() * 32;
+        if (fs[lane] == dg && fs[32 + lane] == of) {
+            trifac_load<C, K>(fac, fs, lane);
+            return;
+        }
+    }
+    tri_factor<C, K>(fac, dg, of, c.nx, lane);
+}
+
+// Exact relaxation of NL lines ys[] of 2D level m by one warp (lines of one colour, so they
+// do not couple to each other).  NBMODE: the neighbouring lines are zero (NB_NONE), read as
+// they are (NB_PLAIN), or read with the coarse correction P u_{m+1} added (NB_CORR, the
+// neighbours are even lines).  OUT: store into u_m, into the plane, or both.
+template <class S, class C, int K, int NL, bool CL, int NBMODE, int OUT>
+__device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
+                                            int m, const int (&ys)[NL], S *plane, bool accumulate, int lane) {
+    const int nx = c.nx, nym = a.ny_m[m];
+    C d[NL][K];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) load_line<C, K>(d[l], line_g<C, CL>(a, c, m, ys[l]), nx, lane);
+    if constexpr (NBMODE != NB_NONE) {
+        const int nyc = (NBMODE == NB_CORR) ? a.ny_m[m + 1] : 0;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const int y = ys[l];
+            const C *lc = c.sm + (a.line_base[m] + y) * kCoefPerLine;
+#pragma unroll
+            for (int s = -1; s <= 1; s += 2) {
+                const int yy = y + s;
+                if (yy < 0 || yy >= nym) continue;
+                C v[K];
+                load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, lane);
+                if constexpr (NBMODE == NB_CORR) {  // neighbour yy is an even line: add P e from level m+1
+                    const C *lcy = c.sm + (a.line_base[m] + yy) * kCoefPerLine;
+                    const int jl = yy / 2 - 1, jh = yy / 2;
+                    const C wm = lcy[6], wp = lcy[7];
+                    if (jl >= 0) {
+                        C e[K];
+                        load_line<C, K>(e, line_u<C, CL>(a, c, m + 1, jl), nx, lane);
+#pragma unroll
+                        for (int j = 0; j < K; ++j) v[j] += wm * e[j];
+                    }
+                    if (jh < nyc) {
+                        C e[K];
+                        load_line<C, K>(e, line_u<C, CL>(a, c, m + 1, jh), nx, lane);
+#pragma unroll
+                        for (int j = 0; j < K; ++j) v[j] += wp * e[j];
+                    }
+                }
+                sub_coupling<C, K>(d[l], v, lc[1 + s], lc[4 + s], lane);
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (lane * K + j >= nx) d[l][j] = C(0);
+        }
+    }
+    // the line matrices: S(y,y) Lx + T(y,y) I  ->  diagonal 2S + T, off-diagonal -S
+    C dg[NL], of[NL];
+    bool same = true;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const C *lc = c.sm + (a.line_base[m] + ys[l]) * kCoefPerLine;
+        dg[l] = C(2) * lc[1] + lc[4];
+        of[l] = -lc[1];
+        same = same && dg[l] == dg[0] && of[l] == of[0];
+    }
+    if (same) {
+        ensure_fac<C, K>(c, fac, m, dg[0], of[0], lane);
+        tri_apply<C, K, NL>(fac, d, nx, lane);
+    } else {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            ensure_fac<C, K>(c, fac, m, dg[l], of[l], lane);
+            C dl[1][K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) dl[0][j] = d[l][j];
+            tri_apply<C, K, 1>(fac, dl, nx, lane);
+#pragma unroll
+            for (int j = 0; j < K; ++j) d[l][j] = dl[0][j];
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const int y = ys[l];
+        if constexpr (OUT != OUT_PLANE) store_line<C, K>(line_u<C, CL>(a, c, m, y), d[l], nx, lane);
+        if constexpr (OUT != OUT_U) {
+            S *p = plane + y * nx;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
                 const int x = lane * K + j;
-                v[j] = (x < nx) ? um[static_cast<long long>(yy) * nx + x] : C(0);
-            }
-            if (nbmode == NB_CORR) {  // neighbour yy is an even line: add P e from level m+1
-                const C *lcy = c.sm + (a.line_base[m] + yy) * kCoefPerLine;
-                const int jl = yy / 2 - 1, jh = yy / 2;
-                const C wm = lcy[6], wp = lcy[7];
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const int x = lane * K + j;
-                    if (x < nx) {
-                        C e = C(0);
-                        if (jl >= 0) e += wm * uc[static_cast<long long>(jl) * nx + x];
-                        if (jh < nyc) e += wp * uc[static_cast<long long>(jh) * nx + x];
-                        v[j] += e;
-                    }
+                if (x < nx) {
+                    const C v = accumulate ? ldv<C>(p + x) + d[l][j] : d[l][j];
+                    stv<S, C>(p + x, v);
                 }
             }
-            C vl = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
-            C vr = __shfl_down_sync(0xffffffffu, v[0], 1);
-            if (lane == 0) vl = C(0);
-            if (lane == 31) vr = C(0);
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const C left = (j == 0) ? vl : v[j - 1];
-                const C right = (j == K - 1) ? vr : v[j + 1];
-                d[j] -= sc * (C(2) * v[j] - left - right) + tc * v[j];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (lane * K + j >= nx) d[j] = C(0);
-    }
-    warp_tridiag<C, K>(C(2) * lc[1] + lc[4], -lc[1], d, nx, lane);
-    if (out != OUT_PLANE) {
-        C *u = arr_u(a, c, m) + static_cast<long long>(y) * nx;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int x = lane * K + j;
-            if (x < nx) u[x] = d[j];
         }
     }
-    if (out != OUT_U) {
-        S *p = plane + static_cast<long long>(y) * nx;
+}
+
+// Lines a warp processes together: more when the line is short and the type is narrow.
+template <class C, int K>
+constexpr int max_lines_per_group() {
+    return (sizeof(C) * K <= 16) ? 4 : ((sizeof(C) * K <= 32) ? 2 : 1);
+}
+
+// Relax every line of one colour of 2D level m that this CTA owns: lines colour + 2k with
+// k = rank + R i; warp w takes i = w, w + nw, ...
+template <class S, class C, int K, bool CL, int NBMODE, int OUT>
+__device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
+                                             int m, int colour, S *plane, bool accumulate, int warp, int nw,
+                                             int lane) {
+    const int nl = (a.ny_m[m] - colour + 1) / 2;
+    const int nown = (nl > c.rank) ? (nl - c.rank + c.R - 1) / c.R : 0;
+    auto Y = [&](int i) { return colour + 2 * (c.rank + c.R * i); };
+    constexpr int NLM = max_lines_per_group<C, K>();
+    int i = warp;
+    if constexpr (NLM > 1) {
+        for (; i + (NLM - 1) * nw < nown; i += NLM * nw) {
+            int ys[NLM];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int x = lane * K + j;
-            if (x < nx) {
-                const C v = accumulate ? ldv<C>(p + x) + d[j] : d[j];
-                stv<S, C>(p + x, v);
-            }
+            for (int l = 0; l < NLM; ++l) ys[l] = Y(i + l * nw);
+            relax_group<S, C, K, NLM, CL, NBMODE, OUT>(a, c, fac, m, ys, plane, accumulate, lane);
         }
     }
+    if constexpr (NLM > 2) {
+        for (; i + nw < nown; i += 2 * nw) {
+            const int ys[2] = {Y(i), Y(i + nw)};
+            relax_group<S, C, K, 2, CL, NBMODE, OUT>(a, c, fac, m, ys, plane, accumulate, lane);
+        }
+    }
+    for (; i < nown; i += nw) {
+        const int ys[1] = {Y(i)};
+        relax_group<S, C, K, 1, CL, NBMODE, OUT>(a, c, fac, m, ys, plane, accumulate, lane);
+    }
+}
+
+// Number of lines of an n-line level owned by this CTA (owned in pairs).
+template <class C>
+__device__ __forceinline__ int owned_count(const PlaneCtx<C> &c, int n) {
+    const int pairs = (n + 1) / 2;
+    const int own_pairs = (pairs > c.rank) ? (pairs - c.rank + c.R - 1) / c.R : 0;
+    int cnt = 2 * own_pairs;
+    // the last pair may be a single line
+    if (own_pairs > 0 && (n & 1) && ((pairs - 1) % c.R) == c.rank) cnt -= 1;
+    return cnt;
 }
 
 // g_{m+1}[j] = wp(2j) r_{2j} + wm(2j+2) r_{2j+2},  r_e = -sum_{dy=+-1} B_{e,e+dy} u_{e+dy}
-template <class C, int K>
-__device__ __forceinline__ void restrict_line(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int jc, int lane) {
+template <class C, int K, int NL, bool CL>
+__device__ __forceinline__ void restrict_group(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m,
+                                               const int (&js)[NL], int lane) {
     const int nx = c.nx, nym = a.ny_m[m];
-    const C *um = arr_u(a, c, m);
-    C acc[K];
+    C acc[NL][K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) acc[j] = C(0);
+    for (int l = 0; l < NL; ++l) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int e = 2 * jc + 2 * k;
-        if (e >= nym) continue;
-        const C *lc = c.sm + (a.line_base[m] + e) * kCoefPerLine;
-        const C w = (k == 0) ? lc[7] : lc[6];
+        for (int j = 0; j < K; ++j) acc[l][j] = C(0);
 #pragma unroll
-        for (int s = -1; s <= 1; s += 2) {
-            const int yy = e + s;
-            if (yy < 0 || yy >= nym) continue;
-            const C sc = lc[1 + s], tc = lc[4 + s];
-            C v[K];
+        for (int k = 0; k < 2; ++k) {
+            const int e = 2 * js[l] + 2 * k;
+            if (e >= nym) continue;
+            const C *lc = c.sm + (a.line_base[m] + e) * kCoefPerLine;
+            const C w = (k == 0) ? lc[7] : lc[6];
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const int x = lane * K + j;
-                v[j] = (x < nx) ? um[static_cast<long long>(yy) * nx + x] : C(0);
-            }
-            C vl = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
-            C vr = __shfl_down_sync(0xffffffffu, v[0], 1);
-            if (lane == 0) vl = C(0);
-            if (lane == 31) vr = C(0);
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const C left = (j == 0) ? vl : v[j - 1];
-                const C right = (j == K - 1) ? vr : v[j + 1];
-                acc[j] -= w * (sc * (C(2) * v[j] - left - right) + tc * v[j]);
+            for (int s = -1; s <= 1; s += 2) {
+                const int yy = e + s;
+                if (yy < 0 || yy >= nym) continue;
+                C v[K];
+                load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, lane);
+                sub_coupling<C, K>(acc[l], v, w * lc[1 + s], w * lc[4 + s], lane);
             }
         }
     }
-    C *gc = arr_g(a, c, m + 1) + static_cast<long long>(jc) * nx;
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const int x = lane * K + j;
-        if (x < nx) gc[x] = acc[j];
+    for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, m + 1, js[l]), acc[l], nx, lane);
+}
+
+template <class C, int K, bool CL>
+__device__ __forceinline__ void restrict_level(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int warp,
+                                               int nw, int lane) {
+    const int nown = owned_count(c, a.ny_m[m + 1]);
+    constexpr int NLM = max_lines_per_group<C, K>();
+    int t = warp;
+    if constexpr (NLM > 1) {
+        for (; t + (NLM - 1) * nw < nown; t += NLM * nw) {
+            int js[NLM];
+#pragma unroll
+            for (int l = 0; l < NLM; ++l) js[l] = owned_line(c, t + l * nw);
+            restrict_group<C, K, NLM, CL>(a, c, m, js, lane);
+        }
+    }
+    if constexpr (NLM > 2) {
+        for (; t + nw < nown; t += 2 * nw) {
+            const int js[2] = {owned_line(c, t), owned_line(c, t + nw)};
+            restrict_group<C, K, 2, CL>(a, c, m, js, lane);
+        }
+    }
+    for (; t < nown; t += nw) {
+        const int js[1] = {owned_line(c, t)};
+        restrict_group<C, K, 1, CL>(a, c, m, js, lane);
     }
 }
 
-template <class S, class C, int K>
+// Load line y of a plane in storage precision into the lane's K registers (0 beyond nx).
+template <class C, class S, int K>
+__device__ __forceinline__ void load_plane_line(C (&v)[K], const S *plane, int y, int nx, int lane) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int x = lane * K + j;
+        v[j] = (x < nx) ? ldv<C>(plane + y * nx + x) : C(0);
+    }
+}
+
+// d -= M (4c - c_{x-1} - c_{x+1} - c_{y-1} - c_{y+1}) + Kc c  for plane pl at line y.
+template <class C, class S, int K>
+__device__ __forceinline__ void sub_plane_term(C (&d)[K], const S *pl, int y, int nx, int ny, C Mc, C Kc, int lane) {
+    C cv[K], up[K], dn[K];
+    load_plane_line<C, S, K>(cv, pl, y, nx, lane);
+#pragma unroll
+    for (int j = 0; j < K; ++j) { up[j] = C(0); dn[j] = C(0); }
+    if (y > 0) load_plane_line<C, S, K>(up, pl, y - 1, nx, lane);
+    if (y + 1 < ny) load_plane_line<C, S, K>(dn, pl, y + 1, nx, lane);
+    C vl = __shfl_up_sync(0xffffffffu, cv[K - 1], 1);
+    C vr = __shfl_down_sync(0xffffffffu, cv[0], 1);
+    if (lane == 0) vl = C(0);
+    if (lane == 31) vr = C(0);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const C left = (j == 0) ? vl : cv[j - 1];
+        const C right = (j == K - 1) ? vr : cv[j + 1];
+        d[j] -= Mc * (C(4) * cv[j] - left - right - up[j] - dn[j]) + Kc * cv[j];
+    }
+}
+
+// g_0 = f_z - sum_dz A_{z,z+dz} u_{z+dz} for NL lines (mode 1: own plane zero; mode 2: all).
+template <class S, class C, int K, int NL, bool CL>
+__device__ __forceinline__ void rhs_group(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, const int (&ys)[NL],
+                                          int mode, const S *fpl, const S *ub, int z, const C *zc, int lane) {
+    const int nx = a.nx, ny = a.ny, np = nx * ny;
+    C d[NL][K];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) load_plane_line<C, S, K>(d[l], fpl, ys[l], nx, lane);
+    if (mode >= 1 && z > 0) {
+        const C Mc = zc[0], Kc = zc[3];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + (z - 1) * np, ys[l], nx, ny, Mc, Kc, lane);
+    }
+    if (mode >= 1 && z + 1 < a.nz) {
+        const C Mc = zc[2], Kc = zc[5];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + (z + 1) * np, ys[l], nx, ny, Mc, Kc, lane);
+    }
+    if (mode == 2) {
+        const C Mc = zc[1], Kc = zc[4];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + z * np, ys[l], nx, ny, Mc, Kc, lane);
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, 0, ys[l]), d[l], nx, lane);
+}
+
+template <class S, class C, int K, bool CL>
+__device__ __forceinline__ void compute_rhs(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int mode, const S *fpl,
+                                            const S *ub, int z, const C *zc, int warp, int nw, int lane) {
+    constexpr int NLM = max_lines_per_group<C, K>();
+    const int nown = owned_count(c, a.ny);
+    int t = warp;
+    if constexpr (NLM > 1) {
+        for (; t + (NLM - 1) * nw < nown; t += NLM * nw) {
+            int ys[NLM];
+#pragma unroll
+            for (int l = 0; l < NLM; ++l) ys[l] = owned_line(c, t + l * nw);
+            rhs_group<S, C, K, NLM, CL>(a, c, ys, mode, fpl, ub, z, zc, lane);
+        }
+    }
+    for (; t < nown; t += nw) {
+        const int ys[1] = {owned_line(c, t)};
+        rhs_group<S, C, K, 1, CL>(a, c, ys, mode, fpl, ub, z, zc, lane);
+    }
+}
+
+// One CTA (CL = false) or one cluster of R CTAs (CL = true) per plane of the colour.
+template <class S, class C, int K, bool CL>
 __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const PlaneRelaxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PlaneCtx<C> c;
     c.sm = reinterpret_cast<C *>(smem_raw);
+    c.g0 = nullptr;
     c.nx = a.nx;
+    int pidx;
+    if constexpr (CL) {
+        c.R = a.R;
+        c.rank = static_cast<int>(cg::this_cluster().block_rank());
+        pidx = static_cast<int>(blockIdx.x) / a.R;
+    } else {
+        c.R = 1;
+        c.rank = 0;
+        pidx = static_cast<int>(blockIdx.x);
+    }
     const int nx = a.nx, ny = a.ny;
     const long long np = static_cast<long long>(nx) * ny;
-    const int z = a.colour + 2 * static_cast<int>(blockIdx.x);
+    const int z = a.colour + 2 * pidx;
     const int b = blockIdx.y;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -296,73 +688,101 @@ __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const PlaneRelaxArg
     const S *fb = reinterpret_cast<const S *>(a.f) + static_cast<long long>(b) * a.vstride;
     S *ub = reinterpret_cast<S *>(a.u) + static_cast<long long>(b) * a.vstride;
     S *plane = ub + static_cast<long long>(z) * np;
-    const double *zc = a.zcoef + static_cast<long long>(z) * kCoefPerPlane;
+    const C *zc = coef_table<C>(a.zcoef, a.zcoef32) + static_cast<long long>(z) * kCoefPerPlane;
     {
-        const double *pc = a.pcoef + static_cast<long long>(z) * a.sum_ny * kCoefPerLine;
-        for (int i = tid; i < a.sum_ny * kCoefPerLine; i += nt) c.sm[i] = static_cast<C>(pc[i]);
+        const C *pc = coef_table<C>(a.pcoef, a.pcoef32) + static_cast<long long>(z) * a.sum_ny * kCoefPerLine;
+        for (int i = tid; i < a.sum_ny * kCoefPerLine; i += nt) c.sm[i] = pc[i];
     }
+    // the interior line matrix of each of the first MF 2D levels is factored once, by warp m
+    c.fs = c.sm + a.off_fs;
+    c.MF = a.MF;
+    TriFac<C, K> fac;
+    __syncthreads();
+    if (warp < a.MF) {
+        const C *lc = c.sm + a.line_base[warp] * kCoefPerLine;  // line 0 carries the interior matrix
+        tri_factor<C, K>(fac, C(2) * lc[1] + lc[4], -lc[1], nx, lane);
+        trifac_store<C, K>(c.fs + warp * trifac_fields<C, K>() * 32, fac, lane);
+    }
+    fac.dg = C(0);  // no real line matrix has a zero diagonal: the first line always refreshes
+    fac.of = C(0);
     const int P = a.P;
     for (int it = 0; it < a.iters; ++it) {
         const int mode = (it == 0) ? a.mode : 2;
-        // 1. plane right-hand side
-        {
-            C *g0 = arr_g(a, c, 0);
-            const C Mm = static_cast<C>(zc[0]), M0 = static_cast<C>(zc[1]), Mp = static_cast<C>(zc[2]);
-            const C Km = static_cast<C>(zc[3]), K0 = static_cast<C>(zc[4]), Kp = static_cast<C>(zc[5]);
-            for (long long i = tid; i < np; i += nt) {
-                const int y = static_cast<int>(i / nx), x = static_cast<int>(i - static_cast<long long>(y) * nx);
-                C v = ldv<C>(fb + static_cast<long long>(z) * np + i);
-                if (mode >= 1) {
-                    if (z > 0) v -= plane_term<C>(ub + static_cast<long long>(z - 1) * np, x, y, nx, ny, Mm, Km);
-                    if (z + 1 < a.nz) v -= plane_term<C>(ub + static_cast<long long>(z + 1) * np, x, y, nx, ny, Mp, Kp);
-                    if (mode == 2) v -= plane_term<C>(plane, x, y, nx, ny, M0, K0);
-                }
-                g0[i] = v;
-            }
+        // 1. plane right-hand side (the first red sweep reads f_z itself when it is in the
+        //    compute precision)
+        const S *fpl = fb + static_cast<long long>(z) * np;
+        c.g0 = nullptr;
+        if constexpr (std::is_same<S, C>::value) {
+            if (mode == 0) c.g0 = const_cast<C *>(reinterpret_cast<const C *>(fpl));
         }
-        __syncthreads();
+        if (c.g0 == nullptr) compute_rhs<S, C, K, CL>(a, c, mode, fpl, ub, z, zc, warp, nw, lane);
+        plane_sync<CL>();
         const bool acc = (mode == 2);
         // 2.-3. the 2D cycle, writing v into the plane on the way up
         if (P == 1) {
-            if (warp == 0) relax_line<S, C, K>(a, c, 0, 0, NB_NONE, OUT_PLANE, plane, acc, lane);
-            __syncthreads();
+            if (warp == 0 && c.rank == 0) {
+                const int ys[1] = {0};
+                relax_group<S, C, K, 1, CL, NB_NONE, OUT_PLANE>(a, c, fac, 0, ys, plane, acc, lane);
+            }
+            plane_sync<CL>();
             continue;
         }
         for (int m = 0; m < P - 1; ++m) {
-            const int nym = a.ny_m[m];
-            for (int y = 2 * warp; y < nym; y += 2 * nw) relax_line<S, C, K>(a, c, m, y, NB_NONE, OUT_U, plane, false, lane);
-            __syncthreads();
-            for (int y = 1 + 2 * warp; y < nym; y += 2 * nw) relax_line<S, C, K>(a, c, m, y, NB_PLAIN, OUT_U, plane, false, lane);
-            __syncthreads();
-            for (int j = warp; j < a.ny_m[m + 1]; j += nw) restrict_line<C, K>(a, c, m, j, lane);
-            __syncthreads();
+            relax_colour<S, C, K, CL, NB_NONE, OUT_U>(a, c, fac, m, 0, plane, false, warp, nw, lane);
+            plane_sync<CL>();
+            relax_colour<S, C, K, CL, NB_PLAIN, OUT_U>(a, c, fac, m, 1, plane, false, warp, nw, lane);
+            plane_sync<CL>();
+            restrict_level<C, K, CL>(a, c, m, warp, nw, lane);
+            plane_sync<CL>();
         }
-        if (warp == 0) relax_line<S, C, K>(a, c, P - 1, 0, NB_NONE, OUT_U, plane, false, lane);
-        __syncthreads();
-        for (int m = P - 2; m >= 0; --m) {
-            const int nym = a.ny_m[m];
-            const int o1 = (m == 0) ? OUT_U_AND_PLANE : OUT_U;
-            for (int y = 1 + 2 * warp; y < nym; y += 2 * nw) relax_line<S, C, K>(a, c, m, y, NB_CORR, o1, plane, acc, lane);
-            __syncthreads();
-            const int o2 = (m == 0) ? OUT_PLANE : OUT_U;
-            for (int y = 2 * warp; y < nym; y += 2 * nw) relax_line<S, C, K>(a, c, m, y, NB_PLAIN, o2, plane, acc, lane);
-            __syncthreads();
+        if (warp == 0 && c.rank == 0) {
+            const int ys[1] = {0};
+            relax_group<S, C, K, 1, CL, NB_NONE, OUT_U>(a, c, fac, P - 1, ys, plane, false, lane);
         }
+        plane_sync<CL>();
+        for (int m = P - 2; m >= 1; --m) {
+            relax_colour<S, C, K, CL, NB_CORR, OUT_U>(a, c, fac, m, 1, plane, acc, warp, nw, lane);
+            plane_sync<CL>();
+            relax_colour<S, C, K, CL, NB_PLAIN, OUT_U>(a, c, fac, m, 0, plane, acc, warp, nw, lane);
+            plane_sync<CL>();
+        }
+        relax_colour<S, C, K, CL, NB_CORR, OUT_U_AND_PLANE>(a, c, fac, 0, 1, plane, acc, warp, nw, lane);
+        plane_sync<CL>();
+        relax_colour<S, C, K, CL, NB_PLAIN, OUT_PLANE>(a, c, fac, 0, 0, plane, acc, warp, nw, lane);
+        plane_sync<CL>();
     }
 }
 
-template <class S, class C, int K>
+template <class S, class C, int K, bool CL>
 int set_smem_attr(size_t smem) {
-    return static_cast<int>(cudaFuncSetAttribute(plane_relax_kernel<S, C, K>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(smem)));
+    cudaError_t e = cudaFuncSetAttribute(plane_relax_kernel<S, C, K, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e == cudaSuccess && CL)
+        e = cudaFuncSetAttribute(plane_relax_kernel<S, C, K, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return static_cast<int>(e);
 }
 
-template <class S, class C, int K>
+template <class S, class C, int K, bool CL>
 cudaError_t launch_pr(int nplanes, int nb, int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
-    dim3 grid(nplanes, nb);
-    plane_relax_kernel<S, C, K><<<grid, threads, smem, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (!CL) {
+        dim3 grid(nplanes, nb);
+        plane_relax_kernel<S, C, K, false><<<grid, threads, smem, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nplanes * a.R, nb, 1);
+        cfg.blockDim = dim3(threads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = a.R;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, plane_relax_kernel<S, C, K, true>, a);
+    }
 }
 
 }  // namespace smg

@@ -1,39 +1,76 @@
 // plane_relax_inst.cu -- instantiates the plane-relaxation kernel for one x-line chunk size
-// K = SMG_K (rows per lane; nx <= 32 K).  The build compiles this unit once per K so the
-// instantiations compile in parallel.
+// K = SMG_K (rows per lane; nx <= 32 K) and one storage precision SMG_PREC (0 FP64, 1 FP32,
+// 2 BF16).  The build compiles this unit once per (K, precision) so the instantiations
+// compile in parallel.
 #include "plane_relax.cuh"
 
-#ifndef SMG_K
-#error "compile with -DSMG_K=<rows per lane>"
+#if !defined(SMG_K) || !defined(SMG_PREC)
+#error "compile with -DSMG_K=<rows per lane> -DSMG_PREC=<0|1|2>"
 #endif
 
 namespace smg {
 
-#define SMG_CAT2(a, b) a##b
-#define SMG_CAT(a, b) SMG_CAT2(a, b)
+#define SMG_CAT4(a, b, c, d) a##b##c##d
+#define SMG_NAME(base, k, p) SMG_CAT4(base, k, _p, p)
 
-cudaError_t SMG_CAT(launch_plane_relax_k, SMG_K)(Prec storage, bool f64, int nplanes, int nb, int threads,
-                                                 const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
-    switch (storage) {
-    case Prec::F64: return launch_pr<double, double, SMG_K>(nplanes, nb, threads, a, smem, st);
-    case Prec::F32:
-        return f64 ? launch_pr<float, double, SMG_K>(nplanes, nb, threads, a, smem, st)
-                   : launch_pr<float, float, SMG_K>(nplanes, nb, threads, a, smem, st);
-    case Prec::BF16:
-        return f64 ? launch_pr<__nv_bfloat16, double, SMG_K>(nplanes, nb, threads, a, smem, st)
-                   : launch_pr<__nv_bfloat16, float, SMG_K>(nplanes, nb, threads, a, smem, st);
-    }
+#if SMG_PREC == 0
+using StorageT = double;
+#elif SMG_PREC == 1
+using StorageT = float;
+#else
+using StorageT = __nv_bfloat16;
+#endif
+
+// a.R > 1: one thread-block cluster of a.R CTAs per plane.
+cudaError_t SMG_NAME(launch_plane_relax_k, SMG_K, SMG_PREC)(bool f64, int nplanes, int nb, int threads,
+                                                            const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
+    const bool cl = a.R > 1;
+    if (f64 || SMG_PREC == 0)
+        return cl ? launch_pr<StorageT, double, SMG_K, true>(nplanes, nb, threads, a, smem, st)
+                  : launch_pr<StorageT, double, SMG_K, false>(nplanes, nb, threads, a, smem, st);
+#if SMG_PREC != 0
+    return cl ? launch_pr<StorageT, float, SMG_K, true>(nplanes, nb, threads, a, smem, st)
+              : launch_pr<StorageT, float, SMG_K, false>(nplanes, nb, threads, a, smem, st);
+#else
     return cudaErrorInvalidValue;
+#endif
 }
 
-int SMG_CAT(set_plane_relax_smem_k, SMG_K)(Prec storage, bool f64, size_t smem) {
-    switch (storage) {
-    case Prec::F64: return set_smem_attr<double, double, SMG_K>(smem);
-    case Prec::F32: return f64 ? set_smem_attr<float, double, SMG_K>(smem) : set_smem_attr<float, float, SMG_K>(smem);
-    case Prec::BF16:
-        return f64 ? set_smem_attr<__nv_bfloat16, double, SMG_K>(smem) : set_smem_attr<__nv_bfloat16, float, SMG_K>(smem);
-    }
+int SMG_NAME(set_plane_relax_smem_k, SMG_K, SMG_PREC)(bool f64, bool cl, size_t smem) {
+    if (f64 || SMG_PREC == 0)
+        return cl ? set_smem_attr<StorageT, double, SMG_K, true>(smem) : set_smem_attr<StorageT, double, SMG_K, false>(smem);
+#if SMG_PREC != 0
+    return cl ? set_smem_attr<StorageT, float, SMG_K, true>(smem) : set_smem_attr<StorageT, float, SMG_K, false>(smem);
+#else
     return static_cast<int>(cudaErrorInvalidValue);
+#endif
+}
+
+bool SMG_NAME(cluster_resident_k, SMG_K, SMG_PREC)(bool f64, int R, int threads, size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(R, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e;
+#if SMG_PREC != 0
+    if (!f64)
+        e = cudaOccupancyMaxActiveClusters(&n, plane_relax_kernel<StorageT, float, SMG_K, true>, &cfg);
+    else
+#endif
+        e = cudaOccupancyMaxActiveClusters(&n, plane_relax_kernel<StorageT, double, SMG_K, true>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
 }
 
 }  // namespace smg

@@ -55,6 +55,8 @@ struct PlaneRelaxArgs {
     long long vstride;       // elements between batch entries of f and u
     const double *zcoef;     // this level's plane coefficients (8 per plane)
     const double *pcoef;     // this level's plane tables (sum_ny * 8 per plane)
+    const float *zcoef32;    // the same two tables rounded to FP32 (for FP32 compute)
+    const float *pcoef32;
     void *gws;               // global workspace (compute type), one slot per CTA
     long long ws_per_plane;  // elements per CTA slot
     int P;                   // 2D levels
@@ -65,6 +67,9 @@ struct PlaneRelaxArgs {
     int off_g[kMaxPlaneLevels];   // element offset of g_m
     unsigned smem_u_mask;         // bit m set: u_m lives in shared memory
     unsigned smem_g_mask;
+    int R;                        // CTAs per plane (thread-block cluster size; 1 = no cluster)
+    int MF;                       // 2D levels whose interior line factors are kept in shared memory
+    int off_fs;                   // element offset of those factor sets in shared memory
 };
 
 // Placement of the per-plane 2D-cycle arrays: shared memory where they fit, else global.
@@ -75,9 +80,18 @@ struct PlaneLayout {
     int off_u[kMaxPlaneLevels] = {0};
     int off_g[kMaxPlaneLevels] = {0};
     unsigned smem_u_mask = 0, smem_g_mask = 0;
+    int MF = 0;                   // factor sets kept in shared memory (2D levels 0..MF-1)
+    int off_fs = 0;
 };
 
+// Elements of one shared-memory factor set of the x-line solver (fields x 32 lanes).
+inline int trifac_set_elems(int K) { return (4 * K + 15) * 32; }
+constexpr int kMaxFactorLevels = 6;
+
 PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget);
+// Layout for a cluster of R CTAs per plane: every array in shared memory, each CTA holding the
+// lines it owns (pairs (y/2) mod R).  smem_bytes = 0 when it does not fit in the budget.
+PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R);
 
 // Kernel launchers (cycle.cu and its instantiation units).
 enum class Prec { F64 = 0, F32 = 1, BF16 = 2 };
@@ -87,14 +101,19 @@ size_t storage_bytes(Prec p);
 cudaError_t launch_plane_relax(Prec storage, bool compute_f64, int K, int nplanes, int nb,
                                int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
 cudaError_t launch_restrict(Prec storage, int nx, int ny, int nzf, int nb, const void *f,
-                            const void *u, void *fc, const double *zcoef, long long vstride_f,
-                            long long vstride_c, cudaStream_t st);
+                            const void *u, void *fc, const double *zcoef, const float *zcoef32,
+                            long long vstride_f, long long vstride_c, cudaStream_t st);
 cudaError_t launch_prolong(Prec storage, int nx, int ny, int nzf, int nb, void *u, const void *uc,
-                           const double *zcoef, long long vstride_f, long long vstride_c,
-                           cudaStream_t st);
+                           const double *zcoef, const float *zcoef32, long long vstride_f,
+                           long long vstride_c, cudaStream_t st);
+// Compares the integer-pipe FP32 <-> FP64 conversions with the hardware ones on n values:
+// mism[0] counts narrowing mismatches, mism[1] widening mismatches (device int[2]).
+cudaError_t launch_check_conversions(long long n, const double *src, int *mism, cudaStream_t st);
 cudaError_t launch_convert_to(Prec storage, long long n, const double *src, void *dst, cudaStream_t st);
 cudaError_t launch_convert_from(Prec storage, long long n, const void *src, double *dst, cudaStream_t st);
 cudaError_t launch_apply_A(int nx, int ny, int nz, int nb, const double *u, double *out, cudaStream_t st);
-int set_plane_relax_smem(Prec storage, bool compute_f64, int K, int threads, size_t smem);
+int set_plane_relax_smem(Prec storage, bool compute_f64, bool cluster, int K, size_t smem);
+// True when a cluster of R CTAs of the plane kernel (FP64 or FP32 compute) can be resident.
+bool cluster_resident(Prec storage, bool compute_f64, int K, int R, int threads, size_t smem);
 
 }  // namespace smg

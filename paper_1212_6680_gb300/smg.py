@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsmg.so")
 SMG_OK, SMG_ERR_ARG, SMG_ERR_CUDA, SMG_ERR_NOCONV, SMG_ERR_BREAKDOWN, SMG_ERR_TIMEOUT, SMG_ERR_NAN = 0, -1, -2, -3, -4, -5, -6
 SMG_PCG, SMG_FPCG, SMG_PSD = 0, 1, 2
 SMG_FP64, SMG_FP32, SMG_BF16 = 0, 1, 2
-SMG_OPT_COARSE_ITERS, SMG_OPT_THREADS, SMG_OPT_PROFILE = 0, 1, 2
+SMG_OPT_COARSE_ITERS, SMG_OPT_THREADS, SMG_OPT_PROFILE, SMG_OPT_CLUSTER_MAX, SMG_OPT_CLUSTER_MAX32 = 0, 1, 2, 3, 4
 
 VARIANTS = {"pcg": SMG_PCG, "fpcg": SMG_FPCG, "psd": SMG_PSD}
 PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}
@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}
 # every symbol include/smg.h declares
 EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg_apply_batched",
            "smg_apply_A", "krylov_solve", "lobpcg_solve", "smg_destroy", "smg_last_error",
-           "smg_profile_read")
+           "smg_profile_read", "smg_launch_count", "smg_check_conversions")
 
 
 class SMGError(RuntimeError):
@@ -52,6 +52,8 @@ def _load():
     L.smg_destroy.argtypes = [vp]
     L.smg_last_error.restype = ctypes.c_char_p
     L.smg_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp]
+    L.smg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.smg_check_conversions.argtypes = [ctypes.c_longlong, vp, vp, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -151,6 +153,17 @@ def smg_profile_read(h: int, which: int):
     by = ctypes.c_double(0.0)
     _check(_lib.smg_profile_read(h, which, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
     return n.value, ms.value, by.value
+
+
+def smg_launch_count(h: int) -> int:
+    n = ctypes.c_longlong(0)
+    _check(_lib.smg_launch_count(h, ctypes.byref(n)))
+    return n.value
+
+
+def smg_check_conversions(src, mismatches, stream=None) -> None:
+    """src: device doubles; mismatches: device int32[2]."""
+    _check(_lib.smg_check_conversions(src.numel(), _ptr(src), _ptr(mismatches), _stream(stream)))
 
 
 def smg_destroy(h: int) -> None:

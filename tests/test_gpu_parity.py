@@ -188,3 +188,22 @@ def test_lobpcg_matches_closed_form(smg, shape, m, npost):
     assert np.all(np.abs(lam - ref) <= 1e-10 * ref), (lam, ref)
     G = Xh @ Xh.T
     assert np.abs(G - np.eye(m)).max() <= 1e-10
+
+
+def test_integer_pipe_conversions_match_hardware(smg):
+    # the library's own FP32 <-> FP64 conversions against the hardware instructions, bit for bit:
+    # random magnitudes over the whole float range, ties, carries into the exponent, overflow to
+    # infinity, denormal results, zeros, infinities and NaN
+    rng = np.random.default_rng(3)
+    vals = [rng.standard_normal(200000) * np.exp(rng.uniform(-90, 90, 200000)),
+            rng.uniform(-1, 1, 100000)]
+    f = rng.standard_normal(50000).astype(np.float32).astype(np.float64)
+    ulp = np.spacing(f.astype(np.float32)).astype(np.float64)
+    vals += [f + ulp / 2, f - ulp / 2, f + ulp / 2 * (1 + 2.0 ** -40), f + ulp * 0.49999]  # ties and near-ties
+    vals.append(np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 3.4028235677973366e38, 3.4028235e38 * 1.0000001,
+                          1.1754943508222875e-38, 1.17549e-38, 1e-40, -1e-45, 1.401298464324817e-45, 2.0 ** -126,
+                          np.nextafter(2.0 ** 128, 0), 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 1e300, -1e-300]))
+    src = torch.from_numpy(np.concatenate(vals)).cuda()
+    mism = torch.zeros(2, dtype=torch.int32, device="cuda")
+    smg.smg_check_conversions(src, mism)
+    assert mism.cpu().tolist() == [0, 0]
