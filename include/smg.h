@@ -149,6 +149,26 @@ int smg_check_conversions(long long n, const double *src, int *mismatches, void 
 /* smg_launch_count -- number of CUDA kernel launches this handle has issued so far. */
 int smg_launch_count(smg_handle h, long long *count);
 
+/*
+ * smg_apply_A_dot_static -- out = A u and *dot = (u, A u), allocating nothing.
+ * The paper has no counterpart: this is an allocation-free form of the operator and inner
+ * product of Algorithm 1 for callers that cannot allocate device memory where they need it
+ * (a host framework that owns every device allocation and lends the library only input and
+ * output buffers, or a section where cudaMalloc / cudaFree must not run because they can
+ * synchronise the device).  No handle is needed.
+ *   nx, ny, nz: grid sizes, >= 1, with nx*ny*nz <= 33,554,432 (the capacity of the scratch);
+ *               larger grids return SMG_ERR_ARG with a message and launch nothing.
+ *   u, out:     device, nx*ny*nz doubles each, caller-owned, must not overlap.
+ *   dot:        device, one double, caller-owned.
+ * Scratch: the per-CTA partial sums live in a file-scope device array (about 32 KB) that every
+ * GPU which loads the library holds until the process exits.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) for that device; make that first
+ * call before any stream capture.  Every call shares the array and clears its counter first:
+ * calls that overlap on the GPU (for example on two streams at once) race and give wrong
+ * results; calls ordered on one stream are safe.  Asynchronous on `stream`.
+ */
+int smg_apply_A_dot_static(int nx, int ny, int nz, const double *u, double *out, double *dot, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

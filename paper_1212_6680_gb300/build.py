@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libsmg.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 KS = (1, 2, 3, 4, 6, 8, 16)
-SOURCES = ["api.cpp", "hierarchy.cpp", "cycle.cu", "krylov_kernels.cu", "lobpcg.cu"]
+SOURCES = ["api.cpp", "hierarchy.cpp", "cycle.cu", "krylov_kernels.cu", "lobpcg.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -52,6 +52,8 @@ struct PendingEvent {
 
 }  // namespace
 
+void smg::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 struct smg_ctx {
     int nx = 0, ny = 0, nz = 0, npre = 1, npost = 1, coarse_iters = 1, threads = 512;
     Prec prec = Prec::F64;

@@ -44,6 +44,9 @@ struct HostHierarchy {
 
 void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H);
 
+// Sets the message smg_last_error() returns on the calling thread.
+void set_last_error(const std::string &msg);
+
 // Arguments of one plane-relaxation launch (one colour of one z-level, all batch entries).
 struct PlaneRelaxArgs {
     int nx, ny, nz;          // level grid (ny is the same on every z-level)

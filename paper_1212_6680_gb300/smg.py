@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}
 # every symbol include/smg.h declares
 EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg_apply_batched",
            "smg_apply_A", "krylov_solve", "lobpcg_solve", "smg_destroy", "smg_last_error",
-           "smg_profile_read", "smg_launch_count", "smg_check_conversions")
+           "smg_profile_read", "smg_launch_count", "smg_check_conversions", "smg_apply_A_dot_static")
 
 
 class SMGError(RuntimeError):
@@ -54,6 +54,7 @@ def _load():
     L.smg_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp]
     L.smg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.smg_check_conversions.argtypes = [ctypes.c_longlong, vp, vp, vp]
+    L.smg_apply_A_dot_static.argtypes = [i, i, i, vp, vp, vp, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -164,6 +165,11 @@ def smg_launch_count(h: int) -> int:
 def smg_check_conversions(src, mismatches, stream=None) -> None:
     """src: device doubles; mismatches: device int32[2]."""
     _check(_lib.smg_check_conversions(src.numel(), _ptr(src), _ptr(mismatches), _stream(stream)))
+
+
+def smg_apply_A_dot_static(nx: int, ny: int, nz: int, u, out, dot, stream=None) -> None:
+    """out = A u and dot[0] = (u, A u) with no device allocation (static scratch)."""
+    _check(_lib.smg_apply_A_dot_static(nx, ny, nz, _ptr(u), _ptr(out), _ptr(dot), _stream(stream)))
 
 
 def smg_destroy(h: int) -> None:
