@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -32,7 +33,7 @@ int fail(int code, const std::string &msg) {
             return fail(SMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
     } while (0)
 
-constexpr size_t kSmemBudget = 224 * 1024;  // of the 227 KB a CTA may use
+constexpr size_t kSmemBudget = 227 * 1024;  // the most dynamic shared memory a CTA may use
 
 // profiling classes: 0 plane relaxation on the finest level, 1 plane relaxation on the other
 // levels (all but the coarsest), 2 the one-plane coarsest solve, 3 restriction + prolongation,
@@ -259,6 +260,10 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     a.MF = lay.MF;
     a.off_fs = lay.off_fs;
     const int K = instantiated_K(h->nx);
+    {
+        auto al16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+        a.vec = (h->nx == 32 * K) && al16(f) && al16(u) && al16(h->d_ws);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = (h->profile == 2) || (h->profile == 1 && l == 0);
     const int cls = coarsest ? 2 : (l == 0 ? 0 : 1);

@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <array>
 #include <cstdio>
+#include <utility>
+#include <vector>
 
 #include "smg_internal.h"
 
@@ -195,13 +197,13 @@ void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H) {
 // (the iterate is touched more often than the right-hand side).  What does not fit in
 // `smem_budget` goes to a global slot per CTA (L2-resident for the sizes of interest).
 // Instantiated x-line chunk size for nx (rows per lane): 1, 2, 3, 4, 6, 8 or 16.
-// Factor sets worth keeping: 2D levels with at least 16 lines (at least 8 per colour, so
-// several warps would factor the same matrix), using at most a quarter of the budget.
+// Factor sets kept in shared memory: every 2D level (the single-line coarsest included), unless
+// they would take more than a third of the budget; then only the finest MF levels keep theirs
+// and the others factor on the fly.
 static int factor_levels(const HostHierarchy &H, int K, size_t elem_bytes, size_t smem_budget) {
-    int mf = 0;
-    while (mf < H.P - 1 && mf < kMaxFactorLevels && H.ny_m[mf] >= 16) ++mf;
-    const size_t set_bytes = static_cast<size_t>(trifac_set_elems(K)) * elem_bytes;
-    while (mf > 0 && static_cast<size_t>(mf) * set_bytes > smem_budget / 4) --mf;
+    const size_t set_bytes = 2 * static_cast<size_t>(trifac_set_elems(K)) * elem_bytes;  // two per level
+    int mf = std::min(H.P, kMaxFactorLevels);
+    while (mf > 0 && static_cast<size_t>(mf) * set_bytes > smem_budget / 3) --mf;
     return mf;
 }
 
@@ -226,26 +228,35 @@ PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t 
     size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
     P.MF = factor_levels(H, P.K, elem_bytes, smem_budget);
     P.off_fs = static_cast<int>(smem_elems);
-    smem_elems += static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
+    smem_elems += 2 * static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
     long long gl = 0;
     const size_t budget_elems = smem_budget / elem_bytes;
-    for (int m = H.P - 1; m >= 0; --m) {
+    // priority: both arrays of levels >= 2 (coarse to fine), then u_1, u_0, g_1, g_0
+    std::vector<std::pair<int, int>> order;  // (level, 0 = u / 1 = g)
+    for (int m = H.P - 1; m >= 2; --m) {
+        order.push_back({m, 0});
+        order.push_back({m, 1});
+    }
+    if (H.P > 1) order.push_back({1, 0});
+    order.push_back({0, 0});
+    if (H.P > 1) order.push_back({1, 1});
+    order.push_back({0, 1});
+    for (const auto &o : order) {
+        const int m = o.first;
         const size_t sz = align4(static_cast<size_t>(H.nx) * H.ny_m[m]);
-        for (int which = 0; which < 2; ++which) {
-            if (smem_elems + sz <= budget_elems) {
-                if (which == 0) {
-                    P.off_u[m] = static_cast<int>(smem_elems);
-                    P.smem_u_mask |= 1u << m;
-                } else {
-                    P.off_g[m] = static_cast<int>(smem_elems);
-                    P.smem_g_mask |= 1u << m;
-                }
-                smem_elems += sz;
+        if (smem_elems + sz <= budget_elems) {
+            if (o.second == 0) {
+                P.off_u[m] = static_cast<int>(smem_elems);
+                P.smem_u_mask |= 1u << m;
             } else {
-                if (which == 0) P.off_u[m] = static_cast<int>(gl);
-                else P.off_g[m] = static_cast<int>(gl);
-                gl += static_cast<long long>(sz);
+                P.off_g[m] = static_cast<int>(smem_elems);
+                P.smem_g_mask |= 1u << m;
             }
+            smem_elems += sz;
+        } else {
+            if (o.second == 0) P.off_u[m] = static_cast<int>(gl);
+            else P.off_g[m] = static_cast<int>(gl);
+            gl += static_cast<long long>(sz);
         }
     }
     P.smem_bytes = smem_elems * elem_bytes;
@@ -260,7 +271,7 @@ PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes,
     size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
     P.MF = factor_levels(H, P.K, elem_bytes, smem_budget);
     P.off_fs = static_cast<int>(smem_elems);
-    smem_elems += static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
+    smem_elems += 2 * static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
     for (int m = H.P - 1; m >= 0; --m) {
         const int pairs = (H.ny_m[m] + 1) / 2;
         const size_t nloc = 2 * static_cast<size_t>((pairs + R - 1) / R);

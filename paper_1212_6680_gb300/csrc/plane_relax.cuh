@@ -36,6 +36,14 @@ namespace smg {
 
 namespace cg = cooperative_groups;
 
+// Step-trace hook for latency studies: compiled out unless SMG_STEP_TRACE names a device
+// function `void f(const PlaneRelaxArgs &, int step)`.
+#ifdef SMG_STEP_TRACE
+#define SMG_TRACE(k) SMG_STEP_TRACE(a, (k))
+#else
+#define SMG_TRACE(k) ((void)0)
+#endif
+
 // ---- storage <-> compute conversion -------------------------------------------------------
 // FP32 <-> FP64 conversions written out on the integer pipe from the IEEE-754 binary32 and
 // binary64 formats (GB300's conversion instruction runs at a small fraction of even its FP64
@@ -105,6 +113,10 @@ struct TriFac {
     C k1[5], k2[5];            // cyclic-reduction multipliers
 };
 
+// 1/x: the correctly rounded single-precision reciprocal, or the double division.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 template <class C, int K>
 __device__ __noinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of, const int n, const int lane) {
     const int i0 = lane * K;
@@ -121,13 +133,13 @@ __device__ __noinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of,
         RB = B(0);
         RC = f.c0;
     } else {
-        f.inv[1] = C(1) / B(1);
+        f.inv[1] = recip(B(1));
         f.ab[1] = A(1) * f.inv[1];
         f.cb[1] = Cu(1) * f.inv[1];
 #pragma unroll
         for (int j = 2; j < K; ++j) {
             const C aj = A(j);
-            f.inv[j] = C(1) / (B(j) - aj * f.cb[j - 1]);
+            f.inv[j] = recip(B(j) - aj * f.cb[j - 1]);
             f.ab[j] = -aj * f.ab[j - 1] * f.inv[j];
             f.cb[j] = Cu(j) * f.inv[j];
         }
@@ -149,7 +161,7 @@ __device__ __noinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of,
 #pragma unroll
     for (int t = 0; t < 5; ++t) {
         const int s = 1 << t;
-        const C rb = C(1) / RB;
+        const C rb = recip(RB);
         C am = __shfl_up_sync(0xffffffffu, RA, s), rbm = __shfl_up_sync(0xffffffffu, rb, s);
         C cm = __shfl_up_sync(0xffffffffu, RC, s);
         C ap = __shfl_down_sync(0xffffffffu, RA, s), rbp = __shfl_down_sync(0xffffffffu, rb, s);
@@ -163,12 +175,13 @@ __device__ __noinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of,
         f.k1[t] = k1;
         f.k2[t] = k2;
     }
-    f.rbf = C(1) / RB;
+    f.rbf = recip(RB);
 }
 
-// A factor set in shared memory: field k of lane l at fs[k * 32 + l].
+// A factor set in shared memory: field k of lane l at fs[k * 32 + l].  Only the fields the
+// right-hand-side sweeps read are kept: inv[1..K-1], cbf[1..K-2], ab[1..K-1], cb[1..K-1].
 template <class C, int K>
-constexpr int trifac_fields() { return 4 * K + 15; }
+constexpr int trifac_fields() { return 2 + (K > 1 ? 4 * K - 5 : 0) + 13; }
 
 template <class C, int K>
 __device__ __forceinline__ void trifac_store(C *fs, const TriFac<C, K> &f, int lane) {
@@ -176,13 +189,13 @@ __device__ __forceinline__ void trifac_store(C *fs, const TriFac<C, K> &f, int l
     fs[(k++) * 32 + lane] = f.dg;
     fs[(k++) * 32 + lane] = f.of;
 #pragma unroll
-    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.inv[j];
+    for (int j = 1; j < K; ++j) fs[(k++) * 32 + lane] = f.inv[j];
 #pragma unroll
-    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.cbf[j];
+    for (int j = 1; j < K - 1; ++j) fs[(k++) * 32 + lane] = f.cbf[j];
 #pragma unroll
-    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.ab[j];
+    for (int j = 1; j < K; ++j) fs[(k++) * 32 + lane] = f.ab[j];
 #pragma unroll
-    for (int j = 0; j < K; ++j) fs[(k++) * 32 + lane] = f.cb[j];
+    for (int j = 1; j < K; ++j) fs[(k++) * 32 + lane] = f.cb[j];
     fs[(k++) * 32 + lane] = f.a0;
     fs[(k++) * 32 + lane] = f.c0;
     fs[(k++) * 32 + lane] = f.rbf;
@@ -198,13 +211,13 @@ __device__ __forceinline__ void trifac_load(TriFac<C, K> &f, const C *fs, int la
     f.dg = fs[(k++) * 32 + lane];
     f.of = fs[(k++) * 32 + lane];
 #pragma unroll
-    for (int j = 0; j < K; ++j) f.inv[j] = fs[(k++) * 32 + lane];
+    for (int j = 1; j < K; ++j) f.inv[j] = fs[(k++) * 32 + lane];
 #pragma unroll
-    for (int j = 0; j < K; ++j) f.cbf[j] = fs[(k++) * 32 + lane];
+    for (int j = 1; j < K - 1; ++j) f.cbf[j] = fs[(k++) * 32 + lane];
 #pragma unroll
-    for (int j = 0; j < K; ++j) f.ab[j] = fs[(k++) * 32 + lane];
+    for (int j = 1; j < K; ++j) f.ab[j] = fs[(k++) * 32 + lane];
 #pragma unroll
-    for (int j = 0; j < K; ++j) f.cb[j] = fs[(k++) * 32 + lane];
+    for (int j = 1; j < K; ++j) f.cb[j] = fs[(k++) * 32 + lane];
     f.a0 = fs[(k++) * 32 + lane];
     f.c0 = fs[(k++) * 32 + lane];
     f.rbf = fs[(k++) * 32 + lane];
@@ -379,10 +392,13 @@ template <class C, int K>
 __device__ __forceinline__ void ensure_fac(const PlaneCtx<C> &c, TriFac<C, K> &fac, int m, C dg, C of, int lane) {
     if (fac.dg == dg && fac.of == of) return;
     if (m < c.MF) {
-        const C *fs = c.fs + m * trifac_fields<C, K>() * 32;
-        if (fs[lane] == dg && fs[32 + lane] == of) {
-            trifac_load<C, K>(fac, fs, lane);
-            return;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {  // the level's interior matrix and its last line's
+            const C *fs = c.fs + (2 * m + t) * trifac_fields<C, K>() * 32;
+            if (fs[lane] == dg && fs[32 + lane] == of) {
+                trifac_load<C, K>(fac, fs, lane);
+                return;
+            }
         }
     }
     tri_factor<C, K>(fac, dg, of, c.nx, lane);
@@ -662,7 +678,7 @@ __device__ __forceinline__ void compute_rhs(const PlaneRelaxArgs &a, const Plane
 
 // One CTA (CL = false) or one cluster of R CTAs (CL = true) per plane of the colour.
 template <class S, class C, int K, bool CL>
-__global__ void __launch_bounds__(512, 1) plane_relax_kernel(const PlaneRelaxArgs a) {
+__global__ void __launch_bounds__(512, 1) plane_relax_kernel(const __grid_constant__ PlaneRelaxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PlaneCtx<C> c;
     c.sm = reinterpret_cast<C *>(smem_raw);
@@ -698,10 +714,15 @@ __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const PlaneRelaxArg
     c.MF = a.MF;
     TriFac<C, K> fac;
     __syncthreads();
-    if (warp < a.MF) {
-        const C *lc = c.sm + a.line_base[warp] * kCoefPerLine;  // line 0 carries the interior matrix
+    SMG_TRACE(0);
+    // factor sets: per 2D level, the interior line matrix (line 0) and the last line's (the only
+    // other one when ny is a power of two); set 2m + t, computed by warps in parallel
+    for (int sidx = warp; sidx < 2 * a.MF; sidx += nw) {
+        const int mm = sidx >> 1;
+        const int y = (sidx & 1) ? a.ny_m[mm] - 1 : 0;
+        const C *lc = c.sm + (a.line_base[mm] + y) * kCoefPerLine;
         tri_factor<C, K>(fac, C(2) * lc[1] + lc[4], -lc[1], nx, lane);
-        trifac_store<C, K>(c.fs + warp * trifac_fields<C, K>() * 32, fac, lane);
+        trifac_store<C, K>(c.fs + sidx * trifac_fields<C, K>() * 32, fac, lane);
     }
     fac.dg = C(0);  // no real line matrix has a zero diagonal: the first line always refreshes
     fac.of = C(0);
@@ -717,6 +738,7 @@ __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const PlaneRelaxArg
         }
         if (c.g0 == nullptr) compute_rhs<S, C, K, CL>(a, c, mode, fpl, ub, z, zc, warp, nw, lane);
         plane_sync<CL>();
+        SMG_TRACE(1);
         const bool acc = (mode == 2);
         // 2.-3. the 2D cycle, writing v into the plane on the way up
         if (P == 1) {
@@ -730,26 +752,34 @@ __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const PlaneRelaxArg
         for (int m = 0; m < P - 1; ++m) {
             relax_colour<S, C, K, CL, NB_NONE, OUT_U>(a, c, fac, m, 0, plane, false, warp, nw, lane);
             plane_sync<CL>();
+            SMG_TRACE(2 + 3 * m);
             relax_colour<S, C, K, CL, NB_PLAIN, OUT_U>(a, c, fac, m, 1, plane, false, warp, nw, lane);
             plane_sync<CL>();
+            SMG_TRACE(3 + 3 * m);
             restrict_level<C, K, CL>(a, c, m, warp, nw, lane);
             plane_sync<CL>();
+            SMG_TRACE(4 + 3 * m);
         }
         if (warp == 0 && c.rank == 0) {
             const int ys[1] = {0};
             relax_group<S, C, K, 1, CL, NB_NONE, OUT_U>(a, c, fac, P - 1, ys, plane, false, lane);
         }
         plane_sync<CL>();
+        SMG_TRACE(60);
         for (int m = P - 2; m >= 1; --m) {
             relax_colour<S, C, K, CL, NB_CORR, OUT_U>(a, c, fac, m, 1, plane, acc, warp, nw, lane);
             plane_sync<CL>();
+            SMG_TRACE(100 - 2 * m);
             relax_colour<S, C, K, CL, NB_PLAIN, OUT_U>(a, c, fac, m, 0, plane, acc, warp, nw, lane);
             plane_sync<CL>();
+            SMG_TRACE(101 - 2 * m);
         }
         relax_colour<S, C, K, CL, NB_CORR, OUT_U_AND_PLANE>(a, c, fac, 0, 1, plane, acc, warp, nw, lane);
         plane_sync<CL>();
+        SMG_TRACE(100);
         relax_colour<S, C, K, CL, NB_PLAIN, OUT_PLANE>(a, c, fac, 0, 0, plane, acc, warp, nw, lane);
         plane_sync<CL>();
+        SMG_TRACE(101);
     }
 }
 

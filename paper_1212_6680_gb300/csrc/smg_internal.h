@@ -73,6 +73,7 @@ struct PlaneRelaxArgs {
     int R;                        // CTAs per plane (thread-block cluster size; 1 = no cluster)
     int MF;                       // 2D levels whose interior line factors are kept in shared memory
     int off_fs;                   // element offset of those factor sets in shared memory
+    int vec;                      // 1: nx == 32 K and f, u, the workspace are 16-byte aligned
 };
 
 // Placement of the per-plane 2D-cycle arrays: shared memory where they fit, else global.
@@ -88,8 +89,8 @@ struct PlaneLayout {
 };
 
 // Elements of one shared-memory factor set of the x-line solver (fields x 32 lanes).
-inline int trifac_set_elems(int K) { return (4 * K + 15) * 32; }
-constexpr int kMaxFactorLevels = 6;
+inline int trifac_set_elems(int K) { return (2 + (K > 1 ? 4 * K - 5 : 0) + 13) * 32; }
+constexpr int kMaxFactorLevels = kMaxPlaneLevels;
 
 PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget);
 // Layout for a cluster of R CTAs per plane: every array in shared memory, each CTA holding the
