@@ -119,6 +119,34 @@ int krylov_solve(smg_handle h, int variant, const double *b, double *x, double t
 int lobpcg_solve(smg_handle h, int m, double *X, double *lambda, double tol, int maxit,
                  int *iters, void *stream);
 
+/*
+ * krylov_solve_batched -- nsys independent systems, each the model problem on its own brick
+ * (dims[3s], dims[3s+1], dims[3s+2] = nx, ny, nz of system s), solved together by flexible PCG
+ * (Algorithm 1 with eq. (2)) preconditioned by SMG with -v npre npost.  Per iteration, one CUDA
+ * graph runs one persistent kernel that performs every step of every system's V-cycle (levels
+ * aligned from the finest, a bounded grid barrier between steps) and the FP64 Krylov kernels of
+ * all systems; converged systems are masked out on the device.  The schedule (threads per CTA,
+ * task order) is chosen by timing the candidates on the first call for a given set of grids.
+ *   dims:  host, 3*nsys ints; 1 <= nx <= 128, 1 <= ny <= 512, 1 <= nz <= 4096.
+ *   prec:  SMG_FP32 (FP32 cycle, FP64 coarsest plane, FP64 Krylov).
+ *   b, x:  host arrays of nsys device pointers (system s has nx*ny*nz doubles); x holds x0 on entry.
+ *   iters: host, nsys ints, always written (preconditioner applications per system).
+ * Stops each system at ||b - A x||_2 <= tol ||b||_2 (true residual); returns SMG_ERR_NOCONV
+ * when some system did not reach it in maxit iterations, SMG_ERR_TIMEOUT when a grid-barrier
+ * wait gave up.  Synchronises `stream` once per iteration.  1 <= nsys <= 4096.
+ */
+int krylov_solve_batched(int nsys, const int *dims, int npre, int npost, int prec, const double *const *b,
+                         double *const *x, double tol, int maxit, int *iters, void *stream);
+
+/*
+ * smg_barrier_selftest -- runs a small persistent kernel of 4 CTAs whose grid barrier waits for
+ * 4 + extra_blocks CTAs, with a wait limit of about limit_seconds (0 < limit_seconds <= 10).
+ * *status (host) receives SMG_OK when the barriers complete (extra_blocks = 0) and
+ * SMG_ERR_TIMEOUT when a wait gave up (extra_blocks > 0): the failure path of the barrier that
+ * krylov_solve_batched relies on, exercised without faulting or hanging the device.
+ */
+int smg_barrier_selftest(int extra_blocks, double limit_seconds, int *status, void *stream);
+
 /* smg_destroy -- free the handle and everything it owns (NULL is accepted). */
 int smg_destroy(smg_handle h);
 

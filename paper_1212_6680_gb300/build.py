@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libsmg.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 KS = (1, 2, 3, 4, 6, 8, 16)
-SOURCES = ["api.cpp", "hierarchy.cpp", "cycle.cu", "krylov_kernels.cu", "lobpcg.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "hierarchy.cpp", "cycle.cu", "krylov_kernels.cu", "lobpcg.cu", "noalloc.cu", "batched.cu"]
 
 
 def nvcc() -> str:
@@ -41,6 +41,9 @@ def _units():
         obj = os.path.join(BUILD, os.path.splitext(s)[0] + ".o")
         lang = ["-x", "cu"] if s.endswith(".cu") else ["-x", "c++"]
         units.append((src, obj, lang, []))
+    for k in (1, 2, 3, 4):
+        src = os.path.join(CSRC, "batched_inst.cu")
+        units.append((src, os.path.join(BUILD, f"batched_k{k}.o"), ["-x", "cu"], [f"-DSMG_K={k}"]))
     for k in KS:
         for prec in (0, 1, 2):
             src = os.path.join(CSRC, "plane_relax_inst.cu")

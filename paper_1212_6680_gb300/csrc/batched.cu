@@ -1,0 +1,1085 @@
+// batched.cu -- krylov_solve_batched: many independent 7-point Laplacian systems on uneven
+// grids solved together by Algorithm 1 of arXiv:1212.6680 (PCG eq. (1), flexible PCG eq. (2),
+// PSD) with the SMG preconditioner.
+//
+// Per iteration, one CUDA graph:
+//   1. the persistent V-cycle kernel (batched.cuh): every relaxation / transfer step of every
+//      system's V-cycle in one launch, the z-levels of all systems aligned from the finest;
+//   2. the FP64 Krylov kernels over all systems at once: vectors are concatenated, every CTA
+//      works on one chunk of one system, per-system sums are finished by one thread per system
+//      (compensated), and the per-system scalars (alpha, beta, norms) live on the device;
+//   3. an 4-byte copy of the number of systems still iterating.
+// A system whose recurrence residual meets the tolerance is masked out on the device (its
+// tasks and chunks are skipped); when none is left, the true residuals are checked and any
+// system that fails continues from its true residual with beta = 0.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/smg.h"
+#include "batched.h"
+#include "plane_relax.cuh"
+
+namespace smg {
+
+// ---- persistent-kernel dispatch over K -----------------------------------------------------------
+#define SMG_DECL_BK(k)                                                                                 \
+    cudaError_t launch_persistent_vcycle_k##k(Prec, int, int, size_t, const PersistArgs &, cudaStream_t, bool); \
+    int set_persistent_smem_k##k(Prec, size_t);                                                        \
+    int persistent_blocks_per_sm_k##k(Prec, int, size_t);
+SMG_DECL_BK(1)
+SMG_DECL_BK(2)
+SMG_DECL_BK(3)
+SMG_DECL_BK(4)
+
+cudaError_t launch_persistent_vcycle(Prec storage, int K, int blocks, int threads, size_t smem, const PersistArgs &p,
+                                     cudaStream_t st, bool cooperative) {
+    switch (K) {
+    case 1: return launch_persistent_vcycle_k1(storage, blocks, threads, smem, p, st, cooperative);
+    case 2: return launch_persistent_vcycle_k2(storage, blocks, threads, smem, p, st, cooperative);
+    case 3: return launch_persistent_vcycle_k3(storage, blocks, threads, smem, p, st, cooperative);
+    case 4: return launch_persistent_vcycle_k4(storage, blocks, threads, smem, p, st, cooperative);
+    }
+    return cudaErrorInvalidValue;
+}
+int set_persistent_smem(Prec storage, int K, size_t smem) {
+    switch (K) {
+    case 1: return set_persistent_smem_k1(storage, smem);
+    case 2: return set_persistent_smem_k2(storage, smem);
+    case 3: return set_persistent_smem_k3(storage, smem);
+    case 4: return set_persistent_smem_k4(storage, smem);
+    }
+    return static_cast<int>(cudaErrorInvalidValue);
+}
+int persistent_blocks_per_sm(Prec storage, int K, int threads, size_t smem) {
+    switch (K) {
+    case 1: return persistent_blocks_per_sm_k1(storage, threads, smem);
+    case 2: return persistent_blocks_per_sm_k2(storage, threads, smem);
+    case 3: return persistent_blocks_per_sm_k3(storage, threads, smem);
+    case 4: return persistent_blocks_per_sm_k4(storage, threads, smem);
+    }
+    return 0;
+}
+
+namespace {
+
+// ---- barrier self-test ------------------------------------------------------------------------------
+__device__ __forceinline__ bool test_barrier(unsigned *count, unsigned *gen, int *err, long long limit,
+                                             unsigned expected) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = *reinterpret_cast<volatile unsigned *>(gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == expected - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*reinterpret_cast<volatile unsigned *>(gen) == g) {
+                if (*reinterpret_cast<volatile int *>(err) != 0) break;
+                if (++spins > limit) {
+                    atomicCAS(err, 0, SMG_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = (*reinterpret_cast<volatile int *>(err) == 0);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void barrier_selftest_kernel(unsigned expected, long long limit, unsigned *count, unsigned *gen, int *err) {
+    for (int s = 0; s < 4; ++s)
+        if (!test_barrier(count, gen, err, limit, expected)) return;
+}
+
+// ---- batched FP64 Krylov kernels --------------------------------------------------------------------
+constexpr int kChunk = 4096;
+constexpr int kBThreads = 256;
+
+struct BSys {
+    int nx, ny, nz;
+    long long off;        // offset of this system in the concatenated FP64 vectors
+    long long f0_off;     // offset of its level-0 f in the storage array
+    long long u0_off;     // offset of its level-0 u
+    int c0, c1;           // its chunks [c0, c1)
+};
+
+struct BScal {
+    double rho, rho_prev, beta, alpha, rr, bb;
+    int restart, status, iters, pad;
+};
+
+struct BKrylov {
+    const BSys *sys;
+    const int *ch_sys;
+    const long long *ch_start;  // global offset of the chunk
+    const int *ch_len;
+    double *r, *p, *q, *dr;
+    const double *const *bptr;
+    double *const *xptr;
+    void *fstore, *ustore;      // storage arrays (level vectors of every system)
+    double *part;               // 2 per chunk
+    BScal *sc;
+    int *active;
+    int *nactive;
+    int nsys, variant, maxit;
+    double tol2;
+};
+
+__device__ __forceinline__ double stencil_at(const double *__restrict__ v, long long i, int x, int y, int z, int nx,
+                                             int ny, int nz) {
+    const long long np = static_cast<long long>(nx) * ny;
+    double nb = 0.0;
+    if (x > 0) nb += v[i - 1];
+    if (x < nx - 1) nb += v[i + 1];
+    if (y > 0) nb += v[i - nx];
+    if (y < ny - 1) nb += v[i + nx];
+    if (z > 0) nb += v[i - np];
+    if (z < nz - 1) nb += v[i + np];
+    return 6.0 * v[i] - nb;
+}
+
+__device__ __forceinline__ void block_sum2(double &a, double &b) {
+    __shared__ double sh[2][kBThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][w] = a;
+        sh[1][w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0.0;
+        b = 0.0;
+        for (int k = 0; k < kBThreads / 32; ++k) {
+            a += sh[0][k];
+            b += sh[1][k];
+        }
+    }
+}
+
+// r = b - A x, f0 = (S) r, partial ||r||^2, ||b||^2   (mode 1: only systems whose active flag is 2)
+template <class S>
+__global__ void __launch_bounds__(kBThreads) kb_init(BKrylov k, int only_flagged) {
+    const int c = blockIdx.x;
+    const int s = k.ch_sys[c];
+    const BSys sy = k.sys[s];
+    double a0 = 0.0, a1 = 0.0;
+    if (!only_flagged || k.active[s] == 2) {
+        const long long g0 = k.ch_start[c];
+        const int len = k.ch_len[c];
+        const double *x = k.xptr[s];
+        const double *b = k.bptr[s];
+        S *f0 = static_cast<S *>(k.fstore) + sy.f0_off;
+        const int npi = sy.nx * sy.ny;
+        for (int t = threadIdx.x; t < len; t += kBThreads) {
+            const long long gi = g0 + t;
+            const int li = static_cast<int>(gi - sy.off);
+            const int z = li / npi, ip = li - z * npi, y = ip / sy.nx, xx = ip - y * sy.nx;
+            const double ri = b[li] - stencil_at(x, li, xx, y, z, sy.nx, sy.ny, sy.nz);
+            k.r[gi] = ri;
+            stv<S, double>(f0 + li, ri);
+            a0 = fma(ri, ri, a0);
+            a1 = fma(b[li], b[li], a1);
+        }
+    }
+    block_sum2(a0, a1);
+    if (threadIdx.x == 0) {
+        k.part[2 * c] = a0;
+        k.part[2 * c + 1] = a1;
+    }
+}
+
+__device__ __forceinline__ void sum_chunks(const BKrylov &k, int s, double &v0, double &v1) {
+    const BSys sy = k.sys[s];
+    double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
+    for (int c = sy.c0; c < sy.c1; ++c) {
+        const double a = k.part[2 * c], b = k.part[2 * c + 1];
+        double t = s0 + a, bp = t - s0;
+        c0 += (s0 - (t - bp)) + (a - bp);
+        s0 = t;
+        t = s1 + b;
+        bp = t - s1;
+        c1 += (s1 - (t - bp)) + (b - bp);
+        s1 = t;
+    }
+    v0 = s0 + c0;
+    v1 = s1 + c1;
+}
+
+// after kb_init: norms; mode 0 (start): every system active unless already converged;
+// mode 1 (after a true-residual check): systems flagged 2 continue (restart), others stop.
+__global__ void kb_fin_init(BKrylov k, int mode) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < k.nsys; s += blockDim.x) {
+        double rr, bb;
+        sum_chunks(k, s, rr, bb);
+        BScal &q = k.sc[s];
+        if (mode == 0) {
+            q = BScal{0, 0, 0, 0, rr, bb, 1, 0, 0, 0};
+            const double bref = bb > 0.0 ? bb : 1.0;
+            k.active[s] = (rr > k.tol2 * bref) ? 1 : 0;
+            if (!isfinite(rr) || !isfinite(bb)) {
+                q.status = SMG_ERR_NAN;
+                k.active[s] = 0;
+            }
+        } else {
+            if (k.active[s] == 2) {
+                q.rr = rr;
+                q.restart = 1;
+                k.active[s] = 1;
+            }
+        }
+        if (k.active[s] == 1) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *k.nactive = cnt;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kBThreads) kb_dots(BKrylov k) {
+    const int c = blockIdx.x;
+    const int s = k.ch_sys[c];
+    double a0 = 0.0, a1 = 0.0;
+    if (k.active[s] == 1) {
+        const BSys sy = k.sys[s];
+        const long long g0 = k.ch_start[c];
+        const int len = k.ch_len[c];
+        const S *u0 = static_cast<const S *>(k.ustore) + sy.u0_off;
+        const bool want = (k.variant == SMG_FPCG) && (k.sc[s].restart == 0);
+        for (int t = threadIdx.x; t < len; t += kBThreads) {
+            const long long gi = g0 + t;
+            const double si = ldv<double>(u0 + (gi - sy.off));
+            a0 = fma(si, k.r[gi], a0);
+            if (want) a1 = fma(si, k.dr[gi], a1);
+        }
+    }
+    block_sum2(a0, a1);
+    if (threadIdx.x == 0) {
+        k.part[2 * c] = a0;
+        k.part[2 * c + 1] = a1;
+    }
+}
+
+__global__ void kb_fin_beta(BKrylov k) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k.nsys; s += gridDim.x * blockDim.x) {
+        if (k.active[s] != 1) continue;
+        double rho, sdr;
+        sum_chunks(k, s, rho, sdr);
+        BScal &q = k.sc[s];
+        double beta = 0.0;
+        if (q.restart == 0 && k.variant != SMG_PSD) {
+            if (q.rho_prev == 0.0) q.status = SMG_ERR_BREAKDOWN;
+            else beta = (k.variant == SMG_PCG) ? rho / q.rho_prev : sdr / q.rho_prev;
+        }
+        if (!isfinite(rho) || !isfinite(beta)) q.status = SMG_ERR_NAN;
+        q.rho = rho;
+        q.beta = beta;
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(kBThreads) kb_upd_p(BKrylov k) {
+    const int c = blockIdx.x;
+    const int s = k.ch_sys[c];
+    if (k.active[s] != 1) return;
+    const BSys sy = k.sys[s];
+    const long long g0 = k.ch_start[c];
+    const int len = k.ch_len[c];
+    const S *u0 = static_cast<const S *>(k.ustore) + sy.u0_off;
+    const double beta = k.sc[s].beta;
+    for (int t = threadIdx.x; t < len; t += kBThreads) {
+        const long long gi = g0 + t;
+        const double si = ldv<double>(u0 + (gi - sy.off));
+        k.p[gi] = (beta == 0.0) ? si : fma(beta, k.p[gi], si);
+    }
+}
+
+__global__ void __launch_bounds__(kBThreads) kb_spmv(BKrylov k) {
+    const int c = blockIdx.x;
+    const int s = k.ch_sys[c];
+    double a0 = 0.0, a1 = 0.0;
+    if (k.active[s] == 1) {
+        const BSys sy = k.sys[s];
+        const long long g0 = k.ch_start[c];
+        const int len = k.ch_len[c];
+        const double *ps = k.p + sy.off;
+        const int npi = sy.nx * sy.ny;
+        for (int t = threadIdx.x; t < len; t += kBThreads) {
+            const long long gi = g0 + t;
+            const int li = static_cast<int>(gi - sy.off);
+            const int z = li / npi, ip = li - z * npi, y = ip / sy.nx, xx = ip - y * sy.nx;
+            const double qi = stencil_at(ps, li, xx, y, z, sy.nx, sy.ny, sy.nz);
+            k.q[gi] = qi;
+            a0 = fma(ps[li], qi, a0);
+        }
+    }
+    block_sum2(a0, a1);
+    if (threadIdx.x == 0) {
+        k.part[2 * c] = a0;
+        k.part[2 * c + 1] = 0.0;
+    }
+}
+
+__global__ void kb_fin_alpha(BKrylov k) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k.nsys; s += gridDim.x * blockDim.x) {
+        if (k.active[s] != 1) continue;
+        double pq, unused;
+        sum_chunks(k, s, pq, unused);
+        BScal &q = k.sc[s];
+        if (!(pq > 0.0)) {
+            q.status = (pq == pq) ? SMG_ERR_BREAKDOWN : SMG_ERR_NAN;
+            q.alpha = 0.0;
+        } else {
+            q.alpha = q.rho / pq;
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(kBThreads) kb_upd_xr(BKrylov k) {
+    const int c = blockIdx.x;
+    const int s = k.ch_sys[c];
+    double a0 = 0.0, a1 = 0.0;
+    if (k.active[s] == 1) {
+        const BSys sy = k.sys[s];
+        const long long g0 = k.ch_start[c];
+        const int len = k.ch_len[c];
+        const double alpha = k.sc[s].alpha;
+        const bool want_dr = (k.variant == SMG_FPCG);
+        double *x = k.xptr[s];
+        S *f0 = static_cast<S *>(k.fstore) + sy.f0_off;
+        for (int t = threadIdx.x; t < len; t += kBThreads) {
+            const long long gi = g0 + t;
+            const long long li = gi - sy.off;
+            x[li] = fma(alpha, k.p[gi], x[li]);
+            const double ro = k.r[gi];
+            const double rn = fma(-alpha, k.q[gi], ro);
+            if (want_dr) k.dr[gi] = rn - ro;
+            k.r[gi] = rn;
+            stv<S, double>(f0 + li, rn);
+            a0 = fma(rn, rn, a0);
+        }
+    }
+    block_sum2(a0, a1);
+    if (threadIdx.x == 0) {
+        k.part[2 * c] = a0;
+        k.part[2 * c + 1] = 0.0;
+    }
+}
+
+__global__ void kb_fin_rr(BKrylov k) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < k.nsys; s += blockDim.x) {
+        if (k.active[s] == 1) {
+            double rr, unused;
+            sum_chunks(k, s, rr, unused);
+            BScal &q = k.sc[s];
+            q.rr = rr;
+            q.rho_prev = q.rho;
+            q.restart = 0;
+            q.iters += 1;
+            const double bref = q.bb > 0.0 ? q.bb : 1.0;
+            if (!isfinite(rr)) q.status = SMG_ERR_NAN;
+            if (rr <= k.tol2 * bref || q.status != 0 || q.iters >= k.maxit) k.active[s] = 0;
+        }
+        if (k.active[s] == 1) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *k.nactive = cnt;
+}
+
+// After the loop: true residual norms (kb_init computes r = b - A x), flag systems to restart.
+__global__ void kb_fin_true(BKrylov k, double *relres, int *nflag) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < k.nsys; s += blockDim.x) {
+        double tt, bb;
+        sum_chunks(k, s, tt, bb);
+        const double bref = bb > 0.0 ? bb : 1.0;
+        relres[s] = sqrt(tt / bref);
+        BScal &q = k.sc[s];
+        if (q.status == 0 && tt > k.tol2 * bref && q.iters < k.maxit) {
+            k.active[s] = 2;  // continue from the true residual
+            atomicAdd(&cnt, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *nflag = cnt;
+}
+
+// ---- host side ------------------------------------------------------------------------------------
+thread_local std::string g_berr;
+
+#define BCHK(call)                                                                      \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_last_error(std::string("krylov_solve_batched: ") + #call + ": " +       \
+                           cudaGetErrorString(e_));                                     \
+            return SMG_ERR_CUDA;                                                        \
+        }                                                                               \
+    } while (0)
+
+int chunk_K(int nx) { return (nx + 31) / 32; }
+
+struct Tuned {
+    int threads = 512;
+    int order = 1;  // 1: tasks of a step in decreasing cost, 0: system order
+};
+std::mutex g_tune_mutex;
+std::map<std::vector<int>, Tuned> g_tune_cache;
+
+struct DevBuf {
+    std::vector<void *> ptrs;
+    ~DevBuf() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    cudaError_t alloc(T **p, size_t n) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = static_cast<T *>(q);
+        return e;
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_barrier_selftest(int blocks, int extra, long long spin_limit, unsigned *count, unsigned *gen,
+                                    int *err, cudaStream_t st) {
+    barrier_selftest_kernel<<<blocks, 32, 0, st>>>(static_cast<unsigned>(blocks + extra), spin_limit, count, gen, err);
+    return cudaGetLastError();
+}
+
+}  // namespace smg
+
+using namespace smg;
+
+namespace {
+
+struct SysPlan {
+    int nx, ny, nz;
+    long long N;
+    HostHierarchy H;
+    PlaneLayout lay, lay_d;
+    size_t zoff, poff;                 // offsets into the concatenated coefficient tables
+    std::vector<long long> foff;       // per level, offset into the storage arrays
+};
+
+// Estimated cost of relaxing one plane (for the longest-first ordering of a step's tasks).
+double plane_cost(const SysPlan &s) { return static_cast<double>(s.nx) * s.ny; }
+
+}  // namespace
+
+extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npost, int prec, const double *const *b,
+                                    double *const *x, double tol, int maxit, int *iters, void *stream) {
+    if (nsys < 1 || nsys > 4096) {
+        set_last_error("nsys must be in [1, 4096]");
+        return SMG_ERR_ARG;
+    }
+    if (!dims || !b || !x || !iters) {
+        set_last_error("null pointer");
+        return SMG_ERR_ARG;
+    }
+    if (npre < 1 || npost < 0 || !(tol > 0.0) || maxit < 0) {
+        set_last_error("npre >= 1, npost >= 0, tol > 0, maxit >= 0 required");
+        return SMG_ERR_ARG;
+    }
+    if (prec != SMG_FP32) {
+        set_last_error("krylov_solve_batched runs the FP32 cycle (SMG_FP32) only");
+        return SMG_ERR_ARG;
+    }
+    for (int s = 0; s < nsys; ++s) {
+        const int nx = dims[3 * s], ny = dims[3 * s + 1], nz = dims[3 * s + 2];
+        if (nx < 1 || ny < 1 || nz < 1 || nx > 128 || ny > kMaxNy || nz > kMaxNz) {
+            set_last_error("each system needs 1 <= nx <= 128, 1 <= ny <= 512, 1 <= nz <= 4096");
+            return SMG_ERR_ARG;
+        }
+        if (!b[s] || !x[s]) {
+            set_last_error("null vector pointer");
+            return SMG_ERR_ARG;
+        }
+        iters[s] = 0;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Prec P = static_cast<Prec>(prec);
+    const size_t sb = storage_bytes(P), cb = (P == Prec::F64) ? 8 : 4;
+    const int variant = SMG_FPCG;
+    constexpr size_t kBudget = 227 * 1024;
+
+    // ---- per-system hierarchies and layouts ----
+    std::vector<SysPlan> sys(nsys);
+    int K = 1, Lmax = 1;
+    size_t ztot = 0, ptot = 0;
+    long long stot = 0, vtot = 0;
+    for (int s = 0; s < nsys; ++s) {
+        SysPlan &p = sys[s];
+        p.nx = dims[3 * s];
+        p.ny = dims[3 * s + 1];
+        p.nz = dims[3 * s + 2];
+        p.N = static_cast<long long>(p.nx) * p.ny * p.nz;
+        build_hierarchy(p.nx, p.ny, p.nz, p.H);
+        K = std::max(K, chunk_K(p.nx));
+        Lmax = std::max(Lmax, p.H.L);
+        p.zoff = ztot;
+        p.poff = ptot;
+        ztot += p.H.zcoef.size();
+        ptot += p.H.pcoef.size();
+        p.foff.resize(p.H.L);
+        for (int l = 0; l < p.H.L; ++l) {
+            p.foff[l] = stot;
+            stot += static_cast<long long>(p.nx) * p.ny * p.H.nz_l[l];
+        }
+        vtot += p.N;
+    }
+    // all systems use the widest chunk K (narrower lines are padded with identity rows); the
+    // layouts size their factor sets for that K
+    for (auto &p : sys) {
+        p.lay = plan_plane_layout(p.H, cb, kBudget, K);
+        p.lay_d = plan_plane_layout(p.H, 8, kBudget, K);
+    }
+
+    DevBuf buf;
+    double *d_zc64, *d_pc64;
+    float *d_zc32, *d_pc32;
+    BCHK(buf.alloc(&d_zc64, ztot));
+    BCHK(buf.alloc(&d_pc64, ptot));
+    BCHK(buf.alloc(&d_zc32, ztot));
+    BCHK(buf.alloc(&d_pc32, ptot));
+    {
+        std::vector<double> z64(ztot), p64(ptot);
+        for (auto &p : sys) {
+            std::copy(p.H.zcoef.begin(), p.H.zcoef.end(), z64.begin() + p.zoff);
+            std::copy(p.H.pcoef.begin(), p.H.pcoef.end(), p64.begin() + p.poff);
+        }
+        std::vector<float> z32(z64.begin(), z64.end()), p32(p64.begin(), p64.end());
+        BCHK(cudaMemcpyAsync(d_zc64, z64.data(), ztot * 8, cudaMemcpyHostToDevice, st));
+        BCHK(cudaMemcpyAsync(d_pc64, p64.data(), ptot * 8, cudaMemcpyHostToDevice, st));
+        BCHK(cudaMemcpyAsync(d_zc32, z32.data(), ztot * 4, cudaMemcpyHostToDevice, st));
+        BCHK(cudaMemcpyAsync(d_pc32, p32.data(), ptot * 4, cudaMemcpyHostToDevice, st));
+        BCHK(cudaStreamSynchronize(st));
+    }
+    void *d_f = nullptr, *d_u = nullptr;
+    {
+        unsigned char *pf, *pu;
+        BCHK(buf.alloc(&pf, static_cast<size_t>(stot) * sb));
+        BCHK(buf.alloc(&pu, static_cast<size_t>(stot) * sb));
+        d_f = pf;
+        d_u = pu;
+    }
+    int dev = 0, nsm = 0;
+    BCHK(cudaGetDevice(&dev));
+    BCHK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+    // ---- tasks, steps ----
+    struct StepTasks {
+        std::vector<BTask> t;
+        std::vector<double> cost;
+    };
+    std::vector<PlaneRelaxArgs> relax;
+    std::vector<int> relax_f64;  // 1: the entry computes in FP64
+    std::vector<BTransfer> xfer;
+    std::map<std::vector<int>, int> relax_index;  // (s, l, colour, mode, f64) -> args index
+    size_t smem_max = 0;
+    long long ws_bytes = 0;
+    auto relax_arg = [&](int s, int l, int colour, int mode, bool f64, int iters_) -> int {
+        std::vector<int> key{s, l, colour, mode, f64 ? 1 : 0};
+        auto it = relax_index.find(key);
+        if (it != relax_index.end()) return it->second;
+        SysPlan &p = sys[s];
+        const PlaneLayout &lay = f64 ? p.lay_d : p.lay;
+        PlaneRelaxArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.nx = p.nx;
+        a.ny = p.ny;
+        a.nz = p.H.nz_l[l];
+        a.colour = colour;
+        a.mode = mode;
+        a.iters = iters_;
+        a.f = static_cast<unsigned char *>(d_f) + p.foff[l] * sb;
+        a.u = static_cast<unsigned char *>(d_u) + p.foff[l] * sb;
+        a.vstride = 0;
+        a.zcoef = d_zc64 + p.zoff + static_cast<size_t>(p.H.plane_base[l]) * kCoefPerPlane;
+        a.pcoef = d_pc64 + p.poff + static_cast<size_t>(p.H.plane_base[l]) * p.H.sum_ny * kCoefPerLine;
+        a.zcoef32 = d_zc32 + p.zoff + static_cast<size_t>(p.H.plane_base[l]) * kCoefPerPlane;
+        a.pcoef32 = d_pc32 + p.poff + static_cast<size_t>(p.H.plane_base[l]) * p.H.sum_ny * kCoefPerLine;
+        a.P = p.H.P;
+        a.sum_ny = p.H.sum_ny;
+        for (int m = 0; m < p.H.P; ++m) {
+            a.ny_m[m] = p.H.ny_m[m];
+            a.line_base[m] = p.H.line_base[m];
+            a.off_u[m] = lay.off_u[m];
+            a.off_g[m] = lay.off_g[m];
+        }
+        a.smem_u_mask = lay.smem_u_mask;
+        a.smem_g_mask = lay.smem_g_mask;
+        a.R = 1;
+        a.MF = lay.MF;
+        a.off_fs = lay.off_fs;
+        a.vec = 0;
+        const size_t elem = f64 ? 8 : cb;
+        smem_max = std::max(smem_max, lay.smem_bytes);
+        ws_bytes = std::max<long long>(ws_bytes, lay.ws_per_plane * static_cast<long long>(elem));
+        a.ws_per_plane = lay.ws_per_plane;  // elements; converted to a common byte stride below
+        relax.push_back(a);
+        relax_f64.push_back((f64 || P == Prec::F64) ? 1 : 0);
+        relax_index[key] = static_cast<int>(relax.size()) - 1;
+        return static_cast<int>(relax.size()) - 1;
+    };
+    auto xfer_arg = [&](int s, int l) -> int {
+        SysPlan &p = sys[s];
+        BTransfer t;
+        t.nx = p.nx;
+        t.ny = p.ny;
+        t.nzf = p.H.nz_l[l];
+        t.f = static_cast<unsigned char *>(d_f) + p.foff[l] * sb;
+        t.u = static_cast<unsigned char *>(d_u) + p.foff[l] * sb;
+        t.fc = static_cast<unsigned char *>(d_f) + p.foff[l + 1] * sb;
+        t.uc = static_cast<unsigned char *>(d_u) + p.foff[l + 1] * sb;
+        t.zc64 = d_zc64 + p.zoff + static_cast<size_t>(p.H.plane_base[l]) * kCoefPerPlane;
+        t.zc32 = d_zc32 + p.zoff + static_cast<size_t>(p.H.plane_base[l]) * kCoefPerPlane;
+        xfer.push_back(t);
+        return static_cast<int>(xfer.size()) - 1;
+    };
+    std::vector<StepTasks> steps;
+    auto add_relax_step = [&](int l, int colour, int mode_first, int sweep, bool with_coarsest) {
+        StepTasks st_;
+        for (int s = 0; s < nsys; ++s) {
+            SysPlan &p = sys[s];
+            if (l < p.H.L - 1) {
+                const int nzl = p.H.nz_l[l];
+                const int nplanes = colour == 0 ? (nzl + 1) / 2 : nzl / 2;
+                const int mode = sweep == 0 ? mode_first : 2;
+                const bool f64c = (P == Prec::F64);
+                const int ai = relax_arg(s, l, colour, mode, f64c, 1);
+                for (int i = 0; i < nplanes; ++i) {
+                    st_.t.push_back(BTask{TASK_RELAX, ai, i, s});
+                    st_.cost.push_back(plane_cost(p));
+                }
+            } else if (with_coarsest && l == p.H.L - 1) {
+                const int ai = relax_arg(s, l, 0, 0, true, 1);
+                st_.t.push_back(BTask{TASK_RELAX_F64, ai, 0, s});
+                st_.cost.push_back(8.0 * plane_cost(p));  // FP64 plane cycle
+            }
+        }
+        steps.push_back(st_);
+    };
+    for (int l = 0; l < Lmax; ++l) {
+        for (int sw = 0; sw < npre; ++sw) {
+            add_relax_step(l, 0, 0, sw, sw == 0);
+            add_relax_step(l, 1, 1, sw, false);
+        }
+        StepTasks sx;
+        for (int s = 0; s < nsys; ++s) {
+            SysPlan &p = sys[s];
+            if (l < p.H.L - 1) {
+                const int xi = xfer_arg(s, l);
+                for (int j = 0; j < p.H.nz_l[l + 1]; ++j) {
+                    sx.t.push_back(BTask{TASK_RESTRICT, xi, j, s});
+                    sx.cost.push_back(0.1 * plane_cost(p));
+                }
+            }
+        }
+        if (!sx.t.empty()) steps.push_back(sx);
+    }
+    for (int l = Lmax - 2; l >= 0; --l) {
+        StepTasks sp;
+        for (int s = 0; s < nsys; ++s) {
+            SysPlan &p = sys[s];
+            if (l < p.H.L - 1) {
+                const int xi = xfer_arg(s, l);
+                for (int z = 0; z < p.H.nz_l[l]; ++z) {
+                    sp.t.push_back(BTask{TASK_PROLONG, xi, z, s});
+                    sp.cost.push_back(0.05 * plane_cost(p));
+                }
+            }
+        }
+        if (!sp.t.empty()) steps.push_back(sp);
+        for (int sw = 0; sw < npost; ++sw) {
+            add_relax_step(l, 1, 2, 1, false);
+            add_relax_step(l, 0, 2, 1, false);
+        }
+    }
+    // drop empty steps
+    steps.erase(std::remove_if(steps.begin(), steps.end(), [](const StepTasks &x) { return x.t.empty(); }),
+                steps.end());
+    // common workspace stride in bytes for every task; one slot per persistent CTA
+    const long long ws_stride = (ws_bytes + 255) / 256 * 256;
+    for (size_t i = 0; i < relax.size(); ++i)
+        relax[i].ws_per_plane = ws_stride / (relax_f64[i] ? 8 : static_cast<long long>(cb));
+
+    // ---- autotuned schedule: threads per CTA and task order within a step ----
+    std::vector<int> key{nsys, prec, npre, npost};
+    for (int s = 0; s < 3 * nsys; ++s) key.push_back(dims[s]);
+    Tuned tune;
+    bool tuned = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            tune = it->second;
+            tuned = true;
+        }
+    }
+    const size_t smem = std::max<size_t>(smem_max, 1024);
+    if (set_persistent_smem(P, K, smem) != 0) {
+        set_last_error("krylov_solve_batched: shared-memory configuration failed");
+        return SMG_ERR_CUDA;
+    }
+
+    // ---- device buffers for the persistent kernel and the Krylov kernels ----
+    PlaneRelaxArgs *d_relax;
+    BTransfer *d_xfer;
+    BTask *d_tasks;
+    int *d_step_begin, *d_active, *d_nactive, *d_err, *d_nflag;
+    unsigned *d_bar;
+    unsigned char *d_ws;
+    BCHK(buf.alloc(&d_relax, relax.size()));
+    BCHK(buf.alloc(&d_xfer, xfer.size()));
+    BCHK(buf.alloc(&d_active, nsys));
+    BCHK(buf.alloc(&d_nactive, 1));
+    BCHK(buf.alloc(&d_nflag, 1));
+    BCHK(buf.alloc(&d_err, 1));
+    BCHK(buf.alloc(&d_bar, 2));
+    BCHK(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), st));
+    BCHK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    size_t ntasks = 0;
+    for (auto &s_ : steps) ntasks += s_.t.size();
+    BCHK(buf.alloc(&d_tasks, ntasks));
+    BCHK(buf.alloc(&d_step_begin, steps.size() + 1));
+    auto upload_tasks = [&](int order) -> int {
+        std::vector<BTask> all;
+        std::vector<int> begin{0};
+        for (auto &s_ : steps) {
+            std::vector<int> idx(s_.t.size());
+            std::iota(idx.begin(), idx.end(), 0);
+            if (order == 1)
+                std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return s_.cost[a] > s_.cost[c]; });
+            for (int i : idx) all.push_back(s_.t[i]);
+            begin.push_back(static_cast<int>(all.size()));
+        }
+        BCHK(cudaMemcpyAsync(d_tasks, all.data(), all.size() * sizeof(BTask), cudaMemcpyHostToDevice, st));
+        BCHK(cudaMemcpyAsync(d_step_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        BCHK(cudaStreamSynchronize(st));
+        return SMG_OK;
+    };
+    // workspace: one slot per CTA of the largest persistent grid any candidate schedule uses
+    int max_blocks = 0;
+    for (int threads : {256, 512}) max_blocks = std::max(max_blocks, nsm * persistent_blocks_per_sm(P, K, threads, smem));
+    if (max_blocks < 1) {
+        set_last_error("krylov_solve_batched: the persistent kernel does not fit on an SM");
+        return SMG_ERR_CUDA;
+    }
+    BCHK(buf.alloc(&d_ws, static_cast<size_t>(std::max<long long>(ws_stride, 256)) * max_blocks));
+    for (auto &a : relax) a.gws = d_ws;
+    BCHK(cudaMemcpyAsync(d_relax, relax.data(), relax.size() * sizeof(PlaneRelaxArgs), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(d_xfer, xfer.data(), xfer.size() * sizeof(BTransfer), cudaMemcpyHostToDevice, st));
+
+    // Krylov data
+    std::vector<BSys> hsys(nsys);
+    std::vector<int> ch_sys;
+    std::vector<long long> ch_start;
+    std::vector<int> ch_len;
+    {
+        long long off = 0;
+        for (int s = 0; s < nsys; ++s) {
+            BSys &q = hsys[s];
+            q.nx = sys[s].nx;
+            q.ny = sys[s].ny;
+            q.nz = sys[s].nz;
+            q.off = off;
+            q.f0_off = sys[s].foff[0];
+            q.u0_off = sys[s].foff[0];
+            q.c0 = static_cast<int>(ch_sys.size());
+            for (long long c = 0; c < sys[s].N; c += kChunk) {
+                ch_sys.push_back(s);
+                ch_start.push_back(off + c);
+                ch_len.push_back(static_cast<int>(std::min<long long>(kChunk, sys[s].N - c)));
+            }
+            q.c1 = static_cast<int>(ch_sys.size());
+            off += sys[s].N;
+        }
+    }
+    const int nch = static_cast<int>(ch_sys.size());
+    BSys *d_sys;
+    int *d_ch_sys, *d_ch_len;
+    long long *d_ch_start;
+    double *d_r, *d_p, *d_q, *d_dr, *d_part, *d_relres;
+    BScal *d_sc;
+    double **d_bptr, **d_xptr;
+    BCHK(buf.alloc(&d_sys, nsys));
+    BCHK(buf.alloc(&d_ch_sys, nch));
+    BCHK(buf.alloc(&d_ch_len, nch));
+    BCHK(buf.alloc(&d_ch_start, nch));
+    BCHK(buf.alloc(&d_r, vtot));
+    BCHK(buf.alloc(&d_p, vtot));
+    BCHK(buf.alloc(&d_q, vtot));
+    BCHK(buf.alloc(&d_dr, vtot));
+    BCHK(buf.alloc(&d_part, 2 * static_cast<size_t>(nch)));
+    BCHK(buf.alloc(&d_relres, nsys));
+    BCHK(buf.alloc(&d_sc, nsys));
+    BCHK(buf.alloc(&d_bptr, nsys));
+    BCHK(buf.alloc(&d_xptr, nsys));
+    BCHK(cudaMemcpyAsync(d_sys, hsys.data(), nsys * sizeof(BSys), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(d_ch_sys, ch_sys.data(), nch * sizeof(int), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(d_ch_len, ch_len.data(), nch * sizeof(int), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(d_ch_start, ch_start.data(), nch * sizeof(long long), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(d_bptr, b, nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(d_xptr, x, nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemsetAsync(d_dr, 0, vtot * sizeof(double), st));
+    BCHK(cudaMemsetAsync(d_p, 0, vtot * sizeof(double), st));
+
+    BKrylov kk;
+    kk.sys = d_sys;
+    kk.ch_sys = d_ch_sys;
+    kk.ch_start = d_ch_start;
+    kk.ch_len = d_ch_len;
+    kk.r = d_r;
+    kk.p = d_p;
+    kk.q = d_q;
+    kk.dr = d_dr;
+    kk.bptr = d_bptr;
+    kk.xptr = d_xptr;
+    kk.fstore = d_f;
+    kk.ustore = d_u;
+    kk.part = d_part;
+    kk.sc = d_sc;
+    kk.active = d_active;
+    kk.nactive = d_nactive;
+    kk.nsys = nsys;
+    kk.variant = variant;
+    kk.maxit = maxit;
+    kk.tol2 = tol * tol;
+
+    int *h_pinned = nullptr;
+    BCHK(cudaMallocHost(&h_pinned, 2 * sizeof(int)));
+    struct PinFree {
+        int *p;
+        ~PinFree() { cudaFreeHost(p); }
+    } pinfree{h_pinned};
+
+    PersistArgs pa;
+    pa.relax = d_relax;
+    pa.xfer = d_xfer;
+    pa.tasks = d_tasks;
+    pa.step_begin = d_step_begin;
+    pa.nsteps = static_cast<int>(steps.size());
+    pa.active = d_active;
+    pa.bar_count = d_bar;
+    pa.bar_gen = d_bar + 1;
+    pa.err = d_err;
+    pa.spin_limit = 10000000;  // about a second of polling
+    int result = SMG_OK;
+
+    auto launch_vcycle = [&](int threads, int blocks) -> cudaError_t {
+        pa.expected_blocks = blocks;
+        return launch_persistent_vcycle(P, K, blocks, threads, smem, pa, st, false);
+    };
+    auto krylov_tail = [&]() -> cudaError_t {
+        switch (P) {
+        case Prec::F64: kb_dots<double><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::F32: kb_dots<float><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::BF16: kb_dots<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
+        }
+        kb_fin_beta<<<(nsys + 127) / 128, 128, 0, st>>>(kk);
+        switch (P) {
+        case Prec::F64: kb_upd_p<double><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::F32: kb_upd_p<float><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::BF16: kb_upd_p<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
+        }
+        kb_spmv<<<nch, kBThreads, 0, st>>>(kk);
+        kb_fin_alpha<<<(nsys + 127) / 128, 128, 0, st>>>(kk);
+        switch (P) {
+        case Prec::F64: kb_upd_xr<double><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::F32: kb_upd_xr<float><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::BF16: kb_upd_xr<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
+        }
+        kb_fin_rr<<<1, 1024, 0, st>>>(kk);
+        return cudaGetLastError();
+    };
+    auto init = [&](int mode) -> cudaError_t {
+        switch (P) {
+        case Prec::F64: kb_init<double><<<nch, kBThreads, 0, st>>>(kk, mode); break;
+        case Prec::F32: kb_init<float><<<nch, kBThreads, 0, st>>>(kk, mode); break;
+        case Prec::BF16: kb_init<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk, mode); break;
+        }
+        kb_fin_init<<<1, 1024, 0, st>>>(kk, mode);
+        return cudaGetLastError();
+    };
+
+    // autotune on the first iteration's input (active = all): time the V-cycle per candidate
+    BCHK(init(0));
+    if (!tuned) {
+        float best = 1e30f;
+        cudaEvent_t e0, e1;
+        BCHK(cudaEventCreate(&e0));
+        BCHK(cudaEventCreate(&e1));
+        for (int threads : {256, 512}) {
+            const int bps = persistent_blocks_per_sm(P, K, threads, smem);
+            if (bps < 1) continue;
+            const int blocks = nsm * bps;
+            for (int order : {0, 1}) {
+                if (upload_tasks(order) != SMG_OK) return SMG_ERR_CUDA;
+                BCHK(launch_vcycle(threads, blocks));  // warm-up
+                BCHK(cudaEventRecord(e0, st));
+                BCHK(launch_vcycle(threads, blocks));
+                BCHK(cudaEventRecord(e1, st));
+                BCHK(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                BCHK(cudaEventElapsedTime(&ms, e0, e1));
+                int herr = 0;
+                BCHK(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+                if (herr != 0) {
+                    set_last_error("krylov_solve_batched: a V-cycle barrier wait timed out");
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return herr;
+                }
+                if (ms < best) {
+                    best = ms;
+                    tune.threads = threads;
+                    tune.order = order;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = tune;
+    }
+    if (upload_tasks(tune.order) != SMG_OK) return SMG_ERR_CUDA;
+    const int bps = std::max(1, persistent_blocks_per_sm(P, K, tune.threads, smem));
+    const int blocks = std::min(max_blocks, nsm * bps);
+    // the tuning runs left the level vectors changed: start every system again from its x0
+    BCHK(init(0));
+
+    // ---- capture one iteration into a CUDA graph ----
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    BCHK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } sguard{cs};
+    BCHK(cudaStreamSynchronize(st));
+    {
+        const cudaStream_t saved = st;
+        st = cs;
+        BCHK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_vcycle(tune.threads, blocks);
+        if (e == cudaSuccess) e = krylov_tail();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_pinned, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        st = saved;
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            set_last_error(std::string("krylov_solve_batched: graph capture: ") +
+                           cudaGetErrorString(e != cudaSuccess ? e : e2));
+            return SMG_ERR_CUDA;
+        }
+        BCHK(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    struct GraphGuard {
+        cudaGraph_t g;
+        cudaGraphExec_t x;
+        ~GraphGuard() {
+            if (x) cudaGraphExecDestroy(x);
+            if (g) cudaGraphDestroy(g);
+        }
+    } gguard{graph, exec};
+
+    // ---- iterate ----
+    BCHK(cudaMemcpyAsync(h_pinned, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BCHK(cudaStreamSynchronize(st));
+    int nact = h_pinned[0];
+    for (int round = 0; round < 8; ++round) {
+        for (int it = 0; it < maxit && nact > 0; ++it) {
+            BCHK(cudaGraphLaunch(exec, st));
+            BCHK(cudaStreamSynchronize(st));
+            nact = h_pinned[0];
+            int herr = 0;
+            BCHK(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (herr != 0) {
+                set_last_error("krylov_solve_batched: a V-cycle barrier wait timed out");
+                return herr;
+            }
+        }
+        // true residuals; systems that fail continue from them
+        switch (P) {
+        case Prec::F64: kb_init<double><<<nch, kBThreads, 0, st>>>(kk, 0); break;
+        case Prec::F32: kb_init<float><<<nch, kBThreads, 0, st>>>(kk, 0); break;
+        case Prec::BF16: kb_init<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk, 0); break;
+        }
+        kb_fin_true<<<1, 1024, 0, st>>>(kk, d_relres, d_nflag);
+        BCHK(cudaMemcpyAsync(h_pinned + 1, d_nflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BCHK(cudaStreamSynchronize(st));
+        if (h_pinned[1] == 0) break;
+        kb_fin_init<<<1, 1024, 0, st>>>(kk, 1);
+        BCHK(cudaMemcpyAsync(h_pinned, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BCHK(cudaStreamSynchronize(st));
+        nact = h_pinned[0];
+    }
+    std::vector<BScal> hs(nsys);
+    std::vector<double> rel(nsys);
+    BCHK(cudaMemcpy(hs.data(), d_sc, nsys * sizeof(BScal), cudaMemcpyDeviceToHost));
+    BCHK(cudaMemcpy(rel.data(), d_relres, nsys * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int s = 0; s < nsys; ++s) {
+        iters[s] = hs[s].iters;
+        if (hs[s].status != 0 && result == SMG_OK) result = hs[s].status;
+        if (result == SMG_OK && !(rel[s] <= tol)) result = SMG_ERR_NOCONV;
+    }
+    if (result == SMG_ERR_NOCONV) set_last_error("krylov_solve_batched: a system did not converge within maxit");
+    else if (result != SMG_OK) set_last_error("krylov_solve_batched: breakdown or NaN in a system");
+    return result;
+}
+
+extern "C" int smg_barrier_selftest(int extra_blocks, double limit_seconds, int *status, void *stream) {
+    if (!status || extra_blocks < 0 || !(limit_seconds > 0.0) || limit_seconds > 10.0) {
+        set_last_error("status must be non-null, extra_blocks >= 0, 0 < limit_seconds <= 10");
+        return SMG_ERR_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 4 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+        set_last_error(std::string("smg_barrier_selftest: ") + cudaGetErrorString(e));
+        return SMG_ERR_CUDA;
+    }
+    cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), st);
+    // one poll takes at least the 100 ns sleep: the limit is a lower bound on the wait
+    const long long spins = static_cast<long long>(limit_seconds * 1e7);
+    e = launch_barrier_selftest(4, extra_blocks, spins, d, d + 1, reinterpret_cast<int *>(d + 2), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status, d + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("smg_barrier_selftest: ") + cudaGetErrorString(e));
+        return SMG_ERR_CUDA;
+    }
+    return SMG_OK;
+}

@@ -11,6 +11,7 @@
 // Both are bandwidth-bound stencils; one thread per output point, x fastest (coalesced), the
 // 15-point residual reads its five planes through L1/L2.
 #include "plane_relax.cuh"
+#include "transfer.cuh"
 
 namespace smg {
 
@@ -73,35 +74,12 @@ template <class S, class C>
 __global__ void restrict_kernel(int nx, int ny, int nzf, int nzc, long long total, const S *__restrict__ f,
                                 const S *__restrict__ u, S *__restrict__ fc, const double *__restrict__ zcoef64,
                                 const float *__restrict__ zcoef32, long long vsf, long long vsc) {
-    const C *zcoef = coef_table<C>(zcoef64, zcoef32);
-    // blockIdx.y: one coarse plane of one batch entry; x-y plane covered by the x-dimension
-    const int ip32 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int npi = nx * ny;
-    if (ip32 >= npi) return;
-    const long long np = npi;
-    const int y = ip32 / nx, x = ip32 - y * nx;
-    const int j = blockIdx.y;
+    // blockIdx.y: one coarse plane, blockIdx.z: one batch entry; x covers the plane
+    const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= nx * ny) return;
     const int b = blockIdx.z;
-    const S *fb = f + b * vsf;
-    const S *ub = u + b * vsf;
-    const long long ip = ip32;
-    C acc = C(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int zf = 2 * j + k;
-        if (zf >= nzf) break;
-        const C *zc = zcoef + static_cast<long long>(zf) * kCoefPerPlane;
-        const C w = (k == 1) ? C(1) : (k == 0 ? zc[7] : zc[6]);
-        C r = ldv<C>(fb + zf * np + ip);
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int zz = zf + dz;
-            if (zz < 0 || zz >= nzf) continue;
-            r -= plane_term<C>(ub + zz * np, x, y, nx, ny, zc[1 + dz], zc[4 + dz]);
-        }
-        acc += w * r;
-    }
-    stv<S, C>(fc + b * vsc + j * np + ip, acc);
+    restrict_point<S, C>(nx, ny, nzf, f + b * vsf, u + b * vsf, fc + b * vsc, coef_table<C>(zcoef64, zcoef32),
+                         blockIdx.y, ip);
 }
 
 // ---- prolongation + correction ----------------------------------------------------------------
@@ -109,27 +87,10 @@ template <class S, class C>
 __global__ void prolong_kernel(int nx, int ny, int nzf, int nzc, long long total, S *__restrict__ u,
                                const S *__restrict__ uc, const double *__restrict__ zcoef64,
                                const float *__restrict__ zcoef32, long long vsf, long long vsc) {
-    const C *zcoef = coef_table<C>(zcoef64, zcoef32);
-    const int ip32 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int npi = nx * ny;
-    if (ip32 >= npi) return;
-    const long long np = npi;
-    const long long ip = ip32;
-    const int z = blockIdx.y;
+    const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= nx * ny) return;
     const int b = blockIdx.z;
-    const S *cb = uc + b * vsc;
-    C e;
-    if (z & 1) {
-        e = ldv<C>(cb + static_cast<long long>((z - 1) / 2) * np + ip);
-    } else {
-        const C *zc = zcoef + static_cast<long long>(z) * kCoefPerPlane;
-        e = C(0);
-        const int jl = z / 2 - 1, jh = z / 2;
-        if (jl >= 0) e += zc[6] * ldv<C>(cb + static_cast<long long>(jl) * np + ip);
-        if (jh < nzc) e += zc[7] * ldv<C>(cb + static_cast<long long>(jh) * np + ip);
-    }
-    S *p = u + b * vsf + static_cast<long long>(z) * np + ip;
-    stv<S, C>(p, ldv<C>(p) + e);
+    prolong_point<S, C>(nx, ny, nzf, u + b * vsf, uc + b * vsc, coef_table<C>(zcoef64, zcoef32), blockIdx.y, ip);
 }
 
 static inline unsigned nblocks(long long total, int threads) {

@@ -221,9 +221,9 @@ static int chunk_K(int nx) {
 // few lines) and finally the finest; u_m before g_m at each level (the iterate is touched more
 // often).  What does not fit in `smem_budget` goes to a global slot per CTA (L2-resident for
 // the sizes of interest).
-PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget) {
+PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int K) {
     PlaneLayout P;
-    P.K = chunk_K(H.nx);
+    P.K = K > 0 ? K : chunk_K(H.nx);
     auto align4 = [](size_t v) { return (v + 3) & ~static_cast<size_t>(3); };
     size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
     P.MF = factor_levels(H, P.K, elem_bytes, smem_budget);

@@ -308,6 +308,7 @@ struct PlaneCtx {
     int R, rank; // cluster size and this CTA's rank in it (1, 0 without a cluster)
     C *fs;       // shared-memory factor sets of the interior line matrix of 2D levels 0..MF-1
     int MF;
+    bool vec;    // nx == 32 K and every array 16-byte aligned: lanes move their K values as vectors
 };
 
 template <class C>
@@ -352,9 +353,54 @@ __device__ __forceinline__ int owned_line(const PlaneCtx<C> &c, int t) {
     return 2 * (c.rank + c.R * (t >> 1)) + (t & 1);
 }
 
+// Vector access to a lane's K consecutive values: 16-byte chunks when K*sizeof(T) allows,
+// else 8-byte chunks, else none (scalar).
+template <class T, int K>
+constexpr int vec_chunk() {
+    return ((K * sizeof(T)) % 16 == 0) ? 16 : (((K * sizeof(T)) % 8 == 0) ? 8 : 0);
+}
+template <int B> struct ChunkT;
+template <> struct ChunkT<16> { using type = uint4; };
+template <> struct ChunkT<8> { using type = uint2; };
+
+template <class T, int K>
+__device__ __forceinline__ void vload(T (&v)[K], const T *p) {
+    constexpr int CB = vec_chunk<T, K>();
+    using CT = typename ChunkT<CB>::type;
+    constexpr int PER = CB / sizeof(T);
+    union U { CT c; T t[PER]; };
+#pragma unroll
+    for (int q = 0; q < K / PER; ++q) {
+        U u;
+        u.c = reinterpret_cast<const CT *>(p)[q];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) v[q * PER + j] = u.t[j];
+    }
+}
+template <class T, int K>
+__device__ __forceinline__ void vstore(T *p, const T (&v)[K]) {
+    constexpr int CB = vec_chunk<T, K>();
+    using CT = typename ChunkT<CB>::type;
+    constexpr int PER = CB / sizeof(T);
+    union U { CT c; T t[PER]; };
+#pragma unroll
+    for (int q = 0; q < K / PER; ++q) {
+        U u;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) u.t[j] = v[q * PER + j];
+        reinterpret_cast<CT *>(p)[q] = u.c;
+    }
+}
+
 // Load a line (K registers per lane, 0 beyond nx).
 template <class C, int K>
-__device__ __forceinline__ void load_line(C (&v)[K], const C *line, int nx, int lane) {
+__device__ __forceinline__ void load_line(C (&v)[K], const C *line, int nx, bool vec, int lane) {
+    if constexpr (vec_chunk<C, K>() != 0) {
+        if (vec) {
+            vload<C, K>(v, line + lane * K);
+            return;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int x = lane * K + j;
@@ -362,7 +408,13 @@ __device__ __forceinline__ void load_line(C (&v)[K], const C *line, int nx, int 
     }
 }
 template <class C, int K>
-__device__ __forceinline__ void store_line(C *line, const C (&v)[K], int nx, int lane) {
+__device__ __forceinline__ void store_line(C *line, const C (&v)[K], int nx, bool vec, int lane) {
+    if constexpr (vec_chunk<C, K>() != 0) {
+        if (vec) {
+            vstore<C, K>(line + lane * K, v);
+            return;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int x = lane * K + j;
@@ -370,18 +422,36 @@ __device__ __forceinline__ void store_line(C *line, const C (&v)[K], int nx, int
     }
 }
 
-// d -= sc * Lx v + tc * v  for one neighbouring line v (x-halo through shuffles).
+// One row of the plane's coefficient table: couplings to lines y-1, y, y+1 and the weights.
+template <class C>
+struct CoefRow {
+    C s[3], t[3], wm, wp;
+};
+template <class C>
+__device__ __forceinline__ CoefRow<C> coef_row(const C *row) {
+    CoefRow<C> r;
+    C v[8];
+    vload<C, 8>(v, row);
+    r.s[0] = v[0]; r.s[1] = v[1]; r.s[2] = v[2];
+    r.t[0] = v[3]; r.t[1] = v[4]; r.t[2] = v[5];
+    r.wm = v[6]; r.wp = v[7];
+    return r;
+}
+
+// d -= sc * Lx v + tc * v  for one neighbouring line v (x-halo through shuffles), written as
+// d += sc (v_{x-1} + v_{x+1}) - (2 sc + tc) v.
 template <class C, int K>
 __device__ __forceinline__ void sub_coupling(C (&d)[K], const C (&v)[K], C sc, C tc, int lane) {
     C vl = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
     C vr = __shfl_down_sync(0xffffffffu, v[0], 1);
     if (lane == 0) vl = C(0);
     if (lane == 31) vr = C(0);
+    const C ac = C(2) * sc + tc;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const C left = (j == 0) ? vl : v[j - 1];
         const C right = (j == K - 1) ? vr : v[j + 1];
-        d[j] -= sc * (C(2) * v[j] - left - right) + tc * v[j];
+        d[j] = fma(sc, left + right, fma(-ac, v[j], d[j]));
     }
 }
 
@@ -414,41 +484,46 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
     const int nx = c.nx, nym = a.ny_m[m];
     C d[NL][K];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) load_line<C, K>(d[l], line_g<C, CL>(a, c, m, ys[l]), nx, lane);
+    CoefRow<C> cr[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        cr[l] = coef_row<C>(c.sm + (a.line_base[m] + ys[l]) * kCoefPerLine);
+        load_line<C, K>(d[l], line_g<C, CL>(a, c, m, ys[l]), nx, c.vec, lane);
+    }
     if constexpr (NBMODE != NB_NONE) {
         const int nyc = (NBMODE == NB_CORR) ? a.ny_m[m + 1] : 0;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             const int y = ys[l];
-            const C *lc = c.sm + (a.line_base[m] + y) * kCoefPerLine;
 #pragma unroll
             for (int s = -1; s <= 1; s += 2) {
                 const int yy = y + s;
                 if (yy < 0 || yy >= nym) continue;
                 C v[K];
-                load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, lane);
+                load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, c.vec, lane);
                 if constexpr (NBMODE == NB_CORR) {  // neighbour yy is an even line: add P e from level m+1
-                    const C *lcy = c.sm + (a.line_base[m] + yy) * kCoefPerLine;
+                    const CoefRow<C> cy = coef_row<C>(c.sm + (a.line_base[m] + yy) * kCoefPerLine);
                     const int jl = yy / 2 - 1, jh = yy / 2;
-                    const C wm = lcy[6], wp = lcy[7];
                     if (jl >= 0) {
                         C e[K];
-                        load_line<C, K>(e, line_u<C, CL>(a, c, m + 1, jl), nx, lane);
+                        load_line<C, K>(e, line_u<C, CL>(a, c, m + 1, jl), nx, c.vec, lane);
 #pragma unroll
-                        for (int j = 0; j < K; ++j) v[j] += wm * e[j];
+                        for (int j = 0; j < K; ++j) v[j] = fma(cy.wm, e[j], v[j]);
                     }
                     if (jh < nyc) {
                         C e[K];
-                        load_line<C, K>(e, line_u<C, CL>(a, c, m + 1, jh), nx, lane);
+                        load_line<C, K>(e, line_u<C, CL>(a, c, m + 1, jh), nx, c.vec, lane);
 #pragma unroll
-                        for (int j = 0; j < K; ++j) v[j] += wp * e[j];
+                        for (int j = 0; j < K; ++j) v[j] = fma(cy.wp, e[j], v[j]);
                     }
                 }
-                sub_coupling<C, K>(d[l], v, lc[1 + s], lc[4 + s], lane);
+                sub_coupling<C, K>(d[l], v, cr[l].s[1 + s], cr[l].t[1 + s], lane);
             }
+            if (!c.vec) {
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (lane * K + j >= nx) d[l][j] = C(0);
+                for (int j = 0; j < K; ++j)
+                    if (lane * K + j >= nx) d[l][j] = C(0);
+            }
         }
     }
     // the line matrices: S(y,y) Lx + T(y,y) I  ->  diagonal 2S + T, off-diagonal -S
@@ -456,9 +531,8 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
     bool same = true;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        const C *lc = c.sm + (a.line_base[m] + ys[l]) * kCoefPerLine;
-        dg[l] = C(2) * lc[1] + lc[4];
-        of[l] = -lc[1];
+        dg[l] = C(2) * cr[l].s[1] + cr[l].t[1];
+        of[l] = -cr[l].s[1];
         same = same && dg[l] == dg[0] && of[l] == of[0];
     }
     if (same) {
@@ -479,15 +553,33 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         const int y = ys[l];
-        if constexpr (OUT != OUT_PLANE) store_line<C, K>(line_u<C, CL>(a, c, m, y), d[l], nx, lane);
+        if constexpr (OUT != OUT_PLANE) store_line<C, K>(line_u<C, CL>(a, c, m, y), d[l], nx, c.vec, lane);
         if constexpr (OUT != OUT_U) {
             S *p = plane + y * nx;
+            bool done = false;
+            if constexpr (vec_chunk<S, K>() != 0) {
+                if (c.vec) {
+                    S sv[K];
+                    if (accumulate) {
+                        vload<S, K>(sv, p + lane * K);
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const int x = lane * K + j;
-                if (x < nx) {
-                    const C v = accumulate ? ldv<C>(p + x) + d[l][j] : d[l][j];
-                    stv<S, C>(p + x, v);
+                        for (int j = 0; j < K; ++j) stv<S, C>(&sv[j], ldv<C>(&sv[j]) + d[l][j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < K; ++j) stv<S, C>(&sv[j], d[l][j]);
+                    }
+                    vstore<S, K>(p + lane * K, sv);
+                    done = true;
+                }
+            }
+            if (!done) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const int x = lane * K + j;
+                    if (x < nx) {
+                        const C v = accumulate ? ldv<C>(p + x) + d[l][j] : d[l][j];
+                        stv<S, C>(p + x, v);
+                    }
                 }
             }
         }
@@ -556,20 +648,20 @@ __device__ __forceinline__ void restrict_group(const PlaneRelaxArgs &a, const Pl
         for (int k = 0; k < 2; ++k) {
             const int e = 2 * js[l] + 2 * k;
             if (e >= nym) continue;
-            const C *lc = c.sm + (a.line_base[m] + e) * kCoefPerLine;
-            const C w = (k == 0) ? lc[7] : lc[6];
+            const CoefRow<C> ce = coef_row<C>(c.sm + (a.line_base[m] + e) * kCoefPerLine);
+            const C w = (k == 0) ? ce.wp : ce.wm;
 #pragma unroll
             for (int s = -1; s <= 1; s += 2) {
                 const int yy = e + s;
                 if (yy < 0 || yy >= nym) continue;
                 C v[K];
-                load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, lane);
-                sub_coupling<C, K>(acc[l], v, w * lc[1 + s], w * lc[4 + s], lane);
+                load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, c.vec, lane);
+                sub_coupling<C, K>(acc[l], v, w * ce.s[1 + s], w * ce.t[1 + s], lane);
             }
         }
     }
 #pragma unroll
-    for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, m + 1, js[l]), acc[l], nx, lane);
+    for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, m + 1, js[l]), acc[l], nx, c.vec, lane);
 }
 
 template <class C, int K, bool CL>
@@ -600,7 +692,16 @@ __device__ __forceinline__ void restrict_level(const PlaneRelaxArgs &a, const Pl
 
 // Load line y of a plane in storage precision into the lane's K registers (0 beyond nx).
 template <class C, class S, int K>
-__device__ __forceinline__ void load_plane_line(C (&v)[K], const S *plane, int y, int nx, int lane) {
+__device__ __forceinline__ void load_plane_line(C (&v)[K], const S *plane, int y, int nx, bool vec, int lane) {
+    if constexpr (vec_chunk<S, K>() != 0) {
+        if (vec) {
+            S sv[K];
+            vload<S, K>(sv, plane + y * nx + lane * K);
+#pragma unroll
+            for (int j = 0; j < K; ++j) v[j] = ldv<C>(&sv[j]);
+            return;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int x = lane * K + j;
@@ -610,13 +711,14 @@ __device__ __forceinline__ void load_plane_line(C (&v)[K], const S *plane, int y
 
 // d -= M (4c - c_{x-1} - c_{x+1} - c_{y-1} - c_{y+1}) + Kc c  for plane pl at line y.
 template <class C, class S, int K>
-__device__ __forceinline__ void sub_plane_term(C (&d)[K], const S *pl, int y, int nx, int ny, C Mc, C Kc, int lane) {
+__device__ __forceinline__ void sub_plane_term(C (&d)[K], const S *pl, int y, int nx, int ny, C Mc, C Kc, bool vec,
+                                               int lane) {
     C cv[K], up[K], dn[K];
-    load_plane_line<C, S, K>(cv, pl, y, nx, lane);
+    load_plane_line<C, S, K>(cv, pl, y, nx, vec, lane);
 #pragma unroll
     for (int j = 0; j < K; ++j) { up[j] = C(0); dn[j] = C(0); }
-    if (y > 0) load_plane_line<C, S, K>(up, pl, y - 1, nx, lane);
-    if (y + 1 < ny) load_plane_line<C, S, K>(dn, pl, y + 1, nx, lane);
+    if (y > 0) load_plane_line<C, S, K>(up, pl, y - 1, nx, vec, lane);
+    if (y + 1 < ny) load_plane_line<C, S, K>(dn, pl, y + 1, nx, vec, lane);
     C vl = __shfl_up_sync(0xffffffffu, cv[K - 1], 1);
     C vr = __shfl_down_sync(0xffffffffu, cv[0], 1);
     if (lane == 0) vl = C(0);
@@ -636,24 +738,24 @@ __device__ __forceinline__ void rhs_group(const PlaneRelaxArgs &a, const PlaneCt
     const int nx = a.nx, ny = a.ny, np = nx * ny;
     C d[NL][K];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) load_plane_line<C, S, K>(d[l], fpl, ys[l], nx, lane);
+    for (int l = 0; l < NL; ++l) load_plane_line<C, S, K>(d[l], fpl, ys[l], nx, c.vec, lane);
     if (mode >= 1 && z > 0) {
         const C Mc = zc[0], Kc = zc[3];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + (z - 1) * np, ys[l], nx, ny, Mc, Kc, lane);
+        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + (z - 1) * np, ys[l], nx, ny, Mc, Kc, c.vec, lane);
     }
     if (mode >= 1 && z + 1 < a.nz) {
         const C Mc = zc[2], Kc = zc[5];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + (z + 1) * np, ys[l], nx, ny, Mc, Kc, lane);
+        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + (z + 1) * np, ys[l], nx, ny, Mc, Kc, c.vec, lane);
     }
     if (mode == 2) {
         const C Mc = zc[1], Kc = zc[4];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + z * np, ys[l], nx, ny, Mc, Kc, lane);
+        for (int l = 0; l < NL; ++l) sub_plane_term<C, S, K>(d[l], ub + z * np, ys[l], nx, ny, Mc, Kc, c.vec, lane);
     }
 #pragma unroll
-    for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, 0, ys[l]), d[l], nx, lane);
+    for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, 0, ys[l]), d[l], nx, c.vec, lane);
 }
 
 template <class S, class C, int K, bool CL>
@@ -676,31 +778,26 @@ __device__ __forceinline__ void compute_rhs(const PlaneRelaxArgs &a, const Plane
     }
 }
 
-// One CTA (CL = false) or one cluster of R CTAs (CL = true) per plane of the colour.
+// The relaxation of one plane (the pidx-th plane of the colour, batch entry b) by one CTA
+// (CL = false) or by this CTA's share of a cluster (CL = true).  `slot` selects the CTA's part
+// of the global workspace.  Used by the per-launch kernel below and by the persistent
+// multi-system kernel.
 template <class S, class C, int K, bool CL>
-__global__ void __launch_bounds__(512, 1) plane_relax_kernel(const __grid_constant__ PlaneRelaxArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void plane_task(const PlaneRelaxArgs &a, int pidx, int b, long long slot, int rank,
+                                           unsigned char *smem_raw) {
     PlaneCtx<C> c;
     c.sm = reinterpret_cast<C *>(smem_raw);
     c.g0 = nullptr;
     c.nx = a.nx;
-    int pidx;
-    if constexpr (CL) {
-        c.R = a.R;
-        c.rank = static_cast<int>(cg::this_cluster().block_rank());
-        pidx = static_cast<int>(blockIdx.x) / a.R;
-    } else {
-        c.R = 1;
-        c.rank = 0;
-        pidx = static_cast<int>(blockIdx.x);
-    }
+    c.vec = a.vec != 0;
+    c.R = CL ? a.R : 1;
+    c.rank = rank;
     const int nx = a.nx, ny = a.ny;
     const long long np = static_cast<long long>(nx) * ny;
     const int z = a.colour + 2 * pidx;
-    const int b = blockIdx.y;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    c.gw = reinterpret_cast<C *>(a.gws) + (static_cast<long long>(b) * gridDim.x + blockIdx.x) * a.ws_per_plane;
+    c.gw = reinterpret_cast<C *>(a.gws) + slot * a.ws_per_plane;
     const S *fb = reinterpret_cast<const S *>(a.f) + static_cast<long long>(b) * a.vstride;
     S *ub = reinterpret_cast<S *>(a.u) + static_cast<long long>(b) * a.vstride;
     S *plane = ub + static_cast<long long>(z) * np;
@@ -781,6 +878,23 @@ __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const __grid_consta
         plane_sync<CL>();
         SMG_TRACE(101);
     }
+}
+
+// One CTA (CL = false) or one cluster of R CTAs (CL = true) per plane of the colour;
+// blockIdx.y is the batch entry.
+template <class S, class C, int K, bool CL>
+__global__ void __launch_bounds__(512, 1) plane_relax_kernel(const __grid_constant__ PlaneRelaxArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int pidx, rank;
+    if constexpr (CL) {
+        rank = static_cast<int>(cg::this_cluster().block_rank());
+        pidx = static_cast<int>(blockIdx.x) / a.R;
+    } else {
+        rank = 0;
+        pidx = static_cast<int>(blockIdx.x);
+    }
+    const long long slot = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
+    plane_task<S, C, K, CL>(a, pidx, static_cast<int>(blockIdx.y), slot, rank, smem_raw);
 }
 
 template <class S, class C, int K, bool CL>

@@ -92,7 +92,8 @@ struct PlaneLayout {
 inline int trifac_set_elems(int K) { return (2 + (K > 1 ? 4 * K - 5 : 0) + 13) * 32; }
 constexpr int kMaxFactorLevels = kMaxPlaneLevels;
 
-PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget);
+// K > 0 sizes the factor sets for that x-line chunk instead of the one nx implies.
+PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int K = 0);
 // Layout for a cluster of R CTAs per plane: every array in shared memory, each CTA holding the
 // lines it owns (pairs (y/2) mod R).  smem_bytes = 0 when it does not fit in the budget.
 PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R);

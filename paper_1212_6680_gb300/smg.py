@@ -27,7 +27,8 @@ PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}
 # every symbol include/smg.h declares
 EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg_apply_batched",
            "smg_apply_A", "krylov_solve", "lobpcg_solve", "smg_destroy", "smg_last_error",
-           "smg_profile_read", "smg_launch_count", "smg_check_conversions", "smg_apply_A_dot_static")
+           "smg_profile_read", "smg_launch_count", "smg_check_conversions", "smg_apply_A_dot_static",
+           "krylov_solve_batched", "smg_barrier_selftest")
 
 
 class SMGError(RuntimeError):
@@ -55,6 +56,8 @@ def _load():
     L.smg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.smg_check_conversions.argtypes = [ctypes.c_longlong, vp, vp, vp]
     L.smg_apply_A_dot_static.argtypes = [i, i, i, vp, vp, vp, vp]
+    L.krylov_solve_batched.argtypes = [i, vp, i, i, i, vp, vp, d, i, vp, vp]
+    L.smg_barrier_selftest.argtypes = [i, d, ip, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -170,6 +173,29 @@ def smg_check_conversions(src, mismatches, stream=None) -> None:
 def smg_apply_A_dot_static(nx: int, ny: int, nz: int, u, out, dot, stream=None) -> None:
     """out = A u and dot[0] = (u, A u) with no device allocation (static scratch)."""
     _check(_lib.smg_apply_A_dot_static(nx, ny, nz, _ptr(u), _ptr(out), _ptr(dot), _stream(stream)))
+
+
+def krylov_solve_batched(dims, b_list, x_list, npre=1, npost=0, prec="fp32", tol=1e-8, maxit=100, stream=None,
+                         check=True):
+    """dims: (nsys, 3) ints (nx, ny, nz); b_list, x_list: per-system device tensors.
+    Returns (status, iters as a numpy array)."""
+    dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+    nsys = dims.shape[0]
+    bp = (ctypes.c_void_p * nsys)(*[_ptr(t) for t in b_list])
+    xp = (ctypes.c_void_p * nsys)(*[_ptr(t) for t in x_list])
+    it = np.zeros(nsys, dtype=np.int32)
+    rc = _lib.krylov_solve_batched(nsys, dims.ctypes.data, npre, npost, PRECISIONS.get(prec, prec),
+                                   ctypes.cast(bp, ctypes.c_void_p), ctypes.cast(xp, ctypes.c_void_p), tol, maxit,
+                                   it.ctypes.data, _stream(stream))
+    if check:
+        _check(rc, allow=(SMG_ERR_NOCONV,))
+    return rc, it
+
+
+def smg_barrier_selftest(extra_blocks: int, limit_seconds: float = 0.5, stream=None) -> int:
+    st = ctypes.c_int(-99)
+    _check(_lib.smg_barrier_selftest(extra_blocks, limit_seconds, ctypes.byref(st), _stream(stream)))
+    return st.value
 
 
 def smg_destroy(h: int) -> None:
