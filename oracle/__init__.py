@@ -5,8 +5,10 @@ TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and 
 benchmark's CPU-baseline leg may import this package.  The product library never loads it,
 and it shares no code with the CUDA path.
 
-The numerical core is ``smg_oracle.c`` (plain loops, FP64); this module compiles it with gcc
-into ``_liboracle.so`` next to the sources and exposes numpy-friendly wrappers.  LOBPCG
+The numerical core is ``smg_oracle.c`` (plain loops, FP64) with ``net_oracle.c`` (the learned
+post-correction: 3x3x3 convolutions, their adjoints and weight gradients, the energy-norm loss);
+this module compiles both with gcc into ``_liboracle.so`` next to the sources and exposes
+numpy-friendly wrappers.  LOBPCG
 (``lobpcg.py``) is written in numpy on top of these wrappers.
 """
 from __future__ import annotations
@@ -19,21 +21,24 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "smg_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "net_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "_liboracle.so")
 _lib = None
 
 VARIANTS = {"pcg": 0, "fpcg": 1, "psd": 2}
+NET_C = 16
+NET_WEIGHTS = 16 * 27 + 16 * 16 * 27 + 16 * 27  # layers [16][1][27], [16][16][27], [1][16][27]
 
 
 def build(force: bool = False) -> str:
     """Compile the C oracle with gcc (portable flags: the same source builds on x86 and Arm)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "smg_oracle.h"))
+        [os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(os.path.join(_HERE, "smg_oracle.h"))]
     ):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-             "-o", tmp, _SRC, "-lm"]
+             "-o", tmp] + _SRCS + ["-lm"]
         )
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -62,6 +67,16 @@ def lib():
         L.orc_plane_cycle.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_krylov.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
                                  ctypes.c_double, ctypes.c_int, ip, dp, dp, dp, dp]
+        i3 = [ctypes.c_int] * 3
+        L.orc_conv3d.argtypes = i3 + [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.orc_conv3d_adj.argtypes = i3 + [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.orc_conv3d_wgrad.argtypes = i3 + [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.orc_net_forward.argtypes = i3 + [dp, dp, dp]
+        L.orc_net_loss_grad.argtypes = i3 + [dp, dp, dp, dp]
+        L.orc_net_loss_grad.restype = ctypes.c_double
+        L.orc_learned_correct.argtypes = i3 + [dp, dp, dp]
+        L.orc_smg_set_learned.argtypes = [vp, dp]
+        L.orc_smg_learned_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
         _lib = L
     return _lib
 
@@ -120,6 +135,20 @@ class SMG:
         lib().orc_smg_apply(self._h, _p(r), _p(s))
         return s
 
+    def set_learned(self, w):
+        """Attach the learned post-correction (7776 weights) or detach it (None)."""
+        if w is None:
+            lib().orc_smg_set_learned(self._h, None)
+        else:
+            w = _f64(w).ravel()
+            assert w.size == NET_WEIGHTS
+            lib().orc_smg_set_learned(self._h, _p(w))
+
+    def learned_stats(self):
+        c, a = ctypes.c_longlong(), ctypes.c_longlong()
+        lib().orc_smg_learned_stats(self._h, ctypes.byref(c), ctypes.byref(a))
+        return c.value, a.value
+
     def num_levels(self):
         return lib().orc_smg_num_levels(self._h)
 
@@ -170,3 +199,67 @@ def krylov(b: np.ndarray, variant: str, smg: SMG | None = None, tol=1e-8, maxit=
         out["xs"] = xs[: it.value + 1].reshape(-1, nz, ny, nx)
         out["rs"] = rs[: it.value + 1].reshape(-1, nz, ny, nx)
     return out
+
+
+# ---- learned post-correction (net_oracle.c) ------------------------------------------------------
+
+def split_weights(w):
+    """The flat 7776-weight array as its three layers, shapes (16,1,27), (16,16,27), (1,16,27)."""
+    w = np.asarray(w).ravel()
+    a, b = NET_C * 27, NET_C * 27 + NET_C * NET_C * 27
+    return w[:a].reshape(NET_C, 1, 27), w[a:b].reshape(NET_C, NET_C, 27), w[b:].reshape(1, NET_C, 27)
+
+
+def conv3d(w: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """w: (cout, cin, 27); x: (cin, nz, ny, nx) -> (cout, nz, ny, nx)."""
+    w, x = _f64(w), _f64(x)
+    cout, cin = w.shape[:2]
+    _, nz, ny, nx = x.shape
+    out = np.empty((cout, nz, ny, nx))
+    lib().orc_conv3d(nx, ny, nz, cin, cout, _p(w), _p(x), _p(out))
+    return out
+
+
+def conv3d_adj(w: np.ndarray, g: np.ndarray) -> np.ndarray:
+    w, g = _f64(w), _f64(g)
+    cout, cin = w.shape[:2]
+    _, nz, ny, nx = g.shape
+    out = np.empty((cin, nz, ny, nx))
+    lib().orc_conv3d_adj(nx, ny, nz, cin, cout, _p(w), _p(g), _p(out))
+    return out
+
+
+def conv3d_wgrad(x: np.ndarray, g: np.ndarray) -> np.ndarray:
+    x, g = _f64(x), _f64(g)
+    cin, nz, ny, nx = x.shape
+    cout = g.shape[0]
+    out = np.empty((cout, cin, 27))
+    lib().orc_conv3d_wgrad(nx, ny, nz, cin, cout, _p(x), _p(g), _p(out))
+    return out
+
+
+def net_forward(w, rho: np.ndarray) -> np.ndarray:
+    """delta = rms(rho) Net(rho / rms(rho)) for a (nz, ny, nx) residual."""
+    w, rho = _f64(w).ravel(), _f64(rho)
+    nz, ny, nx = rho.shape
+    out = np.empty_like(rho)
+    lib().orc_net_forward(nx, ny, nz, _p(w), _p(rho), _p(out))
+    return out
+
+
+def net_loss_grad(w, rho: np.ndarray, e: np.ndarray, want_grad=True):
+    """(loss, gradient (7776,) or None) of L = (e - delta)^T A (e - delta) / e^T A e."""
+    w, rho, e = _f64(w).ravel(), _f64(rho), _f64(e)
+    nz, ny, nx = rho.shape
+    g = np.empty(NET_WEIGHTS) if want_grad else None
+    loss = lib().orc_net_loss_grad(nx, ny, nz, _p(w), _p(rho), _p(e), _p(g) if want_grad else None)
+    return loss, g
+
+
+def learned_correct(w, r: np.ndarray, s0: np.ndarray):
+    """(s, accepted): s0 + delta(r - A s0) if the judge accepts it, else s0."""
+    w, r = _f64(w).ravel(), _f64(r)
+    s = _f64(s0).copy()
+    nz, ny, nx = r.shape
+    acc = lib().orc_learned_correct(nx, ny, nz, _p(w), _p(r), _p(s))
+    return s, bool(acc)

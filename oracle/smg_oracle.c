@@ -352,6 +352,8 @@ struct orc_smg {
     tri_t *M, *K;         /* [L] */
     double **wm, **wp;    /* [L] z-interpolation weights */
     plane_h **ph;         /* [L][nz_l] plane hierarchies */
+    double *learned;      /* NULL, or the 7776 weights of the learned post-correction */
+    long long learned_accepted, learned_calls;
 };
 
 orc_smg *orc_smg_setup(int nx, int ny, int nz, int npre, int npost, int coarse_iters)
@@ -414,6 +416,7 @@ void orc_smg_free(orc_smg *h)
     free(h->wm);
     free(h->wp);
     free(h->nz_l);
+    free(h->learned);
     free(h);
 }
 
@@ -519,6 +522,31 @@ static void smg_vcycle(const orc_smg *h, int l, const double *f, double *u)
 void orc_smg_apply(const orc_smg *h, const double *r, double *s)
 {
     smg_vcycle(h, 0, r, s);
+    if (h->learned) {
+        /* the learned post-correction of net_oracle.c; the counters are bookkeeping only */
+        orc_smg *hm = (orc_smg *)h;
+        hm->learned_calls += 1;
+        hm->learned_accepted += orc_learned_correct(h->nx, h->ny, h->nz, h->learned, r, s);
+    }
+}
+
+int orc_smg_set_learned(orc_smg *h, const double *w)
+{
+    if (!h) return -1;
+    free(h->learned);
+    h->learned = NULL;
+    h->learned_calls = h->learned_accepted = 0;
+    if (w) {
+        h->learned = (double *)malloc(sizeof(double) * ORC_NET_WEIGHTS);
+        memcpy(h->learned, w, sizeof(double) * ORC_NET_WEIGHTS);
+    }
+    return 0;
+}
+
+void orc_smg_learned_stats(const orc_smg *h, long long *calls, long long *accepted)
+{
+    *calls = h->learned_calls;
+    *accepted = h->learned_accepted;
 }
 
 int orc_smg_num_levels(const orc_smg *h) { return h->L; }

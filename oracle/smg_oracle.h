@@ -59,6 +59,27 @@ int orc_krylov(const orc_smg *h, int nx, int ny, int nz, int variant,
                const double *b, double *x, double tol, int maxit,
                int *iters, double *relres, double *hist, double *xs, double *rs);
 
+/* ---- learned post-correction (net_oracle.c; not in the paper) ---------------------------- */
+#define ORC_NET_WEIGHTS 7776 /* 16*1*27 + 16*16*27 + 1*16*27 */
+
+/* 3x3x3 convolution (cross-correlation), zero padding, no bias.  w: [cout][cin][27],
+ * tap t = (dz+1)*9 + (dy+1)*3 + (dx+1); in: [cin][N]; out: [cout][N]. */
+void orc_conv3d(int nx, int ny, int nz, int cin, int cout, const double *w, const double *in, double *out);
+/* Its adjoint in the input: gin = conv^T gout. */
+void orc_conv3d_adj(int nx, int ny, int nz, int cin, int cout, const double *w, const double *gout, double *gin);
+/* Its gradient in the weights of sum <gout, out>. */
+void orc_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const double *in, const double *gout, double *gw);
+/* delta = rms(rho) * Net(rho / rms(rho)). */
+void orc_net_forward(int nx, int ny, int nz, const double *w, const double *rho, double *delta);
+/* L = (e - delta)^T A (e - delta) / e^T A e and, if grad != NULL, dL/dw (7776). */
+double orc_net_loss_grad(int nx, int ny, int nz, const double *w, const double *rho, const double *e, double *grad);
+/* s += delta(r - A s) when the judge accepts it; returns 1 if accepted. */
+int orc_learned_correct(int nx, int ny, int nz, const double *w, const double *r, double *s);
+/* Attach (w != NULL, copied) or detach (NULL) the learned post-correction of a handle:
+ * orc_smg_apply then returns s0 + delta or s0 as the judge decides. */
+int orc_smg_set_learned(orc_smg *h, const double *w);
+void orc_smg_learned_stats(const orc_smg *h, long long *calls, long long *accepted);
+
 #ifdef __cplusplus
 }
 #endif
