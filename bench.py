@@ -22,6 +22,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -39,6 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["fpcg128", "batched64"], default="fpcg128",
+                    help="fpcg128: one 128^3 system (default); batched64: 64 uneven systems, sides in {32..96}")
     return ap.parse_args()
 
 
@@ -134,12 +138,62 @@ def ncu_traffic():
     return None
 
 
+NSYS = 64
+BATCH_WORKLOAD = ("64 independent FPCG-SMG(1,0) solves, 7-point Dirichlet Laplacian, sides i.i.d. uniform in "
+                  "{32..96} per axis, V-cycle FP32, Krylov FP64, tol 1e-8 each")
+
+
+def batched_inputs():
+    """Grid sides (seed 1000 + i for system i) and right-hand sides (same seeds) of the 64 systems."""
+    from paper_1212_6680_gb300 import inputs
+
+    dims = inputs.uneven_dims(NSYS, 32, 96, seed=1000)
+    bs = [inputs.rhs(int(nx), int(ny), int(nz), seed=1000 + i) for i, (nx, ny, nz) in enumerate(dims)]
+    return dims, bs
+
+
+def oracle_batched_sample(nsample):
+    """Oracle FPCG-SMG(1,0) solves of the first `nsample` systems; seconds scaled to all 64 by
+    the unknowns they hold."""
+    import oracle
+
+    oracle.build()
+    dims, bs = batched_inputs()
+    t0 = time.perf_counter()
+    its = []
+    for i in range(nsample):
+        nx, ny, nz = map(int, dims[i])
+        out = oracle.krylov(bs[i], "fpcg", oracle.SMG(nx, ny, nz, 1, 0), tol=TOL, maxit=100)
+        assert out["status"] == 0 and out["relres"] <= TOL
+        its.append(out["iters"])
+    t = time.perf_counter() - t0
+    n_all = float(sum(int(np.prod(d)) for d in dims))
+    n_s = float(sum(int(np.prod(d)) for d in dims[:nsample]))
+    return t * n_all / n_s, its, t
+
+
 def run_reference(args):
     import oracle
     from paper_1212_6680_gb300 import inputs
 
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "batched64":
+        times = []
+        for _ in range(args.steps):
+            v, its, raw = oracle_batched_sample(4)
+            times.append(v)
+        v = statistics.mean(times)
+        sample = (f"oracle FPCG-SMG(1,0) solves of systems 0-3 of the 64 ({raw:.1f} s, iterations {its}), "
+                  "scaled to all 64 by unknowns, single thread")
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": BATCH_WORKLOAD.replace("V-cycle FP32, Krylov FP64", "FP64 CPU oracle")},
+                "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     oracle.build()
     b = inputs.rhs(NX, NY, NZ, seed=0)
@@ -306,10 +360,175 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """64 uneven systems through one batched handle (setup outside the timed region)."""
+    import torch
+
+    from paper_1212_6680_gb300 import build as _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    from paper_1212_6680_gb300 import smg
+
+    dims, b_np = batched_inputs()
+    n_all = sum(b.size for b in b_np)
+    bs = [torch.from_numpy(b.ravel().copy()).cuda() for b in b_np]
+    xs = [torch.zeros_like(b) for b in bs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    t0 = time.perf_counter()
+    h = smg.smg_batched_setup(dims, npre=1, npost=0, prec="fp32")
+    setup_s = time.perf_counter() - t0
+    info0 = smg.smg_batched_info(h)
+
+    def solve(host=None):
+        for x in xs:
+            x.zero_()
+        if host is not None:
+            bh, xh = host
+            for d, hsrc in zip(bs, bh):
+                d.copy_(hsrc, non_blocking=True)
+        rc, its, rel = smg.smg_batched_solve(h, "fpcg", bs, xs, TOL, 100)
+        if host is not None:
+            for hdst, d in zip(xh, xs):
+                hdst.copy_(d, non_blocking=True)
+        return rc, its, rel
+
+    for _ in range(args.warmup):
+        solve()
+    smg.smg_batched_set_profile(h, 1)
+    smg.smg_batched_profile_read(h, 0)
+    smg.smg_batched_profile_read(h, 1)
+    la0 = smg.smg_batched_info(h)["launches"]
+    times = []
+    barrier()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, its, rel = solve()
+            e1.record(stream)
+            barrier()
+            assert rc == smg.SMG_OK and (rel <= TOL).all(), (rc, rel.max())
+            times.append(e0.elapsed_time(e1) / 1e3)
+    wall = time.perf_counter() - wall0
+    launches = smg.smg_batched_info(h)["launches"] - la0
+    pl, pms, pbytes = smg.smg_batched_profile_read(h, 0)
+    kl, kms, _ = smg.smg_batched_profile_read(h, 1)
+    smg.smg_batched_set_profile(h, 0)
+    t_step = statistics.mean(times)
+    t_max = t_step
+    if dist is not None:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    # end to end: pinned host inputs and outputs, copies inside the timed region
+    bh = [torch.from_numpy(b.ravel().copy()).pin_memory() for b in b_np]
+    xh = [torch.zeros(b.size, dtype=torch.float64).pin_memory() for b in b_np]
+    te = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, _, _ = solve(host=(bh, xh))
+        e1.record(stream)
+        barrier()
+        assert rc == smg.SMG_OK
+        te.append(e0.elapsed_time(e1) / 1e3)
+
+    # the same 64 systems one after another through the single-system path (FP32 and FP64 cycles)
+    seq = {}
+    for prec in ("fp32", "fp64"):
+        hs_ = []
+        for i, (nx, ny, nz) in enumerate(dims):
+            hh = smg.smg_setup(int(nx), int(ny), int(nz), 1, 0)
+            smg.smg_set_precision(hh, prec)
+            hs_.append(hh)
+        for i, hh in enumerate(hs_):  # warm-up (first-use costs)
+            xs[i].zero_()
+            smg.krylov_solve(hh, "fpcg", bs[i], xs[i], TOL, 100)
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i, hh in enumerate(hs_):
+            xs[i].zero_()
+            rc1, _, r1 = smg.krylov_solve(hh, "fpcg", bs[i], xs[i], TOL, 100)
+            assert rc1 == smg.SMG_OK and r1 <= TOL
+        e1.record(stream)
+        barrier()
+        seq[prec] = e0.elapsed_time(e1) / 1e3
+        for hh in hs_:
+            smg.smg_destroy(hh)
+    smg.smg_batched_destroy(h)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = (pbytes / 1e9) / (pms / 1e3) if pms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "persistent_vcycle_kernel<float,4> (every V-cycle step of every active system)",
+                "launches": pl, "avg_launch_us": (pms * 1e3 / pl) if pl else None,
+                "algorithmic_bytes_per_launch": (pbytes / pl) if pl else None,
+                "krylov_avg_us_per_iteration": (kms * 1e3 / kl) if kl else None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
+                "fallback 6.8 TB/s"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, its_o, raw = oracle_batched_sample(4)
+        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle FPCG-SMG(1,0) solves of systems 0-3 ({raw:.1f} s, iterations {its_o}), "
+                         f"scaled to all 64 by unknowns, single thread"}
+    line = {
+        "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "nsys": NSYS, "unknowns": int(n_all), "variant": "fpcg",
+                   "npre": 1, "npost": 0, "cycle_precision": "fp32", "iters_max": int(its.max()),
+                   "iters_mean": float(its.mean()), "true_relres_max": float(rel.max()),
+                   "unknowns_per_s": n_all / t_max, "setup_s": setup_s,
+                   "schedule": {k: info0[k] for k in ("threads", "order", "blocks", "tasks")},
+                   "sequential_fp32_s": seq["fp32"], "sequential_fp64_s": seq["fp64"],
+                   "speedup_vs_sequential_fp32": seq["fp32"] / t_step,
+                   "speedup_vs_sequential_fp64": seq["fp64"] / t_step,
+                   "l2": "256 MB buffer written before every timed solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": statistics.mean(te), "unit": "s", "h2d_bytes_per_step": int(n_all) * 8,
+                "d2h_bytes_per_step": int(n_all) * 8},
+        "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched64":
+        run_batched(args)
     else:
         run_ours(args)
 

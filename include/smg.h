@@ -120,20 +120,62 @@ int lobpcg_solve(smg_handle h, int m, double *X, double *lambda, double tol, int
                  int *iters, void *stream);
 
 /*
- * krylov_solve_batched -- nsys independent systems, each the model problem on its own brick
- * (dims[3s], dims[3s+1], dims[3s+2] = nx, ny, nz of system s), solved together by flexible PCG
- * (Algorithm 1 with eq. (2)) preconditioned by SMG with -v npre npost.  Per iteration, one CUDA
- * graph runs one persistent kernel that performs every step of every system's V-cycle (levels
- * aligned from the finest, a bounded grid barrier between steps) and the FP64 Krylov kernels of
- * all systems; converged systems are masked out on the device.  The schedule (threads per CTA,
- * task order) is chosen by timing the candidates on the first call for a given set of grids.
- *   dims:  host, 3*nsys ints; 1 <= nx <= 128, 1 <= ny <= 512, 1 <= nz <= 4096.
- *   prec:  SMG_FP32 (FP32 cycle, FP64 coarsest plane, FP64 Krylov).
- *   b, x:  host arrays of nsys device pointers (system s has nx*ny*nz doubles); x holds x0 on entry.
- *   iters: host, nsys ints, always written (preconditioner applications per system).
+ * Batched solver: nsys independent systems, each the model problem on its own brick
+ * (dims[3s], dims[3s+1], dims[3s+2] = nx, ny, nz of system s), solved together by Algorithm 1
+ * (PCG eq. (1), flexible PCG eq. (2) or PSD) preconditioned by SMG with -v npre npost.  Per
+ * iteration, one CUDA graph runs one persistent kernel that performs every step of every
+ * system's V-cycle (levels aligned from the finest, a bounded grid barrier between steps) and
+ * the FP64 Krylov kernels of all systems; converged systems are masked out on the device.
+ *
+ * smg_batched_setup -- builds the hierarchies, allocates every buffer, chooses the schedule
+ * (threads per CTA, task order within a step) by timing one V-cycle per candidate (cached per
+ * set of grids for the life of the process) and captures the per-iteration graph.
+ *   dims:  host, 3*nsys ints; 1 <= nx <= 128, 1 <= ny <= 512, 1 <= nz <= 4096; 1 <= nsys <= 4096.
+ *   npre, npost: 1 <= npre <= 8, 0 <= npost <= 8.
+ *   prec:  SMG_FP32 (FP32 cycle, FP64 coarsest plane, FP64 Krylov); others return SMG_ERR_ARG.
+ *   *out:  receives the handle (NULL on failure).  Synchronises `stream`.
+ *
+ * smg_batched_solve -- one solve of all systems.
+ *   b, x:   host arrays of nsys device pointers (system s has nx*ny*nz doubles, layout as
+ *           smg_apply); x holds x0 on entry.  Caller-owned.
+ *   iters:  host, nsys ints, always written (preconditioner applications per system).
+ *   relres: host, nsys doubles (NULL allowed): final true relative residual per system.
  * Stops each system at ||b - A x||_2 <= tol ||b||_2 (true residual); returns SMG_ERR_NOCONV
  * when some system did not reach it in maxit iterations, SMG_ERR_TIMEOUT when a grid-barrier
- * wait gave up.  Synchronises `stream` once per iteration.  1 <= nsys <= 4096.
+ * wait gave up, SMG_ERR_BREAKDOWN / SMG_ERR_NAN as krylov_solve.  Synchronises `stream` once
+ * per iteration.  Calls on one handle must not overlap.
+ *
+ * smg_batched_destroy -- frees the handle (NULL accepted).  Synchronises the device.
+ */
+typedef struct smg_batched_ctx *smg_batched_handle;
+int smg_batched_setup(int nsys, const int *dims, int npre, int npost, int prec, smg_batched_handle *out,
+                      void *stream);
+int smg_batched_solve(smg_batched_handle h, int variant, const double *const *b, double *const *x, double tol,
+                      int maxit, int *iters, double *relres, void *stream);
+int smg_batched_destroy(smg_batched_handle h);
+
+/*
+ * smg_batched_info -- the chosen schedule: threads per CTA (256 or 512), task order (0 system
+ * order, 1 longest plane first), persistent CTAs, tasks per V-cycle, and the kernel launches
+ * the handle has issued so far (the persistent V-cycle counts once per launch).  Host outputs.
+ */
+int smg_batched_info(smg_batched_handle h, int *threads, int *order, int *blocks, long long *tasks,
+                     long long *launches);
+
+/*
+ * smg_batched_set_profile / smg_batched_profile_read -- with profiling on, each iteration's
+ * graph replay is timed by its event nodes: class 0 the persistent V-cycle kernel, class 1 the
+ * Krylov kernels.  Read returns replays, total device milliseconds and, for class 0, the
+ * algorithmic bytes of the V-cycles performed (storage words each active system's cycle must
+ * read and write: 2.5 words per point per relaxation sweep, 5 per point for residual +
+ * restriction + prolongation, 2 per point on the coarsest plane); reading resets the class.
+ */
+int smg_batched_set_profile(smg_batched_handle h, int on);
+int smg_batched_profile_read(smg_batched_handle h, int which, long long *launches, double *ms, double *bytes);
+
+/*
+ * krylov_solve_batched -- one-shot form: smg_batched_setup, smg_batched_solve with flexible PCG
+ * (eq. (2)) and relres = NULL, smg_batched_destroy.  Arguments as above.
  */
 int krylov_solve_batched(int nsys, const int *dims, int npre, int npost, int prec, const double *const *b,
                          double *const *x, double tol, int maxit, int *iters, void *stream);

@@ -123,6 +123,13 @@ struct BScal {
     int restart, status, iters, pad;
 };
 
+// Per-solve controls, read from device memory so that a captured graph serves every solve.
+struct BCtl {
+    double tol2;  // tol^2
+    int maxit;
+    int variant;  // SMG_PCG, SMG_FPCG or SMG_PSD
+};
+
 struct BKrylov {
     const BSys *sys;
     const int *ch_sys;
@@ -136,8 +143,8 @@ struct BKrylov {
     BScal *sc;
     int *active;
     int *nactive;
-    int nsys, variant, maxit;
-    double tol2;
+    const BCtl *ctl;            // tolerance, maxit, variant of the current solve (device)
+    int nsys;
 };
 
 __device__ __forceinline__ double stencil_at(const double *__restrict__ v, long long i, int x, int y, int z, int nx,
@@ -237,7 +244,7 @@ __global__ void kb_fin_init(BKrylov k, int mode) {
         if (mode == 0) {
             q = BScal{0, 0, 0, 0, rr, bb, 1, 0, 0, 0};
             const double bref = bb > 0.0 ? bb : 1.0;
-            k.active[s] = (rr > k.tol2 * bref) ? 1 : 0;
+            k.active[s] = (rr > k.ctl->tol2 * bref) ? 1 : 0;
             if (!isfinite(rr) || !isfinite(bb)) {
                 q.status = SMG_ERR_NAN;
                 k.active[s] = 0;
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kBThreads) kb_dots(BKrylov k) {
         const long long g0 = k.ch_start[c];
         const int len = k.ch_len[c];
         const S *u0 = static_cast<const S *>(k.ustore) + sy.u0_off;
-        const bool want = (k.variant == SMG_FPCG) && (k.sc[s].restart == 0);
+        const bool want = (k.ctl->variant == SMG_FPCG) && (k.sc[s].restart == 0);
         for (int t = threadIdx.x; t < len; t += kBThreads) {
             const long long gi = g0 + t;
             const double si = ldv<double>(u0 + (gi - sy.off));
@@ -287,9 +294,9 @@ __global__ void kb_fin_beta(BKrylov k) {
         sum_chunks(k, s, rho, sdr);
         BScal &q = k.sc[s];
         double beta = 0.0;
-        if (q.restart == 0 && k.variant != SMG_PSD) {
+        if (q.restart == 0 && k.ctl->variant != SMG_PSD) {
             if (q.rho_prev == 0.0) q.status = SMG_ERR_BREAKDOWN;
-            else beta = (k.variant == SMG_PCG) ? rho / q.rho_prev : sdr / q.rho_prev;
+            else beta = (k.ctl->variant == SMG_PCG) ? rho / q.rho_prev : sdr / q.rho_prev;
         }
         if (!isfinite(rho) || !isfinite(beta)) q.status = SMG_ERR_NAN;
         q.rho = rho;
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(kBThreads) kb_upd_xr(BKrylov k) {
         const long long g0 = k.ch_start[c];
         const int len = k.ch_len[c];
         const double alpha = k.sc[s].alpha;
-        const bool want_dr = (k.variant == SMG_FPCG);
+        const bool want_dr = (k.ctl->variant == SMG_FPCG);
         double *x = k.xptr[s];
         S *f0 = static_cast<S *>(k.fstore) + sy.f0_off;
         for (int t = threadIdx.x; t < len; t += kBThreads) {
@@ -402,7 +409,7 @@ __global__ void kb_fin_rr(BKrylov k) {
             q.iters += 1;
             const double bref = q.bb > 0.0 ? q.bb : 1.0;
             if (!isfinite(rr)) q.status = SMG_ERR_NAN;
-            if (rr <= k.tol2 * bref || q.status != 0 || q.iters >= k.maxit) k.active[s] = 0;
+            if (rr <= k.ctl->tol2 * bref || q.status != 0 || q.iters >= k.ctl->maxit) k.active[s] = 0;
         }
         if (k.active[s] == 1) atomicAdd(&cnt, 1);
     }
@@ -421,7 +428,7 @@ __global__ void kb_fin_true(BKrylov k, double *relres, int *nflag) {
         const double bref = bb > 0.0 ? bb : 1.0;
         relres[s] = sqrt(tt / bref);
         BScal &q = k.sc[s];
-        if (q.status == 0 && tt > k.tol2 * bref && q.iters < k.maxit) {
+        if (q.status == 0 && tt > k.ctl->tol2 * bref && q.iters < k.ctl->maxit) {
             k.active[s] = 2;  // continue from the true residual
             atomicAdd(&cnt, 1);
         }
@@ -437,7 +444,7 @@ thread_local std::string g_berr;
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \
         if (e_ != cudaSuccess) {                                                        \
-            set_last_error(std::string("krylov_solve_batched: ") + #call + ": " +       \
+            set_last_error(std::string("batched solver: ") + #call + ": " +       \
                            cudaGetErrorString(e_));                                     \
             return SMG_ERR_CUDA;                                                        \
         }                                                                               \
@@ -488,29 +495,121 @@ struct SysPlan {
     PlaneLayout lay, lay_d;
     size_t zoff, poff;                 // offsets into the concatenated coefficient tables
     std::vector<long long> foff;       // per level, offset into the storage arrays
+    double cycle_bytes;                // algorithmic bytes of one V-cycle of this system
 };
 
 // Estimated cost of relaxing one plane (for the longest-first ordering of a step's tasks).
 double plane_cost(const SysPlan &s) { return static_cast<double>(s.nx) * s.ny; }
 
+// Algorithmic traffic of one V-cycle (npre pre-sweeps, npost post-sweeps) of one system, in
+// storage words: a relaxation of a colour reads f and writes u of its planes (and reads u in
+// correction form, mode 2), and reads each opposite-colour plane once when it can be nonzero;
+// residual + restriction and prolongation + correction move 2.5 words per fine point each.
+double vcycle_words(const SysPlan &p, int npre, int npost) {
+    const double np = static_cast<double>(p.nx) * p.ny;
+    double w = 0.0;
+    auto colour = [&](int nzl, int col, int mode) {
+        const int nplanes = col == 0 ? (nzl + 1) / 2 : nzl / 2;
+        const int nother = nzl - nplanes;
+        return (nplanes * (2.0 + (mode == 2 ? 1.0 : 0.0)) + (mode >= 1 ? nother : 0)) * np;
+    };
+    for (int l = 0; l + 1 < p.H.L; ++l) {
+        const int nzl = p.H.nz_l[l];
+        for (int sw = 0; sw < npre; ++sw) w += colour(nzl, 0, sw == 0 ? 0 : 2) + colour(nzl, 1, sw == 0 ? 1 : 2);
+        for (int sw = 0; sw < npost; ++sw) w += colour(nzl, 1, 2) + colour(nzl, 0, 2);
+        w += 5.0 * nzl * np;
+    }
+    w += 2.0 * np;  // the coarsest plane: read f, write u
+    return w;
+}
+
 }  // namespace
 
-extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npost, int prec, const double *const *b,
-                                    double *const *x, double tol, int maxit, int *iters, void *stream) {
+// Everything one set of grids needs, built once: hierarchies, level vectors, Krylov vectors,
+// the task list of the persistent V-cycle, the tuned schedule and the per-iteration graph.
+struct smg_batched_ctx {
+    int nsys = 0, npre = 1, npost = 0, prec = SMG_FP32;
+    Prec P = Prec::F32;
+    int K = 1, Lmax = 1, nsm = 0, nch = 0;
+    std::vector<SysPlan> sys;
+    DevBuf buf;
+    PersistArgs pa{};
+    BKrylov kk{};
+    BCtl *d_ctl = nullptr;
+    int *d_flags = nullptr;            // [0] systems still iterating, [1] barrier error, [2] systems to restart
+    double *d_relres = nullptr;
+    BScal *d_sc = nullptr;
+    double **d_bptr = nullptr, **d_xptr = nullptr;
+    int *h_pinned = nullptr;           // pinned copy of d_flags[0..1]
+    size_t smem = 0;
+    Tuned tune;
+    int blocks = 0;
+    long long ntasks = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // V-cycle start, V-cycle end, iteration end
+    // profiling (smg_batched_profile_read)
+    int profile = 0;
+    long long prof_launches[2] = {0, 0};
+    double prof_ms[2] = {0.0, 0.0}, prof_bytes[2] = {0.0, 0.0};
+    long long kernel_launches = 0;
+    int kernels_per_iter = 0;
+
+    ~smg_batched_ctx() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (h_pinned) cudaFreeHost(h_pinned);
+    }
+
+    cudaError_t launch_vcycle(cudaStream_t st, int threads, int nblocks) {
+        pa.expected_blocks = nblocks;
+        return launch_persistent_vcycle(P, K, nblocks, threads, smem, pa, st, false);
+    }
+    cudaError_t init(cudaStream_t st, int mode) {
+        switch (P) {
+        case Prec::F64: kb_init<double><<<nch, kBThreads, 0, st>>>(kk, mode); break;
+        case Prec::F32: kb_init<float><<<nch, kBThreads, 0, st>>>(kk, mode); break;
+        case Prec::BF16: kb_init<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk, mode); break;
+        }
+        kb_fin_init<<<1, 1024, 0, st>>>(kk, mode);
+        kernel_launches += 2;
+        return cudaGetLastError();
+    }
+    cudaError_t krylov_tail(cudaStream_t st) {
+        switch (P) {
+        case Prec::F64: kb_dots<double><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::F32: kb_dots<float><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::BF16: kb_dots<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
+        }
+        kb_fin_beta<<<(nsys + 127) / 128, 128, 0, st>>>(kk);
+        switch (P) {
+        case Prec::F64: kb_upd_p<double><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::F32: kb_upd_p<float><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::BF16: kb_upd_p<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
+        }
+        kb_spmv<<<nch, kBThreads, 0, st>>>(kk);
+        kb_fin_alpha<<<(nsys + 127) / 128, 128, 0, st>>>(kk);
+        switch (P) {
+        case Prec::F64: kb_upd_xr<double><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::F32: kb_upd_xr<float><<<nch, kBThreads, 0, st>>>(kk); break;
+        case Prec::BF16: kb_upd_xr<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
+        }
+        kb_fin_rr<<<1, 1024, 0, st>>>(kk);
+        return cudaGetLastError();
+    }
+};
+
+namespace {
+
+int check_dims(int nsys, const int *dims) {
     if (nsys < 1 || nsys > 4096) {
         set_last_error("nsys must be in [1, 4096]");
         return SMG_ERR_ARG;
     }
-    if (!dims || !b || !x || !iters) {
+    if (!dims) {
         set_last_error("null pointer");
-        return SMG_ERR_ARG;
-    }
-    if (npre < 1 || npost < 0 || !(tol > 0.0) || maxit < 0) {
-        set_last_error("npre >= 1, npost >= 0, tol > 0, maxit >= 0 required");
-        return SMG_ERR_ARG;
-    }
-    if (prec != SMG_FP32) {
-        set_last_error("krylov_solve_batched runs the FP32 cycle (SMG_FP32) only");
         return SMG_ERR_ARG;
     }
     for (int s = 0; s < nsys; ++s) {
@@ -519,20 +618,20 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
             set_last_error("each system needs 1 <= nx <= 128, 1 <= ny <= 512, 1 <= nz <= 4096");
             return SMG_ERR_ARG;
         }
-        if (!b[s] || !x[s]) {
-            set_last_error("null vector pointer");
-            return SMG_ERR_ARG;
-        }
-        iters[s] = 0;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const Prec P = static_cast<Prec>(prec);
+    return SMG_OK;
+}
+
+int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
+    const int nsys = c.nsys;
+    const Prec P = c.P;
     const size_t sb = storage_bytes(P), cb = (P == Prec::F64) ? 8 : 4;
-    const int variant = SMG_FPCG;
     constexpr size_t kBudget = 227 * 1024;
+    DevBuf &buf = c.buf;
 
     // ---- per-system hierarchies and layouts ----
-    std::vector<SysPlan> sys(nsys);
+    c.sys.resize(nsys);
+    std::vector<SysPlan> &sys = c.sys;
     int K = 1, Lmax = 1;
     size_t ztot = 0, ptot = 0;
     long long stot = 0, vtot = 0;
@@ -555,7 +654,10 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
             stot += static_cast<long long>(p.nx) * p.ny * p.H.nz_l[l];
         }
         vtot += p.N;
+        p.cycle_bytes = vcycle_words(p, c.npre, c.npost) * static_cast<double>(sb);
     }
+    c.K = K;
+    c.Lmax = Lmax;
     // all systems use the widest chunk K (narrower lines are padded with identity rows); the
     // layouts size their factor sets for that K
     for (auto &p : sys) {
@@ -563,7 +665,6 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
         p.lay_d = plan_plane_layout(p.H, 8, kBudget, K);
     }
 
-    DevBuf buf;
     double *d_zc64, *d_pc64;
     float *d_zc32, *d_pc32;
     BCHK(buf.alloc(&d_zc64, ztot));
@@ -588,12 +689,15 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
         unsigned char *pf, *pu;
         BCHK(buf.alloc(&pf, static_cast<size_t>(stot) * sb));
         BCHK(buf.alloc(&pu, static_cast<size_t>(stot) * sb));
+        BCHK(cudaMemsetAsync(pf, 0, static_cast<size_t>(stot) * sb, st));
+        BCHK(cudaMemsetAsync(pu, 0, static_cast<size_t>(stot) * sb, st));
         d_f = pf;
         d_u = pu;
     }
-    int dev = 0, nsm = 0;
+    int dev = 0;
     BCHK(cudaGetDevice(&dev));
-    BCHK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    BCHK(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int nsm = c.nsm;
 
     // ---- tasks, steps ----
     struct StepTasks {
@@ -689,7 +793,7 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
         steps.push_back(st_);
     };
     for (int l = 0; l < Lmax; ++l) {
-        for (int sw = 0; sw < npre; ++sw) {
+        for (int sw = 0; sw < c.npre; ++sw) {
             add_relax_step(l, 0, 0, sw, sw == 0);
             add_relax_step(l, 1, 1, sw, false);
         }
@@ -719,7 +823,7 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
             }
         }
         if (!sp.t.empty()) steps.push_back(sp);
-        for (int sw = 0; sw < npost; ++sw) {
+        for (int sw = 0; sw < c.npost; ++sw) {
             add_relax_step(l, 1, 2, 1, false);
             add_relax_step(l, 0, 2, 1, false);
         }
@@ -732,22 +836,9 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
     for (size_t i = 0; i < relax.size(); ++i)
         relax[i].ws_per_plane = ws_stride / (relax_f64[i] ? 8 : static_cast<long long>(cb));
 
-    // ---- autotuned schedule: threads per CTA and task order within a step ----
-    std::vector<int> key{nsys, prec, npre, npost};
-    for (int s = 0; s < 3 * nsys; ++s) key.push_back(dims[s]);
-    Tuned tune;
-    bool tuned = false;
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
-            tune = it->second;
-            tuned = true;
-        }
-    }
-    const size_t smem = std::max<size_t>(smem_max, 1024);
-    if (set_persistent_smem(P, K, smem) != 0) {
-        set_last_error("krylov_solve_batched: shared-memory configuration failed");
+    c.smem = std::max<size_t>(smem_max, 1024);
+    if (set_persistent_smem(P, K, c.smem) != 0) {
+        set_last_error("batched solver: shared-memory configuration failed");
         return SMG_ERR_CUDA;
     }
 
@@ -755,20 +846,25 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
     PlaneRelaxArgs *d_relax;
     BTransfer *d_xfer;
     BTask *d_tasks;
-    int *d_step_begin, *d_active, *d_nactive, *d_err, *d_nflag;
+    int *d_step_begin, *d_active;
     unsigned *d_bar;
     unsigned char *d_ws;
     BCHK(buf.alloc(&d_relax, relax.size()));
     BCHK(buf.alloc(&d_xfer, xfer.size()));
     BCHK(buf.alloc(&d_active, nsys));
-    BCHK(buf.alloc(&d_nactive, 1));
-    BCHK(buf.alloc(&d_nflag, 1));
-    BCHK(buf.alloc(&d_err, 1));
+    BCHK(buf.alloc(&c.d_flags, 4));
     BCHK(buf.alloc(&d_bar, 2));
+    BCHK(buf.alloc(&c.d_ctl, 1));
     BCHK(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), st));
-    BCHK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    BCHK(cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), st));
+    {
+        std::vector<int> ones(nsys, 1);  // every system active while the schedule is tuned
+        BCHK(cudaMemcpyAsync(d_active, ones.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
+        BCHK(cudaStreamSynchronize(st));
+    }
     size_t ntasks = 0;
     for (auto &s_ : steps) ntasks += s_.t.size();
+    c.ntasks = static_cast<long long>(ntasks);
     BCHK(buf.alloc(&d_tasks, ntasks));
     BCHK(buf.alloc(&d_step_begin, steps.size() + 1));
     auto upload_tasks = [&](int order) -> int {
@@ -778,7 +874,7 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
             std::vector<int> idx(s_.t.size());
             std::iota(idx.begin(), idx.end(), 0);
             if (order == 1)
-                std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return s_.cost[a] > s_.cost[c]; });
+                std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return s_.cost[a] > s_.cost[b]; });
             for (int i : idx) all.push_back(s_.t[i]);
             begin.push_back(static_cast<int>(all.size()));
         }
@@ -789,9 +885,10 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
     };
     // workspace: one slot per CTA of the largest persistent grid any candidate schedule uses
     int max_blocks = 0;
-    for (int threads : {256, 512}) max_blocks = std::max(max_blocks, nsm * persistent_blocks_per_sm(P, K, threads, smem));
+    for (int threads : {256, 512})
+        max_blocks = std::max(max_blocks, nsm * persistent_blocks_per_sm(P, K, threads, c.smem));
     if (max_blocks < 1) {
-        set_last_error("krylov_solve_batched: the persistent kernel does not fit on an SM");
+        set_last_error("batched solver: the persistent kernel does not fit on an SM");
         return SMG_ERR_CUDA;
     }
     BCHK(buf.alloc(&d_ws, static_cast<size_t>(std::max<long long>(ws_stride, 256)) * max_blocks));
@@ -815,22 +912,21 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
             q.f0_off = sys[s].foff[0];
             q.u0_off = sys[s].foff[0];
             q.c0 = static_cast<int>(ch_sys.size());
-            for (long long c = 0; c < sys[s].N; c += kChunk) {
+            for (long long cc = 0; cc < sys[s].N; cc += kChunk) {
                 ch_sys.push_back(s);
-                ch_start.push_back(off + c);
-                ch_len.push_back(static_cast<int>(std::min<long long>(kChunk, sys[s].N - c)));
+                ch_start.push_back(off + cc);
+                ch_len.push_back(static_cast<int>(std::min<long long>(kChunk, sys[s].N - cc)));
             }
             q.c1 = static_cast<int>(ch_sys.size());
             off += sys[s].N;
         }
     }
-    const int nch = static_cast<int>(ch_sys.size());
+    c.nch = static_cast<int>(ch_sys.size());
+    const int nch = c.nch;
     BSys *d_sys;
     int *d_ch_sys, *d_ch_len;
     long long *d_ch_start;
-    double *d_r, *d_p, *d_q, *d_dr, *d_part, *d_relres;
-    BScal *d_sc;
-    double **d_bptr, **d_xptr;
+    double *d_r, *d_p, *d_q, *d_dr, *d_part;
     BCHK(buf.alloc(&d_sys, nsys));
     BCHK(buf.alloc(&d_ch_sys, nch));
     BCHK(buf.alloc(&d_ch_len, nch));
@@ -840,20 +936,18 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
     BCHK(buf.alloc(&d_q, vtot));
     BCHK(buf.alloc(&d_dr, vtot));
     BCHK(buf.alloc(&d_part, 2 * static_cast<size_t>(nch)));
-    BCHK(buf.alloc(&d_relres, nsys));
-    BCHK(buf.alloc(&d_sc, nsys));
-    BCHK(buf.alloc(&d_bptr, nsys));
-    BCHK(buf.alloc(&d_xptr, nsys));
+    BCHK(buf.alloc(&c.d_relres, nsys));
+    BCHK(buf.alloc(&c.d_sc, nsys));
+    BCHK(buf.alloc(&c.d_bptr, nsys));
+    BCHK(buf.alloc(&c.d_xptr, nsys));
     BCHK(cudaMemcpyAsync(d_sys, hsys.data(), nsys * sizeof(BSys), cudaMemcpyHostToDevice, st));
     BCHK(cudaMemcpyAsync(d_ch_sys, ch_sys.data(), nch * sizeof(int), cudaMemcpyHostToDevice, st));
     BCHK(cudaMemcpyAsync(d_ch_len, ch_len.data(), nch * sizeof(int), cudaMemcpyHostToDevice, st));
     BCHK(cudaMemcpyAsync(d_ch_start, ch_start.data(), nch * sizeof(long long), cudaMemcpyHostToDevice, st));
-    BCHK(cudaMemcpyAsync(d_bptr, b, nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
-    BCHK(cudaMemcpyAsync(d_xptr, x, nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
     BCHK(cudaMemsetAsync(d_dr, 0, vtot * sizeof(double), st));
     BCHK(cudaMemsetAsync(d_p, 0, vtot * sizeof(double), st));
 
-    BKrylov kk;
+    BKrylov &kk = c.kk;
     kk.sys = d_sys;
     kk.ch_sys = d_ch_sys;
     kk.ch_start = d_ch_start;
@@ -862,27 +956,21 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
     kk.p = d_p;
     kk.q = d_q;
     kk.dr = d_dr;
-    kk.bptr = d_bptr;
-    kk.xptr = d_xptr;
+    kk.bptr = c.d_bptr;
+    kk.xptr = c.d_xptr;
     kk.fstore = d_f;
     kk.ustore = d_u;
     kk.part = d_part;
-    kk.sc = d_sc;
+    kk.sc = c.d_sc;
     kk.active = d_active;
-    kk.nactive = d_nactive;
+    kk.nactive = c.d_flags;
+    kk.ctl = c.d_ctl;
     kk.nsys = nsys;
-    kk.variant = variant;
-    kk.maxit = maxit;
-    kk.tol2 = tol * tol;
 
-    int *h_pinned = nullptr;
-    BCHK(cudaMallocHost(&h_pinned, 2 * sizeof(int)));
-    struct PinFree {
-        int *p;
-        ~PinFree() { cudaFreeHost(p); }
-    } pinfree{h_pinned};
+    BCHK(cudaMallocHost(&c.h_pinned, 4 * sizeof(int)));
+    for (cudaEvent_t &e : c.ev) BCHK(cudaEventCreate(&e));
 
-    PersistArgs pa;
+    PersistArgs &pa = c.pa;
     pa.relax = d_relax;
     pa.xfer = d_xfer;
     pa.tasks = d_tasks;
@@ -891,95 +979,60 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
     pa.active = d_active;
     pa.bar_count = d_bar;
     pa.bar_gen = d_bar + 1;
-    pa.err = d_err;
+    pa.err = c.d_flags + 1;
     pa.spin_limit = 10000000;  // about a second of polling
-    int result = SMG_OK;
 
-    auto launch_vcycle = [&](int threads, int blocks) -> cudaError_t {
-        pa.expected_blocks = blocks;
-        return launch_persistent_vcycle(P, K, blocks, threads, smem, pa, st, false);
-    };
-    auto krylov_tail = [&]() -> cudaError_t {
-        switch (P) {
-        case Prec::F64: kb_dots<double><<<nch, kBThreads, 0, st>>>(kk); break;
-        case Prec::F32: kb_dots<float><<<nch, kBThreads, 0, st>>>(kk); break;
-        case Prec::BF16: kb_dots<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
+    // ---- autotuned schedule: threads per CTA and task order within a step ----
+    std::vector<int> key{nsys, c.prec, c.npre, c.npost};
+    for (int s = 0; s < 3 * nsys; ++s) key.push_back(dims[s]);
+    bool tuned = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c.tune = it->second;
+            tuned = true;
         }
-        kb_fin_beta<<<(nsys + 127) / 128, 128, 0, st>>>(kk);
-        switch (P) {
-        case Prec::F64: kb_upd_p<double><<<nch, kBThreads, 0, st>>>(kk); break;
-        case Prec::F32: kb_upd_p<float><<<nch, kBThreads, 0, st>>>(kk); break;
-        case Prec::BF16: kb_upd_p<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
-        }
-        kb_spmv<<<nch, kBThreads, 0, st>>>(kk);
-        kb_fin_alpha<<<(nsys + 127) / 128, 128, 0, st>>>(kk);
-        switch (P) {
-        case Prec::F64: kb_upd_xr<double><<<nch, kBThreads, 0, st>>>(kk); break;
-        case Prec::F32: kb_upd_xr<float><<<nch, kBThreads, 0, st>>>(kk); break;
-        case Prec::BF16: kb_upd_xr<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk); break;
-        }
-        kb_fin_rr<<<1, 1024, 0, st>>>(kk);
-        return cudaGetLastError();
-    };
-    auto init = [&](int mode) -> cudaError_t {
-        switch (P) {
-        case Prec::F64: kb_init<double><<<nch, kBThreads, 0, st>>>(kk, mode); break;
-        case Prec::F32: kb_init<float><<<nch, kBThreads, 0, st>>>(kk, mode); break;
-        case Prec::BF16: kb_init<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk, mode); break;
-        }
-        kb_fin_init<<<1, 1024, 0, st>>>(kk, mode);
-        return cudaGetLastError();
-    };
-
-    // autotune on the first iteration's input (active = all): time the V-cycle per candidate
-    BCHK(init(0));
+    }
     if (!tuned) {
+        // the cost of a V-cycle does not depend on the values: time each candidate on the
+        // zero-initialised level vectors with every system active
         float best = 1e30f;
-        cudaEvent_t e0, e1;
-        BCHK(cudaEventCreate(&e0));
-        BCHK(cudaEventCreate(&e1));
         for (int threads : {256, 512}) {
-            const int bps = persistent_blocks_per_sm(P, K, threads, smem);
+            const int bps = persistent_blocks_per_sm(P, K, threads, c.smem);
             if (bps < 1) continue;
-            const int blocks = nsm * bps;
+            const int nb = nsm * bps;
             for (int order : {0, 1}) {
                 if (upload_tasks(order) != SMG_OK) return SMG_ERR_CUDA;
-                BCHK(launch_vcycle(threads, blocks));  // warm-up
-                BCHK(cudaEventRecord(e0, st));
-                BCHK(launch_vcycle(threads, blocks));
-                BCHK(cudaEventRecord(e1, st));
-                BCHK(cudaEventSynchronize(e1));
+                BCHK(c.launch_vcycle(st, threads, nb));  // warm-up
+                BCHK(cudaEventRecord(c.ev[0], st));
+                BCHK(c.launch_vcycle(st, threads, nb));
+                BCHK(cudaEventRecord(c.ev[1], st));
+                BCHK(cudaEventSynchronize(c.ev[1]));
+                c.kernel_launches += 2;
                 float ms = 0.0f;
-                BCHK(cudaEventElapsedTime(&ms, e0, e1));
+                BCHK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]));
                 int herr = 0;
-                BCHK(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+                BCHK(cudaMemcpy(&herr, pa.err, sizeof(int), cudaMemcpyDeviceToHost));
                 if (herr != 0) {
-                    set_last_error("krylov_solve_batched: a V-cycle barrier wait timed out");
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
+                    set_last_error("batched solver: a V-cycle barrier wait timed out");
                     return herr;
                 }
                 if (ms < best) {
                     best = ms;
-                    tune.threads = threads;
-                    tune.order = order;
+                    c.tune.threads = threads;
+                    c.tune.order = order;
                 }
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = tune;
+        g_tune_cache[key] = c.tune;
     }
-    if (upload_tasks(tune.order) != SMG_OK) return SMG_ERR_CUDA;
-    const int bps = std::max(1, persistent_blocks_per_sm(P, K, tune.threads, smem));
-    const int blocks = std::min(max_blocks, nsm * bps);
-    // the tuning runs left the level vectors changed: start every system again from its x0
-    BCHK(init(0));
+    if (upload_tasks(c.tune.order) != SMG_OK) return SMG_ERR_CUDA;
+    const int bps = std::max(1, persistent_blocks_per_sm(P, K, c.tune.threads, c.smem));
+    c.blocks = std::min(max_blocks, nsm * bps);
 
     // ---- capture one iteration into a CUDA graph ----
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
     BCHK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     struct StreamGuard {
@@ -988,74 +1041,220 @@ extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npo
     } sguard{cs};
     BCHK(cudaStreamSynchronize(st));
     {
-        const cudaStream_t saved = st;
-        st = cs;
         BCHK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = launch_vcycle(tune.threads, blocks);
-        if (e == cudaSuccess) e = krylov_tail();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_pinned, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, cs);
-        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-        st = saved;
+        // the events become event-record nodes, so the V-cycle and the Krylov part of every
+        // replay can be timed
+        cudaError_t e = cudaEventRecordWithFlags(c.ev[0], cs, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = c.launch_vcycle(cs, c.tune.threads, c.blocks);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(c.ev[1], cs, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = c.krylov_tail(cs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(c.ev[2], cs, cudaEventRecordExternal);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c.h_pinned, c.d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &c.graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            set_last_error(std::string("krylov_solve_batched: graph capture: ") +
+            set_last_error(std::string("batched solver: graph capture: ") +
                            cudaGetErrorString(e != cudaSuccess ? e : e2));
             return SMG_ERR_CUDA;
         }
-        BCHK(cudaGraphInstantiate(&exec, graph, 0));
+        BCHK(cudaGraphInstantiate(&c.exec, c.graph, 0));
     }
-    struct GraphGuard {
-        cudaGraph_t g;
-        cudaGraphExec_t x;
-        ~GraphGuard() {
-            if (x) cudaGraphExecDestroy(x);
-            if (g) cudaGraphDestroy(g);
-        }
-    } gguard{graph, exec};
+    c.kernels_per_iter = 1 + 8;  // persistent V-cycle + the Krylov tail
+    return SMG_OK;
+}
 
-    // ---- iterate ----
-    BCHK(cudaMemcpyAsync(h_pinned, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+int batched_solve(smg_batched_ctx &c, int variant, const double *const *b, double *const *x, double tol, int maxit,
+                  int *iters, double *relres, cudaStream_t st) {
+    const int nsys = c.nsys;
+    for (int s = 0; s < nsys; ++s) iters[s] = 0;
+    const BCtl ctl{tol * tol, maxit, variant};
+    BCHK(cudaMemcpyAsync(c.d_ctl, &ctl, sizeof(BCtl), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(c.d_bptr, b, nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(c.d_xptr, x, nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
+    BCHK(c.init(st, 0));
+    BCHK(cudaMemcpyAsync(c.h_pinned, c.d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     BCHK(cudaStreamSynchronize(st));
-    int nact = h_pinned[0];
+    int nact = c.h_pinned[0];
     for (int round = 0; round < 8; ++round) {
         for (int it = 0; it < maxit && nact > 0; ++it) {
-            BCHK(cudaGraphLaunch(exec, st));
+            BCHK(cudaGraphLaunch(c.exec, st));
             BCHK(cudaStreamSynchronize(st));
-            nact = h_pinned[0];
-            int herr = 0;
-            BCHK(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
-            if (herr != 0) {
-                set_last_error("krylov_solve_batched: a V-cycle barrier wait timed out");
-                return herr;
+            c.kernel_launches += c.kernels_per_iter;
+            nact = c.h_pinned[0];
+            if (c.h_pinned[1] != 0) {
+                set_last_error("batched solver: a V-cycle barrier wait timed out");
+                return c.h_pinned[1];
+            }
+            if (c.profile) {
+                float m0 = 0.0f, m1 = 0.0f;
+                if (cudaEventElapsedTime(&m0, c.ev[0], c.ev[1]) == cudaSuccess &&
+                    cudaEventElapsedTime(&m1, c.ev[1], c.ev[2]) == cudaSuccess) {
+                    c.prof_launches[0] += 1;
+                    c.prof_ms[0] += m0;
+                    c.prof_launches[1] += 1;
+                    c.prof_ms[1] += m1;
+                }
             }
         }
         // true residuals; systems that fail continue from them
-        switch (P) {
-        case Prec::F64: kb_init<double><<<nch, kBThreads, 0, st>>>(kk, 0); break;
-        case Prec::F32: kb_init<float><<<nch, kBThreads, 0, st>>>(kk, 0); break;
-        case Prec::BF16: kb_init<__nv_bfloat16><<<nch, kBThreads, 0, st>>>(kk, 0); break;
+        switch (c.P) {
+        case Prec::F64: kb_init<double><<<c.nch, kBThreads, 0, st>>>(c.kk, 0); break;
+        case Prec::F32: kb_init<float><<<c.nch, kBThreads, 0, st>>>(c.kk, 0); break;
+        case Prec::BF16: kb_init<__nv_bfloat16><<<c.nch, kBThreads, 0, st>>>(c.kk, 0); break;
         }
-        kb_fin_true<<<1, 1024, 0, st>>>(kk, d_relres, d_nflag);
-        BCHK(cudaMemcpyAsync(h_pinned + 1, d_nflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        kb_fin_true<<<1, 1024, 0, st>>>(c.kk, c.d_relres, c.d_flags + 2);
+        c.kernel_launches += 2;
+        BCHK(cudaMemcpyAsync(c.h_pinned + 2, c.d_flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
         BCHK(cudaStreamSynchronize(st));
-        if (h_pinned[1] == 0) break;
-        kb_fin_init<<<1, 1024, 0, st>>>(kk, 1);
-        BCHK(cudaMemcpyAsync(h_pinned, d_nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (c.h_pinned[2] == 0) break;
+        kb_fin_init<<<1, 1024, 0, st>>>(c.kk, 1);
+        c.kernel_launches += 1;
+        BCHK(cudaMemcpyAsync(c.h_pinned, c.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
         BCHK(cudaStreamSynchronize(st));
-        nact = h_pinned[0];
+        nact = c.h_pinned[0];
     }
     std::vector<BScal> hs(nsys);
     std::vector<double> rel(nsys);
-    BCHK(cudaMemcpy(hs.data(), d_sc, nsys * sizeof(BScal), cudaMemcpyDeviceToHost));
-    BCHK(cudaMemcpy(rel.data(), d_relres, nsys * sizeof(double), cudaMemcpyDeviceToHost));
+    BCHK(cudaMemcpy(hs.data(), c.d_sc, nsys * sizeof(BScal), cudaMemcpyDeviceToHost));
+    BCHK(cudaMemcpy(rel.data(), c.d_relres, nsys * sizeof(double), cudaMemcpyDeviceToHost));
+    int result = SMG_OK;
     for (int s = 0; s < nsys; ++s) {
         iters[s] = hs[s].iters;
+        if (relres) relres[s] = rel[s];
+        if (c.profile) c.prof_bytes[0] += hs[s].iters * c.sys[s].cycle_bytes;
         if (hs[s].status != 0 && result == SMG_OK) result = hs[s].status;
         if (result == SMG_OK && !(rel[s] <= tol)) result = SMG_ERR_NOCONV;
     }
-    if (result == SMG_ERR_NOCONV) set_last_error("krylov_solve_batched: a system did not converge within maxit");
-    else if (result != SMG_OK) set_last_error("krylov_solve_batched: breakdown or NaN in a system");
+    if (result == SMG_ERR_NOCONV) set_last_error("batched solver: a system did not converge within maxit");
+    else if (result != SMG_OK) set_last_error("batched solver: breakdown or NaN in a system");
     return result;
+}
+
+}  // namespace
+
+extern "C" int smg_batched_setup(int nsys, const int *dims, int npre, int npost, int prec, smg_batched_handle *out,
+                                 void *stream) {
+    if (!out) {
+        set_last_error("null pointer");
+        return SMG_ERR_ARG;
+    }
+    *out = nullptr;
+    int rc = check_dims(nsys, dims);
+    if (rc != SMG_OK) return rc;
+    if (npre < 1 || npost < 0 || npre > 8 || npost > 8) {
+        set_last_error("1 <= npre <= 8 and 0 <= npost <= 8 required");
+        return SMG_ERR_ARG;
+    }
+    if (prec != SMG_FP32) {
+        set_last_error("the batched solver runs the FP32 cycle (SMG_FP32) only");
+        return SMG_ERR_ARG;
+    }
+    auto *c = new smg_batched_ctx();
+    c->nsys = nsys;
+    c->npre = npre;
+    c->npost = npost;
+    c->prec = prec;
+    c->P = static_cast<Prec>(prec);
+    rc = batched_build(*c, dims, static_cast<cudaStream_t>(stream));
+    if (rc != SMG_OK) {
+        const std::string msg = smg_last_error();
+        delete c;
+        set_last_error(msg);
+        return rc;
+    }
+    *out = c;
+    return SMG_OK;
+}
+
+extern "C" int smg_batched_solve(smg_batched_handle h, int variant, const double *const *b, double *const *x,
+                                 double tol, int maxit, int *iters, double *relres, void *stream) {
+    if (!h || !b || !x || !iters) {
+        set_last_error("null pointer");
+        return SMG_ERR_ARG;
+    }
+    if (variant != SMG_PCG && variant != SMG_FPCG && variant != SMG_PSD) {
+        set_last_error("variant must be SMG_PCG, SMG_FPCG or SMG_PSD");
+        return SMG_ERR_ARG;
+    }
+    if (!(tol > 0.0) || maxit < 0) {
+        set_last_error("tol > 0 and maxit >= 0 required");
+        return SMG_ERR_ARG;
+    }
+    for (int s = 0; s < h->nsys; ++s) {
+        if (!b[s] || !x[s]) {
+            set_last_error("null vector pointer");
+            return SMG_ERR_ARG;
+        }
+    }
+    return batched_solve(*h, variant, b, x, tol, maxit, iters, relres, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int smg_batched_destroy(smg_batched_handle h) {
+    if (h) {
+        cudaDeviceSynchronize();
+        delete h;
+    }
+    return SMG_OK;
+}
+
+extern "C" int smg_batched_info(smg_batched_handle h, int *threads, int *order, int *blocks, long long *tasks,
+                                long long *launches) {
+    if (!h || !threads || !order || !blocks || !tasks || !launches) {
+        set_last_error("null pointer");
+        return SMG_ERR_ARG;
+    }
+    *threads = h->tune.threads;
+    *order = h->tune.order;
+    *blocks = h->blocks;
+    *tasks = h->ntasks;
+    *launches = h->kernel_launches;
+    return SMG_OK;
+}
+
+extern "C" int smg_batched_set_profile(smg_batched_handle h, int on) {
+    if (!h || on < 0 || on > 1) {
+        set_last_error("a handle and on in {0, 1} required");
+        return SMG_ERR_ARG;
+    }
+    h->profile = on;
+    return SMG_OK;
+}
+
+extern "C" int smg_batched_profile_read(smg_batched_handle h, int which, long long *launches, double *ms,
+                                        double *bytes) {
+    if (!h || which < 0 || which > 1 || !launches || !ms || !bytes) {
+        set_last_error("bad arguments");
+        return SMG_ERR_ARG;
+    }
+    *launches = h->prof_launches[which];
+    *ms = h->prof_ms[which];
+    *bytes = h->prof_bytes[which];
+    h->prof_launches[which] = 0;
+    h->prof_ms[which] = 0.0;
+    h->prof_bytes[which] = 0.0;
+    return SMG_OK;
+}
+
+extern "C" int krylov_solve_batched(int nsys, const int *dims, int npre, int npost, int prec, const double *const *b,
+                                    double *const *x, double tol, int maxit, int *iters, void *stream) {
+    if (!b || !x || !iters || !dims) {
+        set_last_error("null pointer");
+        return SMG_ERR_ARG;
+    }
+    if (!(tol > 0.0) || maxit < 0) {
+        set_last_error("npre >= 1, npost >= 0, tol > 0, maxit >= 0 required");
+        return SMG_ERR_ARG;
+    }
+    if (nsys >= 1 && nsys <= 4096)
+        for (int s = 0; s < nsys; ++s) iters[s] = 0;
+    smg_batched_handle h = nullptr;
+    int rc = smg_batched_setup(nsys, dims, npre, npost, prec, &h, stream);
+    if (rc != SMG_OK) return rc;
+    rc = smg_batched_solve(h, SMG_FPCG, b, x, tol, maxit, iters, nullptr, stream);
+    const std::string msg = rc != SMG_OK ? std::string(smg_last_error()) : std::string();
+    smg_batched_destroy(h);
+    if (rc != SMG_OK) set_last_error(msg);
+    return rc;
 }
 
 extern "C" int smg_barrier_selftest(int extra_blocks, double limit_seconds, int *status, void *stream) {

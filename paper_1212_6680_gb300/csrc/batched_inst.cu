@@ -41,8 +41,7 @@ int SMG_CAT(set_persistent_smem_k, SMG_K)(Prec storage, size_t smem) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (storage) {
     case Prec::F32:
-        e = cudaFuncSetAttribute(persistent_vcycle_kernel<float, SMG_K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
+        e = raise_smem_attr(reinterpret_cast<const void *>(&persistent_vcycle_kernel<float, SMG_K>), smem);
         break;
     default: break;
     }

@@ -899,8 +899,7 @@ __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const __grid_consta
 
 template <class S, class C, int K, bool CL>
 int set_smem_attr(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(plane_relax_kernel<S, C, K, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_attr(reinterpret_cast<const void *>(&plane_relax_kernel<S, C, K, CL>), smem);
     if (e == cudaSuccess && CL)
         e = cudaFuncSetAttribute(plane_relax_kernel<S, C, K, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return static_cast<int>(e);

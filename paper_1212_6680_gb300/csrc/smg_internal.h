@@ -14,8 +14,12 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace smg {
@@ -46,6 +50,24 @@ void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H);
 
 // Sets the message smg_last_error() returns on the calling thread.
 void set_last_error(const std::string &msg);
+
+// The dynamic shared-memory limit of a kernel belongs to the kernel (per device), not to a
+// handle: it is only ever raised, so that a handle with a smaller layout never lowers it under
+// the launches of another handle that is still alive.
+inline cudaError_t raise_smem_attr(const void *kernel, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cur;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int &v = cur[std::make_pair(kernel, dev)];
+    const int want = std::max(v, static_cast<int>(smem));
+    if (want == v && v > 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    if (e == cudaSuccess) v = want;
+    return e;
+}
 
 // Arguments of one plane-relaxation launch (one colour of one z-level, all batch entries).
 struct PlaneRelaxArgs {

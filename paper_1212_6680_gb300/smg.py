@@ -28,7 +28,8 @@ PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}
 EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg_apply_batched",
            "smg_apply_A", "krylov_solve", "lobpcg_solve", "smg_destroy", "smg_last_error",
            "smg_profile_read", "smg_launch_count", "smg_check_conversions", "smg_apply_A_dot_static",
-           "krylov_solve_batched", "smg_barrier_selftest")
+           "krylov_solve_batched", "smg_barrier_selftest", "smg_batched_setup", "smg_batched_solve",
+           "smg_batched_destroy", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read")
 
 
 class SMGError(RuntimeError):
@@ -58,6 +59,13 @@ def _load():
     L.smg_apply_A_dot_static.argtypes = [i, i, i, vp, vp, vp, vp]
     L.krylov_solve_batched.argtypes = [i, vp, i, i, i, vp, vp, d, i, vp, vp]
     L.smg_barrier_selftest.argtypes = [i, d, ip, vp]
+    ll = ctypes.POINTER(ctypes.c_longlong)
+    L.smg_batched_setup.argtypes = [i, vp, i, i, i, ctypes.POINTER(vp), vp]
+    L.smg_batched_solve.argtypes = [vp, i, vp, vp, d, i, vp, vp, vp]
+    L.smg_batched_destroy.argtypes = [vp]
+    L.smg_batched_info.argtypes = [vp, ip, ip, ip, ll, ll]
+    L.smg_batched_set_profile.argtypes = [vp, i]
+    L.smg_batched_profile_read.argtypes = [vp, i, ll, dp, dp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -190,6 +198,53 @@ def krylov_solve_batched(dims, b_list, x_list, npre=1, npost=0, prec="fp32", tol
     if check:
         _check(rc, allow=(SMG_ERR_NOCONV,))
     return rc, it
+
+
+def smg_batched_setup(dims, npre=1, npost=0, prec="fp32", stream=None) -> int:
+    """dims: (nsys, 3) ints (nx, ny, nz).  Returns the batched handle."""
+    dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+    h = ctypes.c_void_p()
+    _check(_lib.smg_batched_setup(dims.shape[0], dims.ctypes.data, npre, npost, PRECISIONS.get(prec, prec),
+                                  ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def smg_batched_solve(h, variant, b_list, x_list, tol=1e-8, maxit=100, stream=None, check=True):
+    """b_list, x_list: per-system device tensors.  Returns (status, iters, relres) (numpy arrays)."""
+    nsys = len(b_list)
+    bp = (ctypes.c_void_p * nsys)(*[_ptr(t) for t in b_list])
+    xp = (ctypes.c_void_p * nsys)(*[_ptr(t) for t in x_list])
+    it = np.zeros(nsys, dtype=np.int32)
+    rel = np.zeros(nsys, dtype=np.float64)
+    rc = _lib.smg_batched_solve(ctypes.c_void_p(h), VARIANTS.get(variant, variant), ctypes.cast(bp, ctypes.c_void_p),
+                                ctypes.cast(xp, ctypes.c_void_p), ctypes.c_double(tol), maxit, it.ctypes.data,
+                                rel.ctypes.data, _stream(stream))
+    if check:
+        _check(rc, allow=(SMG_ERR_NOCONV,))
+    return rc, it, rel
+
+
+def smg_batched_destroy(h) -> None:
+    _check(_lib.smg_batched_destroy(ctypes.c_void_p(h)))
+
+
+def smg_batched_info(h) -> dict:
+    t, o, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    n, la = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.smg_batched_info(ctypes.c_void_p(h), ctypes.byref(t), ctypes.byref(o), ctypes.byref(b),
+                                 ctypes.byref(n), ctypes.byref(la)))
+    return {"threads": t.value, "order": o.value, "blocks": b.value, "tasks": n.value, "launches": la.value}
+
+
+def smg_batched_set_profile(h, on: int) -> None:
+    _check(_lib.smg_batched_set_profile(ctypes.c_void_p(h), on))
+
+
+def smg_batched_profile_read(h, which: int):
+    n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.smg_batched_profile_read(ctypes.c_void_p(h), which, ctypes.byref(n), ctypes.byref(ms),
+                                         ctypes.byref(by)))
+    return n.value, ms.value, by.value
 
 
 def smg_barrier_selftest(extra_blocks: int, limit_seconds: float = 0.5, stream=None) -> int:

@@ -190,6 +190,23 @@ def test_lobpcg_matches_closed_form(smg, shape, m, npost):
     assert np.abs(G - np.eye(m)).max() <= 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_handles_with_different_layouts_coexist(smg, orc, prec):
+    """A handle set up after another one, with the same x-line chunk but a smaller shared-memory
+    layout, must not break the first handle's launches."""
+    big, small = (96, 96, 24), (70, 6, 5)
+    with smg.Handle(*big, 1, 1, precision=prec) as hb, smg.Handle(*small, 1, 1, precision=prec) as hs:
+        for h, shape in ((hb, big), (hs, small), (hb, big)):
+            u = inputs.rhs(*shape, seed=61)
+            r = torch.from_numpy(u.ravel().copy()).cuda()
+            s = torch.empty_like(r)
+            smg.smg_apply(h.h, r, s)
+            torch.cuda.synchronize()
+            ref = orc.SMG(*shape, 1, 1).apply(u)
+            err = rel(s.cpu().numpy(), ref)
+            assert err <= (1e-12 if prec == "fp64" else 2e-5), (shape, err)
+
+
 def test_integer_pipe_conversions_match_hardware(smg):
     # the library's own FP32 <-> FP64 conversions against the hardware instructions, bit for bit:
     # random magnitudes over the whole float range, ties, carries into the exponent, overflow to
