@@ -189,6 +189,60 @@ int krylov_solve_batched(int nsys, const int *dims, int npre, int npost, int pre
  */
 int smg_barrier_selftest(int extra_blocks, double limit_seconds, int *status, void *stream);
 
+/*
+ * Learned post-correction (not in the paper; eq. (2), flexible PCG, is what admits a nonlinear
+ * preconditioner, and PSD admits one too).  After the SMG cycle s0 = T r, the residual
+ * rho = r - A s0 goes through a small network -- 3x3x3 convolutions 1 -> 16 -> 16 -> 1 channels,
+ * zero padding, no bias, ReLU after the first two layers, input divided by its RMS and output
+ * multiplied back -- giving delta; the result is s0 + delta when ||rho - A delta||_2 < ||rho||_2
+ * and s0 otherwise.  Weights: SMG_NET_WEIGHTS values, layer 1 [16][1][27], layer 2 [16][16][27],
+ * layer 3 [1][16][27], each [out channel][in channel][tap], tap (dz+1)*9 + (dy+1)*3 + (dx+1)
+ * weighting the input at (x+dx, y+dy, z+dz).  Activations are BF16 with FP32 accumulation
+ * (SMG_FP32 activations are offered by the handle-free calls for accuracy checks).
+ */
+#define SMG_NET_WEIGHTS 7776
+
+/* smg_set_learned -- attach (enable = 1) the correction with weights_bf16 (host, SMG_NET_WEIGHTS
+ * BF16 bit patterns, copied) to every smg_apply and krylov_solve of the handle, or detach it
+ * (enable = 0, weights ignored).  Meant for handles with npost = 0.  Resets the judge counters. */
+int smg_set_learned(smg_handle h, const void *weights_bf16, int enable);
+
+/* smg_learned_stats -- how many corrections were computed and how many the judge kept (host
+ * outputs; synchronises the device). */
+int smg_learned_stats(smg_handle h, long long *calls, long long *accepted);
+
+/*
+ * smg_collect_pairs -- training pairs along one flexible PCG solve of A x = b from x0 = 0 with
+ * the handle's cycle: before the k-th update, with s_k = T r_k,
+ *   rho_out[k] = r_k - A s_k   and   e_out[k] = xstar - x_k - s_k     (FP32, N values each),
+ * so that e_out[k] is the error left after the cycle when xstar solves A x = b.  b, xstar: device
+ * FP64; rho_out, e_out: device, max_pairs * N floats.  *npairs (host) receives the number of pairs
+ * written (at most max_pairs).  Stops at tol or maxit like krylov_solve; not converging is not
+ * an error here.
+ */
+int smg_collect_pairs(smg_handle h, const double *b, const double *xstar, double tol, int maxit, float *rho_out,
+                      float *e_out, int max_pairs, int *npairs, void *stream);
+
+/* smg_net_forward -- delta = rms(rho) Net(rho / rms(rho)) on an nx x ny x nz grid.  w: host
+ * FP32 [SMG_NET_WEIGHTS] (rounded to BF16 when act_prec = SMG_BF16); rho, delta: device FP64.
+ * act_prec: SMG_BF16 or SMG_FP32 activations.  Synchronises `stream`. */
+int smg_net_forward(int nx, int ny, int nz, int act_prec, const float *w, const double *rho, double *delta,
+                    void *stream);
+
+/* smg_net_loss_grad -- L = (e - delta)^T A (e - delta) / e^T A e for delta = the network's
+ * correction of rho, and dL/dw.  rho, e: device FP64; *loss: host; grad: host FP32
+ * [SMG_NET_WEIGHTS].  Synchronises `stream`. */
+int smg_net_loss_grad(int nx, int ny, int nz, int act_prec, const float *w, const double *rho, const double *e,
+                      double *loss, float *grad, void *stream);
+
+/* smg_net_train -- Adam (beta 0.9, 0.999, eps 1e-8, step size lr) over npairs pairs, one pair per
+ * step, `epochs` passes in an order shuffled from `seed`.  dims: host, 3 ints per pair; rho[i],
+ * e[i]: device FP32 arrays of pair i (layout of smg_collect_pairs).  w: host FP32
+ * [SMG_NET_WEIGHTS], initial weights in, trained weights out.  loss_hist: host, `epochs` mean
+ * losses.  Synchronises `stream` once per epoch. */
+int smg_net_train(int npairs, const int *dims, const float *const *rho, const float *const *e, int epochs, double lr,
+                  unsigned long long seed, int act_prec, float *w, double *loss_hist, void *stream);
+
 /* smg_destroy -- free the handle and everything it owns (NULL is accepted). */
 int smg_destroy(smg_handle h);
 

@@ -74,6 +74,11 @@ def lib():
         L.orc_net_forward.argtypes = i3 + [dp, dp, dp]
         L.orc_net_loss_grad.argtypes = i3 + [dp, dp, dp, dp]
         L.orc_net_loss_grad.restype = ctypes.c_double
+        L.orc_net_forward_ex.argtypes = i3 + [dp, dp, dp, ctypes.c_int]
+        L.orc_net_loss_grad_ex.argtypes = i3 + [dp, dp, dp, dp, ctypes.c_int]
+        L.orc_net_loss_grad_ex.restype = ctypes.c_double
+        L.orc_round_bf16.argtypes = [ctypes.c_double]
+        L.orc_round_bf16.restype = ctypes.c_double
         L.orc_learned_correct.argtypes = i3 + [dp, dp, dp]
         L.orc_smg_set_learned.argtypes = [vp, dp]
         L.orc_smg_learned_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -238,22 +243,28 @@ def conv3d_wgrad(x: np.ndarray, g: np.ndarray) -> np.ndarray:
     return out
 
 
-def net_forward(w, rho: np.ndarray) -> np.ndarray:
-    """delta = rms(rho) Net(rho / rms(rho)) for a (nz, ny, nx) residual."""
+def net_forward(w, rho: np.ndarray, act_bf16: bool = False) -> np.ndarray:
+    """delta = rms(rho) Net(rho / rms(rho)) for a (nz, ny, nx) residual (hidden activations
+    rounded to BF16 when act_bf16)."""
     w, rho = _f64(w).ravel(), _f64(rho)
     nz, ny, nx = rho.shape
     out = np.empty_like(rho)
-    lib().orc_net_forward(nx, ny, nz, _p(w), _p(rho), _p(out))
+    lib().orc_net_forward_ex(nx, ny, nz, _p(w), _p(rho), _p(out), int(act_bf16))
     return out
 
 
-def net_loss_grad(w, rho: np.ndarray, e: np.ndarray, want_grad=True):
+def net_loss_grad(w, rho: np.ndarray, e: np.ndarray, want_grad=True, act_bf16: bool = False):
     """(loss, gradient (7776,) or None) of L = (e - delta)^T A (e - delta) / e^T A e."""
     w, rho, e = _f64(w).ravel(), _f64(rho), _f64(e)
     nz, ny, nx = rho.shape
     g = np.empty(NET_WEIGHTS) if want_grad else None
-    loss = lib().orc_net_loss_grad(nx, ny, nz, _p(w), _p(rho), _p(e), _p(g) if want_grad else None)
+    loss = lib().orc_net_loss_grad_ex(nx, ny, nz, _p(w), _p(rho), _p(e), _p(g) if want_grad else None,
+                                      int(act_bf16))
     return loss, g
+
+
+def round_bf16(v: float) -> float:
+    return lib().orc_round_bf16(float(v))
 
 
 def learned_correct(w, r: np.ndarray, s0: np.ndarray):

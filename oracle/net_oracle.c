@@ -20,8 +20,13 @@
  *             s = s0 + delta when ||rho - A delta||_2 < ||rho||_2, else s = s0 (the judge).
  *
  * Activations are channel-major: a[c][(z*ny + y)*nx + x].
+ *
+ * Optionally (act_bf16 = 1) the two hidden activations are rounded to BF16 after the ReLU, as a
+ * BF16 implementation stores them; the ReLU masks of the backward pass then follow the rounded
+ * values.  Everything else stays FP64.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -98,6 +103,19 @@ void orc_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const double *i
                     }
 }
 
+/* IEEE binary32 rounding of v, then rounding to the nearest BF16 (8 significant bits), ties to
+ * even: the upper 16 bits of the binary32 after adding half an ulp of BF16 (0x7FFF plus the
+ * lowest kept bit). */
+double orc_round_bf16(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof(u));
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, sizeof(f));
+    return (double)f;
+}
+
 #define NET_C 16
 #define NET_W1 0
 #define NET_W2 (NET_C * 27)
@@ -112,21 +130,32 @@ static double rms_of(size_t n, const double *v)
 
 /* Forward pass keeping the pre-activations (h1, h2: NET_C*N each) for the backward pass. */
 static double net_forward_keep(int nx, int ny, int nz, const double *w, const double *rho, double *x0, double *h1,
-                               double *a1, double *h2, double *a2, double *y)
+                               double *a1, double *h2, double *a2, double *y, int act_bf16)
 {
     size_t n = npts(nx, ny, nz);
     double rms = rms_of(n, rho);
     double inv = rms > 0.0 ? 1.0 / rms : 0.0;
     for (size_t i = 0; i < n; ++i) x0[i] = rho[i] * inv;
     orc_conv3d(nx, ny, nz, 1, NET_C, w + NET_W1, x0, h1);
-    for (size_t i = 0; i < n * NET_C; ++i) a1[i] = h1[i] > 0.0 ? h1[i] : 0.0;
+    for (size_t i = 0; i < n * NET_C; ++i) {
+        a1[i] = h1[i] > 0.0 ? h1[i] : 0.0;
+        if (act_bf16) a1[i] = orc_round_bf16(a1[i]);
+    }
     orc_conv3d(nx, ny, nz, NET_C, NET_C, w + NET_W2, a1, h2);
-    for (size_t i = 0; i < n * NET_C; ++i) a2[i] = h2[i] > 0.0 ? h2[i] : 0.0;
+    for (size_t i = 0; i < n * NET_C; ++i) {
+        a2[i] = h2[i] > 0.0 ? h2[i] : 0.0;
+        if (act_bf16) a2[i] = orc_round_bf16(a2[i]);
+    }
     orc_conv3d(nx, ny, nz, NET_C, 1, w + NET_W3, a2, y);
     return rms;
 }
 
 void orc_net_forward(int nx, int ny, int nz, const double *w, const double *rho, double *delta)
+{
+    orc_net_forward_ex(nx, ny, nz, w, rho, delta, 0);
+}
+
+void orc_net_forward_ex(int nx, int ny, int nz, const double *w, const double *rho, double *delta, int act_bf16)
 {
     size_t n = npts(nx, ny, nz);
     double *x0 = (double *)malloc(sizeof(double) * n);
@@ -134,7 +163,7 @@ void orc_net_forward(int nx, int ny, int nz, const double *w, const double *rho,
     double *a1 = (double *)malloc(sizeof(double) * n * NET_C);
     double *h2 = (double *)malloc(sizeof(double) * n * NET_C);
     double *a2 = (double *)malloc(sizeof(double) * n * NET_C);
-    double rms = net_forward_keep(nx, ny, nz, w, rho, x0, h1, a1, h2, a2, delta);
+    double rms = net_forward_keep(nx, ny, nz, w, rho, x0, h1, a1, h2, a2, delta, act_bf16);
     for (size_t i = 0; i < n; ++i) delta[i] *= rms;
     free(x0);
     free(h1);
@@ -144,6 +173,12 @@ void orc_net_forward(int nx, int ny, int nz, const double *w, const double *rho,
 }
 
 double orc_net_loss_grad(int nx, int ny, int nz, const double *w, const double *rho, const double *e, double *grad)
+{
+    return orc_net_loss_grad_ex(nx, ny, nz, w, rho, e, grad, 0);
+}
+
+double orc_net_loss_grad_ex(int nx, int ny, int nz, const double *w, const double *rho, const double *e, double *grad,
+                            int act_bf16)
 {
     size_t n = npts(nx, ny, nz);
     double *x0 = (double *)malloc(sizeof(double) * n);
@@ -159,7 +194,7 @@ double orc_net_loss_grad(int nx, int ny, int nz, const double *w, const double *
     double *ga = (double *)malloc(sizeof(double) * n * NET_C);
     double *gh = (double *)malloc(sizeof(double) * n * NET_C);
 
-    double rms = net_forward_keep(nx, ny, nz, w, rho, x0, h1, a1, h2, a2, y);
+    double rms = net_forward_keep(nx, ny, nz, w, rho, x0, h1, a1, h2, a2, y, act_bf16);
     for (size_t i = 0; i < n; ++i) d[i] = e[i] - rms * y[i];
     orc_apply_A(nx, ny, nz, d, Ad);
     orc_apply_A(nx, ny, nz, e, Ae);
@@ -175,10 +210,10 @@ double orc_net_loss_grad(int nx, int ny, int nz, const double *w, const double *
         for (size_t i = 0; i < n; ++i) gy[i] = sc * Ad[i];
         orc_conv3d_wgrad(nx, ny, nz, NET_C, 1, a2, gy, grad + NET_W3);
         orc_conv3d_adj(nx, ny, nz, NET_C, 1, w + NET_W3, gy, ga);
-        for (size_t i = 0; i < n * NET_C; ++i) gh[i] = h2[i] > 0.0 ? ga[i] : 0.0;
+        for (size_t i = 0; i < n * NET_C; ++i) gh[i] = a2[i] > 0.0 ? ga[i] : 0.0;
         orc_conv3d_wgrad(nx, ny, nz, NET_C, NET_C, a1, gh, grad + NET_W2);
         orc_conv3d_adj(nx, ny, nz, NET_C, NET_C, w + NET_W2, gh, ga);
-        for (size_t i = 0; i < n * NET_C; ++i) gh[i] = h1[i] > 0.0 ? ga[i] : 0.0;
+        for (size_t i = 0; i < n * NET_C; ++i) gh[i] = a1[i] > 0.0 ? ga[i] : 0.0;
         orc_conv3d_wgrad(nx, ny, nz, 1, NET_C, x0, gh, grad + NET_W1);
     }
     free(x0);

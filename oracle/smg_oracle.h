@@ -73,6 +73,12 @@ void orc_conv3d_wgrad(int nx, int ny, int nz, int cin, int cout, const double *i
 void orc_net_forward(int nx, int ny, int nz, const double *w, const double *rho, double *delta);
 /* L = (e - delta)^T A (e - delta) / e^T A e and, if grad != NULL, dL/dw (7776). */
 double orc_net_loss_grad(int nx, int ny, int nz, const double *w, const double *rho, const double *e, double *grad);
+/* The same two with the hidden activations rounded to BF16 when act_bf16 = 1. */
+void orc_net_forward_ex(int nx, int ny, int nz, const double *w, const double *rho, double *delta, int act_bf16);
+double orc_net_loss_grad_ex(int nx, int ny, int nz, const double *w, const double *rho, const double *e, double *grad,
+                            int act_bf16);
+/* Round to binary32, then to the nearest BF16 (ties to even). */
+double orc_round_bf16(double v);
 /* s += delta(r - A s) when the judge accepts it; returns 1 if accepted. */
 int orc_learned_correct(int nx, int ny, int nz, const double *w, const double *r, double *s);
 /* Attach (w != NULL, copied) or detach (NULL) the learned post-correction of a handle:

@@ -13,6 +13,7 @@
 #include "../../include/smg.h"
 #include "krylov.h"
 #include "lobpcg.h"
+#include "net.h"
 #include "smg_internal.h"
 
 using namespace smg;
@@ -89,6 +90,14 @@ struct smg_ctx {
     std::vector<cudaEvent_t> event_pool;
     // LOBPCG state
     LobpcgWork lw;
+    // learned post-correction (smg_set_learned) and training-pair capture (smg_collect_pairs)
+    bool learned = false;
+    NetWork nw;
+    struct Capture {
+        const double *xstar = nullptr;
+        float *rho = nullptr, *e = nullptr;
+        int max = 0, count = 0;
+    } cap;
 
     long long N() const { return static_cast<long long>(nx) * ny * nz; }
     long long Nl(int l) const { return static_cast<long long>(nx) * ny * H.nz_l[l]; }
@@ -407,6 +416,19 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
             break;
         }
         if ((rc = run_cycle(h, 1, f0, u0, st)) != SMG_OK) return rc;
+        if (h->cap.count < h->cap.max) {
+            // training pair of this iteration: rho = r - A s, e = x* - x - s
+            const size_t off = static_cast<size_t>(h->cap.count) * h->N();
+            SMG_CUDA(net_capture(h->prec, h->nx, h->ny, h->nz, h->d_r, u0, x, h->cap.xstar, h->cap.rho + off,
+                                 h->cap.e + off, st));
+            h->cap.count += 1;
+            h->launches += 1;
+        }
+        if (h->learned) {
+            const long long l0 = h->nw.launches;
+            SMG_CUDA(net_learned_correct(h->nw, h->prec, h->nx, h->ny, h->nz, h->d_r, u0, st));
+            h->launches += h->nw.launches - l0;
+        }
         {
             RegionTimer rt(h, st, 4, 0.0);
             SMG_CUDA(kry_iteration_tail(h->prec, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, st));
@@ -522,11 +544,20 @@ int smg_apply_batched(smg_handle h, int nb, const double *R, double *S, void *st
     int rc;
     if ((rc = ensure_levels(h, nb)) != SMG_OK) return rc;
     const long long n = h->N() * nb;
-    if (h->prec == Prec::F64) return run_cycle(h, nb, R, S, st);
-    SMG_CUDA(launch_convert_to(h->prec, n, R, h->d_f[0], st));
-    if ((rc = run_cycle(h, nb, h->d_f[0], h->d_u[0], st)) != SMG_OK) return rc;
-    SMG_CUDA(launch_convert_from(h->prec, n, h->d_u[0], S, st));
-    h->launches += 2;
+    if (h->prec == Prec::F64) {
+        if ((rc = run_cycle(h, nb, R, S, st)) != SMG_OK) return rc;
+    } else {
+        SMG_CUDA(launch_convert_to(h->prec, n, R, h->d_f[0], st));
+        if ((rc = run_cycle(h, nb, h->d_f[0], h->d_u[0], st)) != SMG_OK) return rc;
+        SMG_CUDA(launch_convert_from(h->prec, n, h->d_u[0], S, st));
+        h->launches += 2;
+    }
+    if (h->learned) {
+        const long long l0 = h->nw.launches;
+        for (int b = 0; b < nb; ++b)
+            SMG_CUDA(net_learned_correct(h->nw, Prec::F64, h->nx, h->ny, h->nz, R + b * h->N(), S + b * h->N(), st));
+        h->launches += h->nw.launches - l0;
+    }
     return SMG_OK;
 }
 
@@ -631,6 +662,68 @@ int smg_check_conversions(long long n, const double *src, int *mismatches, void 
     return SMG_OK;
 }
 
+int smg_set_learned(smg_handle h, const void *weights_bf16, int enable) {
+    if (int rc = check_handle(h)) return rc;
+    if (enable != 0 && enable != 1) return fail(SMG_ERR_ARG, "enable must be 0 or 1");
+    if (!enable) {
+        h->learned = false;
+        return SMG_OK;
+    }
+    if (weights_bf16 == nullptr) return fail(SMG_ERR_ARG, "null weights");
+    // BF16 bit patterns widen exactly to FP32 (the upper half of the FP32 word)
+    const unsigned short *wb = static_cast<const unsigned short *>(weights_bf16);
+    std::vector<float> w(kNetWeights);
+    for (int i = 0; i < kNetWeights; ++i) {
+        const uint32_t bits = static_cast<uint32_t>(wb[i]) << 16;
+        std::memcpy(&w[i], &bits, sizeof(float));
+        if (!std::isfinite(w[i])) return fail(SMG_ERR_ARG, "weights must be finite");
+    }
+    SMG_CUDA(net_alloc(h->nw, h->N(), 0, false));
+    SMG_CUDA(cudaMemcpy(h->nw.w, w.data(), kNetWeights * sizeof(float), cudaMemcpyHostToDevice));
+    SMG_CUDA(cudaMemset(h->nw.sc, 0, sizeof(NetScal)));
+    h->learned = true;
+    return SMG_OK;
+}
+
+int smg_learned_stats(smg_handle h, long long *calls, long long *accepted) {
+    if (int rc = check_handle(h)) return rc;
+    if (calls == nullptr || accepted == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    *calls = *accepted = 0;
+    if (h->nw.sc == nullptr) return SMG_OK;
+    NetScal sc;
+    SMG_CUDA(cudaMemcpy(&sc, h->nw.sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    *calls = sc.calls;
+    *accepted = sc.accepts;
+    return SMG_OK;
+}
+
+int smg_collect_pairs(smg_handle h, const double *b, const double *xstar, double tol, int maxit, float *rho_out,
+                      float *e_out, int max_pairs, int *npairs, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (npairs) *npairs = 0;
+    if (!b || !xstar || !rho_out || !e_out || !npairs) return fail(SMG_ERR_ARG, "null pointer");
+    if (max_pairs < 1 || maxit < 0 || !(tol > 0.0)) return fail(SMG_ERR_ARG, "max_pairs >= 1, maxit >= 0, tol > 0");
+    if (!is_device_ptr(b) || !is_device_ptr(xstar) || !is_device_ptr(rho_out) || !is_device_ptr(e_out))
+        return fail(SMG_ERR_ARG, "b, xstar, rho_out, e_out must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *x = nullptr;
+    SMG_CUDA(cudaMalloc(&x, static_cast<size_t>(h->N()) * sizeof(double)));
+    cudaMemsetAsync(x, 0, static_cast<size_t>(h->N()) * sizeof(double), st);
+    h->cap.xstar = xstar;
+    h->cap.rho = rho_out;
+    h->cap.e = e_out;
+    h->cap.max = max_pairs;
+    h->cap.count = 0;
+    int iters = 0;
+    double relres = 0.0;
+    const int rc = krylov_device(h, SMG_FPCG, b, x, tol, maxit, &iters, &relres, st);
+    *npairs = h->cap.count;
+    h->cap = smg_ctx::Capture();
+    cudaStreamSynchronize(st);
+    cudaFree(x);
+    return (rc == SMG_ERR_NOCONV) ? SMG_OK : rc;
+}
+
 int smg_launch_count(smg_handle h, long long *count) {
     if (int rc = check_handle(h)) return rc;
     if (count == nullptr) return fail(SMG_ERR_ARG, "null pointer");
@@ -661,6 +754,7 @@ int smg_destroy(smg_handle h) {
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
     lobpcg_free(h->lw);
+    net_free(h->nw);
     delete h;
     return SMG_OK;
 }

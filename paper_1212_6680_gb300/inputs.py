@@ -71,3 +71,15 @@ def uneven_dims(nsys: int, lo: int = 32, hi: int = 96, seed: int = 1000) -> np.n
         z = splitmix64(seed + i, 3)
         out[i] = lo + (z % np.uint64(hi - lo + 1)).astype(np.int64)
     return out
+
+
+def net_init_weights(seed: int = 77, last_scale: float = 0.1) -> np.ndarray:
+    """Initial weights of the learned post-correction (7776 values in the layout of the C ABI:
+    [16][1][27], [16][16][27], [1][16][27]): Gaussian with standard deviation sqrt(2 / fan_in)
+    (fan_in = input channels x 27), the last layer scaled by `last_scale` so that training starts
+    near a zero correction."""
+    g = gaussian(seed, 16 * 27 + 16 * 16 * 27 + 16 * 27)
+    w1 = g[: 16 * 27] * np.sqrt(2.0 / 27)
+    w2 = g[16 * 27: 16 * 27 + 16 * 16 * 27] * np.sqrt(2.0 / (16 * 27))
+    w3 = g[16 * 27 + 16 * 16 * 27:] * np.sqrt(2.0 / (16 * 27)) * last_scale
+    return np.concatenate([w1, w2, w3])

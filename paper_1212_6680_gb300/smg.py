@@ -29,7 +29,10 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "smg_apply_A", "krylov_solve", "lobpcg_solve", "smg_destroy", "smg_last_error",
            "smg_profile_read", "smg_launch_count", "smg_check_conversions", "smg_apply_A_dot_static",
            "krylov_solve_batched", "smg_barrier_selftest", "smg_batched_setup", "smg_batched_solve",
-           "smg_batched_destroy", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read")
+           "smg_batched_destroy", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
+           "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
+           "smg_net_train")
+NET_WEIGHTS = 7776
 
 
 class SMGError(RuntimeError):
@@ -66,6 +69,12 @@ def _load():
     L.smg_batched_info.argtypes = [vp, ip, ip, ip, ll, ll]
     L.smg_batched_set_profile.argtypes = [vp, i]
     L.smg_batched_profile_read.argtypes = [vp, i, ll, dp, dp]
+    L.smg_set_learned.argtypes = [vp, vp, i]
+    L.smg_learned_stats.argtypes = [vp, ll, ll]
+    L.smg_collect_pairs.argtypes = [vp, vp, vp, d, i, vp, vp, i, ip, vp]
+    L.smg_net_forward.argtypes = [i, i, i, i, vp, vp, vp, vp]
+    L.smg_net_loss_grad.argtypes = [i, i, i, i, vp, vp, vp, dp, vp, vp]
+    L.smg_net_train.argtypes = [i, vp, vp, vp, i, d, ctypes.c_ulonglong, i, vp, vp, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -245,6 +254,76 @@ def smg_batched_profile_read(h, which: int):
     _check(_lib.smg_batched_profile_read(ctypes.c_void_p(h), which, ctypes.byref(n), ctypes.byref(ms),
                                          ctypes.byref(by)))
     return n.value, ms.value, by.value
+
+
+def bf16_bits(w) -> np.ndarray:
+    """FP32 values as BF16 bit patterns (round to nearest, ties to even) -- the weight format of
+    smg_set_learned."""
+    u = np.ascontiguousarray(np.asarray(w, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def smg_set_learned(h, w, enable=True) -> None:
+    """w: SMG_NET_WEIGHTS values (FP32/FP64, rounded to BF16 here) or BF16 bit patterns (uint16)."""
+    if not enable:
+        _check(_lib.smg_set_learned(h, None, 0))
+        return
+    w = np.asarray(w)
+    bits = w if w.dtype == np.uint16 else bf16_bits(w)
+    bits = np.ascontiguousarray(bits.ravel())
+    assert bits.size == NET_WEIGHTS
+    _check(_lib.smg_set_learned(h, bits.ctypes.data, 1))
+
+
+def smg_learned_stats(h):
+    c, a = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.smg_learned_stats(h, ctypes.byref(c), ctypes.byref(a)))
+    return c.value, a.value
+
+
+def smg_collect_pairs(h, b, xstar, rho_out, e_out, max_pairs, tol=1e-8, maxit=100, stream=None) -> int:
+    n = ctypes.c_int(0)
+    _check(_lib.smg_collect_pairs(h, _ptr(b), _ptr(xstar), tol, maxit, _ptr(rho_out), _ptr(e_out), max_pairs,
+                                  ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def _w32(w):
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float32).ravel())
+    assert w.size == NET_WEIGHTS
+    return w
+
+
+def smg_net_forward(dims, act, w, rho, delta, stream=None) -> None:
+    nx, ny, nz = map(int, dims)
+    w = _w32(w)
+    _check(_lib.smg_net_forward(nx, ny, nz, PRECISIONS.get(act, act), w.ctypes.data, _ptr(rho), _ptr(delta),
+                                _stream(stream)))
+
+
+def smg_net_loss_grad(dims, act, w, rho, e, stream=None):
+    nx, ny, nz = map(int, dims)
+    w = _w32(w)
+    loss = ctypes.c_double()
+    g = np.zeros(NET_WEIGHTS, dtype=np.float32)
+    _check(_lib.smg_net_loss_grad(nx, ny, nz, PRECISIONS.get(act, act), w.ctypes.data, _ptr(rho), _ptr(e),
+                                  ctypes.byref(loss), g.ctypes.data, _stream(stream)))
+    return loss.value, g
+
+
+def smg_net_train(dims_list, rho_list, e_list, w, epochs=3, lr=1e-3, seed=0, act="bf16", stream=None):
+    """Returns (trained FP32 weights, per-epoch mean loss)."""
+    npairs = len(rho_list)
+    dims = np.ascontiguousarray(np.asarray(dims_list, dtype=np.int32).reshape(-1, 3))
+    assert dims.shape[0] == npairs == len(e_list)
+    rp = (ctypes.c_void_p * npairs)(*[_ptr(t) for t in rho_list])
+    ep = (ctypes.c_void_p * npairs)(*[_ptr(t) for t in e_list])
+    w = _w32(w).copy()
+    hist = np.zeros(epochs, dtype=np.float64)
+    _check(_lib.smg_net_train(npairs, dims.ctypes.data, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(ep, ctypes.c_void_p),
+                              epochs, lr, seed, PRECISIONS.get(act, act), w.ctypes.data, hist.ctypes.data,
+                              _stream(stream)))
+    return w, hist
 
 
 def smg_barrier_selftest(extra_blocks: int, limit_seconds: float = 0.5, stream=None) -> int:

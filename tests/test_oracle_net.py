@@ -173,3 +173,84 @@ def test_fpcg_with_jacobi_post_step_converges_no_slower(orc):
     learned = orc.krylov(b, "fpcg", h, tol=1e-8)
     assert learned["status"] == 0 and learned["relres"] <= 1e-8
     assert learned["iters"] <= plain["iters"]
+
+
+@pytest.mark.parametrize("v,r", [(1.0 + 2.0**-8, 1.0),                 # tie -> even (1.0)
+                                 (1.0 + 3 * 2.0**-9, 1.0 + 2.0**-7),   # nearest
+                                 (1.0 + 2.0**-7 + 2.0**-8, 1.0 + 2.0**-6),  # tie -> even
+                                 (-1.0 - 3 * 2.0**-9, -1.0 - 2.0**-7),
+                                 (0.15625, 0.15625),                    # representable: unchanged
+                                 (3.0e38, None)])
+def test_round_bf16_known_values(orc, v, r):
+    if r is None:  # large finite value: stays finite, relative error below 2^-8
+        out = orc.round_bf16(v)
+        assert np.isfinite(out) and abs(out - v) <= 2.0**-8 * v
+        return
+    assert orc.round_bf16(v) == r
+
+
+def _bf16(x):
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _restated_grad(orc, w, rho, e, rnd):
+    """The loss gradient written with scipy correlations (an independent restatement of the
+    backward pass), hidden activations passed through `rnd`."""
+    def conv(wl, x):
+        return np.stack([sum(ndimage.correlate(x[ci], wl[co, ci].reshape(3, 3, 3), mode="constant")
+                             for ci in range(wl.shape[1])) for co in range(wl.shape[0])])
+
+    def conv_t(wl, g):
+        return np.stack([sum(ndimage.correlate(g[co], wl[co, ci].reshape(3, 3, 3)[::-1, ::-1, ::-1], mode="constant")
+                             for co in range(wl.shape[0])) for ci in range(wl.shape[1])])
+
+    def wgrad(x, g):
+        nz, ny, nx = x.shape[1:]
+        xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (1, 1)))
+        out = np.zeros((g.shape[0], x.shape[0], 27))
+        for t in range(27):
+            dz, dy, dx = t // 9, (t // 3) % 3, t % 3
+            out[:, :, t] = np.einsum("opqr,ipqr->oi", g, xp[:, dz:dz + nz, dy:dy + ny, dx:dx + nx])
+        return out
+
+    w1, w2, w3 = orc.split_weights(w)
+    rms = np.sqrt((rho ** 2).mean())
+    x0 = rho / rms
+    a1 = rnd(np.maximum(conv(w1, x0[None]), 0))
+    a2 = rnd(np.maximum(conv(w2, a1), 0))
+    d = e - rms * conv(w3, a2)[0]
+    gy = -2 * rms / np.vdot(e, D_apply(e)) * D_apply(d)
+    gh2 = conv_t(w3, gy[None]) * (a2 > 0)
+    gh1 = conv_t(w2, gh2) * (a1 > 0)
+    return np.concatenate([wgrad(x0[None], gh1).ravel(), wgrad(a1, gh2).ravel(), wgrad(a2, gy[None]).ravel()])
+
+
+def D_apply(u):
+    """7-point Dirichlet Laplacian with numpy slicing (independent of the oracle's stencil)."""
+    out = 6.0 * u
+    out[1:] -= u[:-1]
+    out[:-1] -= u[1:]
+    out[:, 1:] -= u[:, :-1]
+    out[:, :-1] -= u[:, 1:]
+    out[:, :, 1:] -= u[:, :, :-1]
+    out[:, :, :-1] -= u[:, :, 1:]
+    return out
+
+
+@pytest.mark.parametrize("act_bf16", [False, True])
+def test_loss_gradient_matches_scipy_restatement(orc, act_bf16):
+    nx, ny, nz = 9, 7, 6
+    w = _bf16(inputs.net_init_weights(seed=111, last_scale=1.0))
+    rho = inputs.rhs(nx, ny, nz, seed=112)
+    e = inputs.rhs(nx, ny, nz, seed=113)
+    _, g = orc.net_loss_grad(w, rho, e, act_bf16=act_bf16)
+    ref = _restated_grad(orc, w, rho, e, _bf16 if act_bf16 else (lambda v: v))
+    for lo, hi in ((0, 432), (432, 7344), (7344, 7776)):
+        assert np.linalg.norm(g[lo:hi] - ref[lo:hi]) <= 1e-10 * np.linalg.norm(ref[lo:hi])
+    # rounding the activations moves the gradient by a measurable amount (why the BF16 GPU path
+    # is held to the BF16-activation oracle)
+    if act_bf16:
+        _, g64 = orc.net_loss_grad(w, rho, e)
+        assert np.linalg.norm(g - g64) > 1e-4 * np.linalg.norm(g64)
