@@ -41,8 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fpcg128", "batched64"], default="fpcg128",
-                    help="fpcg128: one 128^3 system (default); batched64: 64 uneven systems, sides in {32..96}")
+    ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256"], default="fpcg128",
+                    help="fpcg128: one 128^3 system (default); batched64: 64 uneven systems, sides in {32..96}; "
+                         "lobpcg128: 16 smallest eigenpairs at 128^3; learned256: learned post-correction at 256^3")
     return ap.parse_args()
 
 
@@ -178,6 +179,36 @@ def run_reference(args):
 
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload in ("lobpcg128", "learned256"):
+        from paper_1212_6680_gb300 import inputs as _in
+
+        times, sample = [], ""
+        for _ in range(args.steps):
+            if args.workload == "lobpcg128":
+                from oracle import lobpcg as olob
+
+                oracle.build()
+                X0 = _in.initial_block(NX, NY, NZ, LOB_M, seed=7)
+                t0 = time.perf_counter()
+                olob.lobpcg((NZ, NY, NX), np.ascontiguousarray(X0.T), oracle.SMG(NX, NY, NZ, 1, 0), tol=TOL, maxit=1)
+                t1 = time.perf_counter() - t0
+                times.append(t1 * 20)
+                sample = f"oracle LOBPCG set-up + 1 iteration at 128^3, m=16 ({t1:.1f} s) x 20 iterations"
+            else:
+                v, t1 = oracle_learned_sample(_in.net_init_weights(seed=77), 9)
+                times.append(v)
+                sample = (f"one oracle application of the learned preconditioner at 64^3 ({t1:.1f} s) x 64 points "
+                          f"x 9 iterations")
+        v = statistics.mean(times)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": (LOB_WORKLOAD if args.workload == "lobpcg128" else LEARNED_WORKLOAD)
+                           + " (FP64 CPU oracle, bounded sample)"},
+                "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     if args.workload == "batched64":
         times = []
@@ -523,12 +554,326 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def _dist_init():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local, dist
+
+
+def _timed(fn, steps, warmup, barrier, flush, stream):
+    """Per-step device seconds of fn() (L2 flushed before each), after `warmup` untimed calls."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    out, times = None, []
+    for _ in range(steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times, out
+
+
+def closed_form_smallest(nx, ny, nz, m):
+    """The m smallest eigenvalues of the 7-point Dirichlet Laplacian with unit spacing."""
+    ev = [4 * np.sin(np.pi * np.arange(1, n + 1) / (2 * (n + 1))) ** 2 for n in (nx, ny, nz)]
+    lam = (ev[2][:, None, None] + ev[1][None, :, None] + ev[0][None, None, :]).ravel()
+    return np.sort(lam)[:m]
+
+
+LOB_M = 16
+LOB_WORKLOAD = ("LOBPCG-SMG(1,0): 16 smallest eigenpairs, 128^3 7-point Dirichlet Laplacian, Gaussian initial "
+                "block, V-cycle FP32 applied to all 16 vectors per launch, FP64 Rayleigh-Ritz, tol 1e-8")
+
+
+def run_lobpcg(args):
+    import torch
+
+    from paper_1212_6680_gb300 import build as _build
+    from paper_1212_6680_gb300 import inputs
+
+    world, rank, local, dist = _dist_init()
+    _build.build()
+    from paper_1212_6680_gb300 import smg
+
+    n = NX * NY * NZ
+    X0 = inputs.initial_block(NX, NY, NZ, LOB_M, seed=7)
+    X0d = torch.from_numpy(np.ascontiguousarray(X0).ravel().copy()).cuda()
+    X = torch.empty_like(X0d)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ref = closed_form_smallest(NX, NY, NZ, LOB_M)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def arm(npost, prec, steps, warmup, profile=False):
+        h = smg.smg_setup(NX, NY, NZ, 1, npost)
+        smg.smg_set_precision(h, prec)
+        res = {}
+
+        def once():
+            X.copy_(X0d)
+            rc, it, lam = smg.lobpcg_solve(h, LOB_M, X, tol=TOL, maxit=200)
+            assert rc == smg.SMG_OK, smg.smg_last_error()
+            return it, lam
+        if profile:
+            for _ in range(warmup):
+                once()
+            smg.smg_set_option(h, smg.SMG_OPT_PROFILE, 1)
+            smg.smg_profile_read(h, 0)
+            l0 = smg.smg_launch_count(h)
+            with ClockSampler(local) as clk:
+                times, (it, lam) = _timed(once, steps, 0, barrier, flush, stream)
+            res["launches"] = smg.smg_launch_count(h) - l0
+            res["prof"] = smg.smg_profile_read(h, 0)
+            res["clocks"] = clk.summary()
+        else:
+            times, (it, lam) = _timed(once, steps, warmup, barrier, flush, stream)
+        smg.smg_destroy(h)
+        err = float(np.max(np.abs(lam - ref) / ref))
+        assert err <= 1e-10, err
+        res.update({"s": statistics.mean(times), "iters": it, "max_rel_eig_err": err})
+        return res
+
+    main = arm(0, "fp32", args.steps, args.warmup, profile=True)
+    k2 = max(1, min(args.steps, 2))
+    a64 = arm(0, "fp64", k2, 1)
+    a11 = arm(1, "fp32", k2, 1)
+    # end to end: the initial block from pinned host memory, eigenvectors and values back
+    Xh = torch.from_numpy(np.ascontiguousarray(X0).ravel().copy()).pin_memory()
+    Xo = torch.empty(Xh.numel(), dtype=torch.float64).pin_memory()
+    h = smg.smg_setup(NX, NY, NZ, 1, 0)
+    smg.smg_set_precision(h, "fp32")
+
+    def e2e_once():
+        X.copy_(Xh, non_blocking=True)
+        rc, it, lam = smg.lobpcg_solve(h, LOB_M, X, tol=TOL, maxit=200)
+        Xo.copy_(X, non_blocking=True)
+        return rc
+    te, _ = _timed(e2e_once, max(1, min(args.steps, 2)), 1, barrier, flush, stream)
+    smg.smg_destroy(h)
+    t_step = main["s"]
+    t_max = t_step
+    if dist is not None:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    pl, pms, pbytes = main["prof"]
+    achieved = (pbytes / 1e9) / (pms / 1e3) if pms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "plane_relax_kernel<float,float,4> (finest level, 16 vectors per launch)",
+                "launches": pl, "avg_launch_us": (pms * 1e3 / pl) if pl else None,
+                "algorithmic_bytes_per_launch": (pbytes / pl) if pl else None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import lobpcg as olob
+
+        oracle.build()
+        T = oracle.SMG(NX, NY, NZ, 1, 0)
+        t0 = time.perf_counter()
+        olob.lobpcg((NZ, NY, NX), np.ascontiguousarray(X0.T), T, tol=TOL, maxit=1)
+        t1 = time.perf_counter() - t0
+        cpu = {"value": t1 * max(main["iters"], 1), "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle LOBPCG set-up + 1 iteration at 128^3, m=16 ({t1:.1f} s), scaled by the GPU's "
+                         f"{main['iters']} iterations, single thread"}
+    line = {
+        "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": LOB_WORKLOAD, "grid": [NX, NY, NZ], "m": LOB_M, "npre": 1, "npost": 0,
+                   "cycle_precision": "fp32", "iters": main["iters"],
+                   "max_rel_eig_err_vs_closed_form": main["max_rel_eig_err"],
+                   "fp64_cycle_s": a64["s"], "fp64_cycle_iters": a64["iters"],
+                   "balanced_11_s": a11["s"], "balanced_11_iters": a11["iters"],
+                   "l2": "256 MB buffer written before every timed solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": statistics.mean(te), "unit": "s", "h2d_bytes_per_step": n * LOB_M * 8,
+                "d2h_bytes_per_step": n * LOB_M * 8 + LOB_M * 8},
+        "gpu_launches": main["launches"], "clocks": main["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+LN = 256
+LEARNED_WORKLOAD = ("FPCG-SMG(1,0) with the learned post-correction, 256^3 7-point Dirichlet Laplacian, V-cycle "
+                    "FP32, network BF16/FP32-accumulate, Krylov FP64, tol 1e-8; network trained on GPU on pairs "
+                    "from 200 seeded solves with sides in {64..128}")
+
+
+def oracle_learned_sample(w, iters):
+    """Seconds of one oracle application of the learned preconditioner at 64^3, scaled to 256^3
+    (x64 points) and to `iters` iterations; returns (scaled value, raw seconds)."""
+    import oracle
+    from paper_1212_6680_gb300 import inputs
+
+    oracle.build()
+    T = oracle.SMG(64, 64, 64, 1, 0)
+    T.set_learned(np.asarray(w, dtype=np.float64))
+    r = inputs.rhs(64, 64, 64, seed=0)
+    t0 = time.perf_counter()
+    T.apply(r)
+    t1 = time.perf_counter() - t0
+    return t1 * 64 * iters, t1
+
+
+def run_learned(args):
+    import torch
+
+    from paper_1212_6680_gb300 import build as _build
+    from paper_1212_6680_gb300 import inputs
+
+    world, rank, local, dist = _dist_init()
+    _build.build()
+    from paper_1212_6680_gb300 import learned, smg
+
+    w, tinfo = learned.train(nsys=200, lo=64, hi=128, epochs=4, lr=1e-3)
+    n = LN ** 3
+    b_np = inputs.rhs(LN, LN, LN, seed=0).ravel().copy()
+    b = torch.from_numpy(b_np).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def arm(npost, prec, use_w, steps, warmup, profile=False):
+        h = smg.smg_setup(LN, LN, LN, 1, npost)
+        smg.smg_set_precision(h, prec)
+        if use_w:
+            smg.smg_set_learned(h, w)
+
+        def once():
+            x.zero_()
+            rc, it, res = smg.krylov_solve(h, "fpcg", b, x, TOL, 100)
+            assert rc == smg.SMG_OK and res <= TOL, (rc, res)
+            return it, res
+        out = {}
+        if profile:
+            for _ in range(warmup):
+                once()
+            smg.smg_set_option(h, smg.SMG_OPT_PROFILE, 1)
+            smg.smg_profile_read(h, 0)
+            smg.smg_profile_read(h, 5)
+            l0 = smg.smg_launch_count(h)
+            with ClockSampler(local) as clk:
+                times, (it, res) = _timed(once, steps, 0, barrier, flush, stream)
+            out["launches"] = smg.smg_launch_count(h) - l0
+            out["prof0"] = smg.smg_profile_read(h, 0)
+            out["prof5"] = smg.smg_profile_read(h, 5)
+            out["clocks"] = clk.summary()
+        else:
+            times, (it, res) = _timed(once, steps, warmup, barrier, flush, stream)
+        if use_w:
+            out["judge"] = smg.smg_learned_stats(h)
+        smg.smg_destroy(h)
+        out.update({"s": statistics.mean(times), "iters": it, "relres": res})
+        return out
+
+    main = arm(0, "fp32", True, args.steps, args.warmup, profile=True)
+    k2 = max(1, min(args.steps, 3))
+    plain = arm(0, "fp32", False, k2, 1)
+    bal = arm(1, "fp32", False, k2, 1)
+    f64 = arm(0, "fp64", False, k2, 1)
+    # end to end through the C ABI with host buffers
+    h = smg.smg_setup(LN, LN, LN, 1, 0)
+    smg.smg_set_precision(h, "fp32")
+    smg.smg_set_learned(h, w)
+    bh = torch.from_numpy(b_np).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+
+    def e2e_once():
+        xh.zero_()
+        return smg.krylov_solve(h, "fpcg", bh.numpy(), xh.numpy(), TOL, 100)
+    te, _ = _timed(e2e_once, k2, 1, barrier, flush, stream)
+    smg.smg_destroy(h)
+    t_max = main["s"]
+    if dist is not None:
+        tt = torch.tensor([t_max], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    pl, pms, pflops = main["prof5"]
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock (TFLOP/s)
+    achieved = (pflops / 1e12) / (pms / 1e3) if pms > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                "kernel": "learned correction (3 convolutions on FP32 CUDA cores + residual, judge, update)",
+                "launches": pl, "avg_region_us": (pms * 1e3 / pl) if pl else None,
+                "flops_per_region": (pflops / pl) if pl else None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+    l0n, l0ms, l0b = main["prof0"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        v, t1 = oracle_learned_sample(w, main["iters"])
+        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle application of the learned preconditioner at 64^3 ({t1:.1f} s), scaled by "
+                         f"64x the points and the GPU's {main['iters']} iterations (Krylov work not included), "
+                         f"single thread"}
+    line = {
+        "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
+        "config": {"workload": LEARNED_WORKLOAD, "grid": [LN, LN, LN], "variant": "fpcg", "npre": 1, "npost": 0,
+                   "iters": main["iters"], "true_relres": main["relres"], "judge_calls_accepted": main["judge"],
+                   "plain_10_fp32_s": plain["s"], "plain_10_fp32_iters": plain["iters"],
+                   "balanced_11_fp32_s": bal["s"], "balanced_11_fp32_iters": bal["iters"],
+                   "plain_10_fp64_s": f64["s"], "plain_10_fp64_iters": f64["iters"],
+                   "speedup_vs_fp64": f64["s"] / main["s"], "speedup_vs_plain_10": plain["s"] / main["s"],
+                   "speedup_vs_balanced_11": bal["s"] / main["s"],
+                   "level0_relax_avg_us": (l0ms * 1e3 / l0n) if l0n else None,
+                   "training": tinfo, "l2": "256 MB buffer written before every timed solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": statistics.mean(te), "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": main["launches"], "clocks": main["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64":
         run_batched(args)
+    elif args.workload == "lobpcg128":
+        run_lobpcg(args)
+    elif args.workload == "learned256":
+        run_learned(args)
     else:
         run_ours(args)
 

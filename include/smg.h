@@ -243,6 +243,16 @@ int smg_net_loss_grad(int nx, int ny, int nz, int act_prec, const float *w, cons
 int smg_net_train(int npairs, const int *dims, const float *const *rho, const float *const *e, int epochs, double lr,
                   unsigned long long seed, int act_prec, float *w, double *loss_hist, void *stream);
 
+/* smg_net_set_tensor_cores -- process-wide choice for the BF16 16 -> 16 channel layer: 1 (the
+ * default) runs it on the tcgen05 tensor cores, 0 on the CUDA cores (FP32 FMAs, the same BF16
+ * inputs and rounding).  Takes effect at the next launch; not for concurrent use with solves. */
+int smg_net_set_tensor_cores(int on);
+
+/* smg_net_tc_status -- *err (host) = 1 if a tensor-core layer launch gave up waiting for its
+ * accumulators (bounded wait; its output is then incomplete) since the last call, else 0; clears
+ * the flag.  Synchronises the device. */
+int smg_net_tc_status(int *err);
+
 /* smg_destroy -- free the handle and everything it owns (NULL is accepted). */
 int smg_destroy(smg_handle h);
 
@@ -255,7 +265,9 @@ const char *smg_last_error(void);
  * algorithmic bytes (vector elements the launches must read and write), by class `which`:
  * 0 plane relaxation on the finest level, 1 plane relaxation on the other levels except the
  * coarsest, 2 the one-plane coarsest solve, 3 restriction and prolongation, 4 the Krylov
- * kernels of each iteration (classes 1-4 are timed only with SMG_OPT_PROFILE = 2).
+ * kernels of each iteration, 5 the learned post-correction of each iteration (its "bytes" are
+ * the convolutions' flops, 2 x 27 x 288 per point) (classes 1-4 are timed only with
+ * SMG_OPT_PROFILE = 2; classes 0 and 5 with either 1 or 2).
  * Reading resets the counters of that class.  Synchronises the device.
  */
 int smg_profile_read(smg_handle h, int which, long long *launches, double *ms, double *bytes);

@@ -38,8 +38,8 @@ constexpr size_t kSmemBudget = 227 * 1024;  // the most dynamic shared memory a 
 
 // profiling classes: 0 plane relaxation on the finest level, 1 plane relaxation on the other
 // levels (all but the coarsest), 2 the one-plane coarsest solve, 3 restriction + prolongation,
-// 4 the Krylov kernels of one iteration
-constexpr int kProfClasses = 5;
+// 4 the Krylov kernels of one iteration, 5 the learned post-correction of one iteration
+constexpr int kProfClasses = 6;
 
 struct ProfClass {
     long long launches = 0;
@@ -198,7 +198,7 @@ cudaEvent_t take_event(smg_ctx *h) {
     return e;
 }
 
-// Event pair around a non-relaxation region (profile mode 2 only).
+// Event pair around a non-relaxation region (profile mode 2; the learned correction also in mode 1).
 struct RegionTimer {
     smg_ctx *h;
     cudaStream_t st;
@@ -206,7 +206,8 @@ struct RegionTimer {
     double bytes;
     cudaEvent_t e0 = nullptr;
     RegionTimer(smg_ctx *h_, cudaStream_t st_, int cls_, double bytes_) : h(h_), st(st_), cls(cls_), bytes(bytes_) {
-        if (h->profile == 2) {
+        // the learned correction (class 5) is also timed in profile mode 1, beside level 0
+        if (h->profile == 2 || (h->profile == 1 && cls == 5)) {
             e0 = take_event(h);
             cudaEventRecord(e0, st);
         }
@@ -425,6 +426,8 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
             h->launches += 1;
         }
         if (h->learned) {
+            // flops of the three convolutions (2 x 27 x (16 + 256 + 16) per point)
+            RegionTimer rt(h, st, 5, 2.0 * 27 * (16 + 256 + 16) * static_cast<double>(h->N()));
             const long long l0 = h->nw.launches;
             SMG_CUDA(net_learned_correct(h->nw, h->prec, h->nx, h->ny, h->nz, h->d_r, u0, st));
             h->launches += h->nw.launches - l0;

@@ -1,0 +1,237 @@
+// conv_tc.cu -- the 16 -> 16 channel 3x3x3 convolution of the learned post-correction on the
+// 5th-generation tensor cores (tcgen05): out = ReLU(conv(a1)) with BF16 activations and weights
+// and FP32 accumulation in tensor memory.
+//
+// Implicit GEMM by shifted windows.  A CTA owns a 32 x 6 x 6 block of output points and stages
+// the 34 x 8 x 8 halo block of the input in shared memory as two regions (channels 0-7 and
+// 8-15), each a run of 16-byte rows in the halo's linear (z, y, x) order.  For 128 consecutive
+// linear positions q0 .. q0+127 and tap t with linear offset d_t, the A operand (128 points x 16
+// input channels, K-major, no swizzle) is the same layout starting at row q0 + d_t: rows 16 B
+// apart, 8-row core matrices 128 B apart (SBO), the second channel chunk one region further
+// (LBO).  So every tap is one tcgen05.mma (M = 128, N = 16, K = 16) whose A descriptor differs
+// only in its start address, accumulating into the same 16 TMEM columns.  Rows whose position is
+// a halo point give unused results.  B (16 output x 16 input channels per tap, K-major) holds
+// the 27 taps' weights.  One elected thread issues all MMAs of the CTA (13 row blocks x 27 taps),
+// commits them to an mbarrier, and four warps per row block read the accumulators back
+// (tcgen05.ld 32x32b: warp w reads TMEM lanes 32(w%4) ..) for the ReLU + BF16 epilogue.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "net.h"
+
+namespace smg {
+namespace {
+
+constexpr int CTX = 32, CTY = 6, CTZ = 6;
+constexpr int CHX = CTX + 2, CHY = CTY + 2, CHZ = CTZ + 2, CHP = CHX * CHY * CHZ;  // 2176 halo points
+constexpr int QLO = (CHY + 1) * CHX + 1;                 // first interior position
+constexpr int QHI = (CTZ * CHY + CTY) * CHX + CTX;       // last interior position
+constexpr int DMAX = CHY * CHX + CHX + 1;                // largest |tap offset|
+constexpr int NMT = (QHI - QLO + 1 + 127) / 128;         // 128-row blocks per CTA (13)
+constexpr int ROWS = CHP + 128;                          // rows per channel region, with padding
+constexpr int RS = ROWS * 16 + 64;                       // region stride in bytes (LBO)
+constexpr int A_BYTES = 2 * RS;
+constexpr int B_BYTES = 27 * 512;                        // per tap: [chunk][16 out][8 in] BF16
+constexpr int TC_COLS = 256;                             // TMEM columns allocated per CTA
+constexpr int TC_THREADS = 256;
+constexpr size_t TC_SMEM = A_BYTES + B_BYTES + 16;
+constexpr long long kWaitLimit = 1ll << 26;              // mbarrier polls before giving up
+
+// Every A row an MMA can read lies inside the staged regions; every accumulator fits.
+static_assert(QLO - DMAX >= 0, "tap window below the staged rows");
+static_assert(QLO + (NMT - 1) * 128 + 127 + DMAX < ROWS, "tap window beyond the staged rows");
+static_assert(NMT * 16 <= TC_COLS, "accumulators exceed the allocated TMEM columns");
+static_assert(RS % 16 == 0 && RS / 16 < (1 << 14), "LBO must be a 14-bit multiple of 16 B");
+static_assert(2 * TC_SMEM <= 227 * 1024, "two CTAs per SM must fit");
+
+// tcgen05 instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading-dimension byte offset
+// >> 4 (bits 16-29), stride-dimension byte offset >> 4 (bits 32-45), version 1 (bits 46-47), no
+// swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+struct TcArgs {
+    int nx, ny, nz;
+    const __nv_bfloat16 *in;   // [n][16]
+    __nv_bfloat16 *out;        // [n][16]
+    const float *w;            // layer weights [16 out][16 in][27], FP32 (rounded to BF16 here)
+};
+
+// Set to 1 by a CTA whose wait for its accumulators gave up (read and cleared by conv16_tc_status).
+__device__ int g_conv_tc_err = 0;
+
+__global__ void __launch_bounds__(TC_THREADS, 2) conv16_tc_kernel(const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *As = sm;
+    unsigned char *Bs = sm + A_BYTES;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Bs + B_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(Bs + B_BYTES + 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int ntx = (a.nx + CTX - 1) / CTX, nty = (a.ny + CTY - 1) / CTY;
+    int b = blockIdx.x;
+    const int x0 = (b % ntx) * CTX;
+    b /= ntx;
+    const int y0 = (b % nty) * CTY;
+    const int z0 = (b / nty) * CTZ;
+
+    // weights: B[t][chunk][n][8] = w[n][chunk*8 + e][t] as BF16
+    for (int i = threadIdx.x; i < 27 * 256; i += TC_THREADS) {
+        const int e = i & 7, n = (i >> 3) & 15, c = (i >> 7) & 1, t = i >> 8;
+        const float v = a.w[(n * 16 + c * 8 + e) * 27 + t];
+        reinterpret_cast<__nv_bfloat16 *>(Bs)[i] = __float2bfloat16_rn(v);
+    }
+    // input halo block: region c holds channels 8c .. 8c+7 of every halo point; zeros outside
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(a.in);
+    for (int i = threadIdx.x; i < 2 * CHP; i += TC_THREADS) {
+        const int c = i & 1, pt = i >> 1;
+        const int hx = pt % CHX, hy = (pt / CHX) % CHY, hz = pt / (CHX * CHY);
+        const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz) {
+            const long long p = (static_cast<long long>(gz) * a.ny + gy) * a.nx + gx;
+            v = *reinterpret_cast<const uint4 *>(src + p * 32 + c * 16);
+        }
+        *reinterpret_cast<uint4 *>(As + c * RS + pt * 16) = v;
+    }
+    for (int i = threadIdx.x; i < 2 * 128; i += TC_THREADS)  // padding rows (read only by unused rows)
+        *reinterpret_cast<uint4 *>(As + (i >> 7) * RS + (CHP + (i & 127)) * 16) = make_uint4(0u, 0u, 0u, 0u);
+
+    if (threadIdx.x == 0)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TC_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // make the generic-proxy shared-memory writes visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (threadIdx.x == 0) {
+        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+        for (int j = 0; j < NMT; ++j) {
+            const int q0 = QLO + 128 * j;
+            for (int t = 0; t < 27; ++t) {
+                const int d = ((t / 9) - 1) * CHY * CHX + (((t / 3) % 3) - 1) * CHX + (t % 3) - 1;
+                const uint64_t ad = smem_desc(a0 + static_cast<uint32_t>(q0 + d) * 16u, RS, 128);
+                const uint64_t bd = smem_desc(b0 + static_cast<uint32_t>(t) * 512u, 256, 128);
+                const uint32_t acc = t > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + j * 16),
+                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(mbar))
+                     : "memory");
+    }
+
+    // wait for the accumulators (bounded)
+    bool done = false;
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(mbar))
+            : "memory");
+        if (ok) {
+            done = true;
+            break;
+        }
+        __nanosleep(32);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!done) {
+        if (lane == 0) atomicExch(&g_conv_tc_err, 1);
+    } else {
+        const int quarter = warp & 3;
+        for (int j = warp >> 2; j < NMT; j += 2) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(j * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int q = QLO + 128 * j + 32 * quarter + lane;
+            const int hx = q % CHX, hy = (q / CHX) % CHY, hz = q / (CHX * CHY);
+            if (hx < 1 || hx > CTX || hy < 1 || hy > CTY || hz < 1 || hz > CTZ) continue;
+            const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+            if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
+            unsigned w[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float lo = fmaxf(__uint_as_float(r[2 * k]), 0.0f);
+                const float hi = fmaxf(__uint_as_float(r[2 * k + 1]), 0.0f);
+                __nv_bfloat162 bb = __floats2bfloat162_rn(lo, hi);
+                w[k] = *reinterpret_cast<unsigned *>(&bb);
+            }
+            const long long p = (static_cast<long long>(gz) * a.ny + gy) * a.nx + gx;
+            uint4 *dst = reinterpret_cast<uint4 *>(a.out + p * 16);
+            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+    }
+    if (!done && threadIdx.x == 0) {
+        // the MMAs may still be in flight: wait again (bounded) before the memory goes away
+        for (long long it = 0; it < kWaitLimit; ++it) {
+            uint32_t ok;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, "
+                "p;\n\t}\n"
+                : "=r"(ok)
+                : "r"(smem_u32(mbar))
+                : "memory");
+            if (ok) break;
+            __nanosleep(64);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
+}
+
+}  // namespace
+
+cudaError_t conv16_tc(int nx, int ny, int nz, const void *in, void *out, const float *w, cudaStream_t st) {
+    cudaError_t e = raise_smem_attr(reinterpret_cast<const void *>(&conv16_tc_kernel), TC_SMEM);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((nx + CTX - 1) / CTX) * ((ny + CTY - 1) / CTY) * ((nz + CTZ - 1) / CTZ);
+    TcArgs a{nx, ny, nz, static_cast<const __nv_bfloat16 *>(in), static_cast<__nv_bfloat16 *>(out), w};
+    conv16_tc_kernel<<<tiles, TC_THREADS, TC_SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t conv16_tc_status(int *err) {
+    cudaError_t e = cudaMemcpyFromSymbol(err, g_conv_tc_err, sizeof(int));
+    if (e != cudaSuccess) return e;
+    const int zero = 0;
+    return cudaMemcpyToSymbol(g_conv_tc_err, &zero, sizeof(int));
+}
+
+}  // namespace smg

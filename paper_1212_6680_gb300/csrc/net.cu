@@ -573,8 +573,12 @@ cudaError_t forward_t(NetWork &nw, int nx, int ny, int nz, cudaStream_t st) {
     cudaError_t e;
     ConvArgs a{nx, ny, nz, nw.rho, nw.a1, nw.w + kNetW1, nullptr, &nw.sc->inv_rms, wr};
     if ((e = conv<1, 16, float, T, T, EPI_RELU | EPI_SCALE, false>(a, st)) != cudaSuccess) return e;
-    a = ConvArgs{nx, ny, nz, nw.a1, nw.a2, nw.w + kNetW2, nullptr, nullptr, wr};
-    if ((e = conv<16, 16, T, T, T, EPI_RELU, false>(a, st)) != cudaSuccess) return e;
+    if (std::is_same<T, __nv_bfloat16>::value && net_tensor_cores()) {
+        if ((e = conv16_tc(nx, ny, nz, nw.a1, nw.a2, nw.w + kNetW2, st)) != cudaSuccess) return e;
+    } else {
+        a = ConvArgs{nx, ny, nz, nw.a1, nw.a2, nw.w + kNetW2, nullptr, nullptr, wr};
+        if ((e = conv<16, 16, T, T, T, EPI_RELU, false>(a, st)) != cudaSuccess) return e;
+    }
     a = ConvArgs{nx, ny, nz, nw.a2, nw.delta, nw.w + kNetW3, nullptr, &nw.sc->rms, wr};
     if ((e = conv<16, 1, T, float, T, EPI_SCALE, false>(a, st)) != cudaSuccess) return e;
     nw.launches += 3;
@@ -610,6 +614,11 @@ cudaError_t backward_t(NetWork &nw, int nx, int ny, int nz, cudaStream_t st) {
 }
 
 }  // namespace
+
+bool &net_tensor_cores() {
+    static bool on = true;
+    return on;
+}
 
 cudaError_t net_alloc(NetWork &nw, long long n, int act, bool training) {
     if (nw.n >= n && nw.act == act && (nw.training || !training)) return cudaSuccess;

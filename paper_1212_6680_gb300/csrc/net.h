@@ -77,4 +77,11 @@ cudaError_t net_capture(Prec storage, int nx, int ny, int nz, const double *r, c
 cudaError_t net_to_f32(long long n, const double *src, float *dst, cudaStream_t st);
 cudaError_t net_to_f64(long long n, const float *src, double *dst, cudaStream_t st);
 
+// The 16 -> 16 channel layer with ReLU on the tcgen05 tensor cores (BF16 in and out, FP32
+// accumulation): conv_tc.cu.  Used for the BF16 layer 2 while net_tensor_cores() is on.
+cudaError_t conv16_tc(int nx, int ny, int nz, const void *in, void *out, const float *w, cudaStream_t st);
+// 1 if a CTA of conv16_tc gave up waiting for its accumulators since the last call (then cleared).
+cudaError_t conv16_tc_status(int *err);
+bool &net_tensor_cores();
+
 }  // namespace smg

@@ -148,3 +148,16 @@ extern "C" int smg_net_train(int npairs, const int *dims, const float *const *rh
     net_free(nw);
     return SMG_OK;
 }
+
+extern "C" int smg_net_set_tensor_cores(int on) {
+    if (on != 0 && on != 1) return nfail(SMG_ERR_ARG, "on must be 0 or 1");
+    net_tensor_cores() = (on == 1);
+    return SMG_OK;
+}
+
+extern "C" int smg_net_tc_status(int *err) {
+    if (!err) return nfail(SMG_ERR_ARG, "null pointer");
+    cudaError_t e = conv16_tc_status(err);
+    if (e != cudaSuccess) return nfail(SMG_ERR_CUDA, std::string("smg_net_tc_status: ") + cudaGetErrorString(e));
+    return SMG_OK;
+}

@@ -31,7 +31,7 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "krylov_solve_batched", "smg_barrier_selftest", "smg_batched_setup", "smg_batched_solve",
            "smg_batched_destroy", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
-           "smg_net_train")
+           "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status")
 NET_WEIGHTS = 7776
 
 
@@ -75,6 +75,8 @@ def _load():
     L.smg_net_forward.argtypes = [i, i, i, i, vp, vp, vp, vp]
     L.smg_net_loss_grad.argtypes = [i, i, i, i, vp, vp, vp, dp, vp, vp]
     L.smg_net_train.argtypes = [i, vp, vp, vp, i, d, ctypes.c_ulonglong, i, vp, vp, vp]
+    L.smg_net_set_tensor_cores.argtypes = [i]
+    L.smg_net_tc_status.argtypes = [ip]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -324,6 +326,16 @@ def smg_net_train(dims_list, rho_list, e_list, w, epochs=3, lr=1e-3, seed=0, act
                               epochs, lr, seed, PRECISIONS.get(act, act), w.ctypes.data, hist.ctypes.data,
                               _stream(stream)))
     return w, hist
+
+
+def smg_net_set_tensor_cores(on: bool) -> None:
+    _check(_lib.smg_net_set_tensor_cores(1 if on else 0))
+
+
+def smg_net_tc_status() -> int:
+    e = ctypes.c_int(0)
+    _check(_lib.smg_net_tc_status(ctypes.byref(e)))
+    return e.value
 
 
 def smg_barrier_selftest(extra_blocks: int, limit_seconds: float = 0.5, stream=None) -> int:

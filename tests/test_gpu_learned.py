@@ -1,7 +1,7 @@
 """The learned post-correction on the GPU against the FP64 oracle (oracle/net_oracle.c):
 forward pass and loss gradient with FP32 activations (relative 1e-5 against the FP64 oracle)
 and with BF16 weights and activations (against the oracle with the same BF16 rounding of its
-hidden activations: 1e-4 forward, 1e-3 gradient; against the plain FP64 oracle: 5e-2, since
+hidden activations: 3e-4 forward, 1e-3 gradient; against the plain FP64 oracle: 5e-2, since
 rounding the activations alone moves the gradient by about 2% even in exact arithmetic), the
 correction inside smg_apply and flexible PCG with fixed weights (the same weights handed to the
 oracle), the training pairs' defining relation, and training lowering the loss.  Weights are
@@ -65,7 +65,8 @@ def test_forward_matches_oracle(smg, orc, shape, act):
     if act == "fp32":
         assert rel(d, orc.net_forward(w, rho)) <= 1e-5
     else:
-        assert rel(d, orc.net_forward(w, rho, act_bf16=True)) <= 1e-4
+        # FP32 summation order flips a few BF16 roundings of hidden activations by one ulp
+        assert rel(d, orc.net_forward(w, rho, act_bf16=True)) <= 3e-4
         assert rel(d, orc.net_forward(w, rho)) <= 1e-2
 
 
@@ -203,3 +204,26 @@ def test_learned_argument_errors(smg):
         smg.smg_net_forward((0, 4, 4), "bf16", np.zeros(smg.NET_WEIGHTS), 0, 0)
     with pytest.raises(smg.SMGError):
         smg.smg_net_forward((4, 4, 4), "fp64", np.zeros(smg.NET_WEIGHTS), 0, 0)
+
+
+@pytest.mark.parametrize("shape", [(37, 21, 13), (64, 9, 5), (3, 1, 7), (130, 14, 20), (32, 6, 6)])
+def test_tensor_core_layer_matches_cuda_cores_and_oracle(smg, orc, shape):
+    """The tcgen05 16 -> 16 layer (default) against the CUDA-core kernel on the same BF16 inputs
+    and weights (they differ only in FP32 summation order, so in rare BF16 roundings of the hidden
+    activation) and against the BF16-activation oracle."""
+    nx, ny, nz = shape
+    w = bf16_round(smg, inputs.net_init_weights(seed=131, last_scale=1.0))
+    rho = dev(inputs.rhs(nx, ny, nz, seed=132))
+    out = {}
+    try:
+        for tc in (True, False):
+            smg.smg_net_set_tensor_cores(tc)
+            d = torch.empty(nx * ny * nz, dtype=torch.float64, device="cuda")
+            smg.smg_net_forward(shape, "bf16", w, rho, d)
+            out[tc] = d.cpu().numpy()
+    finally:
+        smg.smg_net_set_tensor_cores(True)
+    assert smg.smg_net_tc_status() == 0
+    assert rel(out[True], out[False]) <= 3e-4, rel(out[True], out[False])
+    ref = orc.net_forward(w, rho.cpu().numpy().reshape(nz, ny, nx), act_bf16=True)
+    assert rel(out[True], ref) <= 3e-4
