@@ -129,7 +129,7 @@ def source_hash():
 def ncu_traffic():
     """DRAM bytes per level-0 launch of the plane-relaxation kernel from the committed ncu
     summary, if it was captured from the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "plane_relax_traffic.json")
+    p = os.path.join(ROOT, "profiles", "plane_relax_traffic.txt")
     try:
         d = json.load(open(p))
         if d.get("source_hash") == source_hash():

@@ -171,10 +171,23 @@ __global__ void __launch_bounds__(kConvThreads, 2) conv_kernel(const ConvArgs a)
             const float *xf = reinterpret_cast<const float *>(xs);
             const float v0 = xf[base[0] + off], v1 = xf[base[1] + off];
             const float *wt = ws + t * COUT;
+            if constexpr (COUT % 4 == 0) {
 #pragma unroll
-            for (int o = 0; o < COUT; ++o) {
-                acc[0][o] = fmaf(wt[o], v0, acc[0][o]);
-                acc[1][o] = fmaf(wt[o], v1, acc[1][o]);
+                for (int o4 = 0; o4 < COUT / 4; ++o4) {
+                    const float4 w4 = reinterpret_cast<const float4 *>(wt)[o4];
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        acc[0][4 * o4 + q] = fmaf(wv[q], v0, acc[0][4 * o4 + q]);
+                        acc[1][4 * o4 + q] = fmaf(wv[q], v1, acc[1][4 * o4 + q]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int o = 0; o < COUT; ++o) {
+                    acc[0][o] = fmaf(wt[o], v0, acc[0][o]);
+                    acc[1][o] = fmaf(wt[o], v1, acc[1][o]);
+                }
             }
         } else {
             constexpr int E = Chunk<TI>::E, NG = CIN / E;
@@ -200,10 +213,18 @@ __global__ void __launch_bounds__(kConvThreads, 2) conv_kernel(const ConvArgs a)
                             acc[1][4 * o4 + 3] = fmaf(w4.w, in1[c], acc[1][4 * o4 + 3]);
                         }
                     } else {
+                        // one output channel: the chunk's E weights are consecutive (ci fastest)
+                        float wv;
+                        if constexpr (COUT == 1 && E % 4 == 0) {
+                            const float4 w4 = reinterpret_cast<const float4 *>(ws + (t * CIN + g * E))[c / 4];
+                            wv = (c % 4 == 0) ? w4.x : (c % 4 == 1) ? w4.y : (c % 4 == 2) ? w4.z : w4.w;
+                        } else {
+                            wv = wt[0];
+                        }
 #pragma unroll
                         for (int o = 0; o < COUT; ++o) {
-                            acc[0][o] = fmaf(wt[o], in0[c], acc[0][o]);
-                            acc[1][o] = fmaf(wt[o], in1[c], acc[1][o]);
+                            acc[0][o] = fmaf(COUT == 1 ? wv : wt[o], in0[c], acc[0][o]);
+                            acc[1][o] = fmaf(COUT == 1 ? wv : wt[o], in1[c], acc[1][o]);
                         }
                     }
                 }
@@ -384,21 +405,42 @@ __device__ __forceinline__ void decode(int i, int nx, int ny, int &x, int &y, in
     x = r - y * nx;
 }
 
-// rho = r - A s (stored FP32), part = sum rho^2 of the stored values
+// FP32 value of a storage element (FP64 narrowed on the integer pipe).
+template <class S> __device__ __forceinline__ float ldf(const S *p);
+template <> __device__ __forceinline__ float ldf<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ float ldf<double>(const double *p) { return narrow_f64(*p); }
+
+// A v at point i in FP32 (7-point, Dirichlet).
+template <class V>
+__device__ __forceinline__ float stencil_f32(const V *v, int i, int x, int y, int z, int nx, int ny, int nz) {
+    const int np = nx * ny;
+    float nb = 0.0f;
+    if (x > 0) nb += ldf(v + i - 1);
+    if (x < nx - 1) nb += ldf(v + i + 1);
+    if (y > 0) nb += ldf(v + i - nx);
+    if (y < ny - 1) nb += ldf(v + i + nx);
+    if (z > 0) nb += ldf(v + i - np);
+    if (z < nz - 1) nb += ldf(v + i + np);
+    return fmaf(6.0f, ldf(v + i), -nb);
+}
+
+// rho = r - A s in FP32 (the network's input and the judge's reference need no more: rho is
+// stored as FP32 and fed to BF16 activations), part = sum rho^2 (FP32 per thread, FP64 across).
 template <class S>
 __global__ void __launch_bounds__(kRedThreads) rho_kernel(int nx, int ny, int nz, const double *r, const S *s,
                                                           float *rho, double *part) {
     const int n = nx * ny * nz;
-    double acc = 0.0;
+    float acc = 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int x, y, z;
         decode(i, nx, ny, x, y, z);
-        const float v = narrow_f64(r[i] - stencil_at(s, i, x, y, z, nx, ny, nz));
+        const float v = narrow_f64(r[i]) - stencil_f32(s, i, x, y, z, nx, ny, nz);
         rho[i] = v;
-        acc = fma(static_cast<double>(v), static_cast<double>(v), acc);
+        acc = fmaf(v, v, acc);
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double tot = block_sum(static_cast<double>(acc));
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
 __global__ void __launch_bounds__(kRedThreads) sumsq_kernel(int n, const float *v, double *part) {
@@ -422,19 +464,19 @@ __global__ void fin_rho_kernel(const double *part, int np, long long n, NetScal 
     }
 }
 
-// the judge: part = sum (rho - A delta)^2
+// the judge: part = sum (rho - A delta)^2, in FP32 per thread
 __global__ void __launch_bounds__(kRedThreads) judge_kernel(int nx, int ny, int nz, const float *rho,
                                                             const float *delta, double *part) {
     const int n = nx * ny * nz;
-    double acc = 0.0;
+    float acc = 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int x, y, z;
         decode(i, nx, ny, x, y, z);
-        const double v = static_cast<double>(rho[i]) - stencil_at(delta, i, x, y, z, nx, ny, nz);
-        acc = fma(v, v, acc);
+        const float v = rho[i] - stencil_f32(delta, i, x, y, z, nx, ny, nz);
+        acc = fmaf(v, v, acc);
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double tot = block_sum(static_cast<double>(acc));
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
 __global__ void fin_judge_kernel(const double *part, int np, NetScal *sc) {
@@ -452,8 +494,10 @@ __global__ void fin_judge_kernel(const double *part, int np, NetScal *sc) {
 template <class S>
 __global__ void apply_kernel(int n, const float *delta, S *s, const NetScal *sc) {
     if (!sc->accepted) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        stv<S, double>(s + i, ldv<double>(s + i) + static_cast<double>(delta[i]));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if constexpr (std::is_same<S, double>::value) s[i] += widen_f32(delta[i]);
+        else stv<S, float>(s + i, ldv<float>(s + i) + delta[i]);
+    }
 }
 
 // training loss: d = e - delta; ad = A d; part[2b] = sum d A d, part[2b+1] = sum e A e

@@ -474,13 +474,17 @@ __device__ __forceinline__ void ensure_fac(const PlaneCtx<C> &c, TriFac<C, K> &f
     tri_factor<C, K>(fac, dg, of, c.nx, lane);
 }
 
-// Exact relaxation of NL lines ys[] of 2D level m by one warp (lines of one colour, so they
-// do not couple to each other).  NBMODE: the neighbouring lines are zero (NB_NONE), read as
-// they are (NB_PLAIN), or read with the coarse correction P u_{m+1} added (NB_CORR, the
-// neighbours are even lines).  OUT: store into u_m, into the plane, or both.
-template <class S, class C, int K, int NL, bool CL, int NBMODE, int OUT>
+// Exact relaxation of NL lines ys[0 .. nvalid) of 2D level m by one warp (lines of one colour,
+// so they do not couple to each other); entries past nvalid, if any, repeat a valid line and are
+// solved but not stored.  nbmode: the neighbouring lines are
+// zero (NB_NONE), read as they are (NB_PLAIN), or read with the coarse correction P u_{m+1}
+// added (NB_CORR, the neighbours are even lines).  out: store into u_m, into the plane, or both.
+// The modes are warp-uniform runtime values: one compiled body for every step of the 2D cycle
+// keeps the kernel's code small enough for the instruction cache.
+template <class S, class C, int K, int NL, bool CL>
 __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
-                                            int m, const int (&ys)[NL], S *plane, bool accumulate, int lane) {
+                                            int m, const int (&ys)[NL], int nvalid, S *plane, bool accumulate,
+                                            int nbmode, int out, int lane) {
     const int nx = c.nx, nym = a.ny_m[m];
     C d[NL][K];
 #pragma unroll
@@ -490,8 +494,8 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
         cr[l] = coef_row<C>(c.sm + (a.line_base[m] + ys[l]) * kCoefPerLine);
         load_line<C, K>(d[l], line_g<C, CL>(a, c, m, ys[l]), nx, c.vec, lane);
     }
-    if constexpr (NBMODE != NB_NONE) {
-        const int nyc = (NBMODE == NB_CORR) ? a.ny_m[m + 1] : 0;
+    if (nbmode != NB_NONE) {
+        const int nyc = (nbmode == NB_CORR) ? a.ny_m[m + 1] : 0;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             const int y = ys[l];
@@ -501,7 +505,7 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
                 if (yy < 0 || yy >= nym) continue;
                 C v[K];
                 load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, c.vec, lane);
-                if constexpr (NBMODE == NB_CORR) {  // neighbour yy is an even line: add P e from level m+1
+                if (nbmode == NB_CORR) {  // neighbour yy is an even line: add P e from level m+1
                     const CoefRow<C> cy = coef_row<C>(c.sm + (a.line_base[m] + yy) * kCoefPerLine);
                     const int jl = yy / 2 - 1, jh = yy / 2;
                     if (jl >= 0) {
@@ -552,9 +556,10 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
     }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
+        if (l >= nvalid) break;
         const int y = ys[l];
-        if constexpr (OUT != OUT_PLANE) store_line<C, K>(line_u<C, CL>(a, c, m, y), d[l], nx, c.vec, lane);
-        if constexpr (OUT != OUT_U) {
+        if (out != OUT_PLANE) store_line<C, K>(line_u<C, CL>(a, c, m, y), d[l], nx, c.vec, lane);
+        if (out != OUT_U) {
             S *p = plane + y * nx;
             bool done = false;
             if constexpr (vec_chunk<S, K>() != 0) {
@@ -593,11 +598,11 @@ constexpr int max_lines_per_group() {
 }
 
 // Relax every line of one colour of 2D level m that this CTA owns: lines colour + 2k with
-// k = rank + R i; warp w takes i = w, w + nw, ...
-template <class S, class C, int K, bool CL, int NBMODE, int OUT>
+// k = rank + R i; warp w takes i = w, w + nw, ..., NLM at a time while it has NLM left.
+template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
-                                             int m, int colour, S *plane, bool accumulate, int warp, int nw,
-                                             int lane) {
+                                             int m, int colour, S *plane, bool accumulate, int nbmode, int out,
+                                             int warp, int nw, int lane) {
     const int nl = (a.ny_m[m] - colour + 1) / 2;
     const int nown = (nl > c.rank) ? (nl - c.rank + c.R - 1) / c.R : 0;
     auto Y = [&](int i) { return colour + 2 * (c.rank + c.R * i); };
@@ -608,18 +613,13 @@ __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const Plan
             int ys[NLM];
 #pragma unroll
             for (int l = 0; l < NLM; ++l) ys[l] = Y(i + l * nw);
-            relax_group<S, C, K, NLM, CL, NBMODE, OUT>(a, c, fac, m, ys, plane, accumulate, lane);
+            relax_group<S, C, K, NLM, CL>(a, c, fac, m, ys, NLM, plane, accumulate, nbmode, out, lane);
         }
     }
-    if constexpr (NLM > 2) {
-        for (; i + nw < nown; i += 2 * nw) {
-            const int ys[2] = {Y(i), Y(i + nw)};
-            relax_group<S, C, K, 2, CL, NBMODE, OUT>(a, c, fac, m, ys, plane, accumulate, lane);
-        }
-    }
+    // the rest one line at a time (on the coarse levels the critical path is one line per warp)
     for (; i < nown; i += nw) {
         const int ys[1] = {Y(i)};
-        relax_group<S, C, K, 1, CL, NBMODE, OUT>(a, c, fac, m, ys, plane, accumulate, lane);
+        relax_group<S, C, K, 1, CL>(a, c, fac, m, ys, 1, plane, accumulate, nbmode, out, lane);
     }
 }
 
@@ -837,46 +837,44 @@ __device__ __forceinline__ void plane_task(const PlaneRelaxArgs &a, int pidx, in
         plane_sync<CL>();
         SMG_TRACE(1);
         const bool acc = (mode == 2);
-        // 2.-3. the 2D cycle, writing v into the plane on the way up
-        if (P == 1) {
-            if (warp == 0 && c.rank == 0) {
-                const int ys[1] = {0};
-                relax_group<S, C, K, 1, CL, NB_NONE, OUT_PLANE>(a, c, fac, 0, ys, plane, acc, lane);
+        // 2.-3. the 2D cycle, writing v into the plane on the way up, as one loop over its steps
+        //   down,   m = 0 .. P-2:  even lines (no neighbours), odd lines, restriction
+        //   bottom: the single line of level P-1
+        //   up,     m = P-2 .. 0:  odd lines (neighbours + coarse correction), even lines;
+        //                          level 0 writes the plane (accumulating in correction form)
+        // so that every relaxation goes through the same inlined code.
+        const int nsteps = (P == 1) ? 1 : 5 * P - 4;
+        for (int st = 0; st < nsteps; ++st) {
+            int m, colour, nbmode, out;
+            bool accu = false, is_restrict = false;
+            if (P == 1) {
+                m = 0, colour = 0, nbmode = NB_NONE, out = OUT_PLANE, accu = acc;
+            } else if (st < 3 * (P - 1)) {
+                m = st / 3;
+                const int k = st - 3 * m;
+                is_restrict = (k == 2);
+                colour = k;
+                nbmode = (k == 0) ? NB_NONE : NB_PLAIN;
+                out = OUT_U;
+            } else if (st == 3 * (P - 1)) {
+                m = P - 1, colour = 0, nbmode = NB_NONE, out = OUT_U;
+            } else {
+                const int u = st - 3 * (P - 1) - 1;
+                m = P - 2 - u / 2;
+                colour = (u & 1) ? 0 : 1;
+                nbmode = colour ? NB_CORR : NB_PLAIN;
+                out = (m > 0) ? OUT_U : (colour ? OUT_U_AND_PLANE : OUT_PLANE);
+                accu = acc;
             }
+            // opaque to the optimiser, so that it keeps one copy of the step instead of cloning it
+            // per branch of the decoding above to propagate the constants
+            int accu_i = accu ? 1 : 0, rs_i = is_restrict ? 1 : 0;
+            asm volatile("" : "+r"(m), "+r"(colour), "+r"(nbmode), "+r"(out), "+r"(accu_i), "+r"(rs_i));
+            if (rs_i) restrict_level<C, K, CL>(a, c, m, warp, nw, lane);
+            else relax_colour<S, C, K, CL>(a, c, fac, m, colour, plane, accu_i != 0, nbmode, out, warp, nw, lane);
             plane_sync<CL>();
-            continue;
+            SMG_TRACE(2 + st);
         }
-        for (int m = 0; m < P - 1; ++m) {
-            relax_colour<S, C, K, CL, NB_NONE, OUT_U>(a, c, fac, m, 0, plane, false, warp, nw, lane);
-            plane_sync<CL>();
-            SMG_TRACE(2 + 3 * m);
-            relax_colour<S, C, K, CL, NB_PLAIN, OUT_U>(a, c, fac, m, 1, plane, false, warp, nw, lane);
-            plane_sync<CL>();
-            SMG_TRACE(3 + 3 * m);
-            restrict_level<C, K, CL>(a, c, m, warp, nw, lane);
-            plane_sync<CL>();
-            SMG_TRACE(4 + 3 * m);
-        }
-        if (warp == 0 && c.rank == 0) {
-            const int ys[1] = {0};
-            relax_group<S, C, K, 1, CL, NB_NONE, OUT_U>(a, c, fac, P - 1, ys, plane, false, lane);
-        }
-        plane_sync<CL>();
-        SMG_TRACE(60);
-        for (int m = P - 2; m >= 1; --m) {
-            relax_colour<S, C, K, CL, NB_CORR, OUT_U>(a, c, fac, m, 1, plane, acc, warp, nw, lane);
-            plane_sync<CL>();
-            SMG_TRACE(100 - 2 * m);
-            relax_colour<S, C, K, CL, NB_PLAIN, OUT_U>(a, c, fac, m, 0, plane, acc, warp, nw, lane);
-            plane_sync<CL>();
-            SMG_TRACE(101 - 2 * m);
-        }
-        relax_colour<S, C, K, CL, NB_CORR, OUT_U_AND_PLANE>(a, c, fac, 0, 1, plane, acc, warp, nw, lane);
-        plane_sync<CL>();
-        SMG_TRACE(100);
-        relax_colour<S, C, K, CL, NB_PLAIN, OUT_PLANE>(a, c, fac, 0, 0, plane, acc, warp, nw, lane);
-        plane_sync<CL>();
-        SMG_TRACE(101);
     }
 }
 
