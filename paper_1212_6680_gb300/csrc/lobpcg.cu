@@ -25,22 +25,27 @@ namespace smg {
 
 namespace {
 
-constexpr int kGT = 48;          // Gram output tile (kGT x kGT per CTA)
-constexpr int kGRows = 32;       // rows staged per step
+constexpr int kGT = 16;          // Gram output tile (kGT x kGT per CTA, one output per thread)
+constexpr int kGRows = 64;       // rows staged per step
 constexpr int kGChunk = 8192;    // rows per CTA (split-K)
 constexpr int kMulCols = 16;     // output columns per block_mul thread
 
-// Partial Gram: part[chunk][ti][tj] tile of U^T V over rows [chunk*kGChunk, ...).
-__global__ void gram_partial_kernel(long long n, int k1, int k2, const double *__restrict__ U,
-                                    const double *__restrict__ V, double *__restrict__ part, int ntj) {
+// Partial Gram: part[chunk][ti][tj] tile of U^T V over rows [chunk*kGChunk, ...).  FP64 FMAs are
+// the scarce resource on this part, so the tiles are small (no work on padding beyond the next
+// multiple of 16) and, for a symmetric product (sym = 1, U^T V = V^T U), only the tiles on and
+// above the diagonal are computed.
+__global__ void __launch_bounds__(256) gram_partial_kernel(long long n, int k1, int k2, const double *__restrict__ U,
+                                                           const double *__restrict__ V, double *__restrict__ part,
+                                                           int ntj, int sym) {
     __shared__ double su[kGRows][kGT + 1];
     __shared__ double sv[kGRows][kGT + 1];
     const int tile = blockIdx.y, ti = tile / ntj, tj = tile % ntj;
+    if (sym && tj < ti) return;
     const int i0 = ti * kGT, j0 = tj * kGT;
     const long long r0 = static_cast<long long>(blockIdx.x) * kGChunk;
     const long long r1 = min(n, r0 + kGChunk);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 3 x 3 outputs each
-    double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const int ti_ = threadIdx.x >> 4, tj_ = threadIdx.x & 15;
+    double acc0 = 0.0, acc1 = 0.0;
     for (long long rb = r0; rb < r1; rb += kGRows) {
         for (int t = threadIdx.x; t < kGRows * kGT; t += blockDim.x) {
             const int rr = t % kGRows, cc = t / kGRows;
@@ -49,33 +54,28 @@ __global__ void gram_partial_kernel(long long n, int k1, int k2, const double *_
             sv[rr][cc] = (r < r1 && j0 + cc < k2) ? V[static_cast<long long>(j0 + cc) * n + r] : 0.0;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int rr = 0; rr < kGRows; ++rr) {
-            const double a0 = su[rr][ty], a1 = su[rr][ty + 16], a2 = su[rr][ty + 32];
-            const double b0 = sv[rr][tx], b1 = sv[rr][tx + 16], b2 = sv[rr][tx + 32];
-            acc[0][0] = fma(a0, b0, acc[0][0]);
-            acc[0][1] = fma(a0, b1, acc[0][1]);
-            acc[0][2] = fma(a0, b2, acc[0][2]);
-            acc[1][0] = fma(a1, b0, acc[1][0]);
-            acc[1][1] = fma(a1, b1, acc[1][1]);
-            acc[1][2] = fma(a1, b2, acc[1][2]);
-            acc[2][0] = fma(a2, b0, acc[2][0]);
-            acc[2][1] = fma(a2, b1, acc[2][1]);
-            acc[2][2] = fma(a2, b2, acc[2][2]);
+#pragma unroll 8
+        for (int rr = 0; rr < kGRows; rr += 2) {  // two independent chains
+            acc0 = fma(su[rr][ti_], sv[rr][tj_], acc0);
+            acc1 = fma(su[rr + 1][ti_], sv[rr + 1][tj_], acc1);
         }
         __syncthreads();
     }
-    double *out = part + (static_cast<long long>(blockIdx.x) * gridDim.y + tile) * kGT * kGT;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) out[(ty + 16 * a) * kGT + tx + 16 * b] = acc[a][b];
+    part[(static_cast<long long>(blockIdx.x) * gridDim.y + tile) * kGT * kGT + ti_ * kGT + tj_] = acc0 + acc1;
 }
 
-// G[i][j] (k1 x k2 row-major) = sum over chunks of the partial tiles (compensated summation).
+// G[i][j] (k1 x k2 row-major) = sum over chunks of the partial tiles (compensated summation);
+// with sym, entries below the diagonal tiles come from the mirrored tile.
 __global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int ntiles, const double *__restrict__ part,
-                                   double *__restrict__ G) {
+                                   double *__restrict__ G, int sym) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= k1 * k2) return;
-    const int i = idx / k2, j = idx % k2;
+    int i = idx / k2, j = idx % k2;
+    if (sym && i / kGT > j / kGT) {
+        const int t = i;
+        i = j;
+        j = t;
+    }
     const int ti = i / kGT, tj = j / kGT, tile = ti * ntj + tj;
     double s = 0.0, c = 0.0;
     for (int ch = 0; ch < nchunks; ++ch) {
@@ -230,15 +230,17 @@ struct Ctx {
         }                                                                          \
     } while (0)
 
-// G (k1 x k2, host row-major) = U^T V
-int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G) {
+// G (k1 x k2, host row-major) = U^T V; sym: the product is symmetric (k1 = k2 and U^T V = V^T U,
+// e.g. V = U or V = A U), so only its upper tiles are computed
+int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G, bool sym = false) {
     const int nti = cdiv(k1, kGT), ntj = cdiv(k2, kGT);
     const int nch = cdiv(c.n, kGChunk);
+    const int s = (sym && k1 == k2) ? 1 : 0;
     dim3 grid(nch, nti * ntj);
-    gram_partial_kernel<<<grid, 256, 0, c.st>>>(c.n, k1, k2, U, V, c.w.part, ntj);
+    gram_partial_kernel<<<grid, 256, 0, c.st>>>(c.n, k1, k2, U, V, c.w.part, ntj, s);
     LCHK(cudaGetLastError());
     gram_reduce_kernel<<<cdiv(static_cast<long long>(k1) * k2, 256), 256, 0, c.st>>>(nch, k1, k2, ntj, nti * ntj,
-                                                                                      c.w.part, c.w.gram);
+                                                                                      c.w.part, c.w.gram, s);
     LCHK(cudaGetLastError());
     G.resize(static_cast<size_t>(k1) * k2);
     LCHK(cudaMemcpyAsync(c.w.h_buf, c.w.gram, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c.st));
@@ -262,7 +264,7 @@ int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, d
 // when given.  Returns false when Y^T Y is numerically singular.
 int ortho(Ctx &c, int q, double *Y, double *AY, double *tmp, bool &ok) {
     std::vector<double> G, L(static_cast<size_t>(q) * q), Z(static_cast<size_t>(q) * q);
-    int rc = gram(c, q, Y, q, Y, G);
+    int rc = gram(c, q, Y, q, Y, G, true);
     if (rc) return rc;
     for (int i = 0; i < q; ++i)
         for (int j = 0; j < i; ++j) G[i * q + j] = G[j * q + i] = 0.5 * (G[i * q + j] + G[j * q + i]);
@@ -367,8 +369,8 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
     if ((rc = ops.apply_A(m, X, AX, st))) return rc;
     // Rayleigh-Ritz on X alone
     std::vector<double> GA, GB, theta, C;
-    if ((rc = gram(c, m, X, m, AX, GA))) return rc;
-    if ((rc = gram(c, m, X, m, X, GB))) return rc;
+    if ((rc = gram(c, m, X, m, AX, GA, true))) return rc;
+    if ((rc = gram(c, m, X, m, X, GB, true))) return rc;
     if (!rayleigh_ritz(m, GA, GB, theta, C)) {
         msg = "lobpcg: Rayleigh-Ritz on the initial block failed";
         return SMG_ERR_BREAKDOWN;
@@ -388,7 +390,7 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         residual_kernel<<<cdiv(n * m, 256), 256, 0, st>>>(n, m, X, AX, d_lam, R);
         LCHK(cudaGetLastError());
         std::vector<double> GR;
-        if ((rc = gram(c, m, R, m, R, GR))) return rc;
+        if ((rc = gram(c, m, R, m, R, GR, true))) return rc;
         std::vector<int> active;
         for (int j = 0; j < m; ++j) {
             const double rn = std::sqrt(std::max(0.0, GR[j * m + j]));
@@ -435,8 +437,8 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         }
         // Rayleigh-Ritz on S = [X W P]
         int k = m + na + np;
-        if ((rc = gram(c, k, w.S, k, w.AS, GA))) return rc;
-        if ((rc = gram(c, k, w.S, k, w.S, GB))) return rc;
+        if ((rc = gram(c, k, w.S, k, w.AS, GA, true))) return rc;
+        if ((rc = gram(c, k, w.S, k, w.S, GB, true))) return rc;
         if (!rayleigh_ritz(k, GA, GB, theta, C)) {
             if (np == 0) {
                 msg = "lobpcg: Gram matrix of [X W] is not positive definite";
