@@ -76,8 +76,16 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 struct TcArgs {
     int nx, ny, nz;
     __nv_bfloat16 *out;        // [n][16]
-    const float *w;            // layer weights [16 out][16 in][27], FP32 (rounded to BF16 here)
+    const uint4 *wb;           // the B operand of all taps, prepared by conv16_tc_prep (B_BYTES)
 };
+
+// B[t][chunk][n][8] = w[n][chunk*8 + e][t] as BF16 (the layer's FP32 weights rounded once).
+__global__ void conv16_tc_prep_kernel(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wb) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 27 * 256; i += gridDim.x * blockDim.x) {
+        const int e = i & 7, n = (i >> 3) & 15, c = (i >> 7) & 1, t = i >> 8;
+        wb[i] = __float2bfloat16_rn(w[(n * 16 + c * 8 + e) * 27 + t]);
+    }
+}
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
     for (long long it = 0; it < limit; ++it) {
@@ -137,12 +145,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                 "r"(smem_u32(mbar_ld))
                 : "memory");
     }
-    // weights: B[t][chunk][n][8] = w[n][chunk*8 + e][t] as BF16
-    for (int i = threadIdx.x; i < 27 * 256; i += TC_THREADS) {
-        const int e = i & 7, n = (i >> 3) & 15, c = (i >> 7) & 1, t = i >> 8;
-        const float v = a.w[(n * 16 + c * 8 + e) * 27 + t];
-        reinterpret_cast<__nv_bfloat16 *>(Bs)[i] = __float2bfloat16_rn(v);
-    }
+    // weights: the prepared B operand, 16 bytes per thread and step
+    for (int i = threadIdx.x; i < B_BYTES / 16; i += TC_THREADS) reinterpret_cast<uint4 *>(Bs)[i] = a.wb[i];
     for (int i = threadIdx.x; i < 2 * 128; i += TC_THREADS)  // padding rows (read only by unused rows)
         *reinterpret_cast<uint4 *>(As + (i >> 7) * RS + (CHP + (i & 127)) * 16) = make_uint4(0u, 0u, 0u, 0u);
 
@@ -251,7 +255,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 }  // namespace
 
-cudaError_t conv16_tc(int nx, int ny, int nz, const void *in, void *out, const float *w, cudaStream_t st) {
+cudaError_t conv16_tc_prep(const float *w, void *wb, cudaStream_t st) {
+    conv16_tc_prep_kernel<<<(27 * 256 + 255) / 256, 256, 0, st>>>(w, static_cast<__nv_bfloat16 *>(wb));
+    return cudaGetLastError();
+}
+
+cudaError_t conv16_tc(int nx, int ny, int nz, const void *in, void *out, const void *wb, cudaStream_t st) {
     cudaError_t e = raise_smem_attr(reinterpret_cast<const void *>(&conv16_tc_kernel), TC_SMEM);
     if (e != cudaSuccess) return e;
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
@@ -268,7 +277,7 @@ cudaError_t conv16_tc(int nx, int ny, int nz, const void *in, void *out, const f
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const int tiles = ((nx + CTX - 1) / CTX) * ((ny + CTY - 1) / CTY) * ((nz + CTZ - 1) / CTZ);
-    TcArgs a{nx, ny, nz, static_cast<__nv_bfloat16 *>(out), w};
+    TcArgs a{nx, ny, nz, static_cast<__nv_bfloat16 *>(out), static_cast<const uint4 *>(wb)};
     conv16_tc_kernel<<<tiles, TC_THREADS, TC_SMEM, st>>>(map, a);
     return cudaGetLastError();
 }

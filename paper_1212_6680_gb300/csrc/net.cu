@@ -268,6 +268,138 @@ __global__ void __launch_bounds__(kConvThreads, 2) conv_kernel(const ConvArgs a)
     }
 }
 
+// ---- forward layers 1 and 3 (register-blocked in z) ------------------------------------------------
+// A CTA of 256 threads owns a 32 x 4 x 4 block; thread (x, y, h) computes the 2 points
+// (x, y, z0+2h .. z0+2h+1), so for every (dx, dy) the 4 input values around them are loaded once
+// and serve the 3 dz taps of both points.  Weights are FP32 in shared memory, read as float4
+// broadcasts.
+constexpr int kL3Threads = 256;
+
+// Layer 1: a1[p][o] = ReLU(scale * sum_t w1[o][0][t] rho[p + off_t]),  TO = BF16 or FP32.
+// 256 threads, each two z-points of the 32 x 4 x 4 block.
+template <class TO>
+__global__ void __launch_bounds__(kL3Threads) layer1_kernel(int nx, int ny, int nz, const float *__restrict__ rho,
+                                                          TO *__restrict__ out, const float *__restrict__ w,
+                                                          const double *__restrict__ scale, int wround) {
+    __shared__ __align__(16) float ws[27 * 16];  // [t][o]
+    __shared__ float xs[HZ][HY][HX];
+    int x0, y0, z0;
+    tile_origin(blockIdx.x, nx, ny, x0, y0, z0);
+    for (int i = threadIdx.x; i < 27 * 16; i += blockDim.x) {
+        const int o = i & 15, t = i >> 4;
+        float v = w[o * 27 + t];
+        if (wround) v = __bfloat162float(__float2bfloat16_rn(v));
+        ws[i] = v;
+    }
+    stage_input<1, float>(reinterpret_cast<unsigned char *>(&xs[0][0][0]), rho, nx, ny, nz, x0, y0, z0);
+    __syncthreads();
+    const int lx = threadIdx.x & 31, ly = (threadIdx.x >> 5) & 3, zh = threadIdx.x >> 7;
+    float acc[2][16];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[k][o] = 0.0f;
+#pragma unroll 1
+    for (int dxy = 0; dxy < 9; ++dxy) {
+        const int dy = dxy / 3, dx = dxy % 3;
+        float col[4];
+#pragma unroll
+        for (int zz = 0; zz < 4; ++zz) col[zz] = xs[2 * zh + zz][ly + dy][lx + dx];
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) {
+            const float4 *w4 = reinterpret_cast<const float4 *>(ws + ((dz * 3 + dy) * 3 + dx) * 16);
+#pragma unroll
+            for (int o4 = 0; o4 < 4; ++o4) {
+                const float4 wv = w4[o4];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float v = col[k + dz];
+                    acc[k][4 * o4 + 0] = fmaf(wv.x, v, acc[k][4 * o4 + 0]);
+                    acc[k][4 * o4 + 1] = fmaf(wv.y, v, acc[k][4 * o4 + 1]);
+                    acc[k][4 * o4 + 2] = fmaf(wv.z, v, acc[k][4 * o4 + 2]);
+                    acc[k][4 * o4 + 3] = fmaf(wv.w, v, acc[k][4 * o4 + 3]);
+                }
+            }
+        }
+    }
+    const float sc = static_cast<float>(*scale);
+    const int gx = x0 + lx, gy = y0 + ly;
+    if (gx >= nx || gy >= ny) return;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int gz = z0 + 2 * zh + k;
+        if (gz >= nz) break;
+        float v[16];
+#pragma unroll
+        for (int o = 0; o < 16; ++o) v[o] = fmaxf(acc[k][o] * sc, 0.0f);
+        const long long p = (static_cast<long long>(gz) * ny + gy) * nx + gx;
+        uint4 *dst = reinterpret_cast<uint4 *>(out + p * 16);
+        constexpr int E = Chunk<TO>::E;
+#pragma unroll
+        for (int g = 0; g < 16 / E; ++g) dst[g] = Chunk<TO>::pack(v + g * E);
+    }
+}
+
+// Layer 3: delta[p] = scale * sum_t sum_c w3[0][c][t] a2[p + off_t][c].  256 threads, each two
+// z-points of the 32 x 4 x 4 block; the input halo is copied as raw 16-byte channel chunks
+// (chunk-major, as stage_input) and widened to FP32 at use.
+template <class TI>
+__global__ void __launch_bounds__(kL3Threads) layer3_kernel(int nx, int ny, int nz, const TI *__restrict__ a2,
+                                                          float *__restrict__ out, const float *__restrict__ w,
+                                                          const double *__restrict__ scale, int wround) {
+    extern __shared__ __align__(16) unsigned char sm3[];
+    float *ws = reinterpret_cast<float *>(sm3);       // [t][c]
+    unsigned char *xs = sm3 + 27 * 16 * 4;              // [chunk][HP] x 16 B
+    int x0, y0, z0;
+    tile_origin(blockIdx.x, nx, ny, x0, y0, z0);
+    for (int i = threadIdx.x; i < 27 * 16; i += blockDim.x) {
+        const int c = i & 15, t = i >> 4;
+        float v = w[c * 27 + t];
+        if (wround) v = __bfloat162float(__float2bfloat16_rn(v));
+        ws[i] = v;
+    }
+    stage_input<16, TI>(xs, a2, nx, ny, nz, x0, y0, z0);
+    __syncthreads();
+    constexpr int E = Chunk<TI>::E, NG = 16 / E;
+    const int lx = threadIdx.x & 31, ly = (threadIdx.x >> 5) & 3, zh = threadIdx.x >> 7;  // points z 2zh, 2zh+1
+    float acc[2] = {0.0f, 0.0f};
+#pragma unroll 1
+    for (int dxy = 0; dxy < 9; ++dxy) {
+        const int dy = dxy / 3, dx = dxy % 3;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            float col[4][E];
+#pragma unroll
+            for (int zz = 0; zz < 4; ++zz)
+                Chunk<TI>::unpack(*reinterpret_cast<const uint4 *>(
+                                      xs + g * kRegion + (((2 * zh + zz) * HY + ly + dy) * HX + lx + dx) * 16),
+                                  col[zz]);
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz) {
+                const float *wt = ws + ((dz * 3 + dy) * 3 + dx) * 16 + g * E;
+#pragma unroll
+                for (int q = 0; q < E / 4; ++q) {
+                    const float4 wv = reinterpret_cast<const float4 *>(wt)[q];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const float *v = col[k + dz] + 4 * q;
+                        acc[k] = fmaf(wv.x, v[0], fmaf(wv.y, v[1], fmaf(wv.z, v[2], fmaf(wv.w, v[3], acc[k]))));
+                    }
+                }
+            }
+        }
+    }
+    const float sc = static_cast<float>(*scale);
+    const int gx = x0 + lx, gy = y0 + ly;
+    if (gx >= nx || gy >= ny) return;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int gz = z0 + 2 * zh + k;
+        if (gz >= nz) break;
+        out[(static_cast<long long>(gz) * ny + gy) * nx + gx] = acc[k] * sc;
+    }
+}
+
 // ---- weight gradient --------------------------------------------------------------------------------
 // part[block][entry] = sum over the block's points p of gout[p][co] in[p + off_t][ci], entry
 // (co * CIN + ci) * 27 + t (the master layout).  Thread j < 432 owns tap t = j / 16 and
@@ -615,16 +747,26 @@ template <class T>
 cudaError_t forward_t(NetWork &nw, int nx, int ny, int nz, cudaStream_t st) {
     const int wr = std::is_same<T, __nv_bfloat16>::value ? 1 : 0;
     cudaError_t e;
-    ConvArgs a{nx, ny, nz, nw.rho, nw.a1, nw.w + kNetW1, nullptr, &nw.sc->inv_rms, wr};
-    if ((e = conv<1, 16, float, T, T, EPI_RELU | EPI_SCALE, false>(a, st)) != cudaSuccess) return e;
+    const int tiles = num_tiles(nx, ny, nz);
+    layer1_kernel<T><<<tiles, kL3Threads, 0, st>>>(nx, ny, nz, nw.rho, static_cast<T *>(nw.a1), nw.w + kNetW1,
+                                                   &nw.sc->inv_rms, wr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ConvArgs a;
     if (std::is_same<T, __nv_bfloat16>::value && net_tensor_cores()) {
-        if ((e = conv16_tc(nx, ny, nz, nw.a1, nw.a2, nw.w + kNetW2, st)) != cudaSuccess) return e;
+        if ((e = conv16_tc_prep(nw.w + kNetW2, nw.w2b, st)) != cudaSuccess) return e;
+        if ((e = conv16_tc(nx, ny, nz, nw.a1, nw.a2, nw.w2b, st)) != cudaSuccess) return e;
+        nw.launches += 1;
     } else {
         a = ConvArgs{nx, ny, nz, nw.a1, nw.a2, nw.w + kNetW2, nullptr, nullptr, wr};
         if ((e = conv<16, 16, T, T, T, EPI_RELU, false>(a, st)) != cudaSuccess) return e;
     }
-    a = ConvArgs{nx, ny, nz, nw.a2, nw.delta, nw.w + kNetW3, nullptr, &nw.sc->rms, wr};
-    if ((e = conv<16, 1, T, float, T, EPI_SCALE, false>(a, st)) != cudaSuccess) return e;
+    {
+        constexpr size_t smem3 = 27 * 16 * 4 + static_cast<size_t>(16 / Chunk<T>::E) * kRegion;
+        if ((e = raise_smem_attr(reinterpret_cast<const void *>(&layer3_kernel<T>), smem3)) != cudaSuccess) return e;
+        layer3_kernel<T><<<tiles, kL3Threads, smem3, st>>>(nx, ny, nz, static_cast<const T *>(nw.a2), nw.delta,
+                                                           nw.w + kNetW3, &nw.sc->rms, wr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     nw.launches += 3;
     return cudaSuccess;
 }
@@ -680,6 +822,7 @@ cudaError_t net_alloc(NetWork &nw, long long n, int act, bool training) {
     if (e == cudaSuccess) e = cudaMalloc(&nw.delta, n * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&nw.part, 2 * kRedBlocks * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&nw.sc, sizeof(NetScal));
+    if (e == cudaSuccess) e = cudaMalloc(&nw.w2b, kConv16TcWeightBytes);
     if (e == cudaSuccess) e = cudaMemset(nw.sc, 0, sizeof(NetScal));
     if (keep_w) {
         nw.w = w_old;
@@ -717,7 +860,7 @@ cudaError_t net_alloc(NetWork &nw, long long n, int act, bool training) {
 
 void net_free(NetWork &nw) {
     void *ps[] = {nw.a1, nw.a2, nw.g1, nw.g2, nw.rho, nw.delta, nw.e, nw.ad, nw.part, nw.sc, nw.w, nw.grad,
-                  nw.m, nw.v, nw.wpart};
+                  nw.m, nw.v, nw.wpart, nw.w2b};
     for (void *p : ps) cudaFree(p);
     const long long launches = nw.launches;
     nw = NetWork();

@@ -48,6 +48,7 @@ struct NetWork {
     double *part = nullptr;              // reduction partials
     NetScal *sc = nullptr;
     float *w = nullptr;                  // master weights [7776]
+    void *w2b = nullptr;                 // layer 2 weights as the tensor-core operand
     float *grad = nullptr, *m = nullptr, *v = nullptr;  // training
     float *wpart = nullptr;              // per-block weight-gradient partials
     int wpart_blocks = 0;
@@ -79,7 +80,10 @@ cudaError_t net_to_f64(long long n, const float *src, double *dst, cudaStream_t 
 
 // The 16 -> 16 channel layer with ReLU on the tcgen05 tensor cores (BF16 in and out, FP32
 // accumulation): conv_tc.cu.  Used for the BF16 layer 2 while net_tensor_cores() is on.
-cudaError_t conv16_tc(int nx, int ny, int nz, const void *in, void *out, const float *w, cudaStream_t st);
+cudaError_t conv16_tc(int nx, int ny, int nz, const void *in, void *out, const void *wb, cudaStream_t st);
+// wb (27 * 512 bytes) = the layer's weights w ([16 out][16 in][27] FP32) as conv16_tc's BF16 operand.
+cudaError_t conv16_tc_prep(const float *w, void *wb, cudaStream_t st);
+constexpr size_t kConv16TcWeightBytes = 27 * 512;
 // 1 if a CTA of conv16_tc gave up waiting for its accumulators since the last call (then cleared).
 cudaError_t conv16_tc_status(int *err);
 bool &net_tensor_cores();
