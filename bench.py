@@ -47,6 +47,16 @@ def parse():
     return ap.parse_args()
 
 
+def measured_bf16_peak():
+    """Measured dense BF16 tensor throughput (TFLOP/s, burst) from MEASURED_PEAKS.json, else the
+    fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -824,20 +834,25 @@ def run_learned(args):
         dist.destroy_process_group()
     if rank != 0:
         return
-    pl, pms, pflops = main["prof5"]
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock (TFLOP/s)
-    achieved = (pflops / 1e12) / (pms / 1e3) if pms > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
-                "kernel": "learned correction (3 convolutions on FP32 CUDA cores + residual, judge, update)",
-                "launches": pl, "avg_region_us": (pms * 1e3 / pl) if pl else None,
-                "flops_per_region": (pflops / pl) if pl else None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+    peak, peak_kind = measured_peaks()
     l0n, l0ms, l0b = main["prof0"]
+    achieved = (l0b / 1e9) / (l0ms / 1e3) if l0ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "plane_relax_kernel<float,float,8> (finest level of the 256^3 cycle)",
+                "launches": l0n, "avg_launch_us": (l0ms * 1e3 / l0n) if l0n else None,
+                "algorithmic_bytes_per_launch": (l0b / l0n) if l0n else None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    pl, pms, pflops = main["prof5"]
+    bf16_peak = measured_bf16_peak()
+    learned_region = {"launches": pl, "avg_us": (pms * 1e3 / pl) if pl else None,
+                      "flops": (pflops / pl) if pl else None,
+                      "achieved_tflops": ((pflops / 1e12) / (pms / 1e3)) if pms > 0 else None,
+                      "bf16_tensor_peak_tflops": bf16_peak,
+                      "note": "the whole correction: residual, layer 1 (CUDA cores), layer 2 (tcgen05), layer 3 "
+                              "(CUDA cores), judge, update; flops of the three convolutions"}
     cpu = None
     if not args.no_cpu_baseline:
-        import oracle
-
         v, t1 = oracle_learned_sample(w, main["iters"])
         cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                "sample": f"one oracle application of the learned preconditioner at 64^3 ({t1:.1f} s), scaled by "
@@ -854,7 +869,7 @@ def run_learned(args):
                    "plain_10_fp64_s": f64["s"], "plain_10_fp64_iters": f64["iters"],
                    "speedup_vs_fp64": f64["s"] / main["s"], "speedup_vs_plain_10": plain["s"] / main["s"],
                    "speedup_vs_balanced_11": bal["s"] / main["s"],
-                   "level0_relax_avg_us": (l0ms * 1e3 / l0n) if l0n else None,
+                   "learned_correction": learned_region,
                    "training": tinfo, "l2": "256 MB buffer written before every timed solve",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline, "cpu_baseline": cpu,

@@ -598,7 +598,8 @@ constexpr int max_lines_per_group() {
 }
 
 // Relax every line of one colour of 2D level m that this CTA owns: lines colour + 2k with
-// k = rank + R i; warp w takes i = w, w + nw, ..., NLM at a time while it has NLM left.
+// k = rank + R i; warp w takes i = w, w + nw, ..., NLM at a time while it has NLM left, then
+// pairs, then single lines (three compiled bodies in all).
 template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
                                              int m, int colour, S *plane, bool accumulate, int nbmode, int out,
@@ -614,6 +615,12 @@ __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const Plan
 #pragma unroll
             for (int l = 0; l < NLM; ++l) ys[l] = Y(i + l * nw);
             relax_group<S, C, K, NLM, CL>(a, c, fac, m, ys, NLM, plane, accumulate, nbmode, out, lane);
+        }
+    }
+    if constexpr (NLM > 2) {  // pairs keep two dependency chains interleaved
+        for (; i + nw < nown; i += 2 * nw) {
+            const int ys[2] = {Y(i), Y(i + nw)};
+            relax_group<S, C, K, 2, CL>(a, c, fac, m, ys, 2, plane, accumulate, nbmode, out, lane);
         }
     }
     // the rest one line at a time (on the coarse levels the critical path is one line per warp)
