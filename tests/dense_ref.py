@@ -145,3 +145,16 @@ def assemble_columns(apply, n: int, shape) -> np.ndarray:
         e[j] = 1.0
         M[:, j] = np.asarray(apply(e.reshape(shape))).ravel()
     return M
+
+
+def lap7(u: np.ndarray) -> np.ndarray:
+    """7-point Dirichlet Laplacian of a (nz, ny, nx) array by numpy slicing (an independent
+    restatement of the model operator for residual checks)."""
+    out = 6.0 * u
+    out[1:] -= u[:-1]
+    out[:-1] -= u[1:]
+    out[:, 1:] -= u[:, :-1]
+    out[:, :-1] -= u[:, 1:]
+    out[:, :, 1:] -= u[:, :, :-1]
+    out[:, :, :-1] -= u[:, :, 1:]
+    return out

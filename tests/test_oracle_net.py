@@ -254,3 +254,18 @@ def test_loss_gradient_matches_scipy_restatement(orc, act_bf16):
     if act_bf16:
         _, g64 = orc.net_loss_grad(w, rho, e)
         assert np.linalg.norm(g - g64) > 1e-4 * np.linalg.norm(g64)
+
+
+def test_crop_around_a_point_reproduces_the_full_grid(orc):
+    """The correction at a point depends only on the residual within distance 3 (three 3x3x3
+    layers), and its RMS scaling cancels (positive homogeneity), so the oracle on the neighbourhood
+    clipped to the grid gives the full-grid value -- the basis of the sampled full-size GPU check."""
+    n = 14
+    w = inputs.net_init_weights(seed=141, last_scale=1.0)
+    rho = inputs.rhs(n, n, n, seed=142)
+    full = orc.net_forward(w, rho)
+    for (z, y, x) in [(0, 0, 0), (5, 6, 7), (13, 13, 13), (3, 0, 9), (13, 2, 6)]:
+        zs, ys, xs = max(z - 3, 0), max(y - 3, 0), max(x - 3, 0)
+        c = np.ascontiguousarray(rho[zs:z + 4, ys:y + 4, xs:x + 4])
+        v = orc.net_forward(w, c)[z - zs, y - ys, x - xs]
+        assert abs(v - full[z, y, x]) <= 1e-12 * max(abs(full[z, y, x]), 1.0)
