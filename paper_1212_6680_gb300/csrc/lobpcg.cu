@@ -9,9 +9,10 @@
 // Columns whose residual meets the tolerance are soft-locked (kept in X, dropped from W, P).
 // W is orthogonalised against X and W, P are orthonormalised (Cholesky QR) before the
 // Rayleigh-Ritz step, so S^T S stays well conditioned.
-// Device: FP64 block kernels (Gram products with split-K partial sums, tall-skinny block
-// updates).  Host: the k x k (k <= 3m) FP64 generalized eigenproblem by Cholesky reduction
-// and cyclic Jacobi.
+// Device: block kernels (Gram products with split-K partial sums, tall-skinny block updates)
+// with FP64-accurate products carried out on the FP32 pipes ("double-float" arithmetic, see
+// below).  Host: the k x k (k <= 3m) FP64 generalized eigenproblem by Cholesky reduction and
+// cyclic Jacobi.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -20,6 +21,7 @@
 
 #include "../../include/smg.h"
 #include "lobpcg.h"
+#include "plane_relax.cuh"  // widen_f32 / narrow_f64 (integer-pipe conversions)
 
 namespace smg {
 
@@ -30,6 +32,35 @@ constexpr int kGRows = 64;       // rows staged per step
 constexpr int kGChunk = 8192;    // rows per CTA (split-K)
 constexpr int kMulCols = 16;     // output columns per block_mul thread
 
+// ---- double-float arithmetic -------------------------------------------------------------------
+// On this part an FP64 FMA costs as much SM time as ~64 FP32 ones, and the LOBPCG block kernels
+// are nothing but FP64 multiply-adds.  They run instead on pairs of floats (hi, lo) with
+// hi + lo = the FP64 operand to ~2^-48: Dekker's exact product via FMA (p = a*b,
+// e = fma(a, b, -p), a*b = p + e exactly) plus the two cross terms, accumulated with Knuth's
+// TwoSum (s = a + b and the exact rounding error of that addition), about a dozen FP32 operations
+// per multiply-add.  Each FP64 input is split once (hi = its rounding to FP32, lo = the
+// rounding of the exact remainder); the final value is hi + lo in FP64.
+
+__device__ __forceinline__ void df_split(double x, float &hi, float &lo) {
+    hi = narrow_f64(x);
+    lo = narrow_f64(x - widen_f32(hi));  // x - hi is exact in FP64
+}
+
+// (S, s) += a * b for a = ah + al, b = bh + bl.  The exact steps use the round-to-nearest
+// intrinsics, which the compiler never contracts into FMAs (a fused S + ah*bh would break them).
+__device__ __forceinline__ void df_mac(float &S, float &s, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = fmaf(ah, bh, -p);                  // ah*bh = p + e exactly
+    const float t = fmaf(ah, bl, fmaf(al, bh, e));     // e + the cross terms (al*bl ~ 2^-48 dropped)
+    const float u = __fadd_rn(S, p);                    // TwoSum(S, p)
+    const float bb = __fsub_rn(u, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(u, bb)), __fsub_rn(p, bb));
+    S = u;
+    s = __fadd_rn(s, __fadd_rn(err, t));
+}
+
+__device__ __forceinline__ double df_value(float S, float s) { return widen_f32(S) + widen_f32(s); }
+
 // Partial Gram: part[chunk][ti][tj] tile of U^T V over rows [chunk*kGChunk, ...).  FP64 FMAs are
 // the scarce resource on this part, so the tiles are small (no work on padding beyond the next
 // multiple of 16) and, for a symmetric product (sym = 1, U^T V = V^T U), only the tiles on and
@@ -37,31 +68,34 @@ constexpr int kMulCols = 16;     // output columns per block_mul thread
 __global__ void __launch_bounds__(256) gram_partial_kernel(long long n, int k1, int k2, const double *__restrict__ U,
                                                            const double *__restrict__ V, double *__restrict__ part,
                                                            int ntj, int sym) {
-    __shared__ double su[kGRows][kGT + 1];
-    __shared__ double sv[kGRows][kGT + 1];
+    __shared__ float suh[kGRows][kGT + 1], sul[kGRows][kGT + 1];
+    __shared__ float svh[kGRows][kGT + 1], svl[kGRows][kGT + 1];
     const int tile = blockIdx.y, ti = tile / ntj, tj = tile % ntj;
     if (sym && tj < ti) return;
     const int i0 = ti * kGT, j0 = tj * kGT;
     const long long r0 = static_cast<long long>(blockIdx.x) * kGChunk;
     const long long r1 = min(n, r0 + kGChunk);
     const int ti_ = threadIdx.x >> 4, tj_ = threadIdx.x & 15;
-    double acc0 = 0.0, acc1 = 0.0;
+    float S0 = 0.0f, s0 = 0.0f, S1 = 0.0f, s1 = 0.0f;  // two independent accumulators
     for (long long rb = r0; rb < r1; rb += kGRows) {
         for (int t = threadIdx.x; t < kGRows * kGT; t += blockDim.x) {
             const int rr = t % kGRows, cc = t / kGRows;
             const long long r = rb + rr;
-            su[rr][cc] = (r < r1 && i0 + cc < k1) ? U[static_cast<long long>(i0 + cc) * n + r] : 0.0;
-            sv[rr][cc] = (r < r1 && j0 + cc < k2) ? V[static_cast<long long>(j0 + cc) * n + r] : 0.0;
+            const double u = (r < r1 && i0 + cc < k1) ? U[static_cast<long long>(i0 + cc) * n + r] : 0.0;
+            const double v = (r < r1 && j0 + cc < k2) ? V[static_cast<long long>(j0 + cc) * n + r] : 0.0;
+            df_split(u, suh[rr][cc], sul[rr][cc]);
+            df_split(v, svh[rr][cc], svl[rr][cc]);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int rr = 0; rr < kGRows; rr += 2) {  // two independent chains
-            acc0 = fma(su[rr][ti_], sv[rr][tj_], acc0);
-            acc1 = fma(su[rr + 1][ti_], sv[rr + 1][tj_], acc1);
+#pragma unroll 4
+        for (int rr = 0; rr < kGRows; rr += 2) {
+            df_mac(S0, s0, suh[rr][ti_], sul[rr][ti_], svh[rr][tj_], svl[rr][tj_]);
+            df_mac(S1, s1, suh[rr + 1][ti_], sul[rr + 1][ti_], svh[rr + 1][tj_], svl[rr + 1][tj_]);
         }
         __syncthreads();
     }
-    part[(static_cast<long long>(blockIdx.x) * gridDim.y + tile) * kGT * kGT + ti_ * kGT + tj_] = acc0 + acc1;
+    part[(static_cast<long long>(blockIdx.x) * gridDim.y + tile) * kGT * kGT + ti_ * kGT + tj_] =
+        df_value(S0, s0) + df_value(S1, s1);
 }
 
 // G[i][j] (k1 x k2 row-major) = sum over chunks of the partial tiles (compensated summation);
@@ -88,32 +122,36 @@ __global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int nti
     G[idx] = s + c;
 }
 
-// Y = alpha * U C + beta * Y  (U: n x k, C: k x m2 row-major, Y: n x m2, column stride n)
+// Y = alpha * U C + beta * Y  (U: n x k, C: k x m2 row-major, Y: n x m2, column stride n), the
+// products in double-float arithmetic.
 __global__ void block_mul_kernel(long long n, int k, int m2, const double *__restrict__ U,
                                  const double *__restrict__ C, double alpha, double beta, double *__restrict__ Y) {
-    extern __shared__ double sc[];
+    extern __shared__ float sc2[];  // [k][kMulCols] hi, then lo
+    float *ch = sc2, *cl = sc2 + k * kMulCols;
     const int j0 = blockIdx.y * kMulCols;
     const int nc = min(kMulCols, m2 - j0);
     for (int t = threadIdx.x; t < k * kMulCols; t += blockDim.x) {
         const int i = t / kMulCols, j = t % kMulCols;
-        sc[t] = (j < nc) ? C[i * m2 + j0 + j] : 0.0;
+        df_split((j < nc) ? C[i * m2 + j0 + j] : 0.0, ch[t], cl[t]);
     }
     __syncthreads();
     const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    double acc[kMulCols];
+    float S[kMulCols], sl[kMulCols];
 #pragma unroll
-    for (int j = 0; j < kMulCols; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kMulCols; ++j) S[j] = sl[j] = 0.0f;
     for (int i = 0; i < k; ++i) {
-        const double u = U[static_cast<long long>(i) * n + r];
+        float uh, ul;
+        df_split(U[static_cast<long long>(i) * n + r], uh, ul);
 #pragma unroll
-        for (int j = 0; j < kMulCols; ++j) acc[j] = fma(u, sc[i * kMulCols + j], acc[j]);
+        for (int j = 0; j < kMulCols; ++j) df_mac(S[j], sl[j], uh, ul, ch[i * kMulCols + j], cl[i * kMulCols + j]);
     }
 #pragma unroll
     for (int j = 0; j < kMulCols; ++j) {
         if (j < nc) {
+            const double acc = df_value(S[j], sl[j]);
             double *y = Y + static_cast<long long>(j0 + j) * n + r;
-            *y = (beta == 0.0) ? alpha * acc[j] : fma(alpha, acc[j], beta * *y);
+            *y = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *y);
         }
     }
 }
@@ -253,7 +291,7 @@ int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<d
 int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, double alpha, double beta, double *Y) {
     LCHK(cudaMemcpyAsync(c.w.coef, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, c.st));
     dim3 grid(cdiv(c.n, 256), cdiv(m2, kMulCols));
-    block_mul_kernel<<<grid, 256, sizeof(double) * k * kMulCols, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y);
+    block_mul_kernel<<<grid, 256, 2 * sizeof(float) * k * kMulCols, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y);
     LCHK(cudaGetLastError());
     // the host vector C may be reused right after; the copy above is stream-ordered but reads
     // host memory asynchronously only for pinned memory, so pageable C is safe here
