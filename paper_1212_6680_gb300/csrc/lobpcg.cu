@@ -38,12 +38,38 @@ constexpr int kMulCols = 16;     // output columns per block_mul thread
 // hi + lo = the FP64 operand to ~2^-48: Dekker's exact product via FMA (p = a*b,
 // e = fma(a, b, -p), a*b = p + e exactly) plus the two cross terms, accumulated with Knuth's
 // TwoSum (s = a + b and the exact rounding error of that addition), about a dozen FP32 operations
-// per multiply-add.  Each FP64 input is split once (hi = its rounding to FP32, lo = the
-// rounding of the exact remainder); the final value is hi + lo in FP64.
+// per multiply-add.  Each FP64 input is split once (df_split); the final value is hi + lo in
+// FP64.
 
+// x = hi + lo with integer operations only (no FP64 or conversion instruction): hi keeps the top
+// 24 significant bits of x (truncated, so exactly a float), lo the next 24 of the remaining 29
+// mantissa bits (truncated: |x - hi - lo| < 2^-47 |x| for |x| >= 2^-75; below that lo underflows
+// and only hi remains, 2^-24).  |x| < 2^-126 flushes to zero.  Entries of the normalised block
+// vectors of a 128^3 problem are ~1e-3, far inside the exact range.
 __device__ __forceinline__ void df_split(double x, float &hi, float &lo) {
-    hi = narrow_f64(x);
-    lo = narrow_f64(x - widen_f32(hi));  // x - hi is exact in FP64
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
+    const int E = static_cast<int>((b >> 52) & 0x7ffu) - 1023;  // unbiased exponent
+    if (E < -126 || E > 127) {  // zero, tiny, or beyond the float range (not met by this solver)
+        hi = lo = 0.0f;
+        if (E > 127) hi = __uint_as_float(sign | 0x7f800000u);
+        return;
+    }
+    const unsigned mhi = static_cast<unsigned>((b >> 29) & 0x7fffffu);           // mantissa bits 51..29
+    hi = __uint_as_float(sign | (static_cast<unsigned>(E + 127) << 23) | mhi);
+    const unsigned L = static_cast<unsigned>(b & 0x1fffffffu);                   // mantissa bits 28..0
+    if (L == 0u) {
+        lo = 0.0f;
+        return;
+    }
+    const int k = 31 - __clz(L);                  // L = 1.f x 2^k, lo = L x 2^(E - 52)
+    const int fe = k + E - 52 + 127;
+    if (fe <= 0) {
+        lo = 0.0f;
+        return;
+    }
+    const unsigned mant = (k >= 23) ? ((L >> (k - 23)) & 0x7fffffu) : ((L << (23 - k)) & 0x7fffffu);
+    lo = __uint_as_float(sign | (static_cast<unsigned>(fe) << 23) | mant);
 }
 
 // (S, s) += a * b for a = ah + al, b = bh + bl.  The exact steps use the round-to-nearest
