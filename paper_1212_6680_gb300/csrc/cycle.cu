@@ -10,6 +10,7 @@
 //   u[2j+1] += e[j],  u[2j] += wm(2j) e[j-1] + wp(2j) e[j]                   (P)
 // Both are bandwidth-bound stencils; one thread per output point, x fastest (coalesced), the
 // 15-point residual reads its five planes through L1/L2.
+#include <cstdlib>
 #include "plane_relax.cuh"
 #include "transfer.cuh"
 
@@ -75,6 +76,8 @@ __global__ void restrict_kernel(int nx, int ny, int nzf, int nzc, long long tota
                                 const S *__restrict__ u, S *__restrict__ fc, const double *__restrict__ zcoef64,
                                 const float *__restrict__ zcoef32, long long vsf, long long vsc) {
     // blockIdx.y: one coarse plane, blockIdx.z: one batch entry; x covers the plane
+    pdl_trigger();
+    pdl_wait();
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= nx * ny) return;
     const int b = blockIdx.z;
@@ -87,6 +90,8 @@ template <class S, class C>
 __global__ void prolong_kernel(int nx, int ny, int nzf, int nzc, long long total, S *__restrict__ u,
                                const S *__restrict__ uc, const double *__restrict__ zcoef64,
                                const float *__restrict__ zcoef32, long long vsf, long long vsc) {
+    pdl_trigger();
+    pdl_wait();
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= nx * ny) return;
     const int b = blockIdx.z;
@@ -97,6 +102,16 @@ static inline unsigned nblocks(long long total, int threads) {
     return static_cast<unsigned>((total + threads - 1) / threads);
 }
 
+// Programmatic dependent launch for the kernel chain of one cycle: on unless the environment
+// sets SMG_PDL=0 (read once per process).
+bool &pdl_enabled() {
+    static bool on = [] {
+        const char *v = std::getenv("SMG_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 cudaError_t launch_restrict(Prec storage, int nx, int ny, int nzf, int nb, const void *f, const void *u, void *fc,
                             const double *zcoef, const float *zcoef32, long long vsf, long long vsc, cudaStream_t st) {
     const int nzc = nzf / 2;
@@ -104,24 +119,25 @@ cudaError_t launch_restrict(Prec storage, int nx, int ny, int nzf, int nb, const
     if (total == 0) return cudaSuccess;
     const int T = 256;
     const dim3 grid(nblocks(static_cast<long long>(nx) * ny, T), nzc, nb);
+    cudaError_t e = cudaSuccess;
     switch (storage) {
     case Prec::F64:
-        restrict_kernel<double, double><<<grid, T, 0, st>>>(
+        e = launch_pdl(restrict_kernel<double, double>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<const double *>(f), static_cast<const double *>(u),
             static_cast<double *>(fc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::F32:
-        restrict_kernel<float, float><<<grid, T, 0, st>>>(
+        e = launch_pdl(restrict_kernel<float, float>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<const float *>(f), static_cast<const float *>(u),
             static_cast<float *>(fc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::BF16:
-        restrict_kernel<__nv_bfloat16, float><<<grid, T, 0, st>>>(
+        e = launch_pdl(restrict_kernel<__nv_bfloat16, float>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<const __nv_bfloat16 *>(f), static_cast<const __nv_bfloat16 *>(u),
             static_cast<__nv_bfloat16 *>(fc), zcoef, zcoef32, vsf, vsc);
         break;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_prolong(Prec storage, int nx, int ny, int nzf, int nb, void *u, const void *uc,
@@ -130,22 +146,23 @@ cudaError_t launch_prolong(Prec storage, int nx, int ny, int nzf, int nb, void *
     const long long total = static_cast<long long>(nx) * ny * nzf * nb;
     const int T = 256;
     const dim3 grid(nblocks(static_cast<long long>(nx) * ny, T), nzf, nb);
+    cudaError_t e = cudaSuccess;
     switch (storage) {
     case Prec::F64:
-        prolong_kernel<double, double><<<grid, T, 0, st>>>(
+        e = launch_pdl(prolong_kernel<double, double>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<double *>(u), static_cast<const double *>(uc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::F32:
-        prolong_kernel<float, float><<<grid, T, 0, st>>>(
+        e = launch_pdl(prolong_kernel<float, float>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<float *>(u), static_cast<const float *>(uc), zcoef, zcoef32, vsf, vsc);
         break;
     case Prec::BF16:
-        prolong_kernel<__nv_bfloat16, float><<<grid, T, 0, st>>>(
+        e = launch_pdl(prolong_kernel<__nv_bfloat16, float>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<__nv_bfloat16 *>(u), static_cast<const __nv_bfloat16 *>(uc), zcoef,
             zcoef32, vsf, vsc);
         break;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // ---- conversions ------------------------------------------------------------------------------

@@ -154,6 +154,8 @@ __global__ void k_true_residual(int nx, int ny, int nz, const double *__restrict
 template <class S>
 __global__ void k_dots_beta(long long n, const S *__restrict__ s, const double *__restrict__ r,
                             const double *__restrict__ dr, KrylovScalars *sc, DSum *part, unsigned *counter) {
+    pdl_trigger();
+    pdl_wait();
     const int variant = sc->variant;
     const bool need_sdr = (variant == 1) && (sc->restart == 0);
     double a0 = 0.0, a1 = 0.0;
@@ -185,6 +187,8 @@ __global__ void k_dots_beta(long long n, const S *__restrict__ s, const double *
 // p = s + beta p
 template <class S>
 __global__ void k_update_p(long long n, const S *__restrict__ s, double *__restrict__ p, const KrylovScalars *sc) {
+    pdl_trigger();
+    pdl_wait();
     const double beta = sc->beta;
     const int n32 = static_cast<int>(n);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
@@ -196,6 +200,8 @@ __global__ void k_update_p(long long n, const S *__restrict__ s, double *__restr
 // q = A p ; pq = (p, q) ; alpha = rho / pq
 __global__ void k_spmv_alpha(int nx, int ny, int nz, const double *__restrict__ p, double *__restrict__ q,
                              KrylovScalars *sc, DSum *part, unsigned *counter) {
+    pdl_trigger();
+    pdl_wait();
     const long long np = static_cast<long long>(nx) * ny, n = np * nz;
     double a0 = 0.0;
     const int npi = nx * ny, n32 = npi * nz;
@@ -224,6 +230,8 @@ template <class S>
 __global__ void k_update_xr(long long n, double *__restrict__ x, const double *__restrict__ p, double *__restrict__ r,
                             const double *__restrict__ q, double *__restrict__ dr, S *__restrict__ f0,
                             KrylovScalars *sc, DSum *part, unsigned *counter) {
+    pdl_trigger();
+    pdl_wait();
     const double alpha = sc->alpha;
     const bool want_dr = (sc->variant == 1);
     double a0 = 0.0;
@@ -284,13 +292,18 @@ cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void 
                                double *q, double *dr, void *f0, KrylovWork &w, cudaStream_t st) {
     const long long n = static_cast<long long>(nx) * ny * nz;
     const int nb = reduction_blocks(n);
+    cudaError_t e = cudaSuccess;
     SMG_PREC_SWITCH(st_prec, {
-        k_dots_beta<S><<<nb, 256, 0, st>>>(n, static_cast<const S *>(s), r, dr, w.sc, w.part, w.counter);
-        k_update_p<S><<<nb, 256, 0, st>>>(n, static_cast<const S *>(s), p, w.sc);
-        k_spmv_alpha<<<nb, 256, 0, st>>>(nx, ny, nz, p, q, w.sc, w.part, w.counter);
-        k_update_xr<S><<<nb, 256, 0, st>>>(n, x, p, r, q, dr, static_cast<S *>(f0), w.sc, w.part, w.counter);
+        const S *sp = static_cast<const S *>(s);
+        S *f0p = static_cast<S *>(f0);
+        if (e == cudaSuccess) e = launch_pdl(k_dots_beta<S>, dim3(nb), dim3(256), 0, st, n, sp, r, dr, w.sc, w.part, w.counter);
+        if (e == cudaSuccess) e = launch_pdl(k_update_p<S>, dim3(nb), dim3(256), 0, st, n, sp, p, w.sc);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_spmv_alpha, dim3(nb), dim3(256), 0, st, nx, ny, nz, p, q, w.sc, w.part, w.counter);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_update_xr<S>, dim3(nb), dim3(256), 0, st, n, x, p, r, q, dr, f0p, w.sc, w.part, w.counter);
     });
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace smg

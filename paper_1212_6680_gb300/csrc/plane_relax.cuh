@@ -75,6 +75,10 @@ __device__ __forceinline__ float narrow_f64(double d) {
     return __uint_as_float((hi & 0x80000000u) | (((e - 896u) << 23) + mant));
 }
 
+// Programmatic dependent launch (see launch_pdl): both are no-ops for a kernel launched without it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <class C, class S> __device__ __forceinline__ C ldv(const S *p);
 template <> __device__ __forceinline__ float ldv<float, float>(const float *p) { return *p; }
 template <> __device__ __forceinline__ float ldv<float, __nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
@@ -828,6 +832,9 @@ __device__ __forceinline__ void plane_task(const PlaneRelaxArgs &a, int pidx, in
         tri_factor<C, K>(fac, C(2) * lc[1] + lc[4], -lc[1], nx, lane);
         trifac_store<C, K>(c.fs + sidx * trifac_fields<C, K>() * 32, fac, lane);
     }
+    // everything above reads only the hierarchy's coefficient tables: with programmatic dependent
+    // launch it overlaps the previous kernel; from here on the planes are read and written
+    pdl_wait();
     fac.dg = C(0);  // no real line matrix has a zero diagonal: the first line always refreshes
     fac.of = C(0);
     const int P = a.P;
@@ -890,6 +897,7 @@ __device__ __forceinline__ void plane_task(const PlaneRelaxArgs &a, int pidx, in
 template <class S, class C, int K, bool CL>
 __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const __grid_constant__ PlaneRelaxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     int pidx, rank;
     if constexpr (CL) {
         rank = static_cast<int>(cg::this_cluster().block_rank());
@@ -913,22 +921,22 @@ int set_smem_attr(size_t smem) {
 template <class S, class C, int K, bool CL>
 cudaError_t launch_pr(int nplanes, int nb, int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
     if constexpr (!CL) {
-        dim3 grid(nplanes, nb);
-        plane_relax_kernel<S, C, K, false><<<grid, threads, smem, st>>>(a);
-        return cudaGetLastError();
+        return launch_pdl(plane_relax_kernel<S, C, K, false>, dim3(nplanes, nb), dim3(threads), smem, st, a);
     } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(nplanes * a.R, nb, 1);
         cfg.blockDim = dim3(threads, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = a.R;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = pdl_enabled() ? 2 : 1;
         return cudaLaunchKernelEx(&cfg, plane_relax_kernel<S, C, K, true>, a);
     }
 }

@@ -51,6 +51,29 @@ void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H);
 // Sets the message smg_last_error() returns on the calling thread.
 void set_last_error(const std::string &msg);
 
+// Programmatic dependent launch: a kernel launched through launch_pdl may begin while the previous
+// kernel of the stream is still running.  Every kernel launched this way executes pdl_wait()
+// (griddepcontrol.wait) before it reads or writes anything its predecessors touch, and may call
+// pdl_trigger() so that its own successor can start its independent prologue early.  The
+// process-wide switch (on by default) exists for measurement.
+bool &pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // The dynamic shared-memory limit of a kernel belongs to the kernel (per device), not to a
 // handle: it is only ever raised, so that a handle with a smaller layout never lowers it under
 // the launches of another handle that is still alive.
