@@ -1,5 +1,8 @@
 // batched_inst.cu -- instantiates the persistent multi-system V-cycle kernel for one x-line chunk
 // size K = SMG_K (1..4, i.e. nx <= 128), FP32 storage (FP32 cycle, FP64 coarsest plane).
+// The persistent kernel holds the FP32 and the FP64 plane cycles in one body; the FP64 factors
+// (K > 2) go out of line so that their registers do not weigh on the whole kernel.
+#define SMG_FAC_REG_BYTES 16
 #include "batched.cuh"
 
 #ifndef SMG_K

@@ -112,7 +112,7 @@ template <class S>
 __global__ void k_init_residual(int nx, int ny, int nz, const double *__restrict__ b, const double *__restrict__ x,
                                 double *__restrict__ r, S *__restrict__ f0, KrylovScalars *sc, DSum *part,
                                 unsigned *counter) {
-    const long long np = static_cast<long long>(nx) * ny, n = np * nz;
+    const long long np = static_cast<long long>(nx) * ny;
     double a0 = 0.0, a1 = 0.0;
     const int npi = nx * ny, n32 = npi * nz;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
@@ -137,7 +137,7 @@ __global__ void k_init_residual(int nx, int ny, int nz, const double *__restrict
 // tt = ||b - A x||^2 (true residual).
 __global__ void k_true_residual(int nx, int ny, int nz, const double *__restrict__ b, const double *__restrict__ x,
                                 KrylovScalars *sc, DSum *part, unsigned *counter) {
-    const long long np = static_cast<long long>(nx) * ny, n = np * nz;
+    const long long np = static_cast<long long>(nx) * ny;
     double a0 = 0.0;
     const int npi = nx * ny, n32 = npi * nz;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
@@ -202,7 +202,7 @@ __global__ void k_spmv_alpha(int nx, int ny, int nz, const double *__restrict__ 
                              KrylovScalars *sc, DSum *part, unsigned *counter) {
     pdl_trigger();
     pdl_wait();
-    const long long np = static_cast<long long>(nx) * ny, n = np * nz;
+    const long long np = static_cast<long long>(nx) * ny;
     double a0 = 0.0;
     const int npi = nx * ny, n32 = npi * nz;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {

@@ -122,7 +122,7 @@ __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 template <class C, int K>
-__device__ __noinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of, const int n, const int lane) {
+__device__ __forceinline__ void tri_factor_body(TriFac<C, K> &f, const C dg, const C of, const int n, const int lane) {
     const int i0 = lane * K;
     auto A = [&](int j) -> C { const int i = i0 + j; return (i > 0 && i < n) ? of : C(0); };
     auto B = [&](int j) -> C { const int i = i0 + j; return (i < n) ? dg : C(1); };
@@ -180,6 +180,24 @@ __device__ __noinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of,
         f.k2[t] = k2;
     }
     f.rbf = recip(RB);
+}
+
+template <class C, int K>
+__device__ __noinline__ void tri_factor_call(TriFac<C, K> &f, const C dg, const C of, const int n, const int lane) {
+    tri_factor_body<C, K>(f, dg, of, n, lane);
+}
+
+// Inlined, the factors of the current line matrix stay in registers for the whole 2D cycle; an
+// out-of-line call puts them in local memory instead (every tri_apply then reloads them), which
+// is only worth it when the registers would otherwise spill: the factors take 4K + 15
+// values per lane, so they are kept in registers while K * sizeof(C) <= SMG_FAC_REG_BYTES.
+#ifndef SMG_FAC_REG_BYTES
+#define SMG_FAC_REG_BYTES 32
+#endif
+template <class C, int K>
+__device__ __forceinline__ void tri_factor(TriFac<C, K> &f, const C dg, const C of, const int n, const int lane) {
+    if constexpr (K * sizeof(C) <= SMG_FAC_REG_BYTES) tri_factor_body<C, K>(f, dg, of, n, lane);
+    else tri_factor_call<C, K>(f, dg, of, n, lane);
 }
 
 // A factor set in shared memory: field k of lane l at fs[k * 32 + l].  Only the fields the
@@ -491,7 +509,6 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
                                             int nbmode, int out, int lane) {
     const int nx = c.nx, nym = a.ny_m[m];
     C d[NL][K];
-#pragma unroll
     CoefRow<C> cr[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
