@@ -142,11 +142,6 @@ int ensure_levels(smg_ctx *h, int nb) {
     }
     h->lay_c = plan_plane_layout(H, compute_bytes(h->prec), kSmemBudget);
     h->lay_d = plan_plane_layout(H, 8, kSmemBudget);
-    const long long slots = static_cast<long long>((H.nz + 1) / 2) * nb;
-    const size_t per = std::max(static_cast<size_t>(h->lay_c.ws_per_plane) * compute_bytes(h->prec),
-                                static_cast<size_t>(h->lay_d.ws_per_plane) * 8);
-    h->ws_bytes = std::max<size_t>(per * slots, 256);
-    SMG_CUDA(cudaMalloc(&h->d_ws, h->ws_bytes));
     const bool f64c = (h->prec == Prec::F64);
     const int K = instantiated_K(h->nx);
     if (set_plane_relax_smem(h->prec, f64c, false, K, h->lay_c.smem_bytes) != 0)
@@ -182,6 +177,17 @@ int ensure_levels(smg_ctx *h, int nb) {
         if (cl_smem > 0 && set_plane_relax_smem(h->prec, cf64, true, K, cl_smem) != 0)
             return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, cluster) failed");
     }
+    // global slots for the 2D-cycle arrays that are not on chip: one per CTA (at most one per
+    // plane of a colour of the finest level) or one per cluster, sized for the largest layout
+    size_t per = std::max(static_cast<size_t>(h->lay_c.ws_per_plane) * compute_bytes(h->prec),
+                          static_cast<size_t>(h->lay_d.ws_per_plane) * 8);
+    for (int lr = 1; lr <= 4; ++lr) {
+        if (h->cl_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_cl[lr].ws_per_plane) * 8);
+        if (h->cl32_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_cl32[lr].ws_per_plane) * 4);
+    }
+    const long long slots = static_cast<long long>((H.nz + 1) / 2) * nb;
+    h->ws_bytes = std::max<size_t>(per * slots, 256);
+    SMG_CUDA(cudaMalloc(&h->d_ws, h->ws_bytes));
     h->nb_alloc = nb;
     h->alloc_prec = h->prec;
     return SMG_OK;

@@ -215,6 +215,21 @@ static int chunk_K(int nx) {
     return 16;
 }
 
+// Placement priority of the 2D-cycle arrays: both arrays of levels >= 2 (coarse to fine), then
+// u_1, u_0, g_1, g_0.  Entries are (level, 0 = u / 1 = g).
+static std::vector<std::pair<int, int>> layout_order(const HostHierarchy &H) {
+    std::vector<std::pair<int, int>> order;
+    for (int m = H.P - 1; m >= 2; --m) {
+        order.push_back({m, 0});
+        order.push_back({m, 1});
+    }
+    if (H.P > 1) order.push_back({1, 0});
+    order.push_back({0, 0});
+    if (H.P > 1) order.push_back({1, 1});
+    order.push_back({0, 1});
+    return order;
+}
+
 // Shared memory starts with the plane's coefficient table and the factor sets of the interior
 // line matrices of the first MF 2D levels (the levels with many lines; the others factor on
 // the fly), then the 2D-cycle arrays, placed greedily: the coarsest levels first (latency-bound,
@@ -231,17 +246,7 @@ PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t 
     smem_elems += 2 * static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
     long long gl = 0;
     const size_t budget_elems = smem_budget / elem_bytes;
-    // priority: both arrays of levels >= 2 (coarse to fine), then u_1, u_0, g_1, g_0
-    std::vector<std::pair<int, int>> order;  // (level, 0 = u / 1 = g)
-    for (int m = H.P - 1; m >= 2; --m) {
-        order.push_back({m, 0});
-        order.push_back({m, 1});
-    }
-    if (H.P > 1) order.push_back({1, 0});
-    order.push_back({0, 0});
-    if (H.P > 1) order.push_back({1, 1});
-    order.push_back({0, 1});
-    for (const auto &o : order) {
+    for (const auto &o : layout_order(H)) {
         const int m = o.first;
         const size_t sz = align4(static_cast<size_t>(H.nx) * H.ny_m[m]);
         if (smem_elems + sz <= budget_elems) {
@@ -272,20 +277,32 @@ PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes,
     P.MF = factor_levels(H, P.K, elem_bytes, smem_budget);
     P.off_fs = static_cast<int>(smem_elems);
     smem_elems += 2 * static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
-    for (int m = H.P - 1; m >= 0; --m) {
+    const size_t budget_elems = smem_budget / elem_bytes;
+    if (smem_elems > budget_elems) {
+        P.smem_bytes = 0;
+        return P;
+    }
+    // the same priority as one CTA per plane; each CTA holds its share of an on-chip array, and
+    // an array that does not fit lives whole in the cluster's global slot
+    long long gl = 0;
+    for (const auto &o : layout_order(H)) {
+        const int m = o.first;
         const int pairs = (H.ny_m[m] + 1) / 2;
         const size_t nloc = 2 * static_cast<size_t>((pairs + R - 1) / R);
         const size_t sz = align4(static_cast<size_t>(H.nx) * nloc);
-        P.off_u[m] = static_cast<int>(smem_elems);
-        P.smem_u_mask |= 1u << m;
-        smem_elems += sz;
-        P.off_g[m] = static_cast<int>(smem_elems);
-        P.smem_g_mask |= 1u << m;
-        smem_elems += sz;
+        int &off = (o.second == 0) ? P.off_u[m] : P.off_g[m];
+        unsigned &mask = (o.second == 0) ? P.smem_u_mask : P.smem_g_mask;
+        if (smem_elems + sz <= budget_elems) {
+            off = static_cast<int>(smem_elems);
+            mask |= 1u << m;
+            smem_elems += sz;
+        } else {
+            off = static_cast<int>(gl);
+            gl += static_cast<long long>(align4(static_cast<size_t>(H.nx) * H.ny_m[m]));
+        }
     }
     P.smem_bytes = smem_elems * elem_bytes;
-    if (P.smem_bytes > smem_budget) P.smem_bytes = 0;
-    P.ws_per_plane = 0;
+    P.ws_per_plane = gl;
     return P;
 }
 

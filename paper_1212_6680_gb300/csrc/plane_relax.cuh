@@ -317,14 +317,15 @@ enum : int { OUT_U = 0, OUT_U_AND_PLANE = 1, OUT_PLANE = 2 };
 
 // Where the 2D-cycle arrays live.  CL = false: one CTA owns the plane; every array is either
 // in its shared memory or in its global slot.  CL = true: a thread-block cluster of R CTAs
-// shares the plane; line y of every 2D level belongs to CTA ((y/2) mod R), which keeps it in
-// its shared memory at local line ((y/2) div R)*2 + (y mod 2); other CTAs read it through
-// distributed shared memory.  Lines are owned in pairs so both colours are spread over all
-// CTAs.
+// shares the plane; line y of a 2D level kept on chip belongs to CTA ((y/2) mod R), which
+// keeps it in its shared memory at local line ((y/2) div R)*2 + (y mod 2); other CTAs read it
+// through distributed shared memory.  Lines are owned in pairs so both colours are spread over
+// all CTAs.  An array that does not fit on chip lives whole in the plane's global slot, shared
+// by the cluster.
 template <class C>
 struct PlaneCtx {
     C *sm;       // shared memory base (coefficient table first)
-    C *gw;       // this CTA's global slot (CL = false only)
+    C *gw;       // the global slot: this CTA's (CL = false) or the cluster's (CL = true)
     C *g0;       // when set: the level-0 right-hand side lives here (the plane of f itself)
     int nx;
     int R, rank; // cluster size and this CTA's rank in it (1, 0 without a cluster)
@@ -333,20 +334,12 @@ struct PlaneCtx {
     bool vec;    // nx == 32 K and every array 16-byte aligned: lanes move their K values as vectors
 };
 
-template <class C>
-__device__ __forceinline__ C *arr_u(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m) {
-    return (((a.smem_u_mask >> m) & 1u) ? c.sm : c.gw) + a.off_u[m];
-}
-template <class C>
-__device__ __forceinline__ C *arr_g_local(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m) {
-    return (((a.smem_g_mask >> m) & 1u) ? c.sm : c.gw) + a.off_g[m];
-}
-
 template <class C, bool CL>
-__device__ __forceinline__ C *line_at(const PlaneCtx<C> &c, C *base, int y) {
+__device__ __forceinline__ C *line_at(const PlaneCtx<C> &c, bool on_chip, C *base, int y) {
     if constexpr (!CL) {
         return base + y * c.nx;
     } else {
+        if (!on_chip) return base + y * c.nx;
         const int k = y >> 1;
         const int owner = k % c.R;
         const int local = (k / c.R) * 2 + (y & 1);
@@ -355,12 +348,14 @@ __device__ __forceinline__ C *line_at(const PlaneCtx<C> &c, C *base, int y) {
 }
 template <class C, bool CL>
 __device__ __forceinline__ C *line_u(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int y) {
-    return line_at<C, CL>(c, arr_u(a, c, m), y);
+    const bool on_chip = (a.smem_u_mask >> m) & 1u;
+    return line_at<C, CL>(c, on_chip, (on_chip ? c.sm : c.gw) + a.off_u[m], y);
 }
 template <class C, bool CL>
 __device__ __forceinline__ C *line_g(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int y) {
     if (m == 0 && c.g0 != nullptr) return c.g0 + y * c.nx;  // f itself, in global memory
-    return line_at<C, CL>(c, arr_g_local(a, c, m), y);
+    const bool on_chip = (a.smem_g_mask >> m) & 1u;
+    return line_at<C, CL>(c, on_chip, (on_chip ? c.sm : c.gw) + a.off_g[m], y);
 }
 
 template <bool CL>
@@ -923,7 +918,9 @@ __global__ void __launch_bounds__(512, 1) plane_relax_kernel(const __grid_consta
         rank = 0;
         pidx = static_cast<int>(blockIdx.x);
     }
-    const long long slot = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
+    // global slot: one per CTA, or one per cluster (the plane's arrays that are not on chip)
+    const long long slot = CL ? static_cast<long long>(blockIdx.y) * (gridDim.x / a.R) + pidx
+                              : static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
     plane_task<S, C, K, CL>(a, pidx, static_cast<int>(blockIdx.y), slot, rank, smem_raw);
 }
 

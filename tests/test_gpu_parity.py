@@ -60,6 +60,28 @@ def test_apply_fp64_matches_oracle(smg, orc, shape, npre, npost):
     assert rel(s, ref) <= 1e-12, rel(s, ref)
 
 
+@pytest.mark.parametrize("shape", [(256, 256, 2), (256, 200, 3)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("cluster_max", [16, 1])
+def test_coarsest_plane_cluster_with_global_arrays(smg, orc, shape, prec, tol, cluster_max):
+    """A 256-wide FP64 coarsest plane: spread over a cluster, the 2D-cycle arrays do not all fit
+    in the cluster's shared memory, and the finest ones live in the cluster's global slot."""
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=13)
+    ref = orc.SMG(nx, ny, nz, 1, 1).apply(r)
+    h = smg.smg_setup(nx, ny, nz, 1, 1)
+    try:
+        smg.smg_set_precision(h, prec)
+        smg.smg_set_option(h, smg.SMG_OPT_CLUSTER_MAX, cluster_max)
+        rd, sd = dev(r), torch.empty(nz * ny * nx, dtype=torch.float64, device="cuda")
+        smg.smg_apply(h, rd, sd)
+        torch.cuda.synchronize()
+        s = sd.cpu().numpy()
+    finally:
+        smg.smg_destroy(h)
+    assert rel(s, ref) <= tol, rel(s, ref)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("bf16", 3e-2)])
 @pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 20), (96, 96, 9)])
 @pytest.mark.parametrize("npost", [1, 0])
