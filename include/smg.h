@@ -55,9 +55,11 @@ enum {
     SMG_OPT_PROFILE = 2,      /* time plane-relaxation launches with CUDA events: 0 off,
                                  1 the finest level's launches only, 2 every launch */
     SMG_OPT_CLUSTER_MAX = 3,  /* largest thread-block cluster (CTAs per plane) for the FP64
-                                 plane relaxations: 1, 2, 4, 8 or 16 (default 16) */
+                                 plane relaxations: 1, 2, 4, 8 or 16 (default 16; levels other
+                                 than the one-plane coarsest use at most 8) */
     SMG_OPT_CLUSTER_MAX32 = 4 /* the same for the FP32-compute plane relaxations of the FP32 and
-                                 BF16 cycles (default 1: off) */
+                                 BF16 cycles: 1, 2, 4, 8 or 16, or 0 (default) for 1 while a plane's
+                                 2D-cycle iterate fits in one CTA's shared memory, else 4 */
 };
 
 /*

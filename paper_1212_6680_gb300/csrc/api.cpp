@@ -74,8 +74,8 @@ struct smg_ctx {
     PlaneLayout lay_cl32[5];        // FP32-compute cluster layouts
     bool cl32_ok[5] = {false, false, false, false, false};
     int cluster_max = 16;           // largest cluster for FP64-compute plane relaxations (1 = none)
-    int cluster_max32 = 1;          // largest cluster for FP32-compute plane relaxations (measured: the
-                                    // FP32 plane cycle is latency-bound, clusters only add barrier cost)
+    int cluster_max32 = 0;          // largest cluster for FP32-compute plane relaxations; 0 = chosen
+                                    // per size (see relax)
     int num_sms = 0;
     // Krylov vectors (one right-hand side)
     double *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_dr = nullptr;
@@ -235,12 +235,18 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     const int nplanes = colour == 0 ? (nzl + 1) / 2 : nzl / 2;
     if (nplanes == 0) return SMG_OK;
     const bool f64c = coarsest || h->prec == Prec::F64;
-    // FP64-bound relaxations spread each plane over a cluster of R CTAs while the grid still
-    // fits on the SMs at once
-    // Each plane is spread over a cluster of R CTAs while the grid still fits on the SMs at once
+    // Each plane is spread over a cluster of R CTAs while the grid still fits on the SMs at once.
+    // Defaults (measured on GB300 at 128^3 and 256^3): FP64 planes up to 16 CTAs for the one-plane
+    // coarsest level and up to 8 elsewhere (beyond 8 the cluster barrier costs more than the
+    // FP64 work it spreads); FP32 planes stay on one CTA while its 2D-cycle iterate u_0 fits in
+    // shared memory (the cycle is then latency-bound and a cluster only adds barrier cost), and
+    // use up to 4 CTAs when it does not (256-wide planes).
     int R = 1;
     const bool *ok = f64c ? h->cl_ok : h->cl32_ok;
-    const int rmax = f64c ? h->cluster_max : h->cluster_max32;
+    int rmax;
+    if (f64c) rmax = coarsest ? h->cluster_max : std::min(h->cluster_max, 8);
+    else if (h->cluster_max32 > 0) rmax = h->cluster_max32;
+    else rmax = (h->lay_c.smem_u_mask & 1u) ? 1 : 4;
     for (int cand = 2; cand <= rmax && cand <= 16; cand *= 2)
         if (ok[__builtin_ctz(cand)] && static_cast<long long>(nplanes) * nb * cand <= h->num_sms) R = cand;
     const PlaneLayout &lay = (R > 1) ? (f64c ? h->lay_cl[__builtin_ctz(R)] : h->lay_cl32[__builtin_ctz(R)])
@@ -533,8 +539,8 @@ int smg_set_option(smg_handle h, int option, int value) {
         h->cluster_max = value;
         return SMG_OK;
     case SMG_OPT_CLUSTER_MAX32:
-        if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
-            return fail(SMG_ERR_ARG, "cluster_max must be 1, 2, 4, 8 or 16");
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(SMG_ERR_ARG, "cluster_max32 must be 0 (automatic), 1, 2, 4, 8 or 16");
         h->cluster_max32 = value;
         return SMG_OK;
     case SMG_OPT_PROFILE:

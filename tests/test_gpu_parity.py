@@ -82,6 +82,26 @@ def test_coarsest_plane_cluster_with_global_arrays(smg, orc, shape, prec, tol, c
     assert rel(s, ref) <= tol, rel(s, ref)
 
 
+@pytest.mark.parametrize("cluster_max32", [0, 1, 2, 16])
+def test_fp32_plane_clusters(smg, orc, cluster_max32):
+    """FP32 256-wide planes on one CTA or spread over clusters (0 = the size-dependent default),
+    with the arrays that do not fit on chip in global memory."""
+    nx, ny, nz = 256, 96, 6
+    r = inputs.rhs(nx, ny, nz, seed=17)
+    ref = orc.SMG(nx, ny, nz, 1, 0).apply(r)
+    h = smg.smg_setup(nx, ny, nz, 1, 0)
+    try:
+        smg.smg_set_precision(h, "fp32")
+        smg.smg_set_option(h, smg.SMG_OPT_CLUSTER_MAX32, cluster_max32)
+        rd, sd = dev(r), torch.empty(nz * ny * nx, dtype=torch.float64, device="cuda")
+        smg.smg_apply(h, rd, sd)
+        torch.cuda.synchronize()
+        s = sd.cpu().numpy()
+    finally:
+        smg.smg_destroy(h)
+    assert rel(s, ref) <= 2e-5, rel(s, ref)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("bf16", 3e-2)])
 @pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 20), (96, 96, 9)])
 @pytest.mark.parametrize("npost", [1, 0])
