@@ -7,8 +7,8 @@
 
 namespace smg {
 
-constexpr int kMaxReduceBlocks = 1216;  // size of the partial-sum buffer
-constexpr int kReduceBlocks = 304;      // CTAs of a reduction kernel (2 x 152 SMs)
+constexpr int kMaxReduceBlocks = 1216;  // CTAs of a reduction kernel on HBM-resident vectors (8 x 152 SMs)
+constexpr int kReduceBlocks = 304;      // CTAs of a reduction kernel on L2-resident vectors (2 x 152 SMs)
 
 // Scalars of Algorithm 1 kept on the device between kernels.
 struct KrylovScalars {

@@ -256,12 +256,16 @@ __global__ void k_update_xr(long long n, double *__restrict__ x, const double *_
 }
 
 // ---- launchers --------------------------------------------------------------------------------
-// Two 256-thread CTAs per SM of a 152-SM GB300 at most: each thread then sums tens of
-// products, and the block and grid reductions stay a small fraction of the kernel.
+// Grid of the reduction kernels, measured on GB300: while the Krylov vectors (about six of N
+// doubles) stay in the 129 MB L2, two 256-thread CTAs per SM (each thread sums tens of
+// products; the last CTA's compensated pass over the partials stays short); past that the
+// kernels stream from HBM and need every SM full of warps (8 CTAs per SM) to keep enough loads
+// in flight.
 int reduction_blocks(long long n) {
     long long b = (n + 256LL * 16 - 1) / (256LL * 16);
+    const long long cap = (n <= (4LL << 20)) ? kReduceBlocks : kMaxReduceBlocks;
     if (b < 1) b = 1;
-    if (b > kReduceBlocks) b = kReduceBlocks;
+    if (b > cap) b = cap;
     return static_cast<int>(b);
 }
 
