@@ -607,15 +607,18 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
     }
 }
 
-// Lines a warp processes together: more when the line is short and the type is narrow.
+// Lines a warp processes together: two interleaved dependency chains when a lane's share of a
+// line is at most 16 bytes, else one (measured on GB300: four-line groups lose to the larger
+// code's instruction-fetch stalls, and wide lines gain nothing from pairing).
 template <class C, int K>
 constexpr int max_lines_per_group() {
-    return (sizeof(C) * K <= 16) ? 4 : ((sizeof(C) * K <= 32) ? 2 : 1);
+    return (sizeof(C) * K <= 16) ? 2 : 1;
 }
 
 // Relax every line of one colour of 2D level m that this CTA owns: lines colour + 2k with
 // k = rank + R i; warp w takes i = w, w + nw, ..., NLM at a time while it has NLM left, then
-// pairs, then single lines (three compiled bodies in all).
+// single lines (two compiled bodies: each extra body costs more in instruction fetch than its
+// interleaving gains).
 template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
                                              int m, int colour, S *plane, bool accumulate, int nbmode, int out,
@@ -631,12 +634,6 @@ __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const Plan
 #pragma unroll
             for (int l = 0; l < NLM; ++l) ys[l] = Y(i + l * nw);
             relax_group<S, C, K, NLM, CL>(a, c, fac, m, ys, NLM, plane, accumulate, nbmode, out, lane);
-        }
-    }
-    if constexpr (NLM > 2) {  // pairs keep two dependency chains interleaved
-        for (; i + nw < nown; i += 2 * nw) {
-            const int ys[2] = {Y(i), Y(i + nw)};
-            relax_group<S, C, K, 2, CL>(a, c, fac, m, ys, 2, plane, accumulate, nbmode, out, lane);
         }
     }
     // the rest one line at a time (on the coarse levels the critical path is one line per warp)
@@ -687,27 +684,13 @@ __device__ __forceinline__ void restrict_group(const PlaneRelaxArgs &a, const Pl
     for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, m + 1, js[l]), acc[l], nx, c.vec, lane);
 }
 
+// The restriction of one level, one coarse line per warp at a time (a single compiled body keeps
+// the kernel's code small; the step is short next to the relaxations around it).
 template <class C, int K, bool CL>
 __device__ __forceinline__ void restrict_level(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int warp,
                                                int nw, int lane) {
     const int nown = owned_count(c, a.ny_m[m + 1]);
-    constexpr int NLM = max_lines_per_group<C, K>();
-    int t = warp;
-    if constexpr (NLM > 1) {
-        for (; t + (NLM - 1) * nw < nown; t += NLM * nw) {
-            int js[NLM];
-#pragma unroll
-            for (int l = 0; l < NLM; ++l) js[l] = owned_line(c, t + l * nw);
-            restrict_group<C, K, NLM, CL>(a, c, m, js, lane);
-        }
-    }
-    if constexpr (NLM > 2) {
-        for (; t + nw < nown; t += 2 * nw) {
-            const int js[2] = {owned_line(c, t), owned_line(c, t + nw)};
-            restrict_group<C, K, 2, CL>(a, c, m, js, lane);
-        }
-    }
-    for (; t < nown; t += nw) {
+    for (int t = warp; t < nown; t += nw) {
         const int js[1] = {owned_line(c, t)};
         restrict_group<C, K, 1, CL>(a, c, m, js, lane);
     }
@@ -781,21 +764,12 @@ __device__ __forceinline__ void rhs_group(const PlaneRelaxArgs &a, const PlaneCt
     for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, 0, ys[l]), d[l], nx, c.vec, lane);
 }
 
+// The plane right-hand side, one line per warp at a time (single compiled body, as above).
 template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void compute_rhs(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int mode, const S *fpl,
                                             const S *ub, int z, const C *zc, int warp, int nw, int lane) {
-    constexpr int NLM = max_lines_per_group<C, K>();
     const int nown = owned_count(c, a.ny);
-    int t = warp;
-    if constexpr (NLM > 1) {
-        for (; t + (NLM - 1) * nw < nown; t += NLM * nw) {
-            int ys[NLM];
-#pragma unroll
-            for (int l = 0; l < NLM; ++l) ys[l] = owned_line(c, t + l * nw);
-            rhs_group<S, C, K, NLM, CL>(a, c, ys, mode, fpl, ub, z, zc, lane);
-        }
-    }
-    for (; t < nown; t += nw) {
+    for (int t = warp; t < nown; t += nw) {
         const int ys[1] = {owned_line(c, t)};
         rhs_group<S, C, K, 1, CL>(a, c, ys, mode, fpl, ub, z, zc, lane);
     }
