@@ -87,48 +87,90 @@ __device__ __forceinline__ void df_mac(float &S, float &s, float ah, float al, f
 
 __device__ __forceinline__ double df_value(float S, float s) { return widen_f32(S) + widen_f32(s); }
 
-// Partial Gram: part[chunk][ti][tj] tile of U^T V over rows [chunk*kGChunk, ...).  FP64 FMAs are
-// the scarce resource on this part, so the tiles are small (no work on padding beyond the next
-// multiple of 16) and, for a symmetric product (sym = 1, U^T V = V^T U), only the tiles on and
-// above the diagonal are computed.
-__global__ void __launch_bounds__(256) gram_partial_kernel(long long n, int k1, int k2, const double *__restrict__ U,
-                                                           const double *__restrict__ V, double *__restrict__ part,
-                                                           int ntj, int sym) {
-    __shared__ float suh[kGRows][kGT + 1], sul[kGRows][kGT + 1];
-    __shared__ float svh[kGRows][kGT + 1], svl[kGRows][kGT + 1];
+// Partial Gram: part[chunk][ti][tj] tile of U^T V over rows [chunk*rows, ...).  The tiles are
+// small (no work on padding beyond the next multiple of 16) and, for a symmetric product
+// (sym = 1, U^T V = V^T U), only the tiles on and above the diagonal are computed.  The 256
+// threads form 4 row groups of 64; each thread accumulates a 2 x 2 block of the tile over every
+// 4th staged row, reading its two U and two V operands (hi, lo) as one 16-byte shared-memory load
+// each, so the kernel is bound by the FP32 pipe rather than by shared-memory loads.  The staged
+// rows hold (hi, lo) pairs with the 16-byte column pairs XOR-swizzled by row (conflict-light
+// stores, conflict-free loads).
+__device__ __forceinline__ int gram_swz(int rr, int cc) { return ((((cc >> 1) ^ rr) & 7) << 1) | (cc & 1); }
+
+__global__ void __launch_bounds__(256, 4) gram_partial_kernel(long long n, long long rows, int k1, int k2,
+                                                           const double *__restrict__ U, const double *__restrict__ V,
+                                                           double *__restrict__ part, int ntj, int sym) {
+    __shared__ __align__(16) float2 su[kGRows][kGT], sv[kGRows][kGT];
+    __shared__ double red[4][kGT * kGT];
     const int tile = blockIdx.y, ti = tile / ntj, tj = tile % ntj;
     if (sym && tj < ti) return;
     const int i0 = ti * kGT, j0 = tj * kGT;
-    const long long r0 = static_cast<long long>(blockIdx.x) * kGChunk;
-    const long long r1 = min(n, r0 + kGChunk);
-    const int ti_ = threadIdx.x >> 4, tj_ = threadIdx.x & 15;
-    float S0 = 0.0f, s0 = 0.0f, S1 = 0.0f, s1 = 0.0f;  // two independent accumulators
-    for (long long rb = r0; rb < r1; rb += kGRows) {
-        for (int t = threadIdx.x; t < kGRows * kGT; t += blockDim.x) {
-            const int rr = t % kGRows, cc = t / kGRows;
+    const long long r0 = static_cast<long long>(blockIdx.x) * rows;
+    const long long r1 = min(n, r0 + rows);
+    const int kg = threadIdx.x >> 6, t = threadIdx.x & 63, oi = t >> 3, oj = t & 7;  // outputs (2oi+a, 2oj+b)
+    float S[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // this thread's staged elements: e = threadIdx.x + 256 q, row e % kGRows, column e / kGRows;
+    // the next block's values are loaded into registers before the current block is computed
+    constexpr int kPer = kGRows * kGT / (kGT * kGT);
+    double nu[kPer], nv[kPer];
+    auto fetch = [&](long long rb) {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int e = threadIdx.x + q * kGT * kGT, rr = e % kGRows, cc = e / kGRows;
             const long long r = rb + rr;
-            const double u = (r < r1 && i0 + cc < k1) ? U[static_cast<long long>(i0 + cc) * n + r] : 0.0;
-            const double v = (r < r1 && j0 + cc < k2) ? V[static_cast<long long>(j0 + cc) * n + r] : 0.0;
-            df_split(u, suh[rr][cc], sul[rr][cc]);
-            df_split(v, svh[rr][cc], svl[rr][cc]);
+            nu[q] = (r < r1 && i0 + cc < k1) ? U[static_cast<long long>(i0 + cc) * n + r] : 0.0;
+            nv[q] = (r < r1 && j0 + cc < k2) ? V[static_cast<long long>(j0 + cc) * n + r] : 0.0;
+        }
+    };
+    fetch(r0);
+    for (long long rb = r0; rb < r1; rb += kGRows) {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int e = threadIdx.x + q * kGT * kGT, rr = e % kGRows, cc = e / kGRows;
+            float uh, ul, vh, vl;
+            df_split(nu[q], uh, ul);
+            df_split(nv[q], vh, vl);
+            su[rr][gram_swz(rr, cc)] = make_float2(uh, ul);
+            sv[rr][gram_swz(rr, cc)] = make_float2(vh, vl);
         }
         __syncthreads();
+        if (rb + kGRows < r1) fetch(rb + kGRows);
 #pragma unroll 4
-        for (int rr = 0; rr < kGRows; rr += 2) {
-            df_mac(S0, s0, suh[rr][ti_], sul[rr][ti_], svh[rr][tj_], svl[rr][tj_]);
-            df_mac(S1, s1, suh[rr + 1][ti_], sul[rr + 1][ti_], svh[rr + 1][tj_], svl[rr + 1][tj_]);
+        for (int q = 0; q < kGRows / 4; ++q) {
+            const int rr = 4 * q + kg;
+            const float4 a = *reinterpret_cast<const float4 *>(&su[rr][gram_swz(rr, 2 * oi)]);
+            const float4 b = *reinterpret_cast<const float4 *>(&sv[rr][gram_swz(rr, 2 * oj)]);
+            df_mac(S[0], sl[0], a.x, a.y, b.x, b.y);
+            df_mac(S[1], sl[1], a.x, a.y, b.z, b.w);
+            df_mac(S[2], sl[2], a.z, a.w, b.x, b.y);
+            df_mac(S[3], sl[3], a.z, a.w, b.z, b.w);
         }
         __syncthreads();
     }
-    part[(static_cast<long long>(blockIdx.x) * gridDim.y + tile) * kGT * kGT + ti_ * kGT + tj_] =
-        df_value(S0, s0) + df_value(S1, s1);
+    const int o = (2 * oi) * kGT + 2 * oj;
+    red[kg][o] = df_value(S[0], sl[0]);
+    red[kg][o + 1] = df_value(S[1], sl[1]);
+    red[kg][o + kGT] = df_value(S[2], sl[2]);
+    red[kg][o + kGT + 1] = df_value(S[3], sl[3]);
+    __syncthreads();
+    const int idx = threadIdx.x;  // blockDim.x == kGT * kGT
+    part[(static_cast<long long>(blockIdx.x) * gridDim.y + tile) * kGT * kGT + idx] =
+        (red[0][idx] + red[1][idx]) + (red[2][idx] + red[3][idx]);
 }
 
-// G[i][j] (k1 x k2 row-major) = sum over chunks of the partial tiles (compensated summation);
-// with sym, entries below the diagonal tiles come from the mirrored tile.
+// G[i][j] (k1 x k2 row-major) = sum over chunks of the partial tiles (compensated summation), one
+// warp per entry: the lanes take every 32nd chunk, then the warp combines its 32 sums.  With
+// sym, entries below the diagonal tiles come from the mirrored tile.
+__device__ __forceinline__ void two_sum_add(double &s, double &c, double v) {
+    const double t = s + v;
+    const double bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
 __global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int ntiles, const double *__restrict__ part,
                                    double *__restrict__ G, int sym) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (idx >= k1 * k2) return;
     int i = idx / k2, j = idx % k2;
     if (sym && i / kGT > j / kGT) {
@@ -137,28 +179,29 @@ __global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int nti
         j = t;
     }
     const int ti = i / kGT, tj = j / kGT, tile = ti * ntj + tj;
+    const long long off = static_cast<long long>(tile) * kGT * kGT + (i - ti * kGT) * kGT + (j - tj * kGT);
     double s = 0.0, c = 0.0;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        const double v = part[(static_cast<long long>(ch) * ntiles + tile) * kGT * kGT + (i - ti * kGT) * kGT + (j - tj * kGT)];
-        const double t = s + v;
-        const double bp = t - s;
-        c += (s - (t - bp)) + (v - bp);
-        s = t;
+    for (int ch = lane; ch < nchunks; ch += 32) two_sum_add(s, c, part[static_cast<long long>(ch) * ntiles * kGT * kGT + off]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double so = __shfl_down_sync(0xffffffffu, s, o), co = __shfl_down_sync(0xffffffffu, c, o);
+        two_sum_add(s, c, so);
+        c += co;
     }
-    G[idx] = s + c;
+    if (lane == 0) G[idx] = s + c;
 }
 
 // Y = alpha * U C + beta * Y  (U: n x k, C: k x m2 row-major, Y: n x m2, column stride n), the
 // products in double-float arithmetic.
 __global__ void block_mul_kernel(long long n, int k, int m2, const double *__restrict__ U,
                                  const double *__restrict__ C, double alpha, double beta, double *__restrict__ Y) {
-    extern __shared__ float sc2[];  // [k][kMulCols] hi, then lo
-    float *ch = sc2, *cl = sc2 + k * kMulCols;
+    extern __shared__ __align__(16) float2 cs[];  // [k][kMulCols] (hi, lo) pairs of C's column block
     const int j0 = blockIdx.y * kMulCols;
     const int nc = min(kMulCols, m2 - j0);
     for (int t = threadIdx.x; t < k * kMulCols; t += blockDim.x) {
         const int i = t / kMulCols, j = t % kMulCols;
-        df_split((j < nc) ? C[i * m2 + j0 + j] : 0.0, ch[t], cl[t]);
+        float h, l;
+        df_split((j < nc) ? C[i * m2 + j0 + j] : 0.0, h, l);
+        cs[t] = make_float2(h, l);
     }
     __syncthreads();
     const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -166,11 +209,18 @@ __global__ void block_mul_kernel(long long n, int k, int m2, const double *__res
     float S[kMulCols], sl[kMulCols];
 #pragma unroll
     for (int j = 0; j < kMulCols; ++j) S[j] = sl[j] = 0.0f;
+    double un = U[r];  // the next row's operand is loaded before the current row's multiply-adds
     for (int i = 0; i < k; ++i) {
         float uh, ul;
-        df_split(U[static_cast<long long>(i) * n + r], uh, ul);
+        df_split(un, uh, ul);
+        if (i + 1 < k) un = U[static_cast<long long>(i + 1) * n + r];
+        const float4 *c4 = reinterpret_cast<const float4 *>(cs + i * kMulCols);  // two (hi, lo) pairs per load
 #pragma unroll
-        for (int j = 0; j < kMulCols; ++j) df_mac(S[j], sl[j], uh, ul, ch[i * kMulCols + j], cl[i * kMulCols + j]);
+        for (int j = 0; j < kMulCols; j += 2) {
+            const float4 cc = c4[j / 2];
+            df_mac(S[j], sl[j], uh, ul, cc.x, cc.y);
+            df_mac(S[j + 1], sl[j + 1], uh, ul, cc.z, cc.w);
+        }
     }
 #pragma unroll
     for (int j = 0; j < kMulCols; ++j) {
@@ -395,13 +445,21 @@ struct Ctx {
 // e.g. V = U or V = A U), so only its upper tiles are computed
 int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G, bool sym = false) {
     const int nti = cdiv(k1, kGT), ntj = cdiv(k2, kGT);
-    const int nch = cdiv(c.n, kGChunk);
+    // rows per CTA: kGChunk, halved (down to kGChunk / 8) while the product has fewer than 4 CTAs
+    // per SM and the partial buffer has room (single-tile products would otherwise run one CTA
+    // per SM, stalled on their global loads)
     const int s = (sym && k1 == k2) ? 1 : 0;
+    const int active = s ? nti * (nti + 1) / 2 : nti * ntj;
+    long long rows = kGChunk;
+    while (rows > kGChunk / 8 && static_cast<long long>(cdiv(c.n, rows)) * active < 4LL * c.w.num_sms &&
+           static_cast<long long>(cdiv(c.n, rows / 2)) * nti * ntj <= c.w.part_tiles)
+        rows /= 2;
+    const int nch = static_cast<int>(cdiv(c.n, rows));
     dim3 grid(nch, nti * ntj);
-    gram_partial_kernel<<<grid, 256, 0, c.st>>>(c.n, k1, k2, U, V, c.w.part, ntj, s);
+    gram_partial_kernel<<<grid, kGT * kGT, 0, c.st>>>(c.n, rows, k1, k2, U, V, c.w.part, ntj, s);
     LCHK(cudaGetLastError());
-    gram_reduce_kernel<<<cdiv(static_cast<long long>(k1) * k2, 256), 256, 0, c.st>>>(nch, k1, k2, ntj, nti * ntj,
-                                                                                      c.w.part, c.w.gram, s);
+    gram_reduce_kernel<<<cdiv(static_cast<long long>(k1) * k2 * 32, 256), 256, 0, c.st>>>(
+        nch, k1, k2, ntj, nti * ntj, c.w.part, c.w.gram, s);
     LCHK(cudaGetLastError());
     G.resize(static_cast<size_t>(k1) * k2);
     LCHK(cudaMemcpyAsync(c.w.h_buf, c.w.gram, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c.st));
@@ -414,7 +472,7 @@ int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<d
 int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, double alpha, double beta, double *Y) {
     LCHK(cudaMemcpyAsync(c.w.coef, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, c.st));
     dim3 grid(cdiv(c.n, 256), cdiv(m2, kMulCols));
-    block_mul_kernel<<<grid, 256, 2 * sizeof(float) * k * kMulCols, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y);
+    block_mul_kernel<<<grid, 256, sizeof(float2) * k * kMulCols, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y);
     LCHK(cudaGetLastError());
     // the host vector C may be reused right after; the copy above is stream-ordered but reads
     // host memory asynchronously only for pinned memory, so pageable C is safe here
@@ -510,7 +568,11 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         LCHK(cudaMalloc(&w.T1, blk));
         LCHK(cudaMalloc(&w.T2, blk));
         const int k = 3 * m, nt = cdiv(k, kGT);
-        LCHK(cudaMalloc(&w.part, sizeof(double) * static_cast<size_t>(cdiv(n, kGChunk)) * nt * nt * kGT * kGT));
+        w.part_tiles = static_cast<long long>(cdiv(n, kGChunk)) * nt * nt;
+        int dev = 0;
+        LCHK(cudaGetDevice(&dev));
+        LCHK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        LCHK(cudaMalloc(&w.part, sizeof(double) * static_cast<size_t>(w.part_tiles) * kGT * kGT));
         LCHK(cudaMalloc(&w.gram, sizeof(double) * k * k));
         LCHK(cudaMalloc(&w.coef, sizeof(double) * k * k));
         LCHK(cudaMallocHost(&w.h_buf, sizeof(double) * k * k));

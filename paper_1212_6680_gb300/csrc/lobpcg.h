@@ -24,6 +24,8 @@ struct LobpcgWork {
     double *S = nullptr, *AS = nullptr;   // n x 3m each: [X | W | P]
     double *T1 = nullptr, *T2 = nullptr;  // n x 3m temporaries
     double *part = nullptr;               // Gram partial sums
+    long long part_tiles = 0;             // capacity of part in 16 x 16 tiles
+    int num_sms = 0;                      // SMs of the device (sizes the Gram grids)
     double *gram = nullptr;               // reduced Gram matrices
     double *coef = nullptr;               // small coefficient matrices (k x k)
     double *h_buf = nullptr;              // pinned host buffer
