@@ -267,15 +267,7 @@ def run_ours(args):
     from paper_1212_6680_gb300 import build as _build
     from paper_1212_6680_gb300 import inputs
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    world, rank, local, dist = _dist_init()
     _build.build()
     from paper_1212_6680_gb300 import smg
 
@@ -341,11 +333,7 @@ def run_ours(args):
     pl, pms, pbytes = smg.smg_profile_read(h32, 0)
     smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 0)
     t_step = statistics.mean(times)
-    t_max = t_step
-    if dist is not None:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_step, dist, "cuda")
 
     # ---- comparison arms on the same GPU: FP64 and BF16 cycles ----
     k2 = max(1, min(args.steps, 3))
@@ -407,15 +395,7 @@ def run_batched(args):
 
     from paper_1212_6680_gb300 import build as _build
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    world, rank, local, dist = _dist_init()
     _build.build()
     from paper_1212_6680_gb300 import smg
 
@@ -475,11 +455,7 @@ def run_batched(args):
     kl, kms, _ = smg.smg_batched_profile_read(h, 1)
     smg.smg_batched_set_profile(h, 0)
     t_step = statistics.mean(times)
-    t_max = t_step
-    if dist is not None:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_step, dist, "cuda")
 
     # end to end: pinned host inputs and outputs, copies inside the timed region
     bh = [torch.from_numpy(b.ravel().copy()).pin_memory() for b in b_np]
@@ -564,19 +540,37 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def _dist_init():
+def _dist_init(backend="nccl"):
+    """(world, rank, local rank, torch.distributed or None) from the torchrun environment.  One
+    process per GPU; the replicas share nothing but the barriers around the timed region and the
+    max-over-ranks reduction of its duration."""
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    if backend == "nccl":
+        torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local, dist
+
+
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value: the job takes as long as its slowest replica."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def _timed(fn, steps, warmup, barrier, flush, stream):
@@ -680,11 +674,8 @@ def run_lobpcg(args):
     te, _ = _timed(e2e_once, max(1, min(args.steps, 2)), 1, barrier, flush, stream)
     smg.smg_destroy(h)
     t_step = main["s"]
-    t_max = t_step
+    t_max = max_over_ranks(t_step, dist, "cuda")
     if dist is not None:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
@@ -825,11 +816,8 @@ def run_learned(args):
         return smg.krylov_solve(h, "fpcg", bh.numpy(), xh.numpy(), TOL, 100)
     te, _ = _timed(e2e_once, k2, 1, barrier, flush, stream)
     smg.smg_destroy(h)
-    t_max = main["s"]
+    t_max = max_over_ranks(main["s"], dist, "cuda")
     if dist is not None:
-        tt = torch.tensor([t_max], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
