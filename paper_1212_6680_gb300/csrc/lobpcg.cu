@@ -27,9 +27,9 @@ namespace smg {
 
 namespace {
 
-constexpr int kGT = 16;          // Gram output tile (kGT x kGT per CTA, one output per thread)
+constexpr int kGT = 16;          // Gram output tile (kGT x kGT per CTA of kGT * kGT threads)
 constexpr int kGRows = 64;       // rows staged per step
-constexpr int kGChunk = 8192;    // rows per CTA (split-K)
+constexpr int kGChunk = 8192;    // rows per CTA (split-K; fewer for small products)
 constexpr int kMulCols = 16;     // output columns per block_mul thread
 
 // ---- double-float arithmetic -------------------------------------------------------------------
