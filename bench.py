@@ -41,9 +41,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256"], default="fpcg128",
+    ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256", "bricks"],
+                    default="fpcg128",
                     help="fpcg128: one 128^3 system (default); batched64: 64 uneven systems, sides in {32..96}; "
-                         "lobpcg128: 16 smallest eigenpairs at 128^3; learned256: learned post-correction at 256^3")
+                         "lobpcg128: 16 smallest eigenpairs at 128^3; learned256: learned post-correction at 256^3; "
+                         "bricks: the paper's 16n x n x n bricks, n = 10..32, every Krylov variant and cycle")
     return ap.parse_args()
 
 
@@ -867,6 +869,89 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+BRICK_NS = (10, 16, 20, 32)
+BRICK_WORKLOAD = ("the paper's 16n x n x n bricks (long in x), n = 10, 16, 20, 32, 7-point Dirichlet Laplacian; "
+                  "FPCG-SMG(1,0) with the FP32 and the FP64 cycle timed, iteration counts of PCG eq. (1), FPCG eq. (2) "
+                  "and PSD with the (1,1) and (1,0) FP64 cycles; tol 1e-8")
+
+
+def run_bricks(args):
+    """The brick sweep of the paper's figures 4, 5 and 7 at the sizes whose x-lines a warp solves
+    (16n <= 512): the timed value is the FP32-cycle FPCG-SMG(1,0) solve of the largest brick."""
+    import torch
+
+    from paper_1212_6680_gb300 import build as _build
+    from paper_1212_6680_gb300 import inputs
+
+    world, rank, local, dist = _dist_init()
+    _build.build()
+    from paper_1212_6680_gb300 import smg
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    table = []
+    main_t, main_launches, main_clk = None, 0, None
+    for nb in BRICK_NS:
+        nx, ny, nz = 16 * nb, nb, nb
+        b = torch.from_numpy(inputs.rhs(nx, ny, nz, seed=0).ravel().copy()).cuda()
+        x = torch.zeros_like(b)
+        row = {"n": nb, "grid": [nx, ny, nz], "unknowns": nx * ny * nz}
+        for npost in (1, 0):
+            h = smg.smg_setup(nx, ny, nz, 1, npost)
+            for v in ("pcg", "fpcg", "psd"):
+                x.zero_()
+                rc, it, rr = smg.krylov_solve(h, v, b, x, TOL, 40, check=False)
+                row[f"{v}_{1}{npost}_iters"] = it if rc == smg.SMG_OK else f">40 (relres {rr:.1e})"
+            smg.smg_destroy(h)
+        for prec in ("fp32", "fp64"):
+            h = smg.smg_setup(nx, ny, nz, 1, 0)
+            smg.smg_set_precision(h, prec)
+            last = prec == "fp32" and nb == BRICK_NS[-1]
+
+            def once():
+                x.zero_()
+                rc, it, rr = smg.krylov_solve(h, "fpcg", b, x, TOL, 100)
+                assert rc == smg.SMG_OK and rr <= TOL, (rc, rr)
+                return it
+            l0 = smg.smg_launch_count(h)
+            if last:
+                for _ in range(args.warmup):
+                    once()
+                l0 = smg.smg_launch_count(h)
+                with ClockSampler(local) as clk:
+                    times, it = _timed(once, args.steps, 0, barrier, flush, stream)
+                main_t, main_launches, main_clk = statistics.mean(times), smg.smg_launch_count(h) - l0, clk.summary()
+            else:
+                times, it = _timed(once, max(1, min(args.steps, 3)), 1, barrier, flush, stream)
+            row[f"fpcg_10_{prec}_s"] = statistics.mean(times)
+            row[f"fpcg_10_{prec}_iters"] = it
+            smg.smg_destroy(h)
+        table.append(row)
+    t_max = max_over_ranks(main_t, dist, "cuda")
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": BRICK_WORKLOAD, "timed": f"FPCG-SMG(1,0), FP32 cycle, brick n = {BRICK_NS[-1]}",
+                   "bricks": table, "l2": "256 MB buffer written before every timed solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": main_launches, "clocks": main_clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -877,6 +962,8 @@ def main():
         run_lobpcg(args)
     elif args.workload == "learned256":
         run_learned(args)
+    elif args.workload == "bricks":
+        run_bricks(args)
     else:
         run_ours(args)
 
