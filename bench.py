@@ -41,11 +41,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256", "bricks"],
+    ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256", "bricks", "cg128"],
                     default="fpcg128",
                     help="fpcg128: one 128^3 system (default); batched64: 64 uneven systems, sides in {32..96}; "
                          "lobpcg128: 16 smallest eigenpairs at 128^3; learned256: learned post-correction at 256^3; "
-                         "bricks: the paper's 16n x n x n bricks, n = 10..32, every Krylov variant and cycle")
+                         "bricks: the paper's 16n x n x n bricks, n = 10..32, every Krylov variant and cycle; "
+                         "cg128: no preconditioner at 128^3 (CG by eq. (1) and eq. (2), steepest descent)")
     return ap.parse_args()
 
 
@@ -952,6 +953,80 @@ def run_bricks(args):
     print(json.dumps(line), flush=True)
 
 
+CG_WORKLOAD = ("no preconditioner (T = I) at 128^3, 7-point Dirichlet Laplacian: CG by eq. (1), CG by eq. (2) "
+               "(the flexible form's extra vector r_k - r_(k-1)) and steepest descent; FP64; tol 1e-8")
+
+
+def run_cg(args):
+    """Section 2 / figures 1-2 on the GPU path: the cost per iteration of the flexible form's extra
+    vector without preconditioning, and steepest descent against CG.  The timed value is the
+    eq. (2) CG solve to 1e-8."""
+    import torch
+
+    from paper_1212_6680_gb300 import build as _build
+    from paper_1212_6680_gb300 import inputs
+
+    world, rank, local, dist = _dist_init()
+    _build.build()
+    from paper_1212_6680_gb300 import smg
+
+    b = torch.from_numpy(inputs.rhs(NX, NY, NZ, seed=0).ravel().copy()).cuda()
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    h = smg.smg_setup(NX, NY, NZ, 1, 0)
+    smg.smg_set_option(h, smg.SMG_OPT_PRECOND, 0)
+    res = {}
+    main_t, main_launches, main_clk = None, 0, None
+    for v, maxit in (("fpcg", 5000), ("pcg", 5000), ("psd", 0)):
+        if v == "psd":
+            maxit = res["fpcg"]["iters"]  # steepest descent given CG's iteration count
+
+        def once():
+            x.zero_()
+            rc, it, rr = smg.krylov_solve(h, v, b, x, TOL, maxit, check=False)
+            assert rc in (smg.SMG_OK, smg.SMG_ERR_NOCONV), rc
+            return rc, it, rr
+        if v == "fpcg":
+            for _ in range(args.warmup):
+                once()
+            l0 = smg.smg_launch_count(h)
+            with ClockSampler(local) as clk:
+                times, (rc, it, rr) = _timed(once, args.steps, 0, barrier, flush, stream)
+            main_t, main_launches, main_clk = statistics.mean(times), smg.smg_launch_count(h) - l0, clk.summary()
+            assert rc == smg.SMG_OK and rr <= TOL
+        else:
+            times, (rc, it, rr) = _timed(once, max(1, min(args.steps, 3)), 1, barrier, flush, stream)
+        t = statistics.mean(times)
+        res[v] = {"s": t, "iters": it, "relres": rr, "converged": rc == smg.SMG_OK, "ms_per_iter": t * 1e3 / max(it, 1)}
+    smg.smg_destroy(h)
+    t_max = max_over_ranks(main_t, dist, "cuda")
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": CG_WORKLOAD, "grid": [NX, NY, NZ], "timed": "CG by eq. (2), no preconditioner",
+                   "cg_eq2": res["fpcg"], "cg_eq1": res["pcg"], "steepest_descent": res["psd"],
+                   "extra_vector_cost": res["fpcg"]["ms_per_iter"] / res["pcg"]["ms_per_iter"] - 1.0,
+                   "l2": "256 MB buffer written before every timed solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": main_launches, "clocks": main_clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -964,6 +1039,8 @@ def main():
         run_learned(args)
     elif args.workload == "bricks":
         run_bricks(args)
+    elif args.workload == "cg128":
+        run_cg(args)
     else:
         run_ours(args)
 

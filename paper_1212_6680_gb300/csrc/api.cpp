@@ -74,6 +74,7 @@ struct smg_ctx {
     PlaneLayout lay_cl32[5];        // FP32-compute cluster layouts
     bool cl32_ok[5] = {false, false, false, false, false};
     int cluster_max = 16;           // largest cluster for FP64-compute plane relaxations (1 = none)
+    int precond = 1;                // krylov_solve's preconditioner: 1 the SMG cycle, 0 none (T = I)
     int cluster_max32 = 0;          // largest cluster for FP32-compute plane relaxations; 0 = chosen
                                     // per size (see relax)
     int num_sms = 0;
@@ -390,14 +391,16 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
     if ((rc = ensure_levels(h, 1)) != SMG_OK) return rc;
     if ((rc = ensure_krylov(h)) != SMG_OK) return rc;
     const bool f64 = (h->prec == Prec::F64);
+    const bool ident = (h->precond == 0);                           // T = I: s is r itself
     void *f0 = f64 ? static_cast<void *>(h->d_r) : h->d_f[0];     // cycle input  = (S) r
-    void *u0 = h->d_u[0];                                           // cycle output s = T r
-    void *f0k = f64 ? nullptr : f0;                                 // what the Krylov kernels write
+    void *u0 = ident ? static_cast<void *>(h->d_r) : h->d_u[0];   // s = T r
+    const Prec kp = ident ? Prec::F64 : h->prec;                    // storage type of s
+    void *f0k = (f64 || ident) ? nullptr : f0;                      // what the Krylov kernels write
     KrylovScalars init;
     std::memset(&init, 0, sizeof(init));
     init.variant = variant;
     SMG_CUDA(cudaMemcpyAsync(h->kw.sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-    SMG_CUDA(kry_init_residual(h->prec, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+    SMG_CUDA(kry_init_residual(kp, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
     h->launches += 1;
     const double tol2 = tol * tol;
     int k = 0, status = SMG_ERR_NOCONV;
@@ -420,7 +423,7 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
                 break;
             }
             // continue from the true residual, with beta = 0 on the next step
-            SMG_CUDA(kry_init_residual(h->prec, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+            SMG_CUDA(kry_init_residual(kp, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
             h->launches += 1;
             tt = -1.0;
         }
@@ -428,8 +431,8 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
             status = SMG_ERR_NOCONV;
             break;
         }
-        if ((rc = run_cycle(h, 1, f0, u0, st)) != SMG_OK) return rc;
-        if (h->cap.count < h->cap.max) {
+        if (!ident && (rc = run_cycle(h, 1, f0, u0, st)) != SMG_OK) return rc;
+        if (!ident && h->cap.count < h->cap.max) {
             // training pair of this iteration: rho = r - A s, e = x* - x - s
             const size_t off = static_cast<size_t>(h->cap.count) * h->N();
             SMG_CUDA(net_capture(h->prec, h->nx, h->ny, h->nz, h->d_r, u0, x, h->cap.xstar, h->cap.rho + off,
@@ -437,7 +440,7 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
             h->cap.count += 1;
             h->launches += 1;
         }
-        if (h->learned) {
+        if (!ident && h->learned) {
             // flops of the three convolutions (2 x 27 x (16 + 256 + 16) per point)
             RegionTimer rt(h, st, 5, 2.0 * 27 * (16 + 256 + 16) * static_cast<double>(h->N()));
             const long long l0 = h->nw.launches;
@@ -446,7 +449,7 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
         }
         {
             RegionTimer rt(h, st, 4, 0.0);
-            SMG_CUDA(kry_iteration_tail(h->prec, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, st));
+            SMG_CUDA(kry_iteration_tail(kp, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, st));
         }
         h->launches += 4;
     }
@@ -537,6 +540,10 @@ int smg_set_option(smg_handle h, int option, int value) {
         if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
             return fail(SMG_ERR_ARG, "cluster_max must be 1, 2, 4, 8 or 16");
         h->cluster_max = value;
+        return SMG_OK;
+    case SMG_OPT_PRECOND:
+        if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "precond must be 0 (none) or 1 (SMG)");
+        h->precond = value;
         return SMG_OK;
     case SMG_OPT_CLUSTER_MAX32:
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
