@@ -41,12 +41,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256", "bricks", "cg128"],
+    ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256", "bricks", "cg128",
+                                           "lobpcg_bricks"],
                     default="fpcg128",
                     help="fpcg128: one 128^3 system (default); batched64: 64 uneven systems, sides in {32..96}; "
                          "lobpcg128: 16 smallest eigenpairs at 128^3; learned256: learned post-correction at 256^3; "
                          "bricks: the paper's 16n x n x n bricks, n = 10..32, every Krylov variant and cycle; "
-                         "cg128: no preconditioner at 128^3 (CG by eq. (1) and eq. (2), steepest descent)")
+                         "cg128: no preconditioner at 128^3 (CG by eq. (1) and eq. (2), steepest descent); "
+                         "lobpcg_bricks: LOBPCG, one eigenpair, 4n x 2n x 2n bricks, (1,1) against (1,0)")
     return ap.parse_args()
 
 
@@ -1027,6 +1029,84 @@ def run_cg(args):
     print(json.dumps(line), flush=True)
 
 
+LB_NS = (10, 20, 40, 60, 80, 100, 120)
+LB_WORKLOAD = ("LOBPCG-SMG, one eigenpair, the paper's 4n x 2n x 2n bricks (n = 10..120), FP32 V-cycle with (1,1) "
+               "and (1,0), Gaussian initial vector, tol 1e-8, eigenvalue against the closed form")
+
+
+def run_lobpcg_bricks(args):
+    """Figures 8-9 on the GPU path: iterations and time of one-eigenpair LOBPCG with and without
+    post-smoothing.  The timed value is the (1,0) solve of the largest brick."""
+    import torch
+
+    from paper_1212_6680_gb300 import build as _build
+    from paper_1212_6680_gb300 import inputs
+
+    world, rank, local, dist = _dist_init()
+    _build.build()
+    from paper_1212_6680_gb300 import smg
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    table = []
+    main_t, main_launches, main_clk = None, 0, None
+    for nb in LB_NS:
+        nx, ny, nz = 4 * nb, 2 * nb, 2 * nb
+        X0 = torch.from_numpy(np.ascontiguousarray(inputs.initial_block(nx, ny, nz, 1, seed=7)).ravel().copy()).cuda()
+        X = torch.empty_like(X0)
+        ref = float(closed_form_smallest(nx, ny, nz, 1)[0])
+        row = {"n": nb, "grid": [nx, ny, nz], "unknowns": nx * ny * nz}
+        for npost in (1, 0):
+            h = smg.smg_setup(nx, ny, nz, 1, npost)
+            smg.smg_set_precision(h, "fp32")
+            last = npost == 0 and nb == LB_NS[-1]
+
+            def once():
+                X.copy_(X0)
+                rc, it, lam = smg.lobpcg_solve(h, 1, X, tol=TOL, maxit=200)
+                assert rc == smg.SMG_OK, smg.smg_last_error()
+                return it, float(lam[0])
+            if last:
+                for _ in range(args.warmup):
+                    once()
+                l0 = smg.smg_launch_count(h)
+                with ClockSampler(local) as clk:
+                    times, (it, lam) = _timed(once, args.steps, 0, barrier, flush, stream)
+                main_t, main_launches, main_clk = statistics.mean(times), smg.smg_launch_count(h) - l0, clk.summary()
+            else:
+                times, (it, lam) = _timed(once, max(1, min(args.steps, 3)), 1, barrier, flush, stream)
+            assert abs(lam - ref) <= 1e-10 * ref, (lam, ref)
+            smg.smg_destroy(h)
+            row[f"v1{npost}_s"] = statistics.mean(times)
+            row[f"v1{npost}_iters"] = it
+        row["iters_ratio_10_over_11"] = row["v10_iters"] / row["v11_iters"]
+        row["time_ratio_10_over_11"] = row["v10_s"] / row["v11_s"]
+        table.append(row)
+    t_max = max_over_ranks(main_t, dist, "cuda")
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": LB_WORKLOAD, "timed": f"(1,0) solve, brick n = {LB_NS[-1]}", "bricks": table,
+                   "l2": "256 MB buffer written before every timed solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": main_launches, "clocks": main_clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1041,6 +1121,8 @@ def main():
         run_bricks(args)
     elif args.workload == "cg128":
         run_cg(args)
+    elif args.workload == "lobpcg_bricks":
+        run_lobpcg_bricks(args)
     else:
         run_ours(args)
 

@@ -158,6 +158,53 @@ __global__ void __launch_bounds__(256, 4) gram_partial_kernel(long long n, long 
         (red[0][idx] + red[1][idx]) + (red[2][idx] + red[3][idx]);
 }
 
+// Partial Gram of a narrow product (k1, k2 <= kSmallK): thread t of CTA `chunk` accumulates all
+// k1 x k2 entries over rows chunk*rows + t, + 256, ... (coalesced loads of each column, no
+// padding work), and the CTA adds its 256 partial sums in FP64; part[] takes the tiled kernel's
+// layout (one 16 x 16 tile) so the same reduction follows.
+constexpr int kSmallK = 4;
+__global__ void __launch_bounds__(256) gram_small_kernel(long long n, long long rows, int k1, int k2,
+                                                         const double *__restrict__ U, const double *__restrict__ V,
+                                                         double *__restrict__ part) {
+    __shared__ double red[8][kSmallK * kSmallK];
+    const long long r0 = static_cast<long long>(blockIdx.x) * rows;
+    const long long r1 = min(n, r0 + rows);
+    float S[kSmallK][kSmallK], sl[kSmallK][kSmallK];
+#pragma unroll
+    for (int i = 0; i < kSmallK; ++i)
+#pragma unroll
+        for (int j = 0; j < kSmallK; ++j) S[i][j] = sl[i][j] = 0.0f;
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        float uh[kSmallK], ul[kSmallK], vh[kSmallK], vl[kSmallK];
+#pragma unroll
+        for (int i = 0; i < kSmallK; ++i) {
+            df_split(i < k1 ? U[static_cast<long long>(i) * n + r] : 0.0, uh[i], ul[i]);
+            df_split(i < k2 ? V[static_cast<long long>(i) * n + r] : 0.0, vh[i], vl[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kSmallK; ++i)
+#pragma unroll
+            for (int j = 0; j < kSmallK; ++j)
+                if (i < k1 && j < k2) df_mac(S[i][j], sl[i][j], uh[i], ul[i], vh[j], vl[j]);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kSmallK; ++i)
+#pragma unroll
+        for (int j = 0; j < kSmallK; ++j) {
+            double v = df_value(S[i][j], sl[i][j]);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[w][i * kSmallK + j] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < kSmallK * kSmallK) {
+        const int i = threadIdx.x / kSmallK, j = threadIdx.x % kSmallK;
+        double v = 0.0;
+        for (int q = 0; q < 8; ++q) v += red[q][threadIdx.x];
+        part[static_cast<long long>(blockIdx.x) * kGT * kGT + i * kGT + j] = v;
+    }
+}
+
 // G[i][j] (k1 x k2 row-major) = sum over chunks of the partial tiles (compensated summation), one
 // warp per entry: the lanes take every 32nd chunk, then the warp combines its 32 sums.  With
 // sym, entries below the diagonal tiles come from the mirrored tile.
@@ -191,14 +238,17 @@ __global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int nti
 }
 
 // Y = alpha * U C + beta * Y  (U: n x k, C: k x m2 row-major, Y: n x m2, column stride n), the
-// products in double-float arithmetic.
+// products in double-float arithmetic.  A CTA covers NC output columns (NC a power of two, the
+// smallest that holds the product's columns, at most kMulCols), so narrow products do no work on
+// padding.
+template <int NC>
 __global__ void block_mul_kernel(long long n, int k, int m2, const double *__restrict__ U,
                                  const double *__restrict__ C, double alpha, double beta, double *__restrict__ Y) {
-    extern __shared__ __align__(16) float2 cs[];  // [k][kMulCols] (hi, lo) pairs of C's column block
-    const int j0 = blockIdx.y * kMulCols;
-    const int nc = min(kMulCols, m2 - j0);
-    for (int t = threadIdx.x; t < k * kMulCols; t += blockDim.x) {
-        const int i = t / kMulCols, j = t % kMulCols;
+    extern __shared__ __align__(16) float2 cs[];  // [k][NC] (hi, lo) pairs of C's column block
+    const int j0 = blockIdx.y * NC;
+    const int nc = min(NC, m2 - j0);
+    for (int t = threadIdx.x; t < k * NC; t += blockDim.x) {
+        const int i = t / NC, j = t % NC;
         float h, l;
         df_split((j < nc) ? C[i * m2 + j0 + j] : 0.0, h, l);
         cs[t] = make_float2(h, l);
@@ -206,24 +256,29 @@ __global__ void block_mul_kernel(long long n, int k, int m2, const double *__res
     __syncthreads();
     const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    float S[kMulCols], sl[kMulCols];
+    float S[NC], sl[NC];
 #pragma unroll
-    for (int j = 0; j < kMulCols; ++j) S[j] = sl[j] = 0.0f;
+    for (int j = 0; j < NC; ++j) S[j] = sl[j] = 0.0f;
     double un = U[r];  // the next row's operand is loaded before the current row's multiply-adds
     for (int i = 0; i < k; ++i) {
         float uh, ul;
         df_split(un, uh, ul);
         if (i + 1 < k) un = U[static_cast<long long>(i + 1) * n + r];
-        const float4 *c4 = reinterpret_cast<const float4 *>(cs + i * kMulCols);  // two (hi, lo) pairs per load
+        if constexpr (NC == 1) {
+            const float2 cc = cs[i];
+            df_mac(S[0], sl[0], uh, ul, cc.x, cc.y);
+        } else {
+            const float4 *c4 = reinterpret_cast<const float4 *>(cs + i * NC);  // two (hi, lo) pairs per load
 #pragma unroll
-        for (int j = 0; j < kMulCols; j += 2) {
-            const float4 cc = c4[j / 2];
-            df_mac(S[j], sl[j], uh, ul, cc.x, cc.y);
-            df_mac(S[j + 1], sl[j + 1], uh, ul, cc.z, cc.w);
+            for (int j = 0; j < NC; j += 2) {
+                const float4 cc = c4[j / 2];
+                df_mac(S[j], sl[j], uh, ul, cc.x, cc.y);
+                df_mac(S[j + 1], sl[j + 1], uh, ul, cc.z, cc.w);
+            }
         }
     }
 #pragma unroll
-    for (int j = 0; j < kMulCols; ++j) {
+    for (int j = 0; j < NC; ++j) {
         if (j < nc) {
             const double acc = df_value(S[j], sl[j]);
             double *y = Y + static_cast<long long>(j0 + j) * n + r;
@@ -445,6 +500,22 @@ struct Ctx {
 // e.g. V = U or V = A U), so only its upper tiles are computed
 int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G, bool sym = false) {
     const int nti = cdiv(k1, kGT), ntj = cdiv(k2, kGT);
+    if (k1 <= kSmallK && k2 <= kSmallK) {
+        // narrow product: 4 CTAs per SM (as far as the partial buffer holds), rows a multiple of 256
+        const long long want = std::max<long long>(1, std::min<long long>(4LL * c.w.num_sms, c.w.part_tiles));
+        const long long rows = ((c.n + want - 1) / want + 255) / 256 * 256;
+        const int nch = static_cast<int>(cdiv(c.n, rows));
+        gram_small_kernel<<<nch, 256, 0, c.st>>>(c.n, rows, k1, k2, U, V, c.w.part);
+        LCHK(cudaGetLastError());
+        gram_reduce_kernel<<<cdiv(static_cast<long long>(k1) * k2 * 32, 256), 256, 0, c.st>>>(
+            nch, k1, k2, 1, 1, c.w.part, c.w.gram, 0);
+        LCHK(cudaGetLastError());
+        G.resize(static_cast<size_t>(k1) * k2);
+        LCHK(cudaMemcpyAsync(c.w.h_buf, c.w.gram, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c.st));
+        LCHK(cudaStreamSynchronize(c.st));
+        std::memcpy(G.data(), c.w.h_buf, sizeof(double) * G.size());
+        return SMG_OK;
+    }
     // rows per CTA: kGChunk, halved (down to kGChunk / 8) while the product has fewer than 4 CTAs
     // per SM and the partial buffer has room (single-tile products would otherwise run one CTA
     // per SM, stalled on their global loads)
@@ -471,8 +542,16 @@ int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<d
 // Y = alpha U C + beta Y with C (k x m2, host row-major)
 int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, double alpha, double beta, double *Y) {
     LCHK(cudaMemcpyAsync(c.w.coef, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, c.st));
-    dim3 grid(cdiv(c.n, 256), cdiv(m2, kMulCols));
-    block_mul_kernel<<<grid, 256, sizeof(float2) * k * kMulCols, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y);
+    const int nc = (m2 <= 1) ? 1 : (m2 <= 2) ? 2 : (m2 <= 4) ? 4 : (m2 <= 8) ? 8 : kMulCols;
+    dim3 grid(cdiv(c.n, 256), cdiv(m2, nc));
+    const size_t smem = sizeof(float2) * k * nc;
+    switch (nc) {
+    case 1: block_mul_kernel<1><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
+    case 2: block_mul_kernel<2><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
+    case 4: block_mul_kernel<4><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
+    case 8: block_mul_kernel<8><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
+    default: block_mul_kernel<kMulCols><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
+    }
     LCHK(cudaGetLastError());
     // the host vector C may be reused right after; the copy above is stream-ordered but reads
     // host memory asynchronously only for pinned memory, so pageable C is safe here
