@@ -310,6 +310,23 @@ int smg_launch_count(smg_handle h, long long *count);
  */
 int smg_apply_A_dot_static(int nx, int ny, int nz, const double *u, double *out, double *dot, void *stream);
 
+/*
+ * smg_setup_coefs -- the SMG set-up as smg_setup builds it, on the host only (no device, no
+ * handle): section 3's semicoarsening hierarchy under the readings the library states (odd
+ * planes and lines coarse, interpolation weights from the stencil collapsed in-plane, Galerkin
+ * coarse operators).  For z-level l, plane z of that level and 2D level m of the plane:
+ *   zc:    8 doubles (host, caller-owned): the plane's z-coupling M(z,z-1), M(z,z), M(z,z+1),
+ *          K(z,z-1), K(z,z), K(z,z+1) and its interpolation weights wm(z), wp(z), where level l's
+ *          operator is (A_l u)_z = sum_dz M(z,z+dz) L2D u_(z+dz) + K(z,z+dz) u_(z+dz);
+ *   lines: ny_m x 8 doubles (host, caller-owned), line y of 2D level m: S(y,y-1), S(y,y),
+ *          S(y,y+1), T(y,y-1), T(y,y), T(y,y+1), wm(y), wp(y), where the plane operator on that
+ *          level is (B v)_y = sum_dy S(y,y+dy) Lx v_(y+dy) + T(y,y+dy) v_(y+dy);
+ *   nz_l, ny_m: (host, may be NULL) the number of planes of level l and lines of 2D level m.
+ * Any index out of range (l >= number of z-levels, z >= nz_l, m >= number of 2D levels) or a
+ * size < 1 returns SMG_ERR_ARG and writes nothing.
+ */
+int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, double *lines, int *nz_l, int *ny_m);
+
 #ifdef __cplusplus
 }
 #endif

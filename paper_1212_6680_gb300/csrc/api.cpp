@@ -753,6 +753,25 @@ int smg_launch_count(smg_handle h, long long *count) {
     return SMG_OK;
 }
 
+int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, double *lines, int *nz_l, int *ny_m) {
+    using namespace smg;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(SMG_ERR_ARG, "grid sizes must be >= 1");
+    if (zc == nullptr || lines == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    HostHierarchy H;
+    build_hierarchy(nx, ny, nz, H);
+    if (l < 0 || l >= H.L || z < 0 || z >= H.nz_l[l] || m < 0 || m >= H.P)
+        return fail(SMG_ERR_ARG, "level, plane or 2D level out of range");
+    const size_t plane = static_cast<size_t>(H.plane_base[l] + z);
+    for (int k = 0; k < kCoefPerPlane; ++k) zc[k] = H.zcoef[plane * kCoefPerPlane + k];
+    const double *pc = &H.pcoef[plane * H.sum_ny * kCoefPerLine];
+    for (int y = 0; y < H.ny_m[m]; ++y)
+        for (int k = 0; k < kCoefPerLine; ++k)
+            lines[static_cast<size_t>(y) * kCoefPerLine + k] = pc[static_cast<size_t>(H.line_base[m] + y) * kCoefPerLine + k];
+    if (nz_l) *nz_l = H.nz_l[l];
+    if (ny_m) *ny_m = H.ny_m[m];
+    return SMG_OK;
+}
+
 int smg_destroy(smg_handle h) {
     if (h == nullptr) return SMG_OK;
     free_levels(h);

@@ -32,7 +32,7 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "krylov_solve_batched", "smg_barrier_selftest", "smg_batched_setup", "smg_batched_solve",
            "smg_batched_destroy", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
-           "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status")
+           "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs")
 NET_WEIGHTS = 7776
 
 
@@ -56,6 +56,7 @@ def _load():
     L.krylov_solve.argtypes = [vp, i, vp, vp, d, i, ip, dp, vp]
     L.lobpcg_solve.argtypes = [vp, i, vp, dp, d, i, ip, vp]
     L.smg_destroy.argtypes = [vp]
+    L.smg_setup_coefs.argtypes = [i, i, i, i, i, i, dp, dp, ip, ip]
     L.smg_last_error.restype = ctypes.c_char_p
     L.smg_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp]
     L.smg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -188,6 +189,17 @@ def smg_launch_count(h: int) -> int:
 def smg_check_conversions(src, mismatches, stream=None) -> None:
     """src: device doubles; mismatches: device int32[2]."""
     _check(_lib.smg_check_conversions(src.numel(), _ptr(src), _ptr(mismatches), _stream(stream)))
+
+
+def smg_setup_coefs(nx: int, ny: int, nz: int, l: int, z: int, m: int):
+    """Host-side set-up coefficients of z-level l, plane z, 2D level m: (zc (8,), lines (ny_m, 8))."""
+    zc = np.zeros(8)
+    lines = np.zeros((ny, 8))
+    nzl, nym = ctypes.c_int(0), ctypes.c_int(0)
+    dp_ = ctypes.POINTER(ctypes.c_double)
+    _check(_lib.smg_setup_coefs(nx, ny, nz, l, z, m, zc.ctypes.data_as(dp_), lines.ctypes.data_as(dp_),
+                                ctypes.byref(nzl), ctypes.byref(nym)))
+    return zc, lines[: nym.value].copy()
 
 
 def smg_apply_A_dot_static(nx: int, ny: int, nz: int, u, out, dot, stream=None) -> None:
