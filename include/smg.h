@@ -327,6 +327,25 @@ int smg_apply_A_dot_static(int nx, int ny, int nz, const double *u, double *out,
  */
 int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, double *lines, int *nz_l, int *ny_m);
 
+/*
+ * smg_plane_layout -- where the plane-relaxation kernel keeps the arrays of a plane's 2D cycle
+ * (host only, no device): the layout the library plans for an nx x ny plane computed in
+ * elem_bytes-byte arithmetic (4 or 8) by one CTA (R = 1) or by a cluster of R = 2, 4, 8 or 16
+ * CTAs.  Shared memory holds the plane's coefficient table (sum_ny lines x coef_per_line values)
+ * at offset 0, then the line-solver factor sets of the first MF 2D levels (two sets of
+ * set_elems values each, from off_fs), then the 2D-cycle arrays u_m and g_m that fit; the others
+ * live in a global slot of ws_elems values per CTA (per cluster when R > 1).  Offsets and sizes
+ * are in elements.
+ *   out: host, caller-owned, 64 long longs:
+ *     [0] P (2D levels)  [1] K (x-line rows per lane)  [2] MF  [3] smem_bytes (0: the cluster
+ *     layout does not fit)  [4] ws_elems  [5] off_fs  [6] on-chip mask of the u_m  [7] on-chip
+ *     mask of the g_m  [8] sum_ny  [9] coef_per_line  [10] set_elems
+ *     [16 + m] offset of u_m, [32 + m] offset of g_m, [48 + m] ny_m  (m < P <= 16)
+ * Sizes outside the library's limits (nx, ny in 1..512), elem_bytes other than 4 or 8, or
+ * another R return SMG_ERR_ARG and write nothing.
+ */
+int smg_plane_layout(int nx, int ny, int elem_bytes, int R, long long *out);
+
 #ifdef __cplusplus
 }
 #endif

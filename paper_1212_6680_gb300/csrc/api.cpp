@@ -772,6 +772,36 @@ int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, dou
     return SMG_OK;
 }
 
+int smg_plane_layout(int nx, int ny, int elem_bytes, int R, long long *out) {
+    using namespace smg;
+    if (out == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    if (nx < 1 || ny < 1 || nx > kMaxNx || ny > kMaxNy) return fail(SMG_ERR_ARG, "nx, ny must be in 1..512");
+    if (elem_bytes != 4 && elem_bytes != 8) return fail(SMG_ERR_ARG, "elem_bytes must be 4 or 8");
+    if (R != 1 && R != 2 && R != 4 && R != 8 && R != 16) return fail(SMG_ERR_ARG, "R must be 1, 2, 4, 8 or 16");
+    HostHierarchy H;
+    build_hierarchy(nx, ny, 1, H);
+    const PlaneLayout P = (R == 1) ? plan_plane_layout(H, static_cast<size_t>(elem_bytes), kSmemBudget)
+                                   : plan_plane_layout_cluster(H, static_cast<size_t>(elem_bytes), kSmemBudget, R);
+    for (int i = 0; i < 64; ++i) out[i] = 0;
+    out[0] = H.P;
+    out[1] = P.K;
+    out[2] = P.MF;
+    out[3] = static_cast<long long>(P.smem_bytes);
+    out[4] = P.ws_per_plane;
+    out[5] = P.off_fs;
+    out[6] = P.smem_u_mask;
+    out[7] = P.smem_g_mask;
+    out[8] = H.sum_ny;
+    out[9] = kCoefPerLine;
+    out[10] = trifac_set_elems(P.K);
+    for (int m = 0; m < H.P && m < 16; ++m) {
+        out[16 + m] = P.off_u[m];
+        out[32 + m] = P.off_g[m];
+        out[48 + m] = H.ny_m[m];
+    }
+    return SMG_OK;
+}
+
 int smg_destroy(smg_handle h) {
     if (h == nullptr) return SMG_OK;
     free_levels(h);

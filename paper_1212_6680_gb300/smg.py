@@ -32,7 +32,8 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "krylov_solve_batched", "smg_barrier_selftest", "smg_batched_setup", "smg_batched_solve",
            "smg_batched_destroy", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
-           "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs")
+           "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs",
+           "smg_plane_layout")
 NET_WEIGHTS = 7776
 
 
@@ -57,6 +58,7 @@ def _load():
     L.lobpcg_solve.argtypes = [vp, i, vp, dp, d, i, ip, vp]
     L.smg_destroy.argtypes = [vp]
     L.smg_setup_coefs.argtypes = [i, i, i, i, i, i, dp, dp, ip, ip]
+    L.smg_plane_layout.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_longlong)]
     L.smg_last_error.restype = ctypes.c_char_p
     L.smg_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp]
     L.smg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -200,6 +202,17 @@ def smg_setup_coefs(nx: int, ny: int, nz: int, l: int, z: int, m: int):
     _check(_lib.smg_setup_coefs(nx, ny, nz, l, z, m, zc.ctypes.data_as(dp_), lines.ctypes.data_as(dp_),
                                 ctypes.byref(nzl), ctypes.byref(nym)))
     return zc, lines[: nym.value].copy()
+
+
+def smg_plane_layout(nx: int, ny: int, elem_bytes: int, R: int = 1) -> dict:
+    """The planned shared-memory / global layout of one plane's 2D-cycle arrays (host only)."""
+    out = (ctypes.c_longlong * 64)()
+    _check(_lib.smg_plane_layout(nx, ny, elem_bytes, R, out))
+    v = list(out)
+    P = v[0]
+    return {"P": P, "K": v[1], "MF": v[2], "smem_bytes": v[3], "ws_elems": v[4], "off_fs": v[5],
+            "u_mask": v[6], "g_mask": v[7], "sum_ny": v[8], "coef_per_line": v[9], "set_elems": v[10],
+            "off_u": v[16:16 + P], "off_g": v[32:32 + P], "ny_m": v[48:48 + P]}
 
 
 def smg_apply_A_dot_static(nx: int, ny: int, nz: int, u, out, dot, stream=None) -> None:
