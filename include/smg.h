@@ -324,7 +324,7 @@ int smg_apply_A_dot_static(int nx, int ny, int nz, const double *u, double *out,
  *   nz_l, ny_m: (host, may be NULL) the number of planes of level l and lines of 2D level m.
  * Any index out of range (l >= number of z-levels, z >= nz_l, m >= number of 2D levels) or a
  * size < 1 returns SMG_ERR_ARG and writes nothing.  Each call builds the whole host hierarchy
- * (about 16 nz ny doubles of host memory, freed before it returns): meant for inspection and
+ * (about 32 nz ny doubles of host memory, freed before it returns): meant for inspection and
  * tests, not for a hot loop.
  */
 int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, double *lines, int *nz_l, int *ny_m);
