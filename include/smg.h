@@ -60,9 +60,13 @@ enum {
     SMG_OPT_CLUSTER_MAX32 = 4, /* the same for the FP32-compute plane relaxations of the FP32 and
                                  BF16 cycles: 1, 2, 4, 8 or 16, or 0 (default) for 1 while a plane's
                                  2D-cycle iterate fits in one CTA's shared memory, else 4 */
-    SMG_OPT_PRECOND = 5       /* the preconditioner krylov_solve applies: 1 (default) the SMG cycle,
+    SMG_OPT_PRECOND = 5,      /* the preconditioner krylov_solve applies: 1 (default) the SMG cycle,
                                  0 none (T = I: plain CG by eq. (1) or (2), steepest descent for PSD;
                                  section 2, figures 1-2); lobpcg_solve always uses the cycle */
+    SMG_OPT_LEAN = 6          /* 1 (default): FP32-compute plane relaxations on one CTA per plane
+                                 with nx <= 128 run the 2D cycle with fewer barrier-separated
+                                 steps (the restriction fused with the next level's even lines;
+                                 the same line solves in the same order); 0: the general kernel */
 };
 
 /*

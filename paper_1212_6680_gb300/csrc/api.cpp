@@ -34,7 +34,9 @@ int fail(int code, const std::string &msg) {
             return fail(SMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
     } while (0)
 
-constexpr size_t kSmemBudget = 227 * 1024;  // the most dynamic shared memory a CTA may use
+// the most dynamic shared memory a plane CTA may use: 227 KB less 1 KB for the kernels' static
+// shared memory (the per-level table of the plane cycle, reduction scratch)
+constexpr size_t kSmemBudget = 227 * 1024 - 1024;
 
 // profiling classes: 0 plane relaxation on the finest level, 1 plane relaxation on the other
 // levels (all but the coarsest), 2 the one-plane coarsest solve, 3 restriction + prolongation,
@@ -75,6 +77,8 @@ struct smg_ctx {
     bool cl32_ok[5] = {false, false, false, false, false};
     int cluster_max = 16;           // largest cluster for FP64-compute plane relaxations (1 = none)
     int precond = 1;                // krylov_solve's preconditioner: 1 the SMG cycle, 0 none (T = I)
+    int lean = 1;                   // 1: FP32-compute single-CTA levels use the shortened-step plane cycle
+    std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     int cluster_max32 = 0;          // largest cluster for FP32-compute plane relaxations; 0 = chosen
                                     // per size (see relax)
     int num_sms = 0;
@@ -149,6 +153,8 @@ int ensure_levels(smg_ctx *h, int nb) {
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, level precision) failed");
     if (set_plane_relax_smem(h->prec, true, false, K, h->lay_d.smem_bytes) != 0)
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, FP64 coarsest) failed");
+    if (lean_supported(h->prec, K) && set_plane_lean_smem(h->prec, K, h->lay_c.smem_bytes) != 0)
+        return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, shortened-step cycle) failed");
     if (h->num_sms == 0) {
         int dev = 0;
         SMG_CUDA(cudaGetDevice(&dev));
@@ -295,7 +301,10 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
         e1 = take_event(h);
         cudaEventRecord(e0, st);
     }
-    cudaError_t err = launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
+    const bool use_lean = !f64c && R == 1 && h->lean && iters == 1 && lean_supported(h->prec, K) &&
+                          lay.MF == H.P && h->lean_level[l];
+    cudaError_t err = use_lean ? launch_plane_lean(h->prec, K, nplanes, nb, h->threads, a, lay.smem_bytes, st)
+                               : launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
     if (err != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("plane relaxation launch: ") + cudaGetErrorString(err));
     h->launches += 1;
     if (timed) {
@@ -493,6 +502,8 @@ int smg_setup(int nx, int ny, int nz, int npre, int npost, smg_handle *out) {
     h->npre = npre;
     h->npost = npost;
     build_hierarchy(nx, ny, nz, h->H);
+    h->lean_level.assign(h->H.L, 0);
+    for (int l = 0; l < h->H.L; ++l) h->lean_level[l] = lean_uniform_level(h->H, l) ? 1 : 0;
     const size_t zb = h->H.zcoef.size() * sizeof(double), pb = h->H.pcoef.size() * sizeof(double);
     cudaError_t e = cudaMalloc(&h->d_zcoef, zb);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_pcoef, pb);
@@ -549,6 +560,10 @@ int smg_set_option(smg_handle h, int option, int value) {
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
             return fail(SMG_ERR_ARG, "cluster_max32 must be 0 (automatic), 1, 2, 4, 8 or 16");
         h->cluster_max32 = value;
+        return SMG_OK;
+    case SMG_OPT_LEAN:
+        if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "lean must be 0 or 1");
+        h->lean = value;
         return SMG_OK;
     case SMG_OPT_PROFILE:
         if (value < 0 || value > 2) return fail(SMG_ERR_ARG, "profile must be 0, 1 or 2");

@@ -626,7 +626,7 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
     const int nsys = c.nsys;
     const Prec P = c.P;
     const size_t sb = storage_bytes(P), cb = (P == Prec::F64) ? 8 : 4;
-    constexpr size_t kBudget = 227 * 1024;
+    constexpr size_t kBudget = 227 * 1024 - 1024;  // 1 KB left for static shared memory
     DevBuf &buf = c.buf;
 
     // ---- per-system hierarchies and layouts ----

@@ -192,6 +192,20 @@ void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H) {
     }
 }
 
+bool lean_uniform_level(const HostHierarchy &H, int l) {
+    for (int z = 0; z < H.nz_l[l]; ++z) {
+        const double *pc = &H.pcoef[static_cast<size_t>(H.plane_base[l] + z) * H.sum_ny * kCoefPerLine];
+        for (int m = 0; m < H.P; ++m) {
+            const double *l0 = pc + static_cast<size_t>(H.line_base[m]) * kCoefPerLine;
+            for (int y = 1; y + 1 < H.ny_m[m]; ++y) {
+                const double *ly = pc + static_cast<size_t>(H.line_base[m] + y) * kCoefPerLine;
+                if (ly[1] != l0[1] || ly[4] != l0[4]) return false;
+            }
+        }
+    }
+    return true;
+}
+
 // Greedy placement of the 2D-cycle arrays: the coefficient table first, then the coarsest
 // levels (latency-bound, few lines) and finally the finest; u_m before g_m at each level
 // (the iterate is touched more often than the right-hand side).  What does not fit in

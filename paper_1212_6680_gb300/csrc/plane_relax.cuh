@@ -332,6 +332,13 @@ struct PlaneCtx {
     C *fs;       // shared-memory factor sets of the interior line matrix of 2D levels 0..MF-1
     int MF;
     bool vec;    // nx == 32 K and every array 16-byte aligned: lanes move their K values as vectors
+    unsigned umask, gmask;  // bit m set: u_m / g_m is on chip
+    // Per-2D-level table in shared memory, filled once per CTA (indexing the kernel parameters by
+    // the run-time level m instead would put a slow dependent load at the head of every step):
+    const int *ny;    // lines of level m
+    const int *lb;    // first row of level m in the coefficient table
+    C *const *ub;     // u_m: base in shared memory (local lines when clustered) or in the global slot
+    C *const *gb;     // g_m: the same
 };
 
 template <class C, bool CL>
@@ -347,15 +354,13 @@ __device__ __forceinline__ C *line_at(const PlaneCtx<C> &c, bool on_chip, C *bas
     }
 }
 template <class C, bool CL>
-__device__ __forceinline__ C *line_u(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int y) {
-    const bool on_chip = (a.smem_u_mask >> m) & 1u;
-    return line_at<C, CL>(c, on_chip, (on_chip ? c.sm : c.gw) + a.off_u[m], y);
+__device__ __forceinline__ C *line_u(const PlaneRelaxArgs &, const PlaneCtx<C> &c, int m, int y) {
+    return line_at<C, CL>(c, (c.umask >> m) & 1u, c.ub[m], y);
 }
 template <class C, bool CL>
-__device__ __forceinline__ C *line_g(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int y) {
+__device__ __forceinline__ C *line_g(const PlaneRelaxArgs &, const PlaneCtx<C> &c, int m, int y) {
     if (m == 0 && c.g0 != nullptr) return c.g0 + y * c.nx;  // f itself, in global memory
-    const bool on_chip = (a.smem_g_mask >> m) & 1u;
-    return line_at<C, CL>(c, on_chip, (on_chip ? c.sm : c.gw) + a.off_g[m], y);
+    return line_at<C, CL>(c, (c.gmask >> m) & 1u, c.gb[m], y);
 }
 
 template <bool CL>
@@ -365,9 +370,10 @@ __device__ __forceinline__ void plane_sync() {
 }
 
 // The t-th line of a level that this CTA owns, counting lines in owned pairs (all lines).
-template <class C>
+template <class C, bool CL>
 __device__ __forceinline__ int owned_line(const PlaneCtx<C> &c, int t) {
-    return 2 * (c.rank + c.R * (t >> 1)) + (t & 1);
+    if constexpr (!CL) return t;
+    else return 2 * (c.rank + c.R * (t >> 1)) + (t & 1);
 }
 
 // Vector access to a lane's K consecutive values: 16-byte chunks when K*sizeof(T) allows,
@@ -502,16 +508,16 @@ template <class S, class C, int K, int NL, bool CL>
 __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
                                             int m, const int (&ys)[NL], int nvalid, S *plane, bool accumulate,
                                             int nbmode, int out, int lane) {
-    const int nx = c.nx, nym = a.ny_m[m];
+    const int nx = c.nx, nym = c.ny[m], lbm = c.lb[m];
     C d[NL][K];
     CoefRow<C> cr[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        cr[l] = coef_row<C>(c.sm + (a.line_base[m] + ys[l]) * kCoefPerLine);
+        cr[l] = coef_row<C>(c.sm + (lbm + ys[l]) * kCoefPerLine);
         load_line<C, K>(d[l], line_g<C, CL>(a, c, m, ys[l]), nx, c.vec, lane);
     }
     if (nbmode != NB_NONE) {
-        const int nyc = (nbmode == NB_CORR) ? a.ny_m[m + 1] : 0;
+        const int nyc = (nbmode == NB_CORR) ? c.ny[m + 1] : 0;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             const int y = ys[l];
@@ -522,7 +528,7 @@ __device__ __forceinline__ void relax_group(const PlaneRelaxArgs &a, const Plane
                 C v[K];
                 load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, c.vec, lane);
                 if (nbmode == NB_CORR) {  // neighbour yy is an even line: add P e from level m+1
-                    const CoefRow<C> cy = coef_row<C>(c.sm + (a.line_base[m] + yy) * kCoefPerLine);
+                    const CoefRow<C> cy = coef_row<C>(c.sm + (lbm + yy) * kCoefPerLine);
                     const int jl = yy / 2 - 1, jh = yy / 2;
                     if (jl >= 0) {
                         C e[K];
@@ -623,9 +629,10 @@ template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, TriFac<C, K> &fac,
                                              int m, int colour, S *plane, bool accumulate, int nbmode, int out,
                                              int warp, int nw, int lane) {
-    const int nl = (a.ny_m[m] - colour + 1) / 2;
-    const int nown = (nl > c.rank) ? (nl - c.rank + c.R - 1) / c.R : 0;
-    auto Y = [&](int i) { return colour + 2 * (c.rank + c.R * i); };
+    const int nl = (c.ny[m] - colour + 1) / 2;
+    int nown = nl;
+    if constexpr (CL) nown = (nl > c.rank) ? (nl - c.rank + c.R - 1) / c.R : 0;
+    auto Y = [&](int i) { return CL ? colour + 2 * (c.rank + c.R * i) : colour + 2 * i; };
     constexpr int NLM = max_lines_per_group<C, K>();
     int i = warp;
     if constexpr (NLM > 1) {
@@ -644,8 +651,9 @@ __device__ __forceinline__ void relax_colour(const PlaneRelaxArgs &a, const Plan
 }
 
 // Number of lines of an n-line level owned by this CTA (owned in pairs).
-template <class C>
+template <class C, bool CL>
 __device__ __forceinline__ int owned_count(const PlaneCtx<C> &c, int n) {
+    if constexpr (!CL) return n;
     const int pairs = (n + 1) / 2;
     const int own_pairs = (pairs > c.rank) ? (pairs - c.rank + c.R - 1) / c.R : 0;
     int cnt = 2 * own_pairs;
@@ -658,7 +666,7 @@ __device__ __forceinline__ int owned_count(const PlaneCtx<C> &c, int n) {
 template <class C, int K, int NL, bool CL>
 __device__ __forceinline__ void restrict_group(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m,
                                                const int (&js)[NL], int lane) {
-    const int nx = c.nx, nym = a.ny_m[m];
+    const int nx = c.nx, nym = c.ny[m], lbm = c.lb[m];
     C acc[NL][K];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
@@ -668,7 +676,7 @@ __device__ __forceinline__ void restrict_group(const PlaneRelaxArgs &a, const Pl
         for (int k = 0; k < 2; ++k) {
             const int e = 2 * js[l] + 2 * k;
             if (e >= nym) continue;
-            const CoefRow<C> ce = coef_row<C>(c.sm + (a.line_base[m] + e) * kCoefPerLine);
+            const CoefRow<C> ce = coef_row<C>(c.sm + (lbm + e) * kCoefPerLine);
             const C w = (k == 0) ? ce.wp : ce.wm;
 #pragma unroll
             for (int s = -1; s <= 1; s += 2) {
@@ -689,9 +697,9 @@ __device__ __forceinline__ void restrict_group(const PlaneRelaxArgs &a, const Pl
 template <class C, int K, bool CL>
 __device__ __forceinline__ void restrict_level(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m, int warp,
                                                int nw, int lane) {
-    const int nown = owned_count(c, a.ny_m[m + 1]);
+    const int nown = owned_count<C, CL>(c, c.ny[m + 1]);
     for (int t = warp; t < nown; t += nw) {
-        const int js[1] = {owned_line(c, t)};
+        const int js[1] = {owned_line<C, CL>(c, t)};
         restrict_group<C, K, 1, CL>(a, c, m, js, lane);
     }
 }
@@ -768,9 +776,9 @@ __device__ __forceinline__ void rhs_group(const PlaneRelaxArgs &a, const PlaneCt
 template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void compute_rhs(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int mode, const S *fpl,
                                             const S *ub, int z, const C *zc, int warp, int nw, int lane) {
-    const int nown = owned_count(c, a.ny);
+    const int nown = owned_count<C, CL>(c, a.ny);
     for (int t = warp; t < nown; t += nw) {
-        const int ys[1] = {owned_line(c, t)};
+        const int ys[1] = {owned_line<C, CL>(c, t)};
         rhs_group<S, C, K, 1, CL>(a, c, ys, mode, fpl, ub, z, zc, lane);
     }
 }
@@ -795,6 +803,22 @@ __device__ __forceinline__ void plane_task(const PlaneRelaxArgs &a, int pidx, in
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     c.gw = reinterpret_cast<C *>(a.gws) + slot * a.ws_per_plane;
+    c.umask = a.smem_u_mask;
+    c.gmask = a.smem_g_mask;
+    {
+        __shared__ int s_ny[kMaxPlaneLevels], s_lb[kMaxPlaneLevels];
+        __shared__ C *s_ub[kMaxPlaneLevels], *s_gb[kMaxPlaneLevels];
+        if (tid < a.P) {
+            s_ny[tid] = a.ny_m[tid];
+            s_lb[tid] = a.line_base[tid];
+            s_ub[tid] = (((c.umask >> tid) & 1u) ? c.sm : c.gw) + a.off_u[tid];
+            s_gb[tid] = (((c.gmask >> tid) & 1u) ? c.sm : c.gw) + a.off_g[tid];
+        }
+        c.ny = s_ny;
+        c.lb = s_lb;
+        c.ub = s_ub;
+        c.gb = s_gb;
+    }
     const S *fb = reinterpret_cast<const S *>(a.f) + static_cast<long long>(b) * a.vstride;
     S *ub = reinterpret_cast<S *>(a.u) + static_cast<long long>(b) * a.vstride;
     S *plane = ub + static_cast<long long>(z) * np;
@@ -813,8 +837,8 @@ __device__ __forceinline__ void plane_task(const PlaneRelaxArgs &a, int pidx, in
     // other one when ny is a power of two); set 2m + t, computed by warps in parallel
     for (int sidx = warp; sidx < 2 * a.MF; sidx += nw) {
         const int mm = sidx >> 1;
-        const int y = (sidx & 1) ? a.ny_m[mm] - 1 : 0;
-        const C *lc = c.sm + (a.line_base[mm] + y) * kCoefPerLine;
+        const int y = (sidx & 1) ? c.ny[mm] - 1 : 0;
+        const C *lc = c.sm + (c.lb[mm] + y) * kCoefPerLine;
         tri_factor<C, K>(fac, C(2) * lc[1] + lc[4], -lc[1], nx, lane);
         trifac_store<C, K>(c.fs + sidx * trifac_fields<C, K>() * 32, fac, lane);
     }

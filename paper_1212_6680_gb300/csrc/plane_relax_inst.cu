@@ -2,6 +2,7 @@
 // K = SMG_K (rows per lane; nx <= 32 K) and one storage precision SMG_PREC (0 FP64, 1 FP32,
 // 2 BF16).  The build compiles this unit once per (K, precision) so the instantiations
 // compile in parallel.
+#include "plane_lean.cuh"
 #include "plane_relax.cuh"
 
 #if !defined(SMG_K) || !defined(SMG_PREC)
@@ -72,5 +73,16 @@ bool SMG_NAME(cluster_resident_k, SMG_K, SMG_PREC)(bool f64, int R, int threads,
     }
     return n > 0;
 }
+
+#if SMG_PREC != 0 && SMG_K <= 4
+// The shortened-step FP32 plane cycle (plane_lean.cuh), one CTA per plane.
+cudaError_t SMG_NAME(launch_plane_lean_k, SMG_K, SMG_PREC)(int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
+                                                           size_t smem, cudaStream_t st) {
+    return launch_pdl(plane_lean_kernel<StorageT, SMG_K>, dim3(nplanes, nb), dim3(threads), smem, st, a);
+}
+int SMG_NAME(set_plane_lean_smem_k, SMG_K, SMG_PREC)(size_t smem) {
+    return static_cast<int>(raise_smem_attr(reinterpret_cast<const void *>(&plane_lean_kernel<StorageT, SMG_K>), smem));
+}
+#endif
 
 }  // namespace smg

@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 
 from paper_1212_6680_gb300 import inputs  # noqa: E402
 from tests import dense_ref as D  # noqa: E402
+from tests.parity import assert_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -32,10 +33,6 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
-
-
 N = 128
 
 
@@ -47,7 +44,7 @@ def test_apply_128cube_matches_oracle(smg, orc, prec, tol):
         s = torch.empty(r.size, dtype=torch.float64, device="cuda")
         smg.smg_apply(h.h, dev(r), s)
         got = s.cpu().numpy()
-    assert rel(got, ref) <= tol, rel(got, ref)
+    assert_close(got, ref, tol, (N, N, N), f"{prec} cycle at 128^3")
 
 
 def test_fpcg_128cube_matches_oracle_iterations(smg, orc):

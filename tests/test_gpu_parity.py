@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 from paper_1212_6680_gb300 import inputs  # noqa: E402
+from tests.parity import assert_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -33,10 +34,6 @@ def smg():
 
 def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
 SHAPES = [(32, 32, 32), (33, 17, 20), (7, 5, 3), (1, 1, 8), (8, 1, 1), (5, 6, 1), (64, 48, 40), (130, 9, 6),
@@ -57,7 +54,7 @@ def test_apply_fp64_matches_oracle(smg, orc, shape, npre, npost):
         # applying twice gives identical results (fixed, linear preconditioner)
         smg.smg_apply(h.h, rd, sd)
         assert np.array_equal(sd.cpu().numpy(), s)
-    assert rel(s, ref) <= 1e-12, rel(s, ref)
+    assert_close(s, ref, 1e-12, shape, f"FP64 cycle {shape} ({npre},{npost})")
 
 
 @pytest.mark.parametrize("shape", [(256, 256, 2), (256, 200, 3)])
@@ -79,7 +76,7 @@ def test_coarsest_plane_cluster_with_global_arrays(smg, orc, shape, prec, tol, c
         s = sd.cpu().numpy()
     finally:
         smg.smg_destroy(h)
-    assert rel(s, ref) <= tol, rel(s, ref)
+    assert_close(s, ref, tol, shape, f"{prec} cluster_max {cluster_max}")
 
 
 @pytest.mark.parametrize("cluster_max32", [0, 1, 2, 16])
@@ -99,7 +96,7 @@ def test_fp32_plane_clusters(smg, orc, cluster_max32):
         s = sd.cpu().numpy()
     finally:
         smg.smg_destroy(h)
-    assert rel(s, ref) <= 2e-5, rel(s, ref)
+    assert_close(s, ref, 2e-5, (nx, ny, nz), f"FP32 cluster_max32 {cluster_max32}")
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("bf16", 3e-2)])
@@ -113,7 +110,27 @@ def test_apply_mixed_precision_close_to_oracle(smg, orc, prec, tol, shape, npost
         sd = torch.empty(r.size, dtype=torch.float64, device="cuda")
         smg.smg_apply(h.h, dev(r), sd)
         s = sd.cpu().numpy()
-    assert rel(s, ref) <= tol, rel(s, ref)
+    assert_close(s, ref, tol, shape, f"{prec} cycle {shape} (1,{npost})")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape", [(128, 128, 16), (96, 80, 64), (33, 17, 20), (100, 3, 5), (5, 6, 1), (1, 1, 8)])
+@pytest.mark.parametrize("npost", [1, 0])
+def test_shortened_step_plane_cycle_is_bitwise_the_general_one(smg, orc, prec, shape, npost):
+    """The FP32 plane kernel with fewer barrier-separated steps (SMG_OPT_LEAN = 1, the default for
+    nx <= 128) does the same line solves in the same order as the general kernel: bit-identical
+    cycles, and both within the precision's tolerance of the oracle."""
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=14)
+    out = {}
+    for lean in (1, 0):
+        with smg.Handle(nx, ny, nz, 1, npost, precision=prec) as h:
+            smg.smg_set_option(h.h, smg.SMG_OPT_LEAN, lean)
+            sd = torch.empty(r.size, dtype=torch.float64, device="cuda")
+            smg.smg_apply(h.h, dev(r), sd)
+            out[lean] = sd.cpu().numpy()
+    assert np.array_equal(out[0], out[1])
+    assert_close(out[1], orc.SMG(nx, ny, nz, 1, npost).apply(r), 2e-5 if prec == "fp32" else 3e-2, shape, prec)
 
 
 def test_apply_batched_matches_columns(smg, orc):
@@ -125,7 +142,7 @@ def test_apply_batched_matches_columns(smg, orc):
         smg.smg_apply_batched(h.h, nb, dev(R), Sd)
         S = Sd.cpu().numpy().reshape(nb, -1)
     for j in range(nb):
-        assert rel(S[j], T.apply(R[j].reshape(nz, ny, nx))) <= 1e-12
+        assert_close(S[j], T.apply(R[j].reshape(nz, ny, nx)), 1e-12, (nx, ny, nz), f"column {j}")
 
 
 def test_apply_A_matches_oracle(smg, orc):
@@ -134,7 +151,7 @@ def test_apply_A_matches_oracle(smg, orc):
     with smg.Handle(nx, ny, nz) as h:
         o = torch.empty(u.size, dtype=torch.float64, device="cuda")
         smg.smg_apply_A(h.h, dev(u), o)
-        assert rel(o.cpu().numpy(), orc.apply_A(u)) <= 1e-15
+        assert_close(o.cpu().numpy(), orc.apply_A(u), 1e-15, None, "A u")
 
 
 @pytest.mark.parametrize("variant", ["pcg", "fpcg", "psd"])
@@ -172,7 +189,7 @@ def test_krylov_mixed_precision_reaches_tolerance(smg, orc, prec, variant):
     assert rc == smg.SMG_OK
     assert np.linalg.norm(b - orc.apply_A(xh)) / np.linalg.norm(b) <= 1e-8
     # FP64 solution error of the mixed path vs the oracle's FP64 solve: both within tol of A^{-1} b
-    assert rel(xh, ref["x"]) <= 1e-5
+    assert_close(xh, ref["x"], 1e-5, (nx, ny, nz), "solution vs the oracle's FP64 solve")
     assert it <= ref["iters"] + (2 if prec == "fp32" else 6)
 
 
@@ -245,8 +262,7 @@ def test_handles_with_different_layouts_coexist(smg, orc, prec):
             smg.smg_apply(h.h, r, s)
             torch.cuda.synchronize()
             ref = orc.SMG(*shape, 1, 1).apply(u)
-            err = rel(s.cpu().numpy(), ref)
-            assert err <= (1e-12 if prec == "fp64" else 2e-5), (shape, err)
+            assert_close(s.cpu().numpy(), ref, 1e-12 if prec == "fp64" else 2e-5, shape, f"{prec} {shape}")
 
 
 def test_integer_pipe_conversions_match_hardware(smg):
