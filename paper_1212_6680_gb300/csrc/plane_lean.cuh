@@ -180,28 +180,21 @@ __device__ __forceinline__ void lean_colour(const LeanEnv<K> &e, TriFac<float, K
     }
 }
 
-// g_{m+1}[j] = wp(2j) r_{2j} + wm(2j+2) r_{2j+2},  r_e = -sum_{dy=+-1} B_{e,e+dy} u_{e+dy}
-// (the residual of level m after its down-sweep); the result stays in registers.
+// g_{m+1}[j] from the odd lines 2j-1, 2j+1, 2j+3 of level m (restrict_combine: the residual of
+// level m after its down-sweep); the result stays in registers.
 template <int K>
 __device__ __forceinline__ void lean_restrict_line(const LeanEnv<K> &e, const LeanLevel &L, int j, float (&acc)[K]) {
-    const int nx = e.nx, lane = e.lane;
+    const int nx = e.nx, lane = e.lane, e0 = 2 * j;
+    const bool ha = e0 >= 1, h1 = e0 + 2 < L.ny, hc = e0 + 3 < L.ny;
+    float va[K], vb[K], vc[K];
 #pragma unroll
-    for (int q = 0; q < K; ++q) acc[q] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int ev = 2 * j + 2 * k;
-        if (ev >= L.ny) continue;
-        const CoefRow<float> ce = coef_row<float>(e.coef + (L.lb + ev) * kCoefPerLine);
-        const float w = (k == 0) ? ce.wp : ce.wm;
-#pragma unroll
-        for (int s = -1; s <= 1; s += 2) {
-            const int yy = ev + s;
-            if (yy < 0 || yy >= L.ny) continue;
-            float v[K];
-            load_line<float, K>(v, L.u + yy * nx, nx, e.vec, lane);
-            sub_coupling<float, K>(acc, v, w * ce.s[1 + s], w * ce.t[1 + s], lane);
-        }
-    }
+    for (int q = 0; q < K; ++q) { va[q] = 0.0f; vc[q] = 0.0f; }
+    if (ha) load_line<float, K>(va, L.u + (e0 - 1) * nx, nx, e.vec, lane);
+    load_line<float, K>(vb, L.u + (e0 + 1) * nx, nx, e.vec, lane);
+    if (hc) load_line<float, K>(vc, L.u + (e0 + 3) * nx, nx, e.vec, lane);
+    const CoefRow<float> c0 = coef_row<float>(e.coef + (L.lb + e0) * kCoefPerLine);
+    const CoefRow<float> c1 = coef_row<float>(e.coef + (L.lb + (h1 ? e0 + 2 : e0)) * kCoefPerLine);
+    restrict_combine<float, K>(acc, va, vb, vc, c0, c1, ha, h1, hc, lane);
 }
 
 // Restriction from level m to level m+1, coarse lines in pairs (2k, 2k+1) with k = w + i nw;

@@ -662,34 +662,49 @@ __device__ __forceinline__ int owned_count(const PlaneCtx<C> &c, int n) {
     return cnt;
 }
 
-// g_{m+1}[j] = wp(2j) r_{2j} + wm(2j+2) r_{2j+2},  r_e = -sum_{dy=+-1} B_{e,e+dy} u_{e+dy}
+// g_{m+1}[j] = wp(2j) r_{2j} + wm(2j+2) r_{2j+2},  r_e = -sum_{dy=+-1} B_{e,e+dy} u_{e+dy}: the
+// residual of level m after its down-sweep is zero on odd lines, and on the even lines 2j, 2j+2
+// it comes from the odd lines a = 2j-1, b = 2j+1, c = 2j+3.  Line b couples to both even lines,
+// so its two couplings are summed first (one pass over b instead of two):
+//   g = -wp(2j) B_{2j,2j-1} a - (wp(2j) B_{2j,2j+1} + wm(2j+2) B_{2j+2,2j+1}) b - wm(2j+2) B_{2j+2,2j+3} c.
+// ha: line a exists (j >= 1); h1: even line 2j+2 exists; hc: line c exists.
+template <class C, int K>
+__device__ __forceinline__ void restrict_combine(C (&acc)[K], const C (&va)[K], const C (&vb)[K], const C (&vc)[K],
+                                                 const CoefRow<C> &c0, const CoefRow<C> &c1, bool ha, bool h1,
+                                                 bool hc, int lane) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] = C(0);
+    const C w0 = c0.wp;
+    if (ha) sub_coupling<C, K>(acc, va, w0 * c0.s[0], w0 * c0.t[0], lane);
+    C sb = w0 * c0.s[2], tb = w0 * c0.t[2], w1 = C(0);
+    if (h1) {
+        w1 = c1.wm;
+        sb = fma(w1, c1.s[0], sb);
+        tb = fma(w1, c1.t[0], tb);
+    }
+    sub_coupling<C, K>(acc, vb, sb, tb, lane);
+    if (h1 && hc) sub_coupling<C, K>(acc, vc, w1 * c1.s[2], w1 * c1.t[2], lane);
+}
+
 template <class C, int K, int NL, bool CL>
 __device__ __forceinline__ void restrict_group(const PlaneRelaxArgs &a, const PlaneCtx<C> &c, int m,
                                                const int (&js)[NL], int lane) {
     const int nx = c.nx, nym = c.ny[m], lbm = c.lb[m];
-    C acc[NL][K];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
+        const int e0 = 2 * js[l];
+        const bool ha = e0 >= 1, h1 = e0 + 2 < nym, hc = e0 + 3 < nym;
+        C va[K], vb[K], vc[K], acc[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) acc[l][j] = C(0);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int e = 2 * js[l] + 2 * k;
-            if (e >= nym) continue;
-            const CoefRow<C> ce = coef_row<C>(c.sm + (lbm + e) * kCoefPerLine);
-            const C w = (k == 0) ? ce.wp : ce.wm;
-#pragma unroll
-            for (int s = -1; s <= 1; s += 2) {
-                const int yy = e + s;
-                if (yy < 0 || yy >= nym) continue;
-                C v[K];
-                load_line<C, K>(v, line_u<C, CL>(a, c, m, yy), nx, c.vec, lane);
-                sub_coupling<C, K>(acc[l], v, w * ce.s[1 + s], w * ce.t[1 + s], lane);
-            }
-        }
+        for (int q = 0; q < K; ++q) { va[q] = C(0); vc[q] = C(0); }
+        if (ha) load_line<C, K>(va, line_u<C, CL>(a, c, m, e0 - 1), nx, c.vec, lane);
+        load_line<C, K>(vb, line_u<C, CL>(a, c, m, e0 + 1), nx, c.vec, lane);
+        if (hc) load_line<C, K>(vc, line_u<C, CL>(a, c, m, e0 + 3), nx, c.vec, lane);
+        const CoefRow<C> c0 = coef_row<C>(c.sm + (lbm + e0) * kCoefPerLine);
+        const CoefRow<C> c1 = coef_row<C>(c.sm + (lbm + (h1 ? e0 + 2 : e0)) * kCoefPerLine);
+        restrict_combine<C, K>(acc, va, vb, vc, c0, c1, ha, h1, hc, lane);
+        store_line<C, K>(line_g<C, CL>(a, c, m + 1, js[l]), acc, nx, c.vec, lane);
     }
-#pragma unroll
-    for (int l = 0; l < NL; ++l) store_line<C, K>(line_g<C, CL>(a, c, m + 1, js[l]), acc[l], nx, c.vec, lane);
 }
 
 // The restriction of one level, one coarse line per warp at a time (a single compiled body keeps

@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 from paper_1212_6680_gb300 import inputs  # noqa: E402
+from tests.parity import assert_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -29,10 +30,6 @@ def smg():
 
 def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
 def bf16_round(smg, w):
@@ -63,11 +60,12 @@ def test_forward_matches_oracle(smg, orc, shape, act):
     smg.smg_net_forward(shape, act, w, dev(rho), d)
     d = d.cpu().numpy()
     if act == "fp32":
-        assert rel(d, orc.net_forward(w, rho)) <= 1e-5
+        assert_close(d, orc.net_forward(w, rho), 1e-5, None, "FP32 forward")
     else:
-        # FP32 summation order flips a few BF16 roundings of hidden activations by one ulp
-        assert rel(d, orc.net_forward(w, rho, act_bf16=True)) <= 3e-4
-        assert rel(d, orc.net_forward(w, rho)) <= 1e-2
+        # FP32 summation order flips a few BF16 roundings of hidden activations by one ulp: an
+        # output element moves by at most about one BF16 ulp (2^-8) of the output's scale
+        assert_close(d, orc.net_forward(w, rho, act_bf16=True), 3e-4, None, "BF16 forward", elem_tol=3e-3)
+        assert_close(d, orc.net_forward(w, rho), 1e-2, None, "BF16 forward vs the FP64 network")
 
 
 @pytest.mark.parametrize("shape", [(20, 13, 9), (40, 6, 5)])
@@ -80,12 +78,15 @@ def test_loss_gradient_matches_oracle(smg, orc, shape, act):
     rho = inputs.rhs(nx, ny, nz, seed=112)
     e = inputs.rhs(nx, ny, nz, seed=113)
     loss, g = smg.smg_net_loss_grad(shape, act, w, dev(rho), dev(e))
-    refs = [(False, 1e-5)] if act == "fp32" else [(True, 1e-3), (False, 5e-2)]
-    for act_bf16, tol in refs:
+    # against the plain FP64 network, rounding the hidden activations to BF16 alone moves single
+    # weight gradients by up to ~5% (the element-wise bound there is 1e-1); the oracle with the
+    # same BF16 rounding points is the tight check
+    refs = [(False, 1e-5, 1e-5)] if act == "fp32" else [(True, 1e-3, 1e-3), (False, 5e-2, 1e-1)]
+    for act_bf16, tol, etol in refs:
         loss_ref, g_ref = orc.net_loss_grad(w, rho, e, act_bf16=act_bf16)
         assert abs(loss - loss_ref) <= tol * abs(loss_ref)
         for lo, hi in ((0, 432), (432, 7344), (7344, 7776)):  # each layer on its own scale
-            assert rel(g[lo:hi], g_ref[lo:hi]) <= tol, (act_bf16, lo, rel(g[lo:hi], g_ref[lo:hi]))
+            assert_close(g[lo:hi], g_ref[lo:hi], tol, None, f"gradient [{lo}:{hi}] act_bf16={act_bf16}", elem_tol=etol)
 
 
 @pytest.mark.parametrize("which", ["jacobi", "random"])
@@ -104,7 +105,7 @@ def test_apply_with_learned_correction_matches_oracle(smg, orc, which):
         calls, acc = smg.smg_learned_stats(h.h)
     assert (calls, acc) == (1, T.learned_stats()[1])
     # BF16 activations: the correction carries their rounding; the cycle itself is FP64
-    assert rel(s.cpu().numpy(), ref) <= 2e-3, rel(s.cpu().numpy(), ref)
+    assert_close(s.cpu().numpy(), ref, 2e-3, (nx, ny, nz), "cycle with the learned correction", elem_tol=1e-2)
 
 
 def test_fpcg_learned_jacobi_matches_oracle_iterations(smg, orc):
@@ -163,9 +164,9 @@ def test_collected_pairs_satisfy_their_definition(smg, orc):
     e = e.cpu().numpy().astype(np.float64).reshape(12, nz, ny, nx)
     for k in range(npairs):
         Ae = orc.apply_A(e[k])
-        assert rel(Ae, rho[k]) <= 3e-4, (k, rel(Ae, rho[k]))
+        assert_close(Ae, rho[k], 3e-4, (nx, ny, nz), f"A e_{k} vs rho_{k}", elem_tol=3e-3)
     rho0 = b - orc.apply_A(orc.SMG(nx, ny, nz, 1, 0).apply(b))
-    assert rel(rho[0], rho0) <= 1e-4
+    assert_close(rho[0], rho0, 1e-4, (nx, ny, nz), "rho_0", elem_tol=1e-3)
 
 
 def test_training_lowers_the_loss(smg):
@@ -224,9 +225,9 @@ def test_tensor_core_layer_matches_cuda_cores_and_oracle(smg, orc, shape):
     finally:
         smg.smg_net_set_tensor_cores(True)
     assert smg.smg_net_tc_status() == 0
-    assert rel(out[True], out[False]) <= 3e-4, rel(out[True], out[False])
+    assert_close(out[True], out[False], 3e-4, None, "tensor cores vs CUDA cores", elem_tol=3e-3)
     ref = orc.net_forward(w, rho.cpu().numpy().reshape(nz, ny, nx), act_bf16=True)
-    assert rel(out[True], ref) <= 3e-4
+    assert_close(out[True], ref, 3e-4, None, "tensor cores vs the oracle", elem_tol=3e-3)
 
 
 def test_trained_network_cuts_iterations_on_a_held_out_system(smg):
