@@ -154,6 +154,16 @@ int lobpcg_solve(smg_handle h, int m, double *X, double *lambda, double tol, int
  * wait gave up, SMG_ERR_BREAKDOWN / SMG_ERR_NAN as krylov_solve.  Synchronises `stream` once
  * per iteration.  Calls on one handle must not overlap.
  *
+ * smg_batched_apply -- s_s = T_s r_s for every system s: one application of each system's SMG
+ *   V-cycle (section 3: the fixed, linear preconditioner of Algorithm 1) with the handle's
+ *   npre/npost, storage precision and tuned schedule, all systems together in exactly one launch
+ *   of the persistent V-cycle kernel -- the launch each iteration of smg_batched_solve makes.
+ *   r, s:   host arrays of nsys device pointers (system s: nx*ny*nz doubles, layout as
+ *           smg_apply); r is rounded to the storage precision on entry, s receives the cycle's
+ *           output widened exactly to FP64.  Caller-owned.
+ *   Returns SMG_ERR_TIMEOUT when a grid-barrier wait gave up.  Synchronises `stream`.  Calls on
+ *   one handle must not overlap (the handle's level vectors are shared).
+ *
  * smg_batched_destroy -- frees the handle (NULL accepted).  Synchronises the device.
  */
 typedef struct smg_batched_ctx *smg_batched_handle;
@@ -161,6 +171,7 @@ int smg_batched_setup(int nsys, const int *dims, int npre, int npost, int prec, 
                       void *stream);
 int smg_batched_solve(smg_batched_handle h, int variant, const double *const *b, double *const *x, double tol,
                       int maxit, int *iters, double *relres, void *stream);
+int smg_batched_apply(smg_batched_handle h, const double *const *r, double *const *s, void *stream);
 int smg_batched_destroy(smg_batched_handle h);
 
 /*
@@ -296,8 +307,8 @@ int smg_launch_count(smg_handle h, long long *count);
 
 /*
  * smg_apply_A_dot_static -- out = A u and *dot = (u, A u), allocating nothing.
- * The paper has no counterpart: this is an allocation-free form of the operator and inner
- * product of Algorithm 1 for callers that cannot allocate device memory where they need it
+ * The paper has no counterpart: this is the 7-point operator with its fused inner product
+ * (u, A u), in a form for callers that cannot allocate device memory where they need it
  * (a host framework that owns every device allocation and lends the library only input and
  * output buffers, or a section where cudaMalloc / cudaFree must not run because they can
  * synchronise the device).  No handle is needed.

@@ -287,6 +287,41 @@ __global__ void __launch_bounds__(kBThreads) kb_dots(BKrylov k) {
     }
 }
 
+// smg_batched_apply: every system's r (FP64, caller memory) into its level-0 f in the storage
+// precision, and every system active for the V-cycle that follows.
+template <class S>
+__global__ void __launch_bounds__(kBThreads) kb_apply_in(BKrylov k) {
+    const int c = blockIdx.x;
+    const int s = k.ch_sys[c];
+    const BSys sy = k.sys[s];
+    const long long g0 = k.ch_start[c];
+    const int len = k.ch_len[c];
+    const double *r = k.bptr[s];
+    S *f0 = static_cast<S *>(k.fstore) + sy.f0_off;
+    for (int t = threadIdx.x; t < len; t += kBThreads) {
+        const int li = static_cast<int>(g0 + t - sy.off);
+        stv<S, double>(f0 + li, r[li]);
+    }
+    if (threadIdx.x == 0 && c == sy.c0) k.active[s] = 1;
+}
+
+// smg_batched_apply: every system's level-0 u (the cycle's output, storage precision) widened
+// exactly to FP64 into the caller's s.
+template <class S>
+__global__ void __launch_bounds__(kBThreads) kb_apply_out(BKrylov k) {
+    const int c = blockIdx.x;
+    const int s = k.ch_sys[c];
+    const BSys sy = k.sys[s];
+    const long long g0 = k.ch_start[c];
+    const int len = k.ch_len[c];
+    double *out = k.xptr[s];
+    const S *u0 = static_cast<const S *>(k.ustore) + sy.u0_off;
+    for (int t = threadIdx.x; t < len; t += kBThreads) {
+        const int li = static_cast<int>(g0 + t - sy.off);
+        out[li] = ldv<double>(u0 + li);
+    }
+}
+
 __global__ void kb_fin_beta(BKrylov k) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k.nsys; s += gridDim.x * blockDim.x) {
         if (k.active[s] != 1) continue;
@@ -1187,6 +1222,45 @@ extern "C" int smg_batched_solve(smg_batched_handle h, int variant, const double
         }
     }
     return batched_solve(*h, variant, b, x, tol, maxit, iters, relres, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int smg_batched_apply(smg_batched_handle h, const double *const *r, double *const *out, void *stream) {
+    if (!h || !r || !out) {
+        set_last_error("null pointer");
+        return SMG_ERR_ARG;
+    }
+    for (int s = 0; s < h->nsys; ++s) {
+        if (!r[s] || !out[s]) {
+            set_last_error("null vector pointer");
+            return SMG_ERR_ARG;
+        }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    smg_batched_ctx &c = *h;
+    BCHK(cudaMemcpyAsync(c.d_bptr, r, c.nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
+    BCHK(cudaMemcpyAsync(c.d_xptr, out, c.nsys * sizeof(double *), cudaMemcpyHostToDevice, st));
+    switch (c.P) {
+    case Prec::F64: kb_apply_in<double><<<c.nch, kBThreads, 0, st>>>(c.kk); break;
+    case Prec::F32: kb_apply_in<float><<<c.nch, kBThreads, 0, st>>>(c.kk); break;
+    case Prec::BF16: kb_apply_in<__nv_bfloat16><<<c.nch, kBThreads, 0, st>>>(c.kk); break;
+    }
+    BCHK(cudaGetLastError());
+    BCHK(c.launch_vcycle(st, c.tune.threads, c.blocks));
+    switch (c.P) {
+    case Prec::F64: kb_apply_out<double><<<c.nch, kBThreads, 0, st>>>(c.kk); break;
+    case Prec::F32: kb_apply_out<float><<<c.nch, kBThreads, 0, st>>>(c.kk); break;
+    case Prec::BF16: kb_apply_out<__nv_bfloat16><<<c.nch, kBThreads, 0, st>>>(c.kk); break;
+    }
+    BCHK(cudaGetLastError());
+    c.kernel_launches += 3;
+    int herr = 0;
+    BCHK(cudaMemcpyAsync(&herr, c.pa.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BCHK(cudaStreamSynchronize(st));
+    if (herr != 0) {
+        set_last_error("batched V-cycle: a grid-barrier wait timed out");
+        return herr;
+    }
+    return SMG_OK;
 }
 
 extern "C" int smg_batched_destroy(smg_batched_handle h) {

@@ -78,17 +78,27 @@ __global__ void __launch_bounds__(kNoAllocThreads) apply_A_dot_static_kernel(int
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last && threadIdx.x < 32) {
+        // the last CTA's first warp: each lane sums every 32nd partial with TwoSum (error-free
+        // addition, errors carried in c), then the lanes' (s, c) pairs are combined the same way
         __threadfence();
-        double s = 0.0, c = 0.0;  // TwoSum-compensated sum of the partials
-        for (unsigned b = 0; b < gridDim.x; ++b) {
+        const int lane = threadIdx.x;
+        double s = 0.0, c = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) {
             const double v = *reinterpret_cast<volatile double *>(&partials[b]);
             const double t = s + v;
             const double bp = t - s;
             c += (s - (t - bp)) + (v - bp);
             s = t;
         }
-        *dot = s + c;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double vs = __shfl_down_sync(0xffffffffu, s, o), vc = __shfl_down_sync(0xffffffffu, c, o);
+            const double t = s + vs;
+            const double bp = t - s;
+            c += ((s - (t - bp)) + (vs - bp)) + vc;
+            s = t;
+        }
+        if (lane == 0) *dot = s + c;
     }
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "smg_apply_A", "krylov_solve", "lobpcg_solve", "smg_destroy", "smg_last_error",
            "smg_profile_read", "smg_launch_count", "smg_check_conversions", "smg_apply_A_dot_static",
            "krylov_solve_batched", "smg_barrier_selftest", "smg_batched_setup", "smg_batched_solve",
-           "smg_batched_destroy", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
+           "smg_batched_destroy", "smg_batched_apply", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
            "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs",
            "smg_plane_layout")
@@ -71,6 +71,7 @@ def _load():
     L.smg_batched_setup.argtypes = [i, vp, i, i, i, ctypes.POINTER(vp), vp]
     L.smg_batched_solve.argtypes = [vp, i, vp, vp, d, i, vp, vp, vp]
     L.smg_batched_destroy.argtypes = [vp]
+    L.smg_batched_apply.argtypes = [vp, vp, vp, vp]
     L.smg_batched_info.argtypes = [vp, ip, ip, ip, ll, ll]
     L.smg_batched_set_profile.argtypes = [vp, i]
     L.smg_batched_profile_read.argtypes = [vp, i, ll, dp, dp]
@@ -260,6 +261,15 @@ def smg_batched_solve(h, variant, b_list, x_list, tol=1e-8, maxit=100, stream=No
     if check:
         _check(rc, allow=(SMG_ERR_NOCONV,))
     return rc, it, rel
+
+
+def smg_batched_apply(h, r_list, s_list, stream=None) -> None:
+    """One persistent V-cycle launch: s_list[i] = T_i r_list[i] (per-system device tensors)."""
+    nsys = len(r_list)
+    rp = (ctypes.c_void_p * nsys)(*[_ptr(t) for t in r_list])
+    sp = (ctypes.c_void_p * nsys)(*[_ptr(t) for t in s_list])
+    _check(_lib.smg_batched_apply(ctypes.c_void_p(h), ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(sp, ctypes.c_void_p),
+                                  _stream(stream)))
 
 
 def smg_batched_destroy(h) -> None:

@@ -10,6 +10,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 from paper_1212_6680_gb300 import inputs  # noqa: E402
+from tests.parity import assert_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +41,7 @@ def test_batched_uneven_systems_reach_tolerance(smg, orc, nsys, lo, hi):
         true = np.linalg.norm(b - orc.apply_A(xh)) / np.linalg.norm(b)
         assert true <= 1e-8, (s, true)
         ref = orc.krylov(b, "fpcg", orc.SMG(int(nx), int(ny), int(nz), 1, 0), tol=1e-8, maxit=100)
-        assert iters[s] <= ref["iters"] + 2, (s, iters[s], ref["iters"])
+        assert abs(int(iters[s]) - ref["iters"]) <= 1, (s, iters[s], ref["iters"])
 
 
 def test_batched_matches_single_system_path(smg):
@@ -86,7 +87,7 @@ def _systems(dims, seed0):
 @pytest.mark.parametrize("variant", ["pcg", "fpcg", "psd"])
 def test_batched_handle_variants_match_oracle_counts(smg, orc, variant):
     """Each Krylov variant of Algorithm 1 through one handle: true residual <= tol and the
-    oracle's FP64 iteration count within 2.  PCG eq. (1) uses the balanced (1,1) cycle, for which
+    oracle's FP64 iteration count within 1.  PCG eq. (1) uses the balanced (1,1) cycle, for which
     the paper shows it converges; PSD and FPCG use (1,0)."""
     npost = 1 if variant == "pcg" else 0
     dims = inputs.uneven_dims(6, 10, 36, seed=4000)
@@ -101,7 +102,7 @@ def test_batched_handle_variants_match_oracle_counts(smg, orc, variant):
             true = np.linalg.norm(bh[s] - orc.apply_A(xh)) / np.linalg.norm(bh[s])
             assert true <= 1e-8 and abs(true - rel[s]) <= 1e-3 * true + 1e-15, (s, true, rel[s])
             ref = orc.krylov(bh[s], variant, orc.SMG(int(nx), int(ny), int(nz), 1, npost), tol=1e-8, maxit=100)
-            assert abs(int(iters[s]) - ref["iters"]) <= 2, (s, iters[s], ref["iters"])
+            assert abs(int(iters[s]) - ref["iters"]) <= 1, (s, iters[s], ref["iters"])
     finally:
         smg.smg_batched_destroy(h)
 
@@ -137,3 +138,26 @@ def test_batched_handle_reuse_is_deterministic_and_profiles(smg):
         assert rc == smg.SMG_OK and (iters == 0).all() and (rel <= 1e-8).all()
     finally:
         smg.smg_batched_destroy(h)
+
+
+@pytest.mark.parametrize("npost", [0, 1])
+def test_batched_apply_matches_oracle_cycle(smg, orc, npost):
+    """One launch of the persistent V-cycle (smg_batched_apply) on seeded right-hand sides of
+    uneven systems against the oracle's cycle of each system, element by element and plane by
+    plane at the FP32 cycle's tolerance; two applications give identical results (section 3: the
+    preconditioner is fixed and linear)."""
+    dims = inputs.uneven_dims(10, 8, 70, seed=4200 + npost)
+    rh = [inputs.rhs(int(nx), int(ny), int(nz), seed=4300 + s) for s, (nx, ny, nz) in enumerate(dims)]
+    r = [torch.from_numpy(v.ravel().copy()).cuda() for v in rh]
+    h = smg.smg_batched_setup(dims, npre=1, npost=npost)
+    try:
+        out = [torch.empty_like(v) for v in r]
+        smg.smg_batched_apply(h, r, out)
+        first = [o.clone() for o in out]
+        smg.smg_batched_apply(h, r, out)
+    finally:
+        smg.smg_batched_destroy(h)
+    for s, (nx, ny, nz) in enumerate(dims):
+        assert torch.equal(first[s], out[s])
+        ref = orc.SMG(int(nx), int(ny), int(nz), 1, npost).apply(rh[s])
+        assert_close(out[s].cpu().numpy(), ref, 2e-5, (int(nx), int(ny), int(nz)), f"system {s} {tuple(dims[s])}")

@@ -38,4 +38,7 @@ def test_lobpcg_matches_oracle(smg, orc, shape, m, npost, prec):
     assert rc == smg.SMG_OK, smg.smg_last_error()
     assert np.all(np.abs(lam - ref["lam"]) <= 1e-10 * ref["lam"]), (lam, ref["lam"])
     assert np.abs(Xh @ Xh.T - np.eye(m)).max() <= 1e-10
-    assert it <= ref["iters"] + 5, (it, ref["iters"])
+    # the same seeded block and the same algorithm: the FP64 cycle follows the oracle to the
+    # iteration; the FP32 cycle may take one more or fewer (its preconditioned residuals differ by
+    # FP32 rounding, which moves the soft-locking decisions by an iteration at most)
+    assert abs(it - ref["iters"]) <= 1, (it, ref["iters"])

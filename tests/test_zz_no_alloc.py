@@ -1,5 +1,6 @@
-"""smg_apply_A_dot_static: the allocation-free operator + inner product, checked against the
-regular entry point smg_apply_A on the same inputs, on two calls in a row.
+"""smg_apply_A_dot_static: the allocation-free operator + inner product, checked on two calls in
+a row against the oracle's operator (oracle.apply_A, element by element) and an FP64 NumPy inner
+product, and against the library's regular entry point smg_apply_A on the same inputs.
 
 It serves callers that cannot allocate device memory where they need the product (a host
 framework that owns all device allocations, or a section where cudaMalloc must not run).  The
@@ -13,6 +14,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 from paper_1212_6680_gb300 import inputs  # noqa: E402
+from tests.parity import assert_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -27,21 +29,24 @@ def smg():
 
 
 @pytest.mark.parametrize("shape", [(37, 21, 13), (128, 128, 128), (1, 1, 5)])
-def test_static_scratch_entry_point_matches_apply_A(smg, shape):
+def test_static_scratch_entry_point_matches_oracle_and_apply_A(smg, orc, shape):
     nx, ny, nz = shape
     with smg.Handle(nx, ny, nz) as h:
         for seed in (31, 32):  # two calls in a row share (and must reset) the static scratch
-            u = torch.from_numpy(inputs.rhs(nx, ny, nz, seed=seed).ravel().copy()).cuda()
+            uh = inputs.rhs(nx, ny, nz, seed=seed)
+            u = torch.from_numpy(uh.ravel().copy()).cuda()
             ref = torch.empty_like(u)
             smg.smg_apply_A(h.h, u, ref)
             out = torch.full_like(u, float("nan"))
             dot = torch.zeros(1, dtype=torch.float64, device="cuda")
             smg.smg_apply_A_dot_static(nx, ny, nz, u, out, dot)
             torch.cuda.synchronize()
-            # same FP64 stencil on both sides: relative 1e-15 (the tests' FP64 operator tolerance)
-            err = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
-            assert err <= 1e-15, err
-            d_ref = float(torch.dot(u, ref))
+            got = out.cpu().numpy()
+            Au = orc.apply_A(uh).ravel()
+            # FP64 stencil on both sides, summation order aside: 1e-15 norm- and element-wise
+            assert_close(got, Au, 1e-15, None, "A u vs the oracle")
+            assert_close(got, ref.cpu().numpy(), 1e-15, None, "vs smg_apply_A")
+            d_ref = float(np.dot(uh.ravel(), Au))
             assert abs(float(dot[0]) - d_ref) <= 1e-12 * abs(d_ref)
 
 
