@@ -306,6 +306,21 @@ int smg_check_conversions(long long n, const double *src, int *mismatches, void 
 int smg_launch_count(smg_handle h, long long *count);
 
 /*
+ * smg_gram -- G = U^T V for tall-skinny blocks in FP64 accuracy on the tensor cores: the dense
+ * inner products of block LOBPCG (section 4, "Preconditioning of LOBPCG with SMG": the
+ * Rayleigh-Ritz matrices S^T A S, S^T S and the orthogonalisation products).  Each entry is split
+ * into seven 7-bit integer digits relative to a power of two per column; digit products run as
+ * BF16 tcgen05 MMAs whose FP32 sums over 64 rows are exact, and are combined in 64-bit integers
+ * and FP64.  The error is about 1e-15 of ||u_i|| ||v_j||.
+ *   n:      rows (>= 1).
+ *   U, V:   device, column-major n x k1 and n x k2 (column j at U + j n), 1 <= k1, k2 <= 64.
+ *   G:      device, k1 x k2 doubles, row-major (G[i k2 + j] = u_i . v_j).  Caller-owned.
+ * Allocates and frees its workspace (about 64 KB per 2048 rows) and synchronises `stream`;
+ * returns SMG_ERR_TIMEOUT when a bounded wait for the tensor cores gave up.
+ */
+int smg_gram(long long n, int k1, const double *U, int k2, const double *V, double *G, void *stream);
+
+/*
  * smg_apply_A_dot_static -- out = A u and *dot = (u, A u), allocating nothing.
  * The paper has no counterpart: this is the 7-point operator with its fused inner product
  * (u, A u), in a form for callers that cannot allocate device memory where they need it

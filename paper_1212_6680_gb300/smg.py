@@ -34,7 +34,7 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "smg_batched_destroy", "smg_batched_apply", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
            "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs",
-           "smg_plane_layout")
+           "smg_plane_layout", "smg_gram")
 NET_WEIGHTS = 7776
 
 
@@ -83,6 +83,7 @@ def _load():
     L.smg_net_train.argtypes = [i, vp, vp, vp, i, d, ctypes.c_ulonglong, i, vp, vp, vp]
     L.smg_net_set_tensor_cores.argtypes = [i]
     L.smg_net_tc_status.argtypes = [ip]
+    L.smg_gram.argtypes = [ctypes.c_longlong, i, vp, i, vp, vp, vp]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -379,6 +380,11 @@ def smg_barrier_selftest(extra_blocks: int, limit_seconds: float = 0.5, stream=N
     st = ctypes.c_int(-99)
     _check(_lib.smg_barrier_selftest(extra_blocks, limit_seconds, ctypes.byref(st), _stream(stream)))
     return st.value
+
+
+def smg_gram(n: int, k1: int, U, k2: int, V, G, stream=None) -> None:
+    """G (device, k1 x k2 row-major) = U^T V with U, V column-major device blocks (n rows)."""
+    _check(_lib.smg_gram(n, k1, _ptr(U), k2, _ptr(V), _ptr(G), _stream(stream)))
 
 
 def smg_destroy(h: int) -> None:
