@@ -63,10 +63,14 @@ enum {
     SMG_OPT_PRECOND = 5,      /* the preconditioner krylov_solve applies: 1 (default) the SMG cycle,
                                  0 none (T = I: plain CG by eq. (1) or (2), steepest descent for PSD;
                                  section 2, figures 1-2); lobpcg_solve always uses the cycle */
-    SMG_OPT_LEAN = 6          /* 1 (default): FP32-compute plane relaxations on one CTA per plane
+    SMG_OPT_LEAN = 6,         /* 1 (default): FP32-compute plane relaxations on one CTA per plane
                                  with nx <= 128 run the 2D cycle with fewer barrier-separated
                                  steps (the restriction fused with the next level's even lines;
                                  the same line solves in the same order); 0: the general kernel */
+    SMG_OPT_GRAM_TC = 7       /* lobpcg_solve's Gram products with both block widths >= value (and
+                                 <= 64) run on the tensor cores (smg_gram's digit splitting); the
+                                 others, and all of them with value 0, on the CUDA cores in
+                                 double-float arithmetic (default 16) */
 };
 
 /*

@@ -561,6 +561,10 @@ int smg_set_option(smg_handle h, int option, int value) {
             return fail(SMG_ERR_ARG, "cluster_max32 must be 0 (automatic), 1, 2, 4, 8 or 16");
         h->cluster_max32 = value;
         return SMG_OK;
+    case SMG_OPT_GRAM_TC:
+        if (value < 0 || value > 64) return fail(SMG_ERR_ARG, "gram_tc must be in [0, 64]");
+        h->lw.gram_tc_min = value;
+        return SMG_OK;
     case SMG_OPT_LEAN:
         if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "lean must be 0 or 1");
         h->lean = value;

@@ -51,6 +51,14 @@ constexpr long long kGtWaitLimit = 1ll << 26;  // mbarrier polls before giving u
 
 __device__ int g_gram_tc_err = 0;
 
+// Phase-timing hook for latency studies: compiled out unless SMG_GRAM_TRACE names a device
+// function `void f(int phase)`.
+#ifdef SMG_GRAM_TRACE
+#define GT_TRACE(k) SMG_GRAM_TRACE(k)
+#else
+#define GT_TRACE(k) ((void)0)
+#endif
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -80,29 +88,58 @@ __device__ __forceinline__ bool gt_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// The seven digits of x relative to 2^E (E from the column's largest magnitude), as BF16 bit
-// patterns (exact: integers below 128), sign applied.  Integer operations only.
-__device__ __forceinline__ void gt_digits(double x, int E, uint32_t (&d)[7]) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const uint32_t sign = static_cast<uint32_t>(b >> 48) & 0x8000u;
-    const int ex = static_cast<int>((b >> 52) & 0x7ffu);
-    unsigned long long M = 0;
-    if (ex != 0) {
-        const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
-        // |x| 2^(49 - E) = m 2^(ex - 1075 + 49 - E) = m >> sh, sh >= 4; rounded to nearest
-        const int sh = 1026 + E - ex;
-        if (sh < 60) {
-            M = (m + (1ull << (sh - 1))) >> sh;
-            if (M >= (1ull << 49)) M = (1ull << 49) - 1;
+// The fixed-point magnitude M = round(|x| 2^(49 - E)) < 2^49 of x relative to 2^E (E from the
+// column's largest magnitude) as two 32-bit words (hi has 17 bits), and x's sign bit.  Integer
+// operations only.
+__device__ __forceinline__ void gt_fixed(double x, int E, uint32_t &hi, uint32_t &lo, uint32_t &sgn) {
+    const uint32_t bh = static_cast<uint32_t>(__double2hiint(x)), bl = static_cast<uint32_t>(__double2loint(x));
+    sgn = bh & 0x80000000u;
+    const int ex = static_cast<int>((bh >> 20) & 0x7ffu);
+    hi = 0u;
+    lo = 0u;
+    // |x| 2^(49 - E) = m 2^-sh with the 53-bit significand m and sh = 1026 + E - ex >= 4
+    const int sh = 1026 + E - ex;
+    if (ex != 0 && sh < 54) {
+        uint32_t mh = (bh & 0xfffffu) | 0x100000u, ml = bl;
+        if (sh <= 32) {  // round to nearest: add 2^(sh-1), then shift
+            const uint32_t t = ml + (1u << (sh - 1));
+            mh += (t < ml) ? 1u : 0u;
+            ml = t;
+        } else {
+            mh += 1u << (sh - 33);
+        }
+        if (sh < 32) {
+            lo = __funnelshift_r(ml, mh, sh);
+            hi = mh >> sh;
+        } else {
+            lo = mh >> (sh - 32);
+        }
+        if (hi >= (1u << 17)) {  // rounded up to 2^49: keep the largest 49-bit value
+            hi = (1u << 17) - 1u;
+            lo = 0xffffffffu;
         }
     }
-#pragma unroll
-    for (int s = 0; s < 7; ++s) {
-        const uint32_t v = static_cast<uint32_t>(M >> (42 - 7 * s)) & 127u;
-        // v as a float via 2^23 + v - 2^23; its upper 16 bits are the BF16 pattern (v < 256)
-        const float f = __uint_as_float(0x4B000000u | v) - 8388608.0f;
-        d[s] = (__float_as_uint(f) >> 16) | (v ? sign : 0u);
-    }
+}
+
+// Digit s (7 bits, s = 0 most significant) of M = hi:lo.
+template <int S>
+__device__ __forceinline__ uint32_t gt_digit(uint32_t hi, uint32_t lo) {
+    if constexpr (S == 0) return hi >> 10;
+    else if constexpr (S == 1) return (hi >> 3) & 127u;
+    else if constexpr (S == 2) return __funnelshift_r(lo, hi, 28) & 127u;
+    else return (lo >> (42 - 7 * S)) & 127u;
+}
+
+// The seven digits of two entries (rows r, r+1 of one column) as BF16 pairs: word s holds digit
+// s of the first entry in its low half and of the second in its high half.  A digit v < 128 is
+// made a BF16 value by writing it into the significand of 128 (bits 0x4300 | v = 128 + v
+// exactly) and subtracting 128 in BF16 arithmetic (exact), then the entry's sign is applied.
+template <int S>
+__device__ __forceinline__ uint32_t gt_pair(uint32_t h0, uint32_t l0, uint32_t h1, uint32_t l1, uint32_t sg) {
+    const uint32_t w = 0x43004300u | gt_digit<S>(h0, l0) | (gt_digit<S>(h1, l1) << 16);
+    const __nv_bfloat162 v = __hsub2(*reinterpret_cast<const __nv_bfloat162 *>(&w),
+                                     __halves2bfloat162(__ushort_as_bfloat16(0x4300u), __ushort_as_bfloat16(0x4300u)));
+    return *reinterpret_cast<const uint32_t *>(&v) ^ sg;
 }
 
 // Pre-pass: the largest |x| of every column of U (bit patterns of non-negative doubles order
@@ -112,8 +149,18 @@ __global__ void gram_colmax_kernel(long long n, int k, const double *__restrict_
     const int j = blockIdx.y;
     const double *col = U + static_cast<long long>(j) * ld;
     unsigned long long m = 0;
-    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    // four independent loads in flight per thread
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        unsigned long long b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            b[u] = static_cast<unsigned long long>(__double_as_longlong(col[i + u * stride])) & 0x7fffffffffffffffull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m = b[u] > m ? b[u] : m;
+    }
+    for (; i < n; i += stride) {
         const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(col[i])) & 0x7fffffffffffffffull;
         m = b > m ? b : m;
     }
@@ -130,20 +177,72 @@ __device__ __forceinline__ int gt_exp(unsigned long long mx) {
     return static_cast<int>((mx >> 52) & 0x7ffu) - 1023 + 1;
 }
 
+// Drain: fold the exact regions (weights 0..4) of this thread's accumulator share into acc.
+template <int CPW>
+__device__ __forceinline__ void gt_drain(uint32_t tmem, int q, int cb, int NP, long long (&acc)[CPW]) {
+#pragma unroll
+    for (int c = 0; c < GT_EXACT; ++c) {
+        uint32_t r[CPW];
+        const uint32_t ta = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c * NP + cb * CPW);
+        if constexpr (CPW == 4) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(ta));
+        } else if constexpr (CPW == 8) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(ta));
+        } else if constexpr (CPW == 12) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(ta));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]) : "r"(ta + 8));
+        } else {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int x = 0; x < CPW; ++x) {
+            // an integer-valued float below 2^22 in magnitude: adding 1.5 2^23 puts it in the low
+            // mantissa bits
+            const int v = static_cast<int>(__float_as_uint(__uint_as_float(r[x]) + 12582912.0f)) - 0x4B400000;
+            acc[x] += static_cast<long long>(v) << (7 * (GT_EXACT - 1 - c));
+        }
+    }
+}
+
+// The digit-split Gram of the CTA's row range.  Items (column j, row pair): 8 columns x 4 row
+// pairs per warp access, so a warp's 4-byte digit stores fill 128 contiguous bytes of a K chunk.
+// A thread owns at most GT_ITEMS items; their rows for the next stage are loaded into registers
+// while the current stage's MMAs run.  With two digit buffers (when they fit in shared memory)
+// the digits of stage st are written while the MMAs of stage st-1 read the other buffer.
+constexpr int GT_ITEMS = 8;     // (64 + 64 columns / 8) x 256 items / 512 threads
+constexpr int GT_PREFETCH = 3;  // stages ahead the rows are prefetched into L2
+
 template <int NP>
 __global__ void __launch_bounds__(GT_THREADS, 1)
     gram_tc_kernel(long long n, int k1, const double *__restrict__ U, long long ldu, int k2,
                    const double *__restrict__ V, long long ldv, const unsigned long long *__restrict__ cmax_u,
-                   const unsigned long long *__restrict__ cmax_v, int stages_per_cta, double *__restrict__ part) {
+                   const unsigned long long *__restrict__ cmax_v, int stages_per_cta, int sym,
+                   double *__restrict__ part) {
     constexpr int UBYTES = 7 * GT_KCH * NP * 16;  // seven digit matrices of U (N side)
+    constexpr int BUFB = GT_VBYTES + UBYTES;       // one digit buffer
+    constexpr int NBUF = (2 * BUFB + 1024 <= 227 * 1024) ? 2 : 1;
     constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(NP) >> 3) << 17) |
                                ((128u >> 4) << 24);
     constexpr int CPW = NP / 4;  // accumulator columns each of the four warps of a lane quarter drains
     static_assert(GT_REGIONS * NP <= 512, "regions exceed the tensor memory");
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *Vs = sm;                 // [p 4][kchunk 8][row 128][8 bf16]
-    unsigned char *Us = sm + GT_VBYTES;     // [s 7][kchunk 8][row NP][8 bf16]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(Us + UBYTES);
+    // buffer b: V digits [p 4][kchunk 8][row 128][8 bf16], then U digits [s 7][kchunk 8][row NP][8 bf16]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + NBUF * BUFB);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     int *s_fail = reinterpret_cast<int *>(tslot + 1);
     int *s_eu = s_fail + 1;                 // [64]
@@ -154,7 +253,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     const long long st0 = static_cast<long long>(blockIdx.x) * stages_per_cta;
     const long long st1 = min(nst, st0 + stages_per_cta);
 
-    for (int i = tid; i < (GT_VBYTES + UBYTES) / 16; i += GT_THREADS)
+    for (int i = tid; i < NBUF * BUFB / 16; i += GT_THREADS)
         reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);  // padding rows stay zero
     if (tid < 64) {
         s_eu[tid] = tid < k1 ? gt_exp(cmax_u[tid]) : 0;
@@ -175,6 +274,113 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
 
+    // this thread's items: column jj (U's columns, then V's) and row pair rp; packed jj | rp << 8
+    // a symmetric product (V = U) slices U's columns once and stores them on both sides
+    const int ncol = sym ? k1 : k1 + k2, ncg = (ncol + 7) / 8;
+    int pk[GT_ITEMS];
+    const double *cp[GT_ITEMS];
+#pragma unroll
+    for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+        const int it = tid + q2 * GT_THREADS;
+        const int jj = (it & 7) + 8 * ((it >> 5) % ncg);
+        const int rp = ((it >> 3) & 3) + 4 * ((it >> 5) / ncg);
+        const bool valid = it < ncg * 256 && jj < ncol && rp < GT_ROWS / 2;
+        pk[q2] = valid ? (jj | (rp << 8)) : -1;
+        const int j = jj < k1 ? jj : jj - k1;
+        cp[q2] = valid ? (jj < k1 ? U + static_cast<long long>(j) * ldu : V + static_cast<long long>(j) * ldv) + 2 * rp
+                       : nullptr;
+    }
+    double xa[GT_ITEMS], xb[GT_ITEMS];
+    auto load_stage = [&](long long st) {
+        const long long r0 = st * GT_ROWS;
+#pragma unroll
+        for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+            xa[q2] = 0.0;
+            xb[q2] = 0.0;
+            if (pk[q2] >= 0 && st < st1) {
+                // two scalar loads: a column of an odd-length block is only 8-byte aligned
+                const long long i0 = r0 + 2 * (pk[q2] >> 8);
+                if (i0 < n) xa[q2] = cp[q2][r0];
+                if (i0 + 1 < n) xb[q2] = cp[q2][r0 + 1];
+            }
+        }
+    };
+    auto prefetch_stage = [&](long long st) {
+        if (st >= st1) return;
+        const long long r0 = st * GT_ROWS;
+#pragma unroll
+        for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+            // one prefetch per 32-byte sector: the even lanes of a row-pair group
+            if (pk[q2] >= 0 && ((pk[q2] >> 8) & 1) == 0 && r0 + 2 * (pk[q2] >> 8) < n)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(cp[q2] + r0));
+        }
+    };
+    auto slice_stage = [&](int b) {
+        unsigned char *Vs = sm + b * BUFB, *Us = Vs + GT_VBYTES;
+#pragma unroll
+        for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+            if (pk[q2] < 0) continue;
+            const int jj = pk[q2] & 0xff, rp = pk[q2] >> 8;
+            const bool isu = jj < k1;
+            const int j = isu ? jj : jj - k1;
+            const int E = isu ? s_eu[j] : s_ev[j];
+            uint32_t h0, l0, s0, h1, l1, s1;
+            gt_fixed(xa[q2], E, h0, l0, s0);
+            gt_fixed(xb[q2], E, h1, l1, s1);
+            const uint32_t sg = (s0 >> 16) | s1;
+            uint32_t w[7];
+            w[0] = gt_pair<0>(h0, l0, h1, l1, sg);
+            w[1] = gt_pair<1>(h0, l0, h1, l1, sg);
+            w[2] = gt_pair<2>(h0, l0, h1, l1, sg);
+            w[3] = gt_pair<3>(h0, l0, h1, l1, sg);
+            w[4] = gt_pair<4>(h0, l0, h1, l1, sg);
+            w[5] = gt_pair<5>(h0, l0, h1, l1, sg);
+            w[6] = gt_pair<6>(h0, l0, h1, l1, sg);
+            const int kc = (2 * rp) >> 3, ko = (2 * rp) & 7;
+            if (isu) {
+                unsigned char *base = Us + (kc * NP + j) * 16 + ko * 2;
+#pragma unroll
+                for (int s = 0; s < 7; ++s) *reinterpret_cast<uint32_t *>(base + s * GT_KCH * NP * 16) = w[s];
+            }
+            if (!isu || sym) {
+                unsigned char *base = Vs + (kc * 128 + j) * 16 + ko * 2;
+#pragma unroll
+                for (int s = 0; s < 7; ++s)
+                    *reinterpret_cast<uint32_t *>(base + ((s >> 1) * GT_KCH * 128 + (s & 1) * 64) * 16) = w[s];
+            }
+        }
+    };
+    auto issue_mmas = [&](int b, bool first) {
+        // 19 MMAs per 16-row K-step; exact regions restart every stage, the others accumulate
+        // over the CTA's range (reset only in its first stage)
+        const uint32_t vb = smem_u32(sm + b * BUFB), ub = vb + GT_VBYTES;
+        uint32_t touched = 0;
+        for (int p = 0; p < 4; ++p) {
+            const int smax = min(6, 7 - 2 * p);
+            const uint64_t a0 = gt_desc(vb + static_cast<uint32_t>(p * GT_KCH * 128 * 16), 128 * 16, 128);
+            for (int s = 0; s <= smax; ++s) {
+                const int c = s + 2 * p;
+                const bool fresh = !((touched >> c) & 1u) && (c < GT_EXACT || first);
+                const uint64_t b0 = gt_desc(ub + static_cast<uint32_t>(s * GT_KCH * NP * 16), NP * 16, 128);
+#pragma unroll
+                for (int kk = 0; kk < GT_KCH / 2; ++kk) {
+                    // K-step kk: K chunks 2kk, 2kk+1 (start address + 2kk chunk strides, >> 4)
+                    const uint64_t ad = a0 + static_cast<uint64_t>(kk * 2 * 128);
+                    const uint64_t bd = b0 + static_cast<uint64_t>(kk * 2 * NP);
+                    const uint32_t accf = (fresh && kk == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + c * NP),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(accf));
+                }
+                touched |= 1u << c;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(mbar))
+                     : "memory");
+    };
+
     // this thread's share of the accumulators: lane quarter q (TMEM lanes 32q..), columns
     // [cb CPW, (cb + 1) CPW) of every region
     const int q = warp & 3, cb = warp >> 2;
@@ -183,115 +389,40 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     for (int c = 0; c < CPW; ++c) acc[c] = 0;
     bool ok = true;
     uint32_t phase = 0;
-    for (long long st = st0; st < st1; ++st) {
-        const long long r0 = st * GT_ROWS;
-        // ---- digits of this stage's 64 rows into shared memory ----
-        // an item is (column j, row pair rp): 8 columns x 4 row pairs per warp access, so a warp's
-        // 4-byte stores fill 128 contiguous bytes of a K chunk
-        const int ncol = k1 + k2, ncg = (ncol + 7) / 8;
-        for (int it = tid; it < ncg * 256; it += GT_THREADS) {
-            const int jj = (it & 7) + 8 * ((it >> 5) % ncg);
-            const int rp = ((it >> 3) & 3) + 4 * ((it >> 5) / ncg);
-            if (jj >= ncol || rp >= GT_ROWS / 2) continue;
-            const bool isu = jj < k1;
-            const int j = isu ? jj : jj - k1;
-            const double *col = isu ? U + static_cast<long long>(j) * ldu : V + static_cast<long long>(j) * ldv;
-            const long long i0 = r0 + 2 * rp;
-            const double x0 = i0 < n ? col[i0] : 0.0, x1 = i0 + 1 < n ? col[i0 + 1] : 0.0;
-            uint32_t d0[7], d1[7];
-            const int E = isu ? s_eu[j] : s_ev[j];
-            gt_digits(x0, E, d0);
-            gt_digits(x1, E, d1);
-            const int kc = (2 * rp) >> 3, ko = (2 * rp) & 7;
-#pragma unroll
-            for (int s = 0; s < 7; ++s) {
-                const uint32_t w = d0[s] | (d1[s] << 16);
-                if (isu) {
-                    *reinterpret_cast<uint32_t *>(Us + ((s * GT_KCH + kc) * NP + j) * 16 + ko * 2) = w;
-                } else {
-                    const int p = s >> 1, row = (s & 1) * 64 + j;
-                    *reinterpret_cast<uint32_t *>(Vs + ((p * GT_KCH + kc) * 128 + row) * 16 + ko * 2) = w;
-                }
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // ---- the stage's MMAs, issued by one thread ----
-        if (tid == 0) {
-            uint32_t touched = 0;  // regions written since they were last reset
-            const uint32_t vb = smem_u32(Vs), ub = smem_u32(Us);
-            for (int p = 0; p < 4; ++p) {
-                const int smax = min(6, 7 - 2 * p);
-                for (int s = 0; s <= smax; ++s) {
-                    const int c = s + 2 * p;
-                    // exact regions restart every stage; the others accumulate over the CTA
-                    const bool fresh = c < GT_EXACT ? !((touched >> c) & 1u) : (st == st0 && !((touched >> c) & 1u));
-#pragma unroll
-                    for (int kk = 0; kk < GT_KCH / 2; ++kk) {
-                        const uint64_t ad = gt_desc(vb + static_cast<uint32_t>((p * GT_KCH + 2 * kk) * 128 * 16), 128 * 16, 128);
-                        const uint64_t bd = gt_desc(ub + static_cast<uint32_t>((s * GT_KCH + 2 * kk) * NP * 16), NP * 16, 128);
-                        const uint32_t accf = (fresh && kk == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + c * NP),
-                            "l"(ad), "l"(bd), "r"(IDESC), "r"(accf));
-                    }
-                    touched |= 1u << c;
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(mbar))
-                         : "memory");
-        }
-        // ---- wait (one thread, bounded), then fold the exact regions into the 64-bit accumulators ----
+    // wait (one thread, bounded) for the last committed MMAs, then drain them
+    auto wait_drain = [&]() -> bool {
         if (tid == 0 && !gt_wait(smem_u32(mbar), phase)) *s_fail = 1;
         phase ^= 1u;
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (*s_fail) {
+        if (*s_fail) return false;
+        GT_TRACE(2);
+        gt_drain<CPW>(tmem, q, cb, NP, acc);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // the exact regions and a digit buffer are reused next
+        GT_TRACE(3);
+        return true;
+    };
+    for (int d = 1; d < GT_PREFETCH; ++d) prefetch_stage(st0 + d);
+    if (st0 < st1) load_stage(st0);
+    for (long long st = st0; st < st1 && ok; ++st) {
+        GT_TRACE(0);
+        const int b = NBUF == 2 ? static_cast<int>((st - st0) & 1) : 0;
+        slice_stage(b);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        GT_TRACE(1);
+        // two buffers: the previous stage's MMAs (reading the other buffer) ran during the slicing
+        if (NBUF == 2 && st > st0 && !wait_drain()) {
             ok = false;
             break;
         }
-#pragma unroll
-        for (int c = 0; c < GT_EXACT; ++c) {
-            uint32_t r[CPW];
-            const uint32_t ta = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c * NP + cb * CPW);
-            if constexpr (CPW == 4) {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(ta));
-            } else if constexpr (CPW == 8) {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7])
-                             : "r"(ta));
-            } else if constexpr (CPW == 12) {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7])
-                             : "r"(ta));
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                             : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]) : "r"(ta + 8));
-            } else {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15}, [%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(ta));
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int x = 0; x < CPW; ++x) {
-                // an integer-valued float below 2^22 in magnitude: adding 1.5 2^23 puts it in the
-                // low mantissa bits
-                const int v = static_cast<int>(__float_as_uint(__uint_as_float(r[x]) + 12582912.0f)) - 0x4B400000;
-                acc[x] += static_cast<long long>(v) << (7 * (GT_EXACT - 1 - c));
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // the digits and the exact regions are reused by the next stage
+        if (tid == 0) issue_mmas(b, st == st0);
+        load_stage(st + 1);  // in flight while the MMAs run
+        prefetch_stage(st + GT_PREFETCH);  // into L2, so that the register loads find it there
+        if (NBUF == 1 && !wait_drain()) ok = false;
     }
+    if (ok && NBUF == 2 && st0 < st1 && !wait_drain()) ok = false;
     if (!ok && lane == 0) atomicExch(&g_gram_tc_err, 1);
     // ---- this CTA's partial: exact part + the FP32 regions of weight >= 5 ----
     // lane quarter q: V column jv = 32 (q & 1) + lane, digit-pair weight offset h = q >> 1
@@ -367,10 +498,11 @@ cudaError_t gram_tc(long long n, int k1, const double *U, long long ldu, int k2,
     cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * 128, st);
     if (e != cudaSuccess) return e;
     {
-        const int bx = static_cast<int>(std::min<long long>((n + 255) / 256, std::max(1, 4 * num_sms / std::max(1, k1))));
+        // about 16 CTAs per SM over all columns
+        const int bx = static_cast<int>(std::min<long long>((n + 255) / 256, std::max(1, 16 * num_sms / std::max(1, k1))));
         gram_colmax_kernel<<<dim3(std::max(1, bx), k1), 256, 0, st>>>(n, k1, U, ldu, cmax);
         if (V != U || ldv != ldu || k2 != k1) {
-            const int by = static_cast<int>(std::min<long long>((n + 255) / 256, std::max(1, 4 * num_sms / std::max(1, k2))));
+            const int by = static_cast<int>(std::min<long long>((n + 255) / 256, std::max(1, 16 * num_sms / std::max(1, k2))));
             gram_colmax_kernel<<<dim3(std::max(1, by), k2), 256, 0, st>>>(n, k2, V, ldv, cmax + 64);
         } else {
             e = cudaMemcpyAsync(cmax + 64, cmax, sizeof(unsigned long long) * 64, cudaMemcpyDeviceToDevice, st);
@@ -383,27 +515,29 @@ cudaError_t gram_tc(long long n, int k1, const double *U, long long ldu, int k2,
     per = std::min<long long>(per, GT_MAX_STAGES);
     const int ctas = static_cast<int>((nst + per - 1) / per);
     const int NP = ((k1 + 15) / 16) * 16;
-    const size_t smem = GT_VBYTES + 7 * GT_KCH * NP * 16 + 64 + 2 * 64 * sizeof(int);
+    const int sym = (V == U && ldv == ldu && k2 == k1) ? 1 : 0;
+    const size_t bufb = GT_VBYTES + 7 * GT_KCH * NP * 16;
+    const size_t smem = ((2 * bufb + 1024 <= 227 * 1024) ? 2 : 1) * bufb + 64 + 2 * 64 * sizeof(int);
     switch (NP) {
     case 16:
         e = cudaFuncSetAttribute(gram_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e == cudaSuccess)
-            gram_tc_kernel<16><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), part);
+            gram_tc_kernel<16><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), sym, part);
         break;
     case 32:
         e = cudaFuncSetAttribute(gram_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e == cudaSuccess)
-            gram_tc_kernel<32><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), part);
+            gram_tc_kernel<32><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), sym, part);
         break;
     case 48:
         e = cudaFuncSetAttribute(gram_tc_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e == cudaSuccess)
-            gram_tc_kernel<48><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), part);
+            gram_tc_kernel<48><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), sym, part);
         break;
     default:
         e = cudaFuncSetAttribute(gram_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e == cudaSuccess)
-            gram_tc_kernel<64><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), part);
+            gram_tc_kernel<64><<<ctas, GT_THREADS, smem, st>>>(n, k1, U, ldu, k2, V, ldv, cmax, cmax + 64, static_cast<int>(per), sym, part);
         break;
     }
     if (e != cudaSuccess) return e;

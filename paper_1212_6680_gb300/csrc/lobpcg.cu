@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/smg.h"
+#include "gram_tc.h"
 #include "lobpcg.h"
 #include "plane_relax.cuh"  // widen_f32 / narrow_f64 (integer-pipe conversions)
 
@@ -500,6 +501,21 @@ struct Ctx {
 // e.g. V = U or V = A U), so only its upper tiles are computed
 int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G, bool sym = false) {
     const int nti = cdiv(k1, kGT), ntj = cdiv(k2, kGT);
+    if (c.w.gram_tc_min > 0 && k1 >= c.w.gram_tc_min && k2 >= c.w.gram_tc_min && k1 <= 64 && k2 <= 64) {
+        // FP64-accurate digit-split products on the tensor cores
+        LCHK(gram_tc(c.n, k1, U, c.n, k2, V, c.n, c.w.gram, c.w.tc_work, c.w.num_sms, c.st));
+        G.resize(static_cast<size_t>(k1) * k2);
+        LCHK(cudaMemcpyAsync(c.w.h_buf, c.w.gram, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c.st));
+        LCHK(cudaStreamSynchronize(c.st));
+        int err = 0;
+        LCHK(gram_tc_status(&err));
+        if (err != 0) {
+            c.msg = "lobpcg: a tensor-core Gram product's wait timed out";
+            return SMG_ERR_TIMEOUT;
+        }
+        std::memcpy(G.data(), c.w.h_buf, sizeof(double) * G.size());
+        return SMG_OK;
+    }
     if (k1 <= kSmallK && k2 <= kSmallK) {
         // narrow product: 4 CTAs per SM (as far as the partial buffer holds), rows a multiple of 256
         const long long want = std::max<long long>(1, std::min<long long>(4LL * c.w.num_sms, c.w.part_tiles));
@@ -629,8 +645,11 @@ void lobpcg_free(LobpcgWork &w) {
     cudaFree(w.part);
     cudaFree(w.gram);
     cudaFree(w.coef);
+    cudaFree(w.tc_work);
     if (w.h_buf) cudaFreeHost(w.h_buf);
+    const int tc_min = w.gram_tc_min;
     w = LobpcgWork();
+    w.gram_tc_min = tc_min;
 }
 
 int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double *lambda, double tol, int maxit,
@@ -655,6 +674,7 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         LCHK(cudaMalloc(&w.gram, sizeof(double) * k * k));
         LCHK(cudaMalloc(&w.coef, sizeof(double) * k * k));
         LCHK(cudaMallocHost(&w.h_buf, sizeof(double) * k * k));
+        LCHK(cudaMalloc(&w.tc_work, gram_tc_workspace_bytes(n)));
     }
     const size_t col = sizeof(double) * static_cast<size_t>(n);
     double *X = w.S, *AX = w.AS;

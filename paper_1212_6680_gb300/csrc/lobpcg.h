@@ -29,6 +29,9 @@ struct LobpcgWork {
     double *gram = nullptr;               // reduced Gram matrices
     double *coef = nullptr;               // small coefficient matrices (k x k)
     double *h_buf = nullptr;              // pinned host buffer
+    void *tc_work = nullptr;              // workspace of the tensor-core Gram products
+    int gram_tc_min = 16;                 // products with k1, k2 >= this (and <= 64) run on the
+                                          // tensor cores (gram_tc.cu); 0 = never
 };
 
 int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *X, double *lambda, double tol, int maxit,
