@@ -306,6 +306,15 @@ int smg_profile_read(smg_handle h, int which, long long *launches, double *ms, d
  */
 int smg_check_conversions(long long n, const double *src, int *mismatches, void *stream);
 
+/*
+ * smg_krylov_history -- the relative recurrence residuals ||r_k||_2 / ||b||_2, k = 0 .. iters, of
+ * the handle's last krylov_solve (the quantity figures 2 and 5 of section 3 plot, in the 2-norm):
+ * entry k is read at the top of iteration k, before the stopping test (a restart from the true
+ * residual keeps the recurrence value of that step).  Copies min(max, count) values into hist
+ * (host) and sets *count (host) to the number recorded.
+ */
+int smg_krylov_history(smg_handle h, double *hist, int max, int *count);
+
 /* smg_launch_count -- number of CUDA kernel launches this handle has issued so far. */
 int smg_launch_count(smg_handle h, long long *count);
 

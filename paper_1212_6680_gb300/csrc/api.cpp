@@ -93,6 +93,8 @@ struct smg_ctx {
     ProfClass prof[kProfClasses];
     std::vector<PendingEvent> pending;
     std::vector<cudaEvent_t> event_pool;
+    // relative recurrence residuals ||r_k|| / ||b|| of the last krylov_solve, k = 0 .. iters
+    std::vector<double> hist;
     // LOBPCG state
     LobpcgWork lw;
     // learned post-correction (smg_set_learned) and training-pair capture (smg_collect_pairs)
@@ -414,9 +416,11 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
     const double tol2 = tol * tol;
     int k = 0, status = SMG_ERR_NOCONV;
     double tt = -1.0;
+    h->hist.clear();
     for (k = 0;; ++k) {
         if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
         const KrylovScalars &s = *h->h_sc;
+        h->hist.push_back(std::sqrt(s.rr / (s.bb > 0.0 ? s.bb : 1.0)));
         if (s.status != 0) {
             status = s.status;
             break;
@@ -763,6 +767,14 @@ int smg_collect_pairs(smg_handle h, const double *b, const double *xstar, double
     cudaStreamSynchronize(st);
     cudaFree(x);
     return (rc == SMG_ERR_NOCONV) ? SMG_OK : rc;
+}
+
+int smg_krylov_history(smg_handle h, double *hist, int max, int *count) {
+    if (int rc = check_handle(h)) return rc;
+    if (count == nullptr || max < 0 || (max > 0 && hist == nullptr)) return fail(SMG_ERR_ARG, "bad arguments");
+    *count = static_cast<int>(h->hist.size());
+    for (int k = 0; k < max && k < *count; ++k) hist[k] = h->hist[k];
+    return SMG_OK;
 }
 
 int smg_launch_count(smg_handle h, long long *count) {

@@ -35,7 +35,7 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "smg_batched_destroy", "smg_batched_apply", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
            "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs",
-           "smg_plane_layout", "smg_gram")
+           "smg_plane_layout", "smg_gram", "smg_krylov_history")
 NET_WEIGHTS = 7776
 
 
@@ -85,6 +85,7 @@ def _load():
     L.smg_net_set_tensor_cores.argtypes = [i]
     L.smg_net_tc_status.argtypes = [ip]
     L.smg_gram.argtypes = [ctypes.c_longlong, i, vp, i, vp, vp, vp]
+    L.smg_krylov_history.argtypes = [vp, dp, i, ip]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name == "smg_last_error" else ctypes.c_int
     return L
@@ -381,6 +382,17 @@ def smg_barrier_selftest(extra_blocks: int, limit_seconds: float = 0.5, stream=N
     st = ctypes.c_int(-99)
     _check(_lib.smg_barrier_selftest(extra_blocks, limit_seconds, ctypes.byref(st), _stream(stream)))
     return st.value
+
+
+def smg_krylov_history(h: int) -> np.ndarray:
+    """||r_k|| / ||b||, k = 0 .. iters, of the handle's last krylov_solve."""
+    cnt = ctypes.c_int(0)
+    _check(_lib.smg_krylov_history(ctypes.c_void_p(h), None, 0, ctypes.byref(cnt)))
+    out = np.zeros(cnt.value, dtype=np.float64)
+    if cnt.value:
+        _check(_lib.smg_krylov_history(ctypes.c_void_p(h), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       cnt.value, ctypes.byref(cnt)))
+    return out
 
 
 def smg_gram(n: int, k1: int, U, k2: int, V, G, stream=None) -> None:

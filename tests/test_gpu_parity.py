@@ -282,3 +282,26 @@ def test_integer_pipe_conversions_match_hardware(smg):
     mism = torch.zeros(2, dtype=torch.int32, device="cuda")
     smg.smg_check_conversions(src, mism)
     assert mism.cpu().tolist() == [0, 0]
+
+
+@pytest.mark.parametrize("variant,npost", [("fpcg", 0), ("psd", 0), ("pcg", 1), ("pcg", 0)])
+def test_residual_history_matches_oracle(smg, orc, variant, npost):
+    """The per-iteration relative residual ||r_k|| / ||b|| (figures 2 and 5) of the GPU solve with
+    the FP64 cycle against the oracle's history on the same system: same length, and entry by
+    entry within 1e-6 relative (the two sides differ by rounding only); with the nonsymmetric
+    (1,0) cycle PCG by eq. (1) stalls on both sides (figure 5)."""
+    n = 24
+    b = inputs.rhs(n, n, n, seed=0)
+    maxit = 30
+    ref = orc.krylov(b, variant, orc.SMG(n, n, n, 1, npost), tol=1e-8, maxit=maxit)
+    with smg.Handle(n, n, n, 1, npost) as h:
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        rc, it, relres = smg.krylov_solve(h.h, variant, dev(b), x, tol=1e-8, maxit=maxit, check=False)
+        hist = smg.smg_krylov_history(h.h)
+    assert len(hist) == it + 1 == len(ref["hist"]), (len(hist), it, len(ref["hist"]))
+    assert abs(hist[0] - 1.0) <= 1e-14
+    assert np.all(np.abs(hist - ref["hist"]) <= 1e-6 * ref["hist"]), np.max(np.abs(hist - ref["hist"]) / ref["hist"])
+    if variant == "pcg" and npost == 0:
+        assert rc == smg.SMG_ERR_NOCONV and hist[-1] > 1e-8
+    else:
+        assert rc == smg.SMG_OK and hist[-1] <= 1e-8
