@@ -77,8 +77,10 @@ struct smg_ctx {
     bool cl32_ok[5] = {false, false, false, false, false};
     int cluster_max = 16;           // largest cluster for FP64-compute plane relaxations (1 = none)
     int precond = 1;                // krylov_solve's preconditioner: 1 the SMG cycle, 0 none (T = I)
-    int lean = 1;                   // 1: FP32-compute single-CTA levels use the shortened-step plane cycle
+    int lean = 1;                   // 1: the shortened-step plane cycle where it applies
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
+    PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
+    bool lean64_ok[5] = {false, false, false, false, false};
     int cluster_max32 = 0;          // largest cluster for FP32-compute plane relaxations; 0 = chosen
                                     // per size (see relax)
     int num_sms = 0;
@@ -155,7 +157,8 @@ int ensure_levels(smg_ctx *h, int nb) {
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, level precision) failed");
     if (set_plane_relax_smem(h->prec, true, false, K, h->lay_d.smem_bytes) != 0)
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, FP64 coarsest) failed");
-    if (lean_supported(h->prec, K) && set_plane_lean_smem(h->prec, K, h->lay_c.smem_bytes) != 0)
+    if (h->prec != Prec::F64 && lean_supported(K) &&
+        set_plane_lean_smem(h->prec, false, false, K, h->lay_c.smem_bytes) != 0)
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, shortened-step cycle) failed");
     if (h->num_sms == 0) {
         int dev = 0;
@@ -186,6 +189,21 @@ int ensure_levels(smg_ctx *h, int nb) {
         if (cl_smem > 0 && set_plane_relax_smem(h->prec, cf64, true, K, cl_smem) != 0)
             return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, cluster) failed");
     }
+    // FP64-compute shortened-step layouts (every 2D level's factor sets on chip), one CTA or a
+    // cluster per plane
+    for (int lr = 0; lr <= 4; ++lr) {
+        h->lean64_ok[lr] = false;
+        if (!lean_supported(K)) break;
+        const int R = 1 << lr;
+        PlaneLayout &ly = h->lay_lean64[lr];
+        ly = (lr == 0) ? plan_plane_layout(H, 8, kSmemBudget, 0, true) : plan_plane_layout_cluster(H, 8, kSmemBudget, R, true);
+        if (ly.smem_bytes == 0 || ly.smem_bytes > kSmemBudget || ly.MF != H.P) continue;
+        if (set_plane_lean_smem(h->prec, true, lr > 0, K, ly.smem_bytes) != 0) {
+            cudaGetLastError();
+            continue;
+        }
+        h->lean64_ok[lr] = (lr == 0) || lean_cluster_resident(h->prec, K, R, h->threads, ly.smem_bytes);
+    }
     // global slots for the 2D-cycle arrays that are not on chip: one per CTA (at most one per
     // plane of a colour of the finest level) or one per cluster, sized for the largest layout
     size_t per = std::max(static_cast<size_t>(h->lay_c.ws_per_plane) * compute_bytes(h->prec),
@@ -194,6 +212,8 @@ int ensure_levels(smg_ctx *h, int nb) {
         if (h->cl_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_cl[lr].ws_per_plane) * 8);
         if (h->cl32_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_cl32[lr].ws_per_plane) * 4);
     }
+    for (int lr = 0; lr <= 4; ++lr)
+        if (h->lean64_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_lean64[lr].ws_per_plane) * 8);
     const long long slots = static_cast<long long>((H.nz + 1) / 2) * nb;
     h->ws_bytes = std::max<size_t>(per * slots, 256);
     SMG_CUDA(cudaMalloc(&h->d_ws, h->ws_bytes));
@@ -303,9 +323,39 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
         e1 = take_event(h);
         cudaEventRecord(e0, st);
     }
-    const bool use_lean = !f64c && R == 1 && h->lean && iters == 1 && lean_supported(h->prec, K) &&
-                          lay.MF == H.P && h->lean_level[l];
-    cudaError_t err = use_lean ? launch_plane_lean(h->prec, K, nplanes, nb, h->threads, a, lay.smem_bytes, st)
+    // the shortened-step cycle: FP32 compute on one CTA per plane with the same layout; FP64
+    // compute with its own layouts, the cluster chosen by the same rule as above
+    bool use_lean = false;
+    const PlaneLayout *llay = &lay;
+    if (h->lean && lean_supported(K) && h->lean_level[l]) {
+        if (!f64c) {
+            use_lean = (R == 1 && iters == 1 && lay.MF == H.P);
+        } else {
+            int lrb = -1;
+            for (int lr = 0; lr <= 4; ++lr) {
+                const int cand = 1 << lr;
+                if (cand > rmax && lr > 0) break;
+                if (h->lean64_ok[lr] && (lr == 0 || static_cast<long long>(nplanes) * nb * cand <= h->num_sms)) lrb = lr;
+            }
+            if (lrb >= 0) {
+                use_lean = true;
+                llay = &h->lay_lean64[lrb];
+                a.R = 1 << lrb;
+            }
+        }
+    }
+    if (use_lean && llay != &lay) {
+        a.ws_per_plane = llay->ws_per_plane;
+        for (int m = 0; m < H.P; ++m) {
+            a.off_u[m] = llay->off_u[m];
+            a.off_g[m] = llay->off_g[m];
+        }
+        a.smem_u_mask = llay->smem_u_mask;
+        a.smem_g_mask = llay->smem_g_mask;
+        a.MF = llay->MF;
+        a.off_fs = llay->off_fs;
+    }
+    cudaError_t err = use_lean ? launch_plane_lean(h->prec, f64c, K, nplanes, nb, h->threads, a, llay->smem_bytes, st)
                                : launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
     if (err != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("plane relaxation launch: ") + cudaGetErrorString(err));
     h->launches += 1;

@@ -70,36 +70,45 @@ bool cluster_resident(Prec storage, bool f64, int K, int R, int threads, size_t 
     return false;
 }
 
-// ---- the shortened-step FP32 plane cycle (K <= 4, FP32 or BF16 storage) ------------------------
+// ---- the shortened-step plane cycle (K <= 4) --------------------------------------------------
 #define SMG_DECL_LEAN(k, p)                                                                           \
-    cudaError_t launch_plane_lean_k##k##_p##p(int, int, int, const PlaneRelaxArgs &, size_t, cudaStream_t); \
-    int set_plane_lean_smem_k##k##_p##p(size_t);
-SMG_DECL_LEAN(1, 1) SMG_DECL_LEAN(2, 1) SMG_DECL_LEAN(3, 1) SMG_DECL_LEAN(4, 1)
-SMG_DECL_LEAN(1, 2) SMG_DECL_LEAN(2, 2) SMG_DECL_LEAN(3, 2) SMG_DECL_LEAN(4, 2)
+    cudaError_t launch_plane_lean_k##k##_p##p(bool, int, int, int, const PlaneRelaxArgs &, size_t, cudaStream_t); \
+    int set_plane_lean_smem_k##k##_p##p(bool, bool, size_t);                                          \
+    bool lean_cluster_resident_k##k##_p##p(int, int, size_t);
+#define SMG_DECL_LEAN_K(k) SMG_DECL_LEAN(k, 0) SMG_DECL_LEAN(k, 1) SMG_DECL_LEAN(k, 2)
+SMG_DECL_LEAN_K(1)
+SMG_DECL_LEAN_K(2)
+SMG_DECL_LEAN_K(3)
+SMG_DECL_LEAN_K(4)
 
 #define SMG_LEAN_SWITCH(K, storage, CALL)                                                             \
-    if (storage == Prec::F32) {                                                                       \
-        switch (K) { case 1: return CALL(1, 1); case 2: return CALL(2, 1);                            \
-                     case 3: return CALL(3, 1); case 4: return CALL(4, 1); }                          \
-    } else if (storage == Prec::BF16) {                                                               \
-        switch (K) { case 1: return CALL(1, 2); case 2: return CALL(2, 2);                            \
-                     case 3: return CALL(3, 2); case 4: return CALL(4, 2); }                          \
+    switch (K) {                                                                                      \
+    case 1: SMG_SWITCH_P(1, storage, CALL)                                                            \
+    case 2: SMG_SWITCH_P(2, storage, CALL)                                                            \
+    case 3: SMG_SWITCH_P(3, storage, CALL)                                                            \
+    case 4: SMG_SWITCH_P(4, storage, CALL)                                                            \
     }
 
-cudaError_t launch_plane_lean(Prec storage, int K, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
+bool lean_supported(int K) { return K >= 1 && K <= 4; }
+
+cudaError_t launch_plane_lean(Prec storage, bool f64, int K, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
                               size_t smem, cudaStream_t st) {
-#define SMG_CALL_LEAN(k, p) launch_plane_lean_k##k##_p##p(nplanes, nb, threads, a, smem, st)
+#define SMG_CALL_LEAN(k, p) launch_plane_lean_k##k##_p##p(f64, nplanes, nb, threads, a, smem, st)
     SMG_LEAN_SWITCH(K, storage, SMG_CALL_LEAN)
     return cudaErrorInvalidValue;
 }
 
-int set_plane_lean_smem(Prec storage, int K, size_t smem) {
-#define SMG_CALL_LEAN_SMEM(k, p) set_plane_lean_smem_k##k##_p##p(smem)
+int set_plane_lean_smem(Prec storage, bool f64, bool cl, int K, size_t smem) {
+#define SMG_CALL_LEAN_SMEM(k, p) set_plane_lean_smem_k##k##_p##p(f64, cl, smem)
     SMG_LEAN_SWITCH(K, storage, SMG_CALL_LEAN_SMEM)
     return static_cast<int>(cudaErrorInvalidValue);
 }
 
-bool lean_supported(Prec storage, int K) { return storage != Prec::F64 && K >= 1 && K <= 4; }
+bool lean_cluster_resident(Prec storage, int K, int R, int threads, size_t smem) {
+#define SMG_CALL_LEAN_RES(k, p) lean_cluster_resident_k##k##_p##p(R, threads, smem)
+    SMG_LEAN_SWITCH(K, storage, SMG_CALL_LEAN_RES)
+    return false;
+}
 
 // ---- residual + restriction -------------------------------------------------------------------
 template <class S, class C>

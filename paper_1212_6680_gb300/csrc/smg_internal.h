@@ -137,11 +137,15 @@ struct PlaneLayout {
 inline int trifac_set_elems(int K) { return (2 + (K > 1 ? 4 * K - 5 : 0) + 13) * 32; }
 constexpr int kMaxFactorLevels = kMaxPlaneLevels;
 
-// K > 0 sizes the factor sets for that x-line chunk instead of the one nx implies.
-PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int K = 0);
-// Layout for a cluster of R CTAs per plane: every array in shared memory, each CTA holding the
-// lines it owns (pairs (y/2) mod R).  smem_bytes = 0 when it does not fit in the budget.
-PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R);
+// K > 0 sizes the factor sets for that x-line chunk instead of the one nx implies; all_sets keeps
+// the factor sets of every 2D level in shared memory (the shortened-step kernel needs them).
+PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int K = 0,
+                              bool all_sets = false);
+// Layout for a cluster of R CTAs per plane: each CTA holds the lines it owns (pairs (y/2) mod R)
+// of the arrays kept on chip; an array that does not fit lives whole in the cluster's global
+// slot.  smem_bytes = 0 when the coefficient table and factor sets alone exceed the budget.
+PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R,
+                                      bool all_sets = false);
 
 // Kernel launchers (cycle.cu and its instantiation units).
 enum class Prec { F64 = 0, F32 = 1, BF16 = 2 };
@@ -163,13 +167,15 @@ cudaError_t launch_convert_to(Prec storage, long long n, const double *src, void
 cudaError_t launch_convert_from(Prec storage, long long n, const void *src, double *dst, cudaStream_t st);
 cudaError_t launch_apply_A(int nx, int ny, int nz, int nb, const double *u, double *out, cudaStream_t st);
 int set_plane_relax_smem(Prec storage, bool compute_f64, bool cluster, int K, size_t smem);
-// The shortened-step FP32 plane cycle (plane_lean.cuh): FP32 or BF16 storage, nx <= 128 (K <= 4),
-// one CTA per plane, every 2D level's factor sets in shared memory, and every line of a 2D level
-// but its last sharing one line matrix (lean_uniform_level).
-bool lean_supported(Prec storage, int K);
-cudaError_t launch_plane_lean(Prec storage, int K, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
-                              size_t smem, cudaStream_t st);
-int set_plane_lean_smem(Prec storage, int K, size_t smem);
+// The shortened-step plane cycle (plane_lean.cuh): nx <= 128 (K <= 4), every 2D level's factor
+// sets in shared memory, and every line of a 2D level but its last sharing one line matrix
+// (lean_uniform_level); FP32 compute on one CTA per plane, FP64 compute on one CTA or a cluster
+// of a.R CTAs.
+bool lean_supported(int K);
+cudaError_t launch_plane_lean(Prec storage, bool compute_f64, int K, int nplanes, int nb, int threads,
+                              const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
+int set_plane_lean_smem(Prec storage, bool compute_f64, bool cluster, int K, size_t smem);
+bool lean_cluster_resident(Prec storage, int K, int R, int threads, size_t smem);
 // True when, on every plane of z-level l and every 2D level, the lines before the last share the
 // line matrix (S(y,y), T(y,y)) of line 0.
 bool lean_uniform_level(const HostHierarchy &H, int l);
