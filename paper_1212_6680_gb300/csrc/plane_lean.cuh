@@ -238,9 +238,11 @@ __device__ __forceinline__ void lean_restrict_line(const LeanEnv<C, K> &e, const
 }
 
 // Restriction from level m to level m+1 over the coarse line pairs (2k, 2k+1) this CTA owns
-// (k = rank + R i), warp w taking i = w, w + nw, ...; every coarse line's g is stored, and the
-// even one of the pair is solved at once (level m+1's down-sweep relaxes its even lines with zero
-// neighbours).
+// (k = rank + R i); every coarse line's g is stored, and the even one of the pair is solved at
+// once (level m+1's down-sweep relaxes its even lines with zero neighbours).  While the CTA owns
+// at most half as many pairs as it has warps, the two lines of a pair go to two warps (w takes
+// the even line, w + nw/2 the odd one) so that neither waits for the other's restriction;
+// otherwise warp w takes whole pairs i = w, w + nw, ...
 template <class C, int K, bool CL>
 __device__ __forceinline__ void lean_restrict_solve(const LeanEnv<C, K> &e, TriFac<C, K> &fac, int &key, int m) {
     const LeanLevel<C> L = e.lv[m], Lc = e.lv[m + 1];
@@ -248,6 +250,23 @@ __device__ __forceinline__ void lean_restrict_solve(const LeanEnv<C, K> &e, TriF
     const int npairs = (Lc.ny + 1) / 2;
     int nown = npairs;
     if constexpr (CL) nown = (npairs > e.rank) ? ((npairs - e.rank + (1 << e.lr) - 1) >> e.lr) : 0;
+    const int half = e.nw >> 1;
+    if (2 * nown <= e.nw) {
+        const bool odd = e.warp >= half;
+        const int i = odd ? e.warp - half : e.warp;
+        if (i >= nown) return;
+        const int k = CL ? e.rank + (i << e.lr) : i;
+        const int j = 2 * k + (odd ? 1 : 0);
+        if (j >= Lc.ny) return;
+        C g[1][K];
+        lean_restrict_line<C, K, CL>(e, L, j, g[0]);
+        store_line<C, K>(lean_line<C, K, CL>(e, Lc.g, Lc.gon, j), g[0], nx, e.vec, lane);
+        if (odd) return;
+        lean_fac<C, K>(fac, key, Lc, m + 1, j == Lc.ny - 1 ? 1 : 0, lane);
+        tri_apply<C, K, 1>(fac, g, nx, lane);
+        store_line<C, K>(lean_line<C, K, CL>(e, Lc.u, Lc.uon, j), g[0], nx, e.vec, lane);
+        return;
+    }
     for (int i = e.warp; i < nown; i += e.nw) {
         const int k = CL ? e.rank + (i << e.lr) : i;
         const int j0 = 2 * k, j1 = 2 * k + 1;
