@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     ):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
              "-o", tmp] + _SRCS + ["-lm"]
         )
         os.replace(tmp, _LIB_PATH)
@@ -58,6 +58,8 @@ def lib():
         L.orc_smg_setup.restype = vp
         L.orc_smg_free.argtypes = [vp]
         L.orc_smg_apply.argtypes = [vp, dp, dp]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = ctypes.c_int
         L.orc_smg_num_levels.argtypes = [vp]
         L.orc_smg_level_nz.argtypes = [vp, ctypes.c_int]
         L.orc_smg_level_coefs.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
@@ -274,3 +276,8 @@ def learned_correct(w, r: np.ndarray, s0: np.ndarray):
     nz, ny, nx = r.shape
     acc = lib().orc_learned_correct(nx, ny, nz, _p(w), _p(r), _p(s))
     return s, bool(acc)
+
+
+def set_threads(n: int) -> int:
+    """Threads the C oracle's loops may use (1 = sequential); results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))

@@ -39,6 +39,9 @@
  *
  * Every loop below is the definition written out; no blocking, fusion or reordering.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "smg_oracle.h"
 
 #include <math.h>
@@ -53,6 +56,9 @@
 
 void orc_apply_A(int nx, int ny, int nz, const double *u, double *out)
 {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (nz > 4)
+#endif
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -286,6 +292,12 @@ static void line_relax(const plane_h *ph, int m, int y, const double *g, double 
     free(rhs);
 }
 
+#ifdef _OPENMP
+#define ORC_PAR_LINES _Pragma("omp parallel for schedule(dynamic, 1) if (!omp_in_parallel() && ny > 8)")
+#else
+#define ORC_PAR_LINES
+#endif
+
 /* One 2D V-cycle on level m: u = C_m g, zero initial guess. */
 static void plane_vcycle(const plane_h *ph, int m, const double *g, double *u)
 {
@@ -296,8 +308,11 @@ static void plane_vcycle(const plane_h *ph, int m, const double *g, double *u)
         for (int y = 0; y < ny; ++y) line_relax(ph, m, y, g, u);
         return;
     }
-    /* pre-relaxation: even lines, then odd lines */
+    /* pre-relaxation: even lines, then odd lines (the lines of one colour are independent; with
+       OpenMP they are shared among threads when no outer loop already is) */
+    ORC_PAR_LINES
     for (int y = 0; y < ny; y += 2) line_relax(ph, m, y, g, u);
+    ORC_PAR_LINES
     for (int y = 1; y < ny; y += 2) line_relax(ph, m, y, g, u);
     /* residual and restriction g_c = P^T (g - B u) */
     double *r = (double *)malloc(sizeof(double) * np);
@@ -326,7 +341,9 @@ static void plane_vcycle(const plane_h *ph, int m, const double *g, double *u)
                 u[(size_t)y * nx + x] += cw[p] * uc[(size_t)cj[p] * nx + x];
     }
     /* post-relaxation: odd lines, then even lines */
+    ORC_PAR_LINES
     for (int y = 1; y < ny; y += 2) line_relax(ph, m, y, g, u);
+    ORC_PAR_LINES
     for (int y = 0; y < ny; y += 2) line_relax(ph, m, y, g, u);
     free(r);
     free(gc);
@@ -461,6 +478,29 @@ static void plane_relax(const orc_smg *h, int l, int z, const double *f, double 
     for (size_t i = 0; i < np; ++i) u[(size_t)z * np + i] += v[i];
 }
 
+/* The planes z0, z0 + 2, ... < nzl of one colour, relaxed independently (each reads only the
+   other colour's planes); with OpenMP they are shared among threads, each with its own scratch. */
+static void relax_colour(const orc_smg *h, int l, int z0, const double *f, double *u)
+{
+    int nzl = h->nz_l[l];
+    size_t np = (size_t)h->nx * (size_t)h->ny;
+#ifdef _OPENMP
+#pragma omp parallel if (nzl > 2)
+#endif
+    {
+        double *g = (double *)malloc(sizeof(double) * np);
+        double *v = (double *)malloc(sizeof(double) * np);
+        double *tmp = (double *)malloc(sizeof(double) * np);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int z = z0; z < nzl; z += 2) plane_relax(h, l, z, f, u, g, v, tmp);
+        free(g);
+        free(v);
+        free(tmp);
+    }
+}
+
 /* One 3D V-cycle on level l: u = T_l f, zero initial guess. */
 static void smg_vcycle(const orc_smg *h, int l, const double *f, double *u)
 {
@@ -479,37 +519,56 @@ static void smg_vcycle(const orc_smg *h, int l, const double *f, double *u)
         return;
     }
     for (int s = 0; s < h->npre; ++s) {
-        for (int z = 0; z < nzl; z += 2) plane_relax(h, l, z, f, u, g, v, tmp);
-        for (int z = 1; z < nzl; z += 2) plane_relax(h, l, z, f, u, g, v, tmp);
+        relax_colour(h, l, 0, f, u);
+        relax_colour(h, l, 1, f, u);
     }
     /* residual r = f - A_l u and restriction f_c = P^T r */
     double *r = (double *)malloc(sizeof(double) * nl);
-    for (int z = 0; z < nzl; ++z) {
-        level_apply_plane(h, l, z, u, g, tmp);
-        for (size_t i = 0; i < np; ++i) r[(size_t)z * np + i] = f[(size_t)z * np + i] - g[i];
+#ifdef _OPENMP
+#pragma omp parallel if (nzl > 2)
+#endif
+    {
+        double *gz = (double *)malloc(sizeof(double) * np);
+        double *tz = (double *)malloc(sizeof(double) * np);
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int z = 0; z < nzl; ++z) {
+            level_apply_plane(h, l, z, u, gz, tz);
+            for (size_t i = 0; i < np; ++i) r[(size_t)z * np + i] = f[(size_t)z * np + i] - gz[i];
+        }
+        free(gz);
+        free(tz);
     }
     int nzc = h->nz_l[l + 1];
     double *fc = (double *)calloc(np * (size_t)nzc, sizeof(double));
     double *uc = (double *)calloc(np * (size_t)nzc, sizeof(double));
-    for (int z = 0; z < nzl; ++z) {
-        int cj[2];
-        double cw[2];
-        int cnt = prolong_row(z, nzl, h->wm[l], h->wp[l], cj, cw);
-        for (int p = 0; p < cnt; ++p)
-            for (size_t i = 0; i < np; ++i) fc[(size_t)cj[p] * np + i] += cw[p] * r[(size_t)z * np + i];
-    }
+    /* every point sums its fine planes in plane order (the order does not depend on threads) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (size_t i = 0; i < np; ++i)
+        for (int z = 0; z < nzl; ++z) {
+            int cj[2];
+            double cw[2];
+            int cnt = prolong_row(z, nzl, h->wm[l], h->wp[l], cj, cw);
+            for (int p = 0; p < cnt; ++p) fc[(size_t)cj[p] * np + i] += cw[p] * r[(size_t)z * np + i];
+        }
     smg_vcycle(h, l + 1, fc, uc);
     /* prolongation and correction u += P u_c */
-    for (int z = 0; z < nzl; ++z) {
-        int cj[2];
-        double cw[2];
-        int cnt = prolong_row(z, nzl, h->wm[l], h->wp[l], cj, cw);
-        for (int p = 0; p < cnt; ++p)
-            for (size_t i = 0; i < np; ++i) u[(size_t)z * np + i] += cw[p] * uc[(size_t)cj[p] * np + i];
-    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (size_t i = 0; i < np; ++i)
+        for (int z = 0; z < nzl; ++z) {
+            int cj[2];
+            double cw[2];
+            int cnt = prolong_row(z, nzl, h->wm[l], h->wp[l], cj, cw);
+            for (int p = 0; p < cnt; ++p) u[(size_t)z * np + i] += cw[p] * uc[(size_t)cj[p] * np + i];
+        }
     for (int s = 0; s < h->npost; ++s) {
-        for (int z = 1; z < nzl; z += 2) plane_relax(h, l, z, f, u, g, v, tmp);
-        for (int z = 0; z < nzl; z += 2) plane_relax(h, l, z, f, u, g, v, tmp);
+        relax_colour(h, l, 1, f, u);
+        relax_colour(h, l, 0, f, u);
     }
     free(r);
     free(fc);
@@ -517,6 +576,20 @@ static void smg_vcycle(const orc_smg *h, int l, const double *f, double *u)
     free(g);
     free(v);
     free(tmp);
+}
+
+/* Threads the oracle's loops may use (OpenMP builds; 1 = plain sequential execution).  The results
+   do not depend on it: every parallel loop writes disjoint outputs whose values are computed in a
+   fixed order. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 void orc_smg_apply(const orc_smg *h, const double *r, double *s)

@@ -33,6 +33,10 @@ orc_smg *orc_smg_setup(int nx, int ny, int nz, int npre, int npost, int coarse_i
 void orc_smg_free(orc_smg *h);
 /* s = T r : one V-cycle with zero initial guess. */
 void orc_smg_apply(const orc_smg *h, const double *r, double *s);
+/* Threads the oracle may use (built with OpenMP: the planes of a colour, the lines of a colour,
+ * the points of a transfer are shared among threads; every output is computed in a fixed order,
+ * so results are bitwise independent of the count).  n >= 1 sets it; returns the count in force. */
+int orc_set_threads(int n);
 
 /* Introspection for the Galerkin / interpolation pins. */
 int orc_smg_num_levels(const orc_smg *h);
