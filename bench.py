@@ -136,7 +136,7 @@ def source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1212_6680_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.startswith("plane_relax"):
+        if f.startswith("plane_"):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -144,7 +144,7 @@ def source_hash():
 def ncu_traffic():
     """DRAM bytes per level-0 launch of the plane-relaxation kernel from the committed ncu
     summary, if it was captured from the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "plane_relax_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "plane_lean_traffic_level0_128cube.txt")
     try:
         d = json.load(open(p))
         if d.get("source_hash") == source_hash():
@@ -186,6 +186,30 @@ def oracle_batched_sample(nsample):
     n_all = float(sum(int(np.prod(d)) for d in dims))
     n_s = float(sum(int(np.prod(d)) for d in dims[:nsample]))
     return t * n_all / n_s, its, t
+
+
+def oracle_solve_baseline():
+    """The oracle's full FPCG-SMG(1,0) solve at 128^3 timed on every host core (OpenMP) and on one."""
+    import oracle
+    from paper_1212_6680_gb300 import inputs
+
+    oracle.build()
+    bo = inputs.rhs(NX, NY, NZ, seed=0)
+    T = oracle.SMG(NX, NY, NZ, 1, 0)
+    cores = os.cpu_count() or 1
+    out_t = {}
+    for nt in (cores, 1):
+        oracle.set_threads(nt)
+        t0 = time.perf_counter()
+        out = oracle.krylov(bo, "fpcg", T, tol=TOL, maxit=100)
+        out_t[nt] = time.perf_counter() - t0
+        assert out["status"] == 0 and out["relres"] <= TOL
+    oracle.set_threads(cores)
+    return {"value": out_t[cores], "unit": "s", "cores": cores, "kind": "oracle",
+            "single_thread_s": out_t[1],
+            "sample": f"one full FPCG-SMG(1,0) solve at 128^3 in FP64 ({out['iters']} iterations) on {cores} "
+                      f"host cores (OpenMP over planes, lines and transfer points; bitwise the single-thread "
+                      f"result), and on one thread"}
 
 
 def run_reference(args):
@@ -242,10 +266,12 @@ def run_reference(args):
         print(json.dumps(line), flush=True)
         return
     oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     b = inputs.rhs(NX, NY, NZ, seed=0)
     T = oracle.SMG(NX, NY, NZ, 1, 0)
-    for _ in range(args.warmup):  # warm-up: one V-cycle each
-        T.apply(b)
+    for _ in range(args.warmup):  # warm-up: one full solve each
+        oracle.krylov(b, "fpcg", T, tol=TOL, maxit=100)
     times, iters = [], None
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -254,13 +280,14 @@ def run_reference(args):
         iters = out["iters"]
         assert out["status"] == 0 and out["relres"] <= TOL
     v = statistics.mean(times)
-    sample = f"full FPCG-SMG(1,0) solve, 128^3, FP64, {iters} iterations, single thread"
+    sample = (f"full FPCG-SMG(1,0) solve, 128^3, FP64, {iters} iterations, {cores} host cores (OpenMP over planes, "
+              f"lines and transfer points; bitwise the single-thread result)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("V-cycle FP32", "V-cycle FP64 (CPU oracle)"),
                        "grid": [NX, NY, NZ], "iters": iters},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -340,6 +367,14 @@ def run_ours(args):
     t_step = statistics.mean(times)
     t_max = max_over_ranks(t_step, dist, "cuda")
 
+    # ---- every plane-relaxation launch of one solve timed (all z-levels, the FP64 coarsest plane) ----
+    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 2)
+    for c in range(6):
+        smg.smg_profile_read(h32, c)
+    x.zero_()
+    smg.krylov_solve(h32, "fpcg", b, x, TOL, 100)
+    prof_all = {c: smg.smg_profile_read(h32, c) for c in range(5)}
+    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 0)
     # ---- comparison arms on the same GPU: FP64 and BF16 cycles ----
     k2 = max(1, min(args.steps, 3))
     t64, it64, _ = timed_solves(handles["fp64"], k2, 1)
@@ -360,23 +395,28 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-                "kernel": "plane_relax_kernel<float,float,4> (finest level)",
+                "kernel": "plane_lean_kernel<float,float,4,false> (finest level)",
                 "launches": pl, "avg_launch_us": (pms * 1e3 / pl) if pl else None,
                 "algorithmic_bytes_per_launch": (pbytes / pl) if pl else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s"}
+    # the same ratio over every plane-relaxation launch of a solve (all z-levels, FP32, and the FP64
+    # coarsest plane), and each class of the cycle (CUDA events around every launch: the profiled
+    # solve's launches lose their programmatic-dependent-launch overlap)
+    names = {0: "plane relaxation, finest level", 1: "plane relaxation, other levels", 2: "coarsest plane (FP64)",
+             3: "restriction + prolongation", 4: "Krylov kernels"}
+    classes = {}
+    for c, (nl, ms, by) in prof_all.items():
+        classes[names[c]] = {"launches": nl, "us_per_launch": (ms * 1e3 / nl) if nl else None,
+                             "ms_per_solve": ms, "GB_per_s": ((by / 1e9) / (ms / 1e3)) if (ms > 0 and by > 0) else None}
+    rl_ms = sum(prof_all[c][1] for c in (0, 1, 2))
+    rl_by = sum(prof_all[c][2] for c in (0, 1, 2))
+    if rl_ms > 0:
+        roofline["all_levels"] = {"achieved": (rl_by / 1e9) / (rl_ms / 1e3), "frac": ((rl_by / 1e9) / (rl_ms / 1e3)) / peak,
+                                  "unit": "GB/s", "note": "every plane-relaxation launch of one solve"}
     cpu = None
     if not args.no_cpu_baseline:
-        import oracle
-
-        oracle.build()
-        bo = inputs.rhs(NX, NY, NZ, seed=0)
-        T = oracle.SMG(NX, NY, NZ, 1, 0)
-        t0 = time.perf_counter()
-        out = oracle.krylov(bo, "fpcg", T, tol=TOL, maxit=100)
-        tc = time.perf_counter() - t0
-        cpu = {"value": tc, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"one full FPCG-SMG(1,0) solve at 128^3 in FP64 ({out['iters']} iterations), single thread"}
+        cpu = oracle_solve_baseline()
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -386,7 +426,8 @@ def run_ours(args):
                    "l2": "256 MB buffer written before every timed solve", "parallelism": "replicas" if world > 1 else "single GPU",
                    "fp64_cycle_s": statistics.mean(t64), "fp64_cycle_iters": it64,
                    "bf16_cycle_s": statistics.mean(t16), "bf16_cycle_iters": it16,
-                   "speedup_fp32_vs_fp64": statistics.mean(t64) / t_step},
+                   "speedup_fp32_vs_fp64": statistics.mean(t64) / t_step,
+                   "cycle_classes_profiled_solve": classes},
         "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": statistics.mean(te), "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed_region": wall,
