@@ -42,7 +42,8 @@ enum {
     SMG_ERR_NOCONV = -3,    /* maxit reached; the last iterate is returned */
     SMG_ERR_BREAKDOWN = -4, /* (p, Ap) <= 0 or (s_{k-1}, r_{k-1}) = 0 in Algorithm 1 */
     SMG_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
-    SMG_ERR_NAN = -6        /* NaN or Inf met in a residual norm or inner product */
+    SMG_ERR_NAN = -6,       /* NaN or Inf met in a residual norm or inner product */
+    SMG_ERR_HOST = -7       /* a host allocation failed (message in smg_last_error) */
 };
 
 enum { SMG_PCG = 0, SMG_FPCG = 1, SMG_PSD = 2 };       /* eq. (1), eq. (2), beta = 0 */
@@ -366,9 +367,10 @@ int smg_apply_A_dot_static(int nx, int ny, int nz, const double *u, double *out,
  *          level is (B v)_y = sum_dy S(y,y+dy) Lx v_(y+dy) + T(y,y+dy) v_(y+dy);
  *   nz_l, ny_m: (host, may be NULL) the number of planes of level l and lines of 2D level m.
  * Any index out of range (l >= number of z-levels, z >= nz_l, m >= number of 2D levels) or a
- * size < 1 returns SMG_ERR_ARG and writes nothing.  Each call builds the whole host hierarchy
- * (about 32 nz ny doubles of host memory, freed before it returns): meant for inspection and
- * tests, not for a hot loop.
+ * grid that smg_setup refuses (a size < 1 or above its limits) returns SMG_ERR_ARG and writes
+ * nothing; the sizes and l, m are checked before anything is allocated.  Each call builds the
+ * whole host hierarchy (about 32 nz ny doubles of host memory, freed before it returns; a failed
+ * host allocation returns SMG_ERR_HOST): meant for inspection and tests, not for a hot loop.
  */
 int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, double *lines, int *nz_l, int *ny_m);
 

@@ -27,6 +27,15 @@ int fail(int code, const std::string &msg) {
     return code;
 }
 
+// The grid limits every set-up shares: nullptr when (nx, ny, nz) is accepted, else the reason.
+const char *grid_size_error(int nx, int ny, int nz) {
+    if (nx < 1 || ny < 1 || nz < 1) return "grid sizes must be >= 1";
+    if (nx > kMaxNx) return "nx must be <= 512";
+    if (ny > kMaxNy) return "ny must be <= 512";
+    if (nz > kMaxNz) return "nz must be <= 4096";
+    return nullptr;
+}
+
 #define SMG_CUDA(call)                                                                               \
     do {                                                                                             \
         cudaError_t e_ = (call);                                                                     \
@@ -543,10 +552,7 @@ const char *smg_last_error(void) { return g_last_error.c_str(); }
 int smg_setup(int nx, int ny, int nz, int npre, int npost, smg_handle *out) {
     if (out == nullptr) return fail(SMG_ERR_ARG, "out is null");
     *out = nullptr;
-    if (nx < 1 || ny < 1 || nz < 1) return fail(SMG_ERR_ARG, "grid sizes must be >= 1");
-    if (nx > kMaxNx) return fail(SMG_ERR_ARG, "nx must be <= 512");
-    if (ny > kMaxNy) return fail(SMG_ERR_ARG, "ny must be <= 512");
-    if (nz > kMaxNz) return fail(SMG_ERR_ARG, "nz must be <= 4096");
+    if (const char *e = grid_size_error(nx, ny, nz)) return fail(SMG_ERR_ARG, e);
     if (npre < 1) return fail(SMG_ERR_ARG, "npre must be >= 1");
     if (npost < 0) return fail(SMG_ERR_ARG, "npost must be >= 0");
     smg_ctx *h = new smg_ctx();
@@ -836,12 +842,17 @@ int smg_launch_count(smg_handle h, long long *count) {
 
 int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, double *lines, int *nz_l, int *ny_m) {
     using namespace smg;
-    if (nx < 1 || ny < 1 || nz < 1) return fail(SMG_ERR_ARG, "grid sizes must be >= 1");
+    if (const char *e = grid_size_error(nx, ny, nz)) return fail(SMG_ERR_ARG, e);
     if (zc == nullptr || lines == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    if (l < 0 || l >= hierarchy_levels(nz) || m < 0 || m >= hierarchy_levels(ny))
+        return fail(SMG_ERR_ARG, "level or 2D level out of range");
     HostHierarchy H;
-    build_hierarchy(nx, ny, nz, H);
-    if (l < 0 || l >= H.L || z < 0 || z >= H.nz_l[l] || m < 0 || m >= H.P)
-        return fail(SMG_ERR_ARG, "level, plane or 2D level out of range");
+    try {
+        build_hierarchy(nx, ny, nz, H);
+    } catch (const std::exception &ex) {
+        return fail(SMG_ERR_HOST, std::string("building the hierarchy failed: ") + ex.what());
+    }
+    if (z < 0 || z >= H.nz_l[l]) return fail(SMG_ERR_ARG, "plane out of range");
     const size_t plane = static_cast<size_t>(H.plane_base[l] + z);
     for (int k = 0; k < kCoefPerPlane; ++k) zc[k] = H.zcoef[plane * kCoefPerPlane + k];
     const double *pc = &H.pcoef[plane * H.sum_ny * kCoefPerLine];

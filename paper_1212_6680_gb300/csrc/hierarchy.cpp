@@ -97,6 +97,8 @@ int num_levels(int n) {
 
 }  // namespace
 
+int hierarchy_levels(int n) { return num_levels(n); }
+
 void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H) {
     H = HostHierarchy();
     H.nx = nx;

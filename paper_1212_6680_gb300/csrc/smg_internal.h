@@ -46,6 +46,8 @@ struct HostHierarchy {
     std::vector<double> pcoef;     // [nplanes_total * sum_ny * 8]
 };
 
+// Levels of a semicoarsening hierarchy over n points (n, n/2, ... down to 1).
+int hierarchy_levels(int n);
 void build_hierarchy(int nx, int ny, int nz, HostHierarchy &H);
 
 // Sets the message smg_last_error() returns on the calling thread.

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsmg.so")
 
 SMG_OK, SMG_ERR_ARG, SMG_ERR_CUDA, SMG_ERR_NOCONV, SMG_ERR_BREAKDOWN, SMG_ERR_TIMEOUT, SMG_ERR_NAN = 0, -1, -2, -3, -4, -5, -6
+SMG_ERR_HOST = -7
 SMG_PCG, SMG_FPCG, SMG_PSD = 0, 1, 2
 SMG_FP64, SMG_FP32, SMG_BF16 = 0, 1, 2
 SMG_OPT_COARSE_ITERS, SMG_OPT_THREADS, SMG_OPT_PROFILE, SMG_OPT_CLUSTER_MAX, SMG_OPT_CLUSTER_MAX32 = 0, 1, 2, 3, 4

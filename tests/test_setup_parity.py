@@ -45,3 +45,20 @@ def test_setup_coefficients_reject_bad_indices(smg):
         smg.smg_setup_coefs(8, 8, 8, 0, 8, 0)
     with pytest.raises(Exception):
         smg.smg_setup_coefs(0, 8, 8, 0, 0, 0)
+
+
+@pytest.mark.parametrize("shape", [(1 << 20, 8, 8), (8, 1 << 20, 8), (8, 8, 1 << 30), (8, 8, -3)])
+def test_setup_coefficients_refuse_grids_smg_setup_refuses(smg, shape):
+    """Sizes outside smg_setup's limits are refused before the host hierarchy is built (an
+    nz of 2^30 would otherwise ask for tens of GB of host memory), and nothing is written."""
+    import ctypes
+
+    nx, ny, nz = shape
+    zc = np.full(8, 7.0)
+    lines = np.full((8, 8), 7.0)
+    dp_ = ctypes.POINTER(ctypes.c_double)
+    rc = smg._lib.smg_setup_coefs(nx, ny, nz, 0, 0, 0, zc.ctypes.data_as(dp_), lines.ctypes.data_as(dp_), None, None)
+    assert rc == smg.SMG_ERR_ARG
+    assert np.all(zc == 7.0) and np.all(lines == 7.0)
+    with pytest.raises(Exception):
+        smg.smg_setup_coefs(8, 8, 8, 0, 0, 5)  # m past the number of 2D levels
