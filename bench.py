@@ -135,9 +135,8 @@ def source_hash():
 
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1212_6680_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.startswith("plane_"):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ("plane_lean.cuh", "plane_relax.cuh", "plane_relax_inst.cu"):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
