@@ -80,8 +80,11 @@ enum {
  * sweeps (npost = 0 is the paper's nonsymmetric "no post-relaxation" cycle).  The hierarchy
  * is computed on the host in FP64 (z-semicoarsening, Galerkin coarse operators, per-plane
  * y-hierarchies) and copied to the current device; work vectors for one right-hand side are
- * allocated.  Sizes: 1 <= nx <= 512, 1 <= ny <= 512, 1 <= nz <= 4096.  *out receives the handle.
- * The cycle precision starts as SMG_FP64.
+ * allocated.  Sizes: 1 <= nx <= 2048, 1 <= ny <= 512, 1 <= nz <= 4096.  x-lines of up to 512
+ * rows are solved by one warp; longer ones (the paper's 16n x n x n bricks up to n = 128) are cut
+ * into 512-row segments, one warp each, joined exactly through a reduced system of the segment
+ * ends, on one CTA per plane (the cluster and shortened-step options then do not apply).  *out
+ * receives the handle.  The cycle precision starts as SMG_FP64.
  */
 int smg_setup(int nx, int ny, int nz, int npre, int npost, smg_handle *out);
 

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libsmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 KS = (1, 2, 3, 4, 6, 8, 16)
 SOURCES = ["api.cpp", "hierarchy.cpp", "cycle.cu", "krylov_kernels.cu", "lobpcg.cu", "noalloc.cu", "batched.cu", "net.cu",
-           "net_api.cpp", "conv_tc.cu", "gram_tc.cu"]
+           "net_api.cpp", "conv_tc.cu", "gram_tc.cu", "plane_wide.cu"]
 
 
 def nvcc() -> str:

@@ -30,7 +30,7 @@ int fail(int code, const std::string &msg) {
 // The grid limits every set-up shares: nullptr when (nx, ny, nz) is accepted, else the reason.
 const char *grid_size_error(int nx, int ny, int nz) {
     if (nx < 1 || ny < 1 || nz < 1) return "grid sizes must be >= 1";
-    if (nx > kMaxNx) return "nx must be <= 512";
+    if (nx > kMaxNxWide) return "nx must be <= 2048";
     if (ny > kMaxNy) return "ny must be <= 512";
     if (nz > kMaxNz) return "nz must be <= 4096";
     return nullptr;
@@ -46,6 +46,8 @@ const char *grid_size_error(int nx, int ny, int nz) {
 // the most dynamic shared memory a plane CTA may use: 227 KB less 1 KB for the kernels' static
 // shared memory (the per-level table of the plane cycle, reduction scratch)
 constexpr size_t kSmemBudget = 227 * 1024 - 1024;
+// the wide-line kernel keeps its exchange buffers and level table in static shared memory
+constexpr size_t kWideSmemBudget = kSmemBudget - 2048;
 
 // profiling classes: 0 plane relaxation on the finest level, 1 plane relaxation on the other
 // levels (all but the coarsest), 2 the one-plane coarsest solve, 3 restriction + prolongation,
@@ -144,6 +146,8 @@ int instantiated_K(int nx) {
     return 16;
 }
 
+int alloc_plane_workspace(smg_ctx *h, int nb);
+
 // Allocate level vectors for nb right-hand sides in the current precision, and the plane
 // workspace; configure the kernels' dynamic shared memory.
 int ensure_levels(smg_ctx *h, int nb) {
@@ -158,9 +162,26 @@ int ensure_levels(smg_ctx *h, int nb) {
         SMG_CUDA(cudaMalloc(&h->d_f[l], bytes));
         SMG_CUDA(cudaMalloc(&h->d_u[l], bytes));
     }
+    const bool f64c = (h->prec == Prec::F64);
+    const bool wide = wide_segments(h->nx) > 1;
+    if (wide) {
+        // x-lines over several warps (plane_wide.cu): one CTA per plane, segment factors formed on
+        // the fly, no cluster and no shortened-step layouts
+        h->lay_c = plan_plane_layout(H, compute_bytes(h->prec), kWideSmemBudget, 16, false, true);
+        h->lay_d = plan_plane_layout(H, 8, kWideSmemBudget, 16, false, true);
+        if (set_plane_wide_smem(h->prec, f64c, h->lay_c.smem_bytes) != 0 ||
+            set_plane_wide_smem(h->prec, true, h->lay_d.smem_bytes) != 0)
+            return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, wide lines) failed");
+        for (int lr = 0; lr <= 4; ++lr) h->cl_ok[lr] = h->cl32_ok[lr] = h->lean64_ok[lr] = false;
+        if (h->num_sms == 0) {
+            int dev = 0;
+            SMG_CUDA(cudaGetDevice(&dev));
+            SMG_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        return alloc_plane_workspace(h, nb);
+    }
     h->lay_c = plan_plane_layout(H, compute_bytes(h->prec), kSmemBudget);
     h->lay_d = plan_plane_layout(H, 8, kSmemBudget);
-    const bool f64c = (h->prec == Prec::F64);
     const int K = instantiated_K(h->nx);
     if (set_plane_relax_smem(h->prec, f64c, false, K, h->lay_c.smem_bytes) != 0)
         return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, level precision) failed");
@@ -213,8 +234,13 @@ int ensure_levels(smg_ctx *h, int nb) {
         }
         h->lean64_ok[lr] = (lr == 0) || lean_cluster_resident(h->prec, K, R, h->threads, ly.smem_bytes);
     }
-    // global slots for the 2D-cycle arrays that are not on chip: one per CTA (at most one per
-    // plane of a colour of the finest level) or one per cluster, sized for the largest layout
+    return alloc_plane_workspace(h, nb);
+}
+
+// Global slots for the 2D-cycle arrays that are not on chip: one per CTA (at most one per plane
+// of a colour of the finest level) or one per cluster, sized for the largest usable layout.
+int alloc_plane_workspace(smg_ctx *h, int nb) {
+    const HostHierarchy &H = h->H;
     size_t per = std::max(static_cast<size_t>(h->lay_c.ws_per_plane) * compute_bytes(h->prec),
                           static_cast<size_t>(h->lay_d.ws_per_plane) * 8);
     for (int lr = 1; lr <= 4; ++lr) {
@@ -279,12 +305,15 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     // FP64 work it spreads); FP32 planes stay on one CTA while its 2D-cycle iterate u_0 fits in
     // shared memory (the cycle is then latency-bound and a cluster only adds barrier cost), and
     // use up to 4 CTAs when it does not (256-wide planes).
+    // Planes with x-lines longer than 512 rows run on one CTA each (plane_wide.cu).
     int R = 1;
+    const int W = wide_segments(h->nx);
     const bool *ok = f64c ? h->cl_ok : h->cl32_ok;
     int rmax;
     if (f64c) rmax = coarsest ? h->cluster_max : std::min(h->cluster_max, 8);
     else if (h->cluster_max32 > 0) rmax = h->cluster_max32;
     else rmax = (h->lay_c.smem_u_mask & 1u) ? 1 : 4;
+    if (W > 1) rmax = 1;
     for (int cand = 2; cand <= rmax && cand <= 16; cand *= 2)
         if (ok[__builtin_ctz(cand)] && static_cast<long long>(nplanes) * nb * cand <= h->num_sms) R = cand;
     const PlaneLayout &lay = (R > 1) ? (f64c ? h->lay_cl[__builtin_ctz(R)] : h->lay_cl32[__builtin_ctz(R)])
@@ -320,9 +349,11 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     a.MF = lay.MF;
     a.off_fs = lay.off_fs;
     const int K = instantiated_K(h->nx);
+    a.W = W;
     {
         auto al16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-        a.vec = (h->nx == 32 * K) && al16(f) && al16(u) && al16(h->d_ws);
+        const bool shape = (W > 1) ? (h->nx % 8 == 0) : (h->nx == 32 * K);
+        a.vec = shape && al16(f) && al16(u) && al16(h->d_ws);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = (h->profile == 2) || (h->profile == 1 && l == 0);
@@ -336,7 +367,7 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     // compute with its own layouts, the cluster chosen by the same rule as above
     bool use_lean = false;
     const PlaneLayout *llay = &lay;
-    if (h->lean && lean_supported(K) && h->lean_level[l]) {
+    if (W == 1 && h->lean && lean_supported(K) && h->lean_level[l]) {
         if (!f64c) {
             use_lean = (R == 1 && iters == 1 && lay.MF == H.P);
         } else {
@@ -364,8 +395,9 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
         a.MF = llay->MF;
         a.off_fs = llay->off_fs;
     }
-    cudaError_t err = use_lean ? launch_plane_lean(h->prec, f64c, K, nplanes, nb, h->threads, a, llay->smem_bytes, st)
-                               : launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
+    cudaError_t err = (W > 1)  ? launch_plane_wide(h->prec, f64c, nplanes, nb, h->threads, a, lay.smem_bytes, st)
+                      : use_lean ? launch_plane_lean(h->prec, f64c, K, nplanes, nb, h->threads, a, llay->smem_bytes, st)
+                                 : launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
     if (err != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("plane relaxation launch: ") + cudaGetErrorString(err));
     h->launches += 1;
     if (timed) {

@@ -252,12 +252,14 @@ static std::vector<std::pair<int, int>> layout_order(const HostHierarchy &H) {
 // few lines) and finally the finest; u_m before g_m at each level (the iterate is touched more
 // often).  What does not fit in `smem_budget` goes to a global slot per CTA (L2-resident for
 // the sizes of interest).
-PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int K, bool all_sets) {
+PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int K, bool all_sets,
+                              bool no_sets) {
     PlaneLayout P;
     P.K = K > 0 ? K : chunk_K(H.nx);
     auto align4 = [](size_t v) { return (v + 3) & ~static_cast<size_t>(3); };
     size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
-    P.MF = all_sets ? std::min(H.P, kMaxFactorLevels) : factor_levels(H, P.K, elem_bytes, smem_budget);
+    P.MF = no_sets ? 0
+                   : (all_sets ? std::min(H.P, kMaxFactorLevels) : factor_levels(H, P.K, elem_bytes, smem_budget));
     P.off_fs = static_cast<int>(smem_elems);
     smem_elems += 2 * static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
     long long gl = 0;

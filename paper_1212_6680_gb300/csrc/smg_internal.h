@@ -27,7 +27,8 @@ namespace smg {
 constexpr int kMaxPlaneLevels = 16;
 constexpr int kCoefPerLine = 8;
 constexpr int kCoefPerPlane = 8;
-constexpr int kMaxNx = 512;
+constexpr int kMaxNx = 512;     // one warp per x-line (16 rows per lane)
+constexpr int kMaxNxWide = 2048; // x-lines split over up to 4 warps (plane_wide.cu)
 constexpr int kMaxNy = 512;    // the plane's coefficient table (8 values per line of every 2D level) sits in shared memory
 constexpr int kMaxNz = 4096;
 
@@ -121,6 +122,8 @@ struct PlaneRelaxArgs {
     int MF;                       // 2D levels whose interior line factors are kept in shared memory
     int off_fs;                   // element offset of those factor sets in shared memory
     int vec;                      // 1: nx == 32 K and f, u, the workspace are 16-byte aligned
+                                  // (wide lines: nx % 8 == 0 and the same alignment)
+    int W;                        // x-line segments of 512 rows (1 unless nx > 512: plane_wide.cu)
 };
 
 // Placement of the per-plane 2D-cycle arrays: shared memory where they fit, else global.
@@ -140,9 +143,10 @@ inline int trifac_set_elems(int K) { return (2 + (K > 1 ? 4 * K - 5 : 0) + 13) *
 constexpr int kMaxFactorLevels = kMaxPlaneLevels;
 
 // K > 0 sizes the factor sets for that x-line chunk instead of the one nx implies; all_sets keeps
-// the factor sets of every 2D level in shared memory (the shortened-step kernel needs them).
+// the factor sets of every 2D level in shared memory (the shortened-step kernel needs them);
+// no_sets keeps none (the wide-line kernel factors its segments on the fly).
 PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int K = 0,
-                              bool all_sets = false);
+                              bool all_sets = false, bool no_sets = false);
 // Layout for a cluster of R CTAs per plane: each CTA holds the lines it owns (pairs (y/2) mod R)
 // of the arrays kept on chip; an array that does not fit lives whole in the cluster's global
 // slot.  smem_bytes = 0 when the coefficient table and factor sets alone exceed the budget.
@@ -181,6 +185,12 @@ bool lean_cluster_resident(Prec storage, int K, int R, int threads, size_t smem)
 // True when, on every plane of z-level l and every 2D level, the lines before the last share the
 // line matrix (S(y,y), T(y,y)) of line 0.
 bool lean_uniform_level(const HostHierarchy &H, int l);
+// Plane relaxation for nx > 512 (plane_wide.cu): x-lines cut into wide_segments(nx) segments of
+// 512 rows, one warp each, coupled through a reduced system; one CTA per plane (a.W segments).
+int wide_segments(int nx);
+cudaError_t launch_plane_wide(Prec storage, bool compute_f64, int nplanes, int nb, int threads,
+                              const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
+int set_plane_wide_smem(Prec storage, bool compute_f64, size_t smem);
 // True when a cluster of R CTAs of the plane kernel (FP64 or FP32 compute) can be resident.
 bool cluster_resident(Prec storage, bool compute_f64, int K, int R, int threads, size_t smem);
 

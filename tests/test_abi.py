@@ -46,7 +46,7 @@ def call_setup(smg, *args):
 
 
 @pytest.mark.parametrize("args", [(0, 4, 4, 1, 1), (4, 0, 4, 1, 1), (4, 4, 0, 1, 1), (4, 4, 4, 0, 1),
-                                  (4, 4, 4, 1, -1), (513, 4, 4, 1, 1), (4, 513, 4, 1, 1), (4, 4, 5000, 1, 1)])
+                                  (4, 4, 4, 1, -1), (2049, 4, 4, 1, 1), (4, 513, 4, 1, 1), (4, 4, 5000, 1, 1)])
 def test_setup_rejects_bad_arguments(smg, args):
     rc, h = call_setup(smg, *args)
     assert rc == smg.SMG_ERR_ARG
