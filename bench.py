@@ -912,15 +912,17 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
-BRICK_NS = (10, 16, 20, 32)
-BRICK_WORKLOAD = ("the paper's 16n x n x n bricks (long in x), n = 10, 16, 20, 32, 7-point Dirichlet Laplacian; "
-                  "FPCG-SMG(1,0) with the FP32 and the FP64 cycle timed, iteration counts of PCG eq. (1), FPCG eq. (2) "
-                  "and PSD with the (1,1) and (1,0) FP64 cycles; tol 1e-8")
+BRICK_NS = (10, 16, 20, 32, 48, 64, 80)
+BRICK_WORKLOAD = ("the paper's 16n x n x n bricks (long in x), n = 10, 16, 20, 32, 48, 64, 80, 7-point Dirichlet "
+                  "Laplacian; FPCG-SMG(1,0) with the FP32 and the FP64 cycle timed, iteration counts of PCG eq. (1), "
+                  "FPCG eq. (2) and PSD with the (1,1) and (1,0) FP64 cycles, and figure 5's residual histories "
+                  "((1,0) FP64 cycle) at n = 80; tol 1e-8")
 
 
 def run_bricks(args):
-    """The brick sweep of the paper's figures 4, 5 and 7 at the sizes whose x-lines a warp solves
-    (16n <= 512): the timed value is the FP32-cycle FPCG-SMG(1,0) solve of the largest brick."""
+    """The brick sweep of the paper's figures 4, 5 and 7 up to n = 80 (x-lines of 1280 rows, split
+    over three warps from n = 33 on): the timed value is the FP32-cycle FPCG-SMG(1,0) solve of the
+    largest brick."""
     import torch
 
     from paper_1212_6680_gb300 import build as _build
@@ -951,6 +953,8 @@ def run_bricks(args):
                 x.zero_()
                 rc, it, rr = smg.krylov_solve(h, v, b, x, TOL, 40, check=False)
                 row[f"{v}_{1}{npost}_iters"] = it if rc == smg.SMG_OK else f">40 (relres {rr:.1e})"
+                if npost == 0 and nb == BRICK_NS[-1]:
+                    row[f"{v}_10_history"] = [float(f"{v_:.3e}") for v_ in smg.smg_krylov_history(h)]
             smg.smg_destroy(h)
         for prec in ("fp32", "fp64"):
             h = smg.smg_setup(nx, ny, nz, 1, 0)
@@ -982,6 +986,22 @@ def run_bricks(args):
         dist.destroy_process_group()
     if rank != 0:
         return
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        nb = BRICK_NS[-1]
+        cores = os.cpu_count() or 1
+        oracle.set_threads(cores)
+        bo = inputs.rhs(16 * nb, nb, nb, seed=0)
+        t0 = time.perf_counter()
+        out = oracle.krylov(bo, "fpcg", oracle.SMG(16 * nb, nb, nb, 1, 0), tol=TOL, maxit=100)
+        tc = time.perf_counter() - t0
+        assert out["status"] == 0
+        cpu = {"value": tc, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"one full FPCG-SMG(1,0) solve of the n = {nb} brick in FP64 ({out['iters']} iterations, "
+                         f"set-up included) on {cores} host cores (OpenMP)"}
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -989,7 +1009,7 @@ def run_bricks(args):
         "config": {"workload": BRICK_WORKLOAD, "timed": f"FPCG-SMG(1,0), FP32 cycle, brick n = {BRICK_NS[-1]}",
                    "bricks": table, "l2": "256 MB buffer written before every timed solve",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "roofline": None, "cpu_baseline": cpu, "e2e": None,
         "gpu_launches": main_launches, "clocks": main_clk,
     }
     print(json.dumps(line), flush=True)
