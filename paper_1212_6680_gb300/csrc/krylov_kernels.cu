@@ -255,6 +255,218 @@ __global__ void k_update_xr(long long n, double *__restrict__ x, const double *_
     }
 }
 
+// ---- the same four kernels on 4-element chunks ---------------------------------------------------
+// Used when nx % 4 == 0 and every vector is 16-byte aligned: each thread moves four consecutive
+// elements of a vector with 16-byte loads and stores (the element values, the operations on them
+// and the order of the six neighbour terms of A p are those of the scalar kernels; only the
+// assignment of elements to threads, and so the partial sums' grouping, differs).
+__device__ __forceinline__ void ld4(double (&v)[4], const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+template <class S> __device__ __forceinline__ void lds4(double (&v)[4], const S *p);
+template <> __device__ __forceinline__ void lds4<double>(double (&v)[4], const double *p) { ld4(v, p); }
+template <> __device__ __forceinline__ void lds4<float>(double (&v)[4], const float *p) {
+    const float4 a = reinterpret_cast<const float4 *>(p)[0];
+    v[0] = widen_f32(a.x); v[1] = widen_f32(a.y); v[2] = widen_f32(a.z); v[3] = widen_f32(a.w);
+}
+template <> __device__ __forceinline__ void lds4<__nv_bfloat16>(double (&v)[4], const __nv_bfloat16 *p) {
+    const uint2 a = reinterpret_cast<const uint2 *>(p)[0];
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&a.x), hi = *reinterpret_cast<const __nv_bfloat162 *>(&a.y);
+    v[0] = widen_f32(__low2float(lo)); v[1] = widen_f32(__high2float(lo));
+    v[2] = widen_f32(__low2float(hi)); v[3] = widen_f32(__high2float(hi));
+}
+template <class S> __device__ __forceinline__ void sts4(S *p, const double (&v)[4]);
+template <> __device__ __forceinline__ void sts4<double>(double *p, const double (&v)[4]) { st4(p, v); }
+template <> __device__ __forceinline__ void sts4<float>(float *p, const double (&v)[4]) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(narrow_f64(v[0]), narrow_f64(v[1]), narrow_f64(v[2]), narrow_f64(v[3]));
+}
+template <> __device__ __forceinline__ void sts4<__nv_bfloat16>(__nv_bfloat16 *p, const double (&v)[4]) {
+    __nv_bfloat162 lo, hi;
+    lo.x = __float2bfloat16_rn(narrow_f64(v[0])); lo.y = __float2bfloat16_rn(narrow_f64(v[1]));
+    hi.x = __float2bfloat16_rn(narrow_f64(v[2])); hi.y = __float2bfloat16_rn(narrow_f64(v[3]));
+    uint2 a;
+    a.x = *reinterpret_cast<unsigned *>(&lo);
+    a.y = *reinterpret_cast<unsigned *>(&hi);
+    reinterpret_cast<uint2 *>(p)[0] = a;
+}
+
+template <class S>
+__global__ void k_dots_beta4(int nc, const S *__restrict__ s, const double *__restrict__ r,
+                             const double *__restrict__ dr, KrylovScalars *sc, DSum *part, unsigned *counter) {
+    pdl_trigger();
+    pdl_wait();
+    const int variant = sc->variant;
+    const bool need_sdr = (variant == 1) && (sc->restart == 0);
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll 2
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        double sv[4], rv[4];
+        lds4<S>(sv, s + 4 * c);
+        ld4(rv, r + 4 * c);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a0 = fma(sv[k], rv[k], a0);
+        if (need_sdr) {
+            double dv[4];
+            ld4(dv, dr + 4 * c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a1 = fma(sv[k], dv[k], a1);
+        }
+    }
+    double v[2] = {a0, a1};
+    double tot[2];
+    if (grid_reduce<2>(v, part, counter, tot) && threadIdx.x == 0) {
+        const double rho = tot[0];
+        double beta = 0.0;
+        if (sc->restart == 0 && variant != 2) {
+            if (sc->rho_prev == 0.0) {
+                sc->status = -4;
+            } else {
+                beta = (variant == 0) ? rho / sc->rho_prev : tot[1] / sc->rho_prev;
+            }
+        }
+        if (!isfinite(rho) || !isfinite(beta)) sc->status = -6;
+        sc->rho = rho;
+        sc->sdr = tot[1];
+        sc->beta = beta;
+    }
+}
+
+template <class S>
+__global__ void k_update_p4(int nc, const S *__restrict__ s, double *__restrict__ p, const KrylovScalars *sc) {
+    pdl_trigger();
+    pdl_wait();
+    const double beta = sc->beta;
+#pragma unroll 2
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        double sv[4], pv[4];
+        lds4<S>(sv, s + 4 * c);
+        if (beta == 0.0) {
+            st4(p + 4 * c, sv);
+        } else {
+            ld4(pv, p + 4 * c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pv[k] = fma(beta, pv[k], sv[k]);
+            st4(p + 4 * c, pv);
+        }
+    }
+}
+
+// q = A p on four consecutive points of an x-row (nx % 4 == 0), the neighbour terms summed in the
+// order of stencil7.
+__global__ void k_spmv_alpha4(int nx, int ny, int nz, const double *__restrict__ p, double *__restrict__ q,
+                              KrylovScalars *sc, DSum *part, unsigned *counter) {
+    pdl_trigger();
+    pdl_wait();
+    const int nq = nx >> 2, npi = nx * ny, nc = (npi >> 2) * nz;
+    double a0 = 0.0;
+#pragma unroll 2
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int row = c / nq, xq = c - row * nq;
+        const int zz = row / ny, yy = row - zz * ny, xx = 4 * xq;
+        const int i = 4 * c;
+        double pc[4], nb[4] = {0.0, 0.0, 0.0, 0.0};
+        ld4(pc, p + i);
+        const double pl = (xx > 0) ? p[i - 1] : 0.0, pr = (xx + 4 < nx) ? p[i + 4] : 0.0;
+        // x-1, x+1
+        if (xx > 0) nb[0] += pl;
+        nb[1] += pc[0];
+        nb[2] += pc[1];
+        nb[3] += pc[2];
+        nb[0] += pc[1];
+        nb[1] += pc[2];
+        nb[2] += pc[3];
+        if (xx + 4 < nx) nb[3] += pr;
+        double t[4];
+        if (yy > 0) {
+            ld4(t, p + i - nx);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) nb[k] += t[k];
+        }
+        if (yy < ny - 1) {
+            ld4(t, p + i + nx);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) nb[k] += t[k];
+        }
+        if (zz > 0) {
+            ld4(t, p + i - npi);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) nb[k] += t[k];
+        }
+        if (zz < nz - 1) {
+            ld4(t, p + i + npi);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) nb[k] += t[k];
+        }
+        double qv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            qv[k] = 6.0 * pc[k] - nb[k];
+            a0 = fma(pc[k], qv[k], a0);
+        }
+        st4(q + i, qv);
+    }
+    double v[1] = {a0};
+    double tot[1];
+    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        sc->pq = pq;
+        if (!(pq > 0.0)) {
+            sc->status = (pq == pq) ? -4 : -6;
+            sc->alpha = 0.0;
+        } else {
+            sc->alpha = sc->rho / pq;
+        }
+    }
+}
+
+template <class S>
+__global__ void k_update_xr4(int nc, double *__restrict__ x, const double *__restrict__ p, double *__restrict__ r,
+                             const double *__restrict__ q, double *__restrict__ dr, S *__restrict__ f0,
+                             KrylovScalars *sc, DSum *part, unsigned *counter) {
+    pdl_trigger();
+    pdl_wait();
+    const double alpha = sc->alpha;
+    const bool want_dr = (sc->variant == 1);
+    double a0 = 0.0;
+#pragma unroll 2
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int i = 4 * c;
+        double xv[4], pv[4], ro[4], qv[4], rn[4];
+        ld4(xv, x + i);
+        ld4(pv, p + i);
+        ld4(ro, r + i);
+        ld4(qv, q + i);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            xv[k] = fma(alpha, pv[k], xv[k]);
+            rn[k] = fma(-alpha, qv[k], ro[k]);
+            a0 = fma(rn[k], rn[k], a0);
+        }
+        st4(x + i, xv);
+        st4(r + i, rn);
+        if (want_dr) {
+            double dv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dv[k] = rn[k] - ro[k];
+            st4(dr + i, dv);
+        }
+        if (f0 != nullptr) sts4<S>(f0 + i, rn);
+    }
+    double v[1] = {a0};
+    double tot[1];
+    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->rho_prev = sc->rho;
+        sc->restart = 0;
+        if (!isfinite(tot[0])) sc->status = -6;
+    }
+}
+
 // ---- launchers --------------------------------------------------------------------------------
 // Grid of the reduction kernels, measured on GB300: while the Krylov vectors (about six of N
 // doubles) stay in the 129 MB L2, two 256-thread CTAs per SM (each thread sums tens of
@@ -264,6 +476,16 @@ __global__ void k_update_xr(long long n, double *__restrict__ x, const double *_
 int reduction_blocks(long long n) {
     long long b = (n + 256LL * 16 - 1) / (256LL * 16);
     const long long cap = (n <= (4LL << 20)) ? kReduceBlocks : kMaxReduceBlocks;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return static_cast<int>(b);
+}
+
+// Grid of the 4-element-chunk kernels: four 256-thread CTAs per SM (a thread handles a few chunks
+// at 128^3; the partials stay within the reduction buffer).
+int reduction_blocks4(long long n) {
+    long long b = (n / 4 + 255) / 256;
+    const long long cap = (n <= (4LL << 20)) ? 4 * 152 : kMaxReduceBlocks;
     if (b < 1) b = 1;
     if (b > cap) b = cap;
     return static_cast<int>(b);
@@ -297,6 +519,22 @@ cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void 
     const long long n = static_cast<long long>(nx) * ny * nz;
     const int nb = reduction_blocks(n);
     cudaError_t e = cudaSuccess;
+    auto al16 = [](const void *v) { return v == nullptr || (reinterpret_cast<uintptr_t>(v) & 15u) == 0; };
+    if (nx % 4 == 0 && al16(s) && al16(x) && al16(r) && al16(p) && al16(q) && al16(dr) && al16(f0)) {
+        const int nc = static_cast<int>(n / 4);
+        const int nb4 = reduction_blocks4(n);
+        SMG_PREC_SWITCH(st_prec, {
+            const S *sp = static_cast<const S *>(s);
+            S *f0p = static_cast<S *>(f0);
+            if (e == cudaSuccess) e = launch_pdl(k_dots_beta4<S>, dim3(nb4), dim3(256), 0, st, nc, sp, r, dr, w.sc, w.part, w.counter);
+            if (e == cudaSuccess) e = launch_pdl(k_update_p4<S>, dim3(nb4), dim3(256), 0, st, nc, sp, p, w.sc);
+            if (e == cudaSuccess)
+                e = launch_pdl(k_spmv_alpha4, dim3(nb4), dim3(256), 0, st, nx, ny, nz, p, q, w.sc, w.part, w.counter);
+            if (e == cudaSuccess)
+                e = launch_pdl(k_update_xr4<S>, dim3(nb4), dim3(256), 0, st, nc, x, p, r, q, dr, f0p, w.sc, w.part, w.counter);
+        });
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     SMG_PREC_SWITCH(st_prec, {
         const S *sp = static_cast<const S *>(s);
         S *f0p = static_cast<S *>(f0);
