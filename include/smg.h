@@ -68,10 +68,18 @@ enum {
                                  with nx <= 128 run the 2D cycle with fewer barrier-separated
                                  steps (the restriction fused with the next level's even lines;
                                  the same line solves in the same order); 0: the general kernel */
-    SMG_OPT_GRAM_TC = 7       /* lobpcg_solve's Gram products with both block widths >= value (and
+    SMG_OPT_GRAM_TC = 7,      /* lobpcg_solve's Gram products with both block widths >= value (and
                                  <= 64) run on the tensor cores (smg_gram's digit splitting); the
                                  others, and all of them with value 0, on the CUDA cores in
                                  double-float arithmetic (default 16) */
+    SMG_OPT_GRAPH = 8         /* 1 (default): krylov_solve runs its iterations as one CUDA graph
+                                 whose conditional while node repeats V-cycle + Krylov kernels on
+                                 the device until the recurrence residual meets tol, maxit is
+                                 reached or a breakdown is flagged (the host then checks the true
+                                 residual as in the host loop); the graph is rebuilt after any
+                                 option, precision or weight change and when x changes.  Not used
+                                 with the learned correction, pair capture or profiling.  0: the
+                                 host launches every iteration and reads the scalars after each */
 };
 
 /*

@@ -108,6 +108,23 @@ struct smg_ctx {
     std::vector<cudaEvent_t> event_pool;
     // relative recurrence residuals ||r_k|| / ||b|| of the last krylov_solve, k = 0 .. iters
     std::vector<double> hist;
+    double *d_hist = nullptr;       // device copy written by the x/r update (hist_cap entries)
+    int hist_cap = 0;
+    // Device-side solve loop (SMG_OPT_GRAPH): one CUDA graph whose conditional while node repeats
+    // V-cycle + Krylov tail until the recurrence residual meets tol, maxit is reached or a
+    // breakdown is flagged; rebuilt when anything that changes an iteration's launches changes.
+    int use_graph = 1;
+    long long gen = 0;              // bumped by every such change
+    struct SolveGraph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        long long gen = -1;
+        const double *x = nullptr;  // the iterate the graph's kernels update
+        bool ident = false;
+        long long body_launches = 0;
+    } sg;
+    cudaStream_t gs = nullptr;      // capture and launch stream of the graph
+    cudaEvent_t gev = nullptr;
     // LOBPCG state
     LobpcgWork lw;
     // learned post-correction (smg_set_learned) and training-pair capture (smg_collect_pairs)
@@ -126,6 +143,7 @@ struct smg_ctx {
 namespace {
 
 void free_levels(smg_ctx *h) {
+    h->gen += 1;
     for (void *p : h->d_f) cudaFree(p);
     for (void *p : h->d_u) cudaFree(p);
     h->d_f.clear();
@@ -487,47 +505,125 @@ int read_scalars(smg_ctx *h, cudaStream_t st) {
     return SMG_OK;
 }
 
+void drop_solve_graph(smg_ctx *h) {
+    if (h->sg.exec) cudaGraphExecDestroy(h->sg.exec);
+    if (h->sg.g) cudaGraphDestroy(h->sg.g);
+    h->sg = smg_ctx::SolveGraph();
+}
+
+// Build (or keep) the graph of the device-side solve loop: a conditional while node whose body is
+// one iteration -- the V-cycle s = T r (unless T = I) and the four Krylov kernels -- captured from
+// the same launch code as the host loop.  Returns false when the graph cannot be built (the host
+// loop is used then).
+bool ensure_solve_graph(smg_ctx *h, void *f0, void *u0, Prec kp, void *f0k, bool ident, double *x) {
+    if (h->sg.exec && h->sg.gen == h->gen && h->sg.x == x && h->sg.ident == ident) return true;
+    drop_solve_graph(h);
+    if (h->gs == nullptr && cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (h->gev == nullptr && cudaEventCreateWithFlags(&h->gev, cudaEventDisableTiming) != cudaSuccess) return false;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node;
+    bool ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    const long long l0 = h->launches;
+    if (ok) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(h->gs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            bool launched = ident || run_cycle(h, 1, f0, u0, h->gs) == SMG_OK;
+            launched = launched && kry_iteration_tail(kp, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr,
+                                                      f0k, h->kw, h->gs, cond, 1) == cudaSuccess;
+            h->launches += 4;
+            cudaGraph_t out = nullptr;
+            ok = (cudaStreamEndCapture(h->gs, &out) == cudaSuccess) && launched;
+        }
+    }
+    h->sg.body_launches = h->launches - l0;
+    h->launches = l0;
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        h->use_graph = 0;  // this handle falls back to the host loop for good
+        return false;
+    }
+    h->sg.g = g;
+    h->sg.exec = exec;
+    h->sg.gen = h->gen;
+    h->sg.x = x;
+    h->sg.ident = ident;
+    return true;
+}
+
 int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double tol, int maxit, int *iters,
                   double *relres, cudaStream_t st) {
     int rc;
     if ((rc = ensure_levels(h, 1)) != SMG_OK) return rc;
     if ((rc = ensure_krylov(h)) != SMG_OK) return rc;
+    if (h->hist_cap < maxit + 2) {
+        cudaFree(h->d_hist);
+        h->d_hist = nullptr;
+        h->hist_cap = 0;
+        SMG_CUDA(cudaMalloc(&h->d_hist, sizeof(double) * (maxit + 2)));
+        h->hist_cap = maxit + 2;
+    }
     const bool f64 = (h->prec == Prec::F64);
     const bool ident = (h->precond == 0);                           // T = I: s is r itself
     void *f0 = f64 ? static_cast<void *>(h->d_r) : h->d_f[0];     // cycle input  = (S) r
     void *u0 = ident ? static_cast<void *>(h->d_r) : h->d_u[0];   // s = T r
     const Prec kp = ident ? Prec::F64 : h->prec;                    // storage type of s
     void *f0k = (f64 || ident) ? nullptr : f0;                      // what the Krylov kernels write
+    const double tol2 = tol * tol;
+    // the device-side loop: not with the learned correction, training-pair capture or per-launch
+    // profiling (their host-side steps and events sit between the kernels of an iteration)
+    const bool graph = h->use_graph && !h->learned && h->cap.count >= h->cap.max && h->profile == 0 &&
+                       ensure_solve_graph(h, f0, u0, kp, f0k, ident, x);
+    cudaStream_t ls = st;  // the stream the solve runs on
+    if (graph) {
+        SMG_CUDA(cudaEventRecord(h->gev, st));
+        SMG_CUDA(cudaStreamWaitEvent(h->gs, h->gev, 0));
+        ls = h->gs;
+    }
     KrylovScalars init;
     std::memset(&init, 0, sizeof(init));
     init.variant = variant;
-    SMG_CUDA(cudaMemcpyAsync(h->kw.sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-    SMG_CUDA(kry_init_residual(kp, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+    init.maxit = maxit;
+    init.tol2 = tol2;
+    init.hist = h->d_hist;
+    SMG_CUDA(cudaMemcpyAsync(h->kw.sc, &init, sizeof(init), cudaMemcpyHostToDevice, ls));
+    SMG_CUDA(kry_init_residual(kp, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, ls));
     h->launches += 1;
-    const double tol2 = tol * tol;
     int k = 0, status = SMG_ERR_NOCONV;
     double tt = -1.0;
-    h->hist.clear();
-    for (k = 0;; ++k) {
-        if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
+    if ((rc = read_scalars(h, ls)) != SMG_OK) return rc;
+    h->hist.assign(1, std::sqrt(h->h_sc->rr / (h->h_sc->bb > 0.0 ? h->h_sc->bb : 1.0)));
+    for (;;) {
         const KrylovScalars &s = *h->h_sc;
-        h->hist.push_back(std::sqrt(s.rr / (s.bb > 0.0 ? s.bb : 1.0)));
         if (s.status != 0) {
             status = s.status;
             break;
         }
         const double bb = s.bb > 0.0 ? s.bb : 1.0;
         if (s.rr <= tol2 * bb) {
-            SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, st));
+            SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, ls));
             h->launches += 1;
-            if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
+            if ((rc = read_scalars(h, ls)) != SMG_OK) return rc;
             tt = h->h_sc->tt;
             if (tt <= tol2 * bb) {
                 status = SMG_OK;
                 break;
             }
             // continue from the true residual, with beta = 0 on the next step
-            SMG_CUDA(kry_init_residual(kp, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, st));
+            SMG_CUDA(kry_init_residual(kp, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, ls));
             h->launches += 1;
             tt = -1.0;
         }
@@ -535,33 +631,53 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
             status = SMG_ERR_NOCONV;
             break;
         }
-        if (!ident && (rc = run_cycle(h, 1, f0, u0, st)) != SMG_OK) return rc;
+        if (graph) {
+            // iterations until the recurrence residual meets tol, maxit or a breakdown
+            SMG_CUDA(cudaGraphLaunch(h->sg.exec, ls));
+            if ((rc = read_scalars(h, ls)) != SMG_OK) return rc;
+            h->launches += h->sg.body_launches * (h->h_sc->it - k);
+            k = h->h_sc->it;
+            continue;
+        }
+        if (!ident && (rc = run_cycle(h, 1, f0, u0, ls)) != SMG_OK) return rc;
         if (!ident && h->cap.count < h->cap.max) {
             // training pair of this iteration: rho = r - A s, e = x* - x - s
             const size_t off = static_cast<size_t>(h->cap.count) * h->N();
             SMG_CUDA(net_capture(h->prec, h->nx, h->ny, h->nz, h->d_r, u0, x, h->cap.xstar, h->cap.rho + off,
-                                 h->cap.e + off, st));
+                                 h->cap.e + off, ls));
             h->cap.count += 1;
             h->launches += 1;
         }
         if (!ident && h->learned) {
             // flops of the three convolutions (2 x 27 x (16 + 256 + 16) per point)
-            RegionTimer rt(h, st, 5, 2.0 * 27 * (16 + 256 + 16) * static_cast<double>(h->N()));
+            RegionTimer rt(h, ls, 5, 2.0 * 27 * (16 + 256 + 16) * static_cast<double>(h->N()));
             const long long l0 = h->nw.launches;
-            SMG_CUDA(net_learned_correct(h->nw, h->prec, h->nx, h->ny, h->nz, h->d_r, u0, st));
+            SMG_CUDA(net_learned_correct(h->nw, h->prec, h->nx, h->ny, h->nz, h->d_r, u0, ls));
             h->launches += h->nw.launches - l0;
         }
         {
-            RegionTimer rt(h, st, 4, 0.0);
-            SMG_CUDA(kry_iteration_tail(kp, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, st));
+            RegionTimer rt(h, ls, 4, 0.0);
+            SMG_CUDA(kry_iteration_tail(kp, h->nx, h->ny, h->nz, u0, x, h->d_r, h->d_p, h->d_q, h->d_dr, f0k, h->kw, ls));
         }
         h->launches += 4;
+        k += 1;
+        if ((rc = read_scalars(h, ls)) != SMG_OK) return rc;
     }
     if (tt < 0.0) {
-        SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, st));
+        SMG_CUDA(kry_true_residual(h->nx, h->ny, h->nz, b, x, h->kw, ls));
         h->launches += 1;
-        if ((rc = read_scalars(h, st)) != SMG_OK) return rc;
+        if ((rc = read_scalars(h, ls)) != SMG_OK) return rc;
         tt = h->h_sc->tt;
+    }
+    // the recurrence residuals of iterations 1 .. k, written on the device
+    h->hist.resize(static_cast<size_t>(k) + 1);
+    if (k > 0) {
+        SMG_CUDA(cudaMemcpyAsync(h->hist.data() + 1, h->d_hist + 1, sizeof(double) * k, cudaMemcpyDeviceToHost, ls));
+        SMG_CUDA(cudaStreamSynchronize(ls));
+    }
+    if (graph) {
+        SMG_CUDA(cudaEventRecord(h->gev, ls));
+        SMG_CUDA(cudaStreamWaitEvent(st, h->gev, 0));
     }
     const double bb = h->h_sc->bb > 0.0 ? h->h_sc->bb : 1.0;
     *iters = k;
@@ -625,12 +741,18 @@ int smg_set_precision(smg_handle h, int prec) {
     if (int rc = check_handle(h)) return rc;
     if (prec != SMG_FP64 && prec != SMG_FP32 && prec != SMG_BF16) return fail(SMG_ERR_ARG, "unknown precision");
     h->prec = static_cast<Prec>(prec);
+    h->gen += 1;
     return SMG_OK;
 }
 
 int smg_set_option(smg_handle h, int option, int value) {
     if (int rc = check_handle(h)) return rc;
+    h->gen += 1;
     switch (option) {
+    case SMG_OPT_GRAPH:
+        if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "graph must be 0 or 1");
+        h->use_graph = value;
+        return SMG_OK;
     case SMG_OPT_COARSE_ITERS:
         if (value < 1 || value > 64) return fail(SMG_ERR_ARG, "coarse_iters must be in [1, 64]");
         h->coarse_iters = value;
@@ -798,6 +920,7 @@ int smg_check_conversions(long long n, const double *src, int *mismatches, void 
 int smg_set_learned(smg_handle h, const void *weights_bf16, int enable) {
     if (int rc = check_handle(h)) return rc;
     if (enable != 0 && enable != 1) return fail(SMG_ERR_ARG, "enable must be 0 or 1");
+    h->gen += 1;
     if (!enable) {
         h->learned = false;
         return SMG_OK;
@@ -950,6 +1073,10 @@ int smg_destroy(smg_handle h) {
     for (auto e : h->event_pool) cudaEventDestroy(e);
     lobpcg_free(h->lw);
     net_free(h->nw);
+    drop_solve_graph(h);
+    if (h->gs) cudaStreamDestroy(h->gs);
+    if (h->gev) cudaEventDestroy(h->gev);
+    cudaFree(h->d_hist);
     delete h;
     return SMG_OK;
 }

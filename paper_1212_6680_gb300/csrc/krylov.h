@@ -22,7 +22,11 @@ struct KrylovScalars {
     int restart;      // 1: next beta = 0 (first step, or continuing from a true residual)
     int status;       // 0 or an SMG_ERR_* code raised on the device
     int variant;      // SMG_PCG, SMG_FPCG, SMG_PSD
+    int it;           // iterations done (the x/r update of each increments it)
+    int maxit;        // the solve's iteration limit
     int pad;
+    double tol2;      // tol^2: the device-side loop continues while rr > tol2 * bb
+    double *hist;     // when set: hist[it] = sqrt(rr / bb) after every x/r update
 };
 
 struct DSum;
@@ -39,7 +43,11 @@ cudaError_t kry_init_residual(Prec st_prec, int nx, int ny, int nz, const double
 cudaError_t kry_true_residual(int nx, int ny, int nz, const double *b, const double *x, KrylovWork &w,
                               cudaStream_t st);
 // One iteration after s = T r: dots + beta, p update, q = A p + alpha, x/r update + ||r||^2.
+// With use_cond, the x/r update's last CTA also sets the conditional node `cond` of the CUDA
+// graph that repeats the iteration: 1 (run another) while status == 0, rr > tol2 bb and
+// it < maxit, else 0.
 cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void *s, double *x, double *r, double *p,
-                               double *q, double *dr, void *f0, KrylovWork &w, cudaStream_t st);
+                               double *q, double *dr, void *f0, KrylovWork &w, cudaStream_t st,
+                               cudaGraphConditionalHandle cond = 0, int use_cond = 0);
 
 }  // namespace smg

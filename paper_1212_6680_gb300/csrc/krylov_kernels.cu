@@ -107,6 +107,24 @@ __device__ __forceinline__ double stencil7(const double *__restrict__ u, long lo
     return 6.0 * u[i] - nb;
 }
 
+// After the x/r update (last CTA, one thread): rr = ||r_new||^2, the iteration count, the residual
+// history and, inside the CUDA graph that repeats the iteration, its loop condition.
+__device__ __forceinline__ void finish_update(KrylovScalars *sc, double rr, cudaGraphConditionalHandle cond,
+                                              int use_cond) {
+    sc->rr = rr;
+    sc->rho_prev = sc->rho;
+    sc->restart = 0;
+    if (!isfinite(rr)) sc->status = -6;
+    const int it = sc->it + 1;
+    sc->it = it;
+    const double bb = sc->bb > 0.0 ? sc->bb : 1.0;
+    if (sc->hist != nullptr) sc->hist[it] = sqrt(rr / bb);
+    if (use_cond) {
+        const bool go = sc->status == 0 && !(rr <= sc->tol2 * bb) && it < sc->maxit;
+        cudaGraphSetConditional(cond, go ? 1u : 0u);
+    }
+}
+
 // r = b - A x ; f0 = (S) r ; rr = ||r||^2 ; bb = ||b||^2 ; restart = 1.
 template <class S>
 __global__ void k_init_residual(int nx, int ny, int nz, const double *__restrict__ b, const double *__restrict__ x,
@@ -229,7 +247,8 @@ __global__ void k_spmv_alpha(int nx, int ny, int nz, const double *__restrict__ 
 template <class S>
 __global__ void k_update_xr(long long n, double *__restrict__ x, const double *__restrict__ p, double *__restrict__ r,
                             const double *__restrict__ q, double *__restrict__ dr, S *__restrict__ f0,
-                            KrylovScalars *sc, DSum *part, unsigned *counter) {
+                            KrylovScalars *sc, DSum *part, unsigned *counter, cudaGraphConditionalHandle cond,
+                            int use_cond) {
     pdl_trigger();
     pdl_wait();
     const double alpha = sc->alpha;
@@ -247,12 +266,7 @@ __global__ void k_update_xr(long long n, double *__restrict__ x, const double *_
     }
     double v[1] = {a0};
     double tot[1];
-    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
-        sc->rr = tot[0];
-        sc->rho_prev = sc->rho;
-        sc->restart = 0;
-        if (!isfinite(tot[0])) sc->status = -6;
-    }
+    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) finish_update(sc, tot[0], cond, use_cond);
 }
 
 // ---- the same four kernels on 4-element chunks ---------------------------------------------------
@@ -427,7 +441,8 @@ __global__ void k_spmv_alpha4(int nx, int ny, int nz, const double *__restrict__
 template <class S>
 __global__ void k_update_xr4(int nc, double *__restrict__ x, const double *__restrict__ p, double *__restrict__ r,
                              const double *__restrict__ q, double *__restrict__ dr, S *__restrict__ f0,
-                             KrylovScalars *sc, DSum *part, unsigned *counter) {
+                             KrylovScalars *sc, DSum *part, unsigned *counter, cudaGraphConditionalHandle cond,
+                             int use_cond) {
     pdl_trigger();
     pdl_wait();
     const double alpha = sc->alpha;
@@ -459,12 +474,7 @@ __global__ void k_update_xr4(int nc, double *__restrict__ x, const double *__res
     }
     double v[1] = {a0};
     double tot[1];
-    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
-        sc->rr = tot[0];
-        sc->rho_prev = sc->rho;
-        sc->restart = 0;
-        if (!isfinite(tot[0])) sc->status = -6;
-    }
+    if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) finish_update(sc, tot[0], cond, use_cond);
 }
 
 // ---- launchers --------------------------------------------------------------------------------
@@ -515,7 +525,8 @@ cudaError_t kry_true_residual(int nx, int ny, int nz, const double *b, const dou
 }
 
 cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void *s, double *x, double *r, double *p,
-                               double *q, double *dr, void *f0, KrylovWork &w, cudaStream_t st) {
+                               double *q, double *dr, void *f0, KrylovWork &w, cudaStream_t st,
+                               cudaGraphConditionalHandle cond, int use_cond) {
     const long long n = static_cast<long long>(nx) * ny * nz;
     const int nb = reduction_blocks(n);
     cudaError_t e = cudaSuccess;
@@ -531,7 +542,8 @@ cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void 
             if (e == cudaSuccess)
                 e = launch_pdl(k_spmv_alpha4, dim3(nb4), dim3(256), 0, st, nx, ny, nz, p, q, w.sc, w.part, w.counter);
             if (e == cudaSuccess)
-                e = launch_pdl(k_update_xr4<S>, dim3(nb4), dim3(256), 0, st, nc, x, p, r, q, dr, f0p, w.sc, w.part, w.counter);
+                e = launch_pdl(k_update_xr4<S>, dim3(nb4), dim3(256), 0, st, nc, x, p, r, q, dr, f0p, w.sc, w.part, w.counter,
+                               cond, use_cond);
         });
         return e != cudaSuccess ? e : cudaGetLastError();
     }
@@ -543,7 +555,8 @@ cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void 
         if (e == cudaSuccess)
             e = launch_pdl(k_spmv_alpha, dim3(nb), dim3(256), 0, st, nx, ny, nz, p, q, w.sc, w.part, w.counter);
         if (e == cudaSuccess)
-            e = launch_pdl(k_update_xr<S>, dim3(nb), dim3(256), 0, st, n, x, p, r, q, dr, f0p, w.sc, w.part, w.counter);
+            e = launch_pdl(k_update_xr<S>, dim3(nb), dim3(256), 0, st, n, x, p, r, q, dr, f0p, w.sc, w.part, w.counter, cond,
+                           use_cond);
     });
     return e != cudaSuccess ? e : cudaGetLastError();
 }

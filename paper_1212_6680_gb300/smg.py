@@ -24,6 +24,7 @@ SMG_OPT_COARSE_ITERS, SMG_OPT_THREADS, SMG_OPT_PROFILE, SMG_OPT_CLUSTER_MAX, SMG
 SMG_OPT_PRECOND = 5
 SMG_OPT_LEAN = 6
 SMG_OPT_GRAM_TC = 7
+SMG_OPT_GRAPH = 8
 
 VARIANTS = {"pcg": SMG_PCG, "fpcg": SMG_FPCG, "psd": SMG_PSD}
 PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}
