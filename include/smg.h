@@ -72,7 +72,7 @@ enum {
                                  <= 64) run on the tensor cores (smg_gram's digit splitting); the
                                  others, and all of them with value 0, on the CUDA cores in
                                  double-float arithmetic (default 16) */
-    SMG_OPT_GRAPH = 8         /* 1 (default): krylov_solve runs its iterations as one CUDA graph
+    SMG_OPT_GRAPH = 8,        /* 1 (default): krylov_solve runs its iterations as one CUDA graph
                                  whose conditional while node repeats V-cycle + Krylov kernels on
                                  the device until the recurrence residual meets tol, maxit is
                                  reached or a breakdown is flagged (the host then checks the true
@@ -80,6 +80,14 @@ enum {
                                  option, precision or weight change and when x changes.  Not used
                                  with the learned correction, pair capture or profiling.  0: the
                                  host launches every iteration and reads the scalars after each */
+    SMG_OPT_FUSED_TAIL = 9    /* 1: the Krylov part of an iteration (Algorithm 1's dots, p update,
+                                 A p and x/r update) runs as one cooperative kernel with bounded
+                                 grid-wide barriers between its phases when its CTAs all fit on the
+                                 GPU (nx % 4 == 0, aligned vectors); bit-identical to 0 (default),
+                                 four kernels chained by programmatic dependent launch, which is
+                                 faster on GB300 (the barriers cost more than the kernel
+                                 boundaries).  A barrier wait that gives up returns SMG_ERR_TIMEOUT
+                                 from krylov_solve */
 };
 
 /*

@@ -494,6 +494,8 @@ int ensure_krylov(smg_ctx *h) {
     SMG_CUDA(cudaMalloc(&h->kw.part, sizeof(double) * 2 * 2 * kMaxReduceBlocks));
     SMG_CUDA(cudaMalloc(&h->kw.counter, sizeof(unsigned)));
     SMG_CUDA(cudaMemset(h->kw.counter, 0, sizeof(unsigned)));
+    SMG_CUDA(cudaMalloc(&h->kw.bar, 4 * sizeof(unsigned)));
+    SMG_CUDA(cudaMemset(h->kw.bar, 0, 4 * sizeof(unsigned)));
     SMG_CUDA(cudaMemset(h->kw.sc, 0, sizeof(KrylovScalars)));
     SMG_CUDA(cudaMallocHost(&h->h_sc, sizeof(KrylovScalars)));
     return SMG_OK;
@@ -600,6 +602,9 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
     init.tol2 = tol2;
     init.hist = h->d_hist;
     SMG_CUDA(cudaMemcpyAsync(h->kw.sc, &init, sizeof(init), cudaMemcpyHostToDevice, ls));
+    // reduction counter and grid-barrier words start clean (a wait that gave up leaves them set)
+    SMG_CUDA(cudaMemsetAsync(h->kw.counter, 0, sizeof(unsigned), ls));
+    SMG_CUDA(cudaMemsetAsync(h->kw.bar, 0, 4 * sizeof(unsigned), ls));
     SMG_CUDA(kry_init_residual(kp, h->nx, h->ny, h->nz, b, x, h->d_r, f0k, h->kw, ls));
     h->launches += 1;
     int k = 0, status = SMG_ERR_NOCONV;
@@ -685,6 +690,7 @@ int krylov_device(smg_ctx *h, int variant, const double *b, double *x, double to
     if (status == SMG_ERR_NOCONV) return fail(SMG_ERR_NOCONV, "maximum number of iterations reached");
     if (status == SMG_ERR_BREAKDOWN) return fail(status, "breakdown: (p, Ap) <= 0 or (s_{k-1}, r_{k-1}) = 0");
     if (status == SMG_ERR_NAN) return fail(status, "NaN or Inf in a residual norm or inner product");
+    if (status == SMG_ERR_TIMEOUT) return fail(status, "a grid-barrier wait of the Krylov kernel gave up");
     return status;
 }
 
@@ -752,6 +758,10 @@ int smg_set_option(smg_handle h, int option, int value) {
     case SMG_OPT_GRAPH:
         if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "graph must be 0 or 1");
         h->use_graph = value;
+        return SMG_OK;
+    case SMG_OPT_FUSED_TAIL:
+        if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "fused_tail must be 0 or 1");
+        h->kw.fused = value != 0;
         return SMG_OK;
     case SMG_OPT_COARSE_ITERS:
         if (value < 1 || value > 64) return fail(SMG_ERR_ARG, "coarse_iters must be in [1, 64]");
@@ -1065,6 +1075,7 @@ int smg_destroy(smg_handle h) {
     cudaFree(h->kw.sc);
     cudaFree(h->kw.part);
     cudaFree(h->kw.counter);
+    cudaFree(h->kw.bar);
     if (h->h_sc) cudaFreeHost(h->h_sc);
     for (auto &p : h->pending) {
         cudaEventDestroy(p.a);

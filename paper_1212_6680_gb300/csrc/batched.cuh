@@ -11,40 +11,11 @@
 
 #include "../../include/smg.h"
 #include "batched.h"
+#include "grid_sync.cuh"
 #include "plane_relax.cuh"
 #include "transfer.cuh"
 
 namespace smg {
-
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, int *err, long long limit,
-                                             unsigned expected) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned g = *reinterpret_cast<volatile unsigned *>(gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == expected - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*reinterpret_cast<volatile unsigned *>(gen) == g) {
-                if (*reinterpret_cast<volatile int *>(err) != 0) break;
-                if (++spins > limit) {
-                    atomicCAS(err, 0, SMG_ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        ok = (*reinterpret_cast<volatile int *>(err) == 0);
-    }
-    __syncthreads();
-    return ok != 0;
-}
 
 template <class S, int K>
 __global__ void __launch_bounds__(512, 1) persistent_vcycle_kernel(const __grid_constant__ PersistArgs p) {

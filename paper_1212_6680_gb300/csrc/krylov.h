@@ -35,6 +35,8 @@ struct KrylovWork {
     KrylovScalars *sc = nullptr;   // device
     DSum *part = nullptr;          // device, kMaxReduceBlocks * 2 partial sums
     unsigned *counter = nullptr;   // device, 1 counter (reset by the last block)
+    unsigned *bar = nullptr;       // device, grid-barrier count and generation, then an error word
+    bool fused = false;            // the iteration tail as one cooperative kernel where it fits
 };
 
 int reduction_blocks(long long n);

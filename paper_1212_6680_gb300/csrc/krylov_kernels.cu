@@ -11,6 +11,7 @@
 // (FP64, FP32 or BF16): widening it to FP64 is exact, so no FP64 copy of s is made.
 #include <cuda_bf16.h>
 
+#include "grid_sync.cuh"
 #include "krylov.h"
 #include "plane_relax.cuh"
 
@@ -477,6 +478,203 @@ __global__ void k_update_xr4(int nc, double *__restrict__ x, const double *__res
     if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) finish_update(sc, tot[0], cond, use_cond);
 }
 
+// ---- the four kernels above as one cooperative kernel ---------------------------------------------
+// The iteration tail with three grid-wide barriers in place of three kernel boundaries: dots and
+// beta | p update | q = A p and alpha | x, r update.  Same grid, same 4-element chunks per thread
+// and the same last-CTA reductions as the separate kernels, so every value (partial sums
+// included) is bit-identical to theirs.  Neighbour values of p are written by other CTAs in the
+// p phase, so the stencil phase reads p through L2 (ld.global.cg).
+__device__ __forceinline__ void ld4cg(double (&v)[4], const double *p) {
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_tail_fused(int nx, int ny, int nz, const S *__restrict__ s, double *x,
+                                                    double *r, double *p, double *q, double *dr, S *f0,
+                                                    KrylovScalars *sc, DSum *part, unsigned *counter, unsigned *bar,
+                                                    long long spin_limit, cudaGraphConditionalHandle cond,
+                                                    int use_cond) {
+    const int nq = nx >> 2, npi = nx * ny, nc = (npi >> 2) * nz;
+    const int stride = gridDim.x * blockDim.x, c0 = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned *bcount = bar, *bgen = bar + 1;
+    int *berr = reinterpret_cast<int *>(bar + 2);
+    const unsigned nblk = gridDim.x;
+    // A barrier wait that gave up ends this launch and stops the solve: the first CTA to see it
+    // records SMG_ERR_TIMEOUT and ends the graph's loop (no x/r update completes then, so nothing
+    // else sets the loop condition in this launch).
+    auto give_up = [&]() {
+        if (threadIdx.x == 0 && atomicCAS(bar + 3, 0u, 1u) == 0u) {
+            sc->status = SMG_ERR_TIMEOUT;
+            if (use_cond) cudaGraphSetConditional(cond, 0u);
+        }
+    };
+    if (*reinterpret_cast<volatile int *>(berr) != 0) {  // an earlier launch of this solve gave up
+        give_up();
+        return;
+    }
+    // ---- rho = (s, r), sdr = (s, r - r_prev); beta ----
+    {
+        const int variant = sc->variant;
+        const bool need_sdr = (variant == 1) && (sc->restart == 0);
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll 2
+        for (int c = c0; c < nc; c += stride) {
+            double sv[4], rv[4];
+            lds4<S>(sv, s + 4 * c);
+            ld4(rv, r + 4 * c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a0 = fma(sv[k], rv[k], a0);
+            if (need_sdr) {
+                double dv[4];
+                ld4(dv, dr + 4 * c);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a1 = fma(sv[k], dv[k], a1);
+            }
+        }
+        double v[2] = {a0, a1};
+        double tot[2];
+        if (grid_reduce<2>(v, part, counter, tot) && threadIdx.x == 0) {
+            const double rho = tot[0];
+            double beta = 0.0;
+            if (sc->restart == 0 && variant != 2) {
+                if (sc->rho_prev == 0.0) {
+                    sc->status = -4;
+                } else {
+                    beta = (variant == 0) ? rho / sc->rho_prev : tot[1] / sc->rho_prev;
+                }
+            }
+            if (!isfinite(rho) || !isfinite(beta)) sc->status = -6;
+            sc->rho = rho;
+            sc->sdr = tot[1];
+            sc->beta = beta;
+        }
+    }
+    if (!grid_barrier(bcount, bgen, berr, spin_limit, nblk)) {
+        give_up();
+        return;
+    }
+    // ---- p = s + beta p ----
+    {
+        const double beta = __ldcg(&sc->beta);
+#pragma unroll 2
+        for (int c = c0; c < nc; c += stride) {
+            double sv[4], pv[4];
+            lds4<S>(sv, s + 4 * c);
+            if (beta == 0.0) {
+                st4(p + 4 * c, sv);
+            } else {
+                ld4(pv, p + 4 * c);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pv[k] = fma(beta, pv[k], sv[k]);
+                st4(p + 4 * c, pv);
+            }
+        }
+    }
+    if (!grid_barrier(bcount, bgen, berr, spin_limit, nblk)) {
+        give_up();
+        return;
+    }
+    // ---- q = A p, pq = (p, q), alpha ----
+    {
+        double a0 = 0.0;
+#pragma unroll 2
+        for (int c = c0; c < nc; c += stride) {
+            const int row = c / nq, xq = c - row * nq;
+            const int zz = row / ny, yy = row - zz * ny, xx = 4 * xq;
+            const int i = 4 * c;
+            double pc[4], nb[4] = {0.0, 0.0, 0.0, 0.0};
+            ld4cg(pc, p + i);
+            const double pl = (xx > 0) ? __ldcg(p + i - 1) : 0.0, pr = (xx + 4 < nx) ? __ldcg(p + i + 4) : 0.0;
+            if (xx > 0) nb[0] += pl;
+            nb[1] += pc[0];
+            nb[2] += pc[1];
+            nb[3] += pc[2];
+            nb[0] += pc[1];
+            nb[1] += pc[2];
+            nb[2] += pc[3];
+            if (xx + 4 < nx) nb[3] += pr;
+            double t[4];
+            if (yy > 0) {
+                ld4cg(t, p + i - nx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nb[k] += t[k];
+            }
+            if (yy < ny - 1) {
+                ld4cg(t, p + i + nx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nb[k] += t[k];
+            }
+            if (zz > 0) {
+                ld4cg(t, p + i - npi);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nb[k] += t[k];
+            }
+            if (zz < nz - 1) {
+                ld4cg(t, p + i + npi);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nb[k] += t[k];
+            }
+            double qv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                qv[k] = 6.0 * pc[k] - nb[k];
+                a0 = fma(pc[k], qv[k], a0);
+            }
+            st4(q + i, qv);
+        }
+        double v[1] = {a0};
+        double tot[1];
+        if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) {
+            const double pq = tot[0];
+            sc->pq = pq;
+            if (!(pq > 0.0)) {
+                sc->status = (pq == pq) ? -4 : -6;
+                sc->alpha = 0.0;
+            } else {
+                sc->alpha = sc->rho / pq;
+            }
+        }
+    }
+    if (!grid_barrier(bcount, bgen, berr, spin_limit, nblk)) {
+        give_up();
+        return;
+    }
+    // ---- x += alpha p, r_new = r - alpha q, dr, f0 = (S) r_new, rr ----
+    {
+        const double alpha = __ldcg(&sc->alpha);
+        const bool want_dr = (sc->variant == 1);
+        double a0 = 0.0;
+#pragma unroll 2
+        for (int c = c0; c < nc; c += stride) {
+            const int i = 4 * c;
+            double xv[4], pv[4], ro[4], qv[4], rn[4];
+            ld4(xv, x + i);
+            ld4(pv, p + i);
+            ld4(ro, r + i);
+            ld4(qv, q + i);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                xv[k] = fma(alpha, pv[k], xv[k]);
+                rn[k] = fma(-alpha, qv[k], ro[k]);
+                a0 = fma(rn[k], rn[k], a0);
+            }
+            st4(x + i, xv);
+            st4(r + i, rn);
+            if (want_dr) {
+                double dv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dv[k] = rn[k] - ro[k];
+                st4(dr + i, dv);
+            }
+            if (f0 != nullptr) sts4<S>(f0 + i, rn);
+        }
+        double v[1] = {a0};
+        double tot[1];
+        if (grid_reduce<1>(v, part, counter, tot) && threadIdx.x == 0) finish_update(sc, tot[0], cond, use_cond);
+    }
+}
+
 // ---- launchers --------------------------------------------------------------------------------
 // Grid of the reduction kernels, measured on GB300: while the Krylov vectors (about six of N
 // doubles) stay in the 129 MB L2, two 256-thread CTAs per SM (each thread sums tens of
@@ -499,6 +697,28 @@ int reduction_blocks4(long long n) {
     if (b < 1) b = 1;
     if (b > cap) b = cap;
     return static_cast<int>(b);
+}
+
+// Polls of a grid-barrier wait in the fused tail before it gives up (about a second).
+constexpr long long kTailSpinLimit = 10000000;
+
+// True when nb CTAs of the fused tail can all be resident on this device (cached per device).
+template <class S>
+bool fused_tail_fits(int nb) {
+    static int per_sm[64] = {0};
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (per_sm[dev] == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tail_fused<S>, 256, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        per_sm[dev] = b > 0 ? b : -1;
+    }
+    return per_sm[dev] > 0 && static_cast<long long>(per_sm[dev]) * sms[dev] >= nb;
 }
 
 #define SMG_PREC_SWITCH(storage, ...)                               \
@@ -537,6 +757,21 @@ cudaError_t kry_iteration_tail(Prec st_prec, int nx, int ny, int nz, const void 
         SMG_PREC_SWITCH(st_prec, {
             const S *sp = static_cast<const S *>(s);
             S *f0p = static_cast<S *>(f0);
+            if (w.fused && w.bar != nullptr && fused_tail_fits<S>(nb4)) {
+                // one cooperative launch: the runtime refuses it unless every CTA is resident
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(nb4);
+                cfg.blockDim = dim3(256);
+                cfg.stream = st;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeCooperative;
+                attr[0].val.cooperative = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                e = cudaLaunchKernelEx(&cfg, k_tail_fused<S>, nx, ny, nz, sp, x, r, p, q, dr, f0p, w.sc, w.part, w.counter,
+                                       w.bar, static_cast<long long>(kTailSpinLimit), cond, use_cond);
+                return e != cudaSuccess ? e : cudaGetLastError();
+            }
             if (e == cudaSuccess) e = launch_pdl(k_dots_beta4<S>, dim3(nb4), dim3(256), 0, st, nc, sp, r, dr, w.sc, w.part, w.counter);
             if (e == cudaSuccess) e = launch_pdl(k_update_p4<S>, dim3(nb4), dim3(256), 0, st, nc, sp, p, w.sc);
             if (e == cudaSuccess)

@@ -24,7 +24,7 @@ def smg():
     return m
 
 
-def solve(smg, shape, variant, prec, graph, maxit=40, npost=0, precond=1, x_new=False):
+def solve(smg, shape, variant, prec, graph, maxit=40, npost=0, precond=1, x_new=False, fused=1):
     nx, ny, nz = shape
     b = torch.from_numpy(inputs.rhs(nx, ny, nz, seed=3).ravel().copy()).cuda()
     h = smg.smg_setup(nx, ny, nz, 1, npost)
@@ -32,6 +32,7 @@ def solve(smg, shape, variant, prec, graph, maxit=40, npost=0, precond=1, x_new=
         smg.smg_set_precision(h, prec)
         smg.smg_set_option(h, smg.SMG_OPT_GRAPH, graph)
         smg.smg_set_option(h, smg.SMG_OPT_PRECOND, precond)
+        smg.smg_set_option(h, smg.SMG_OPT_FUSED_TAIL, fused)
         x = torch.zeros_like(b)
         out = []
         for rep in range(2):  # a second solve on the same handle (the graph is reused or rebuilt)
@@ -84,3 +85,21 @@ def test_device_loop_wide_lines_and_no_preconditioner(smg, precond):
     g = solve(smg, (600, 10, 8), "fpcg", "fp32", 1, precond=precond, maxit=60)
     h = solve(smg, (600, 10, 8), "fpcg", "fp32", 0, precond=precond, maxit=60)
     same(g, h)
+
+
+@pytest.mark.parametrize("variant", ["pcg", "fpcg", "psd"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_fused_krylov_tail_is_bitwise_the_four_kernels(smg, variant, prec, graph):
+    """SMG_OPT_FUSED_TAIL: the iteration's Krylov part as one cooperative kernel with grid-wide
+    barriers gives the same bits as the four separate kernels (same grid, chunks and reductions)."""
+    f = solve(smg, (40, 36, 32), variant, prec, graph, fused=1)
+    u = solve(smg, (40, 36, 32), variant, prec, graph, fused=0)
+    same(f, u)
+
+
+def test_fused_krylov_tail_128cube(smg):
+    f = solve(smg, (128, 128, 128), "fpcg", "fp32", 1, fused=1)
+    u = solve(smg, (128, 128, 128), "fpcg", "fp32", 1, fused=0)
+    same(f, u)
+    assert f[0][0] == smg.SMG_OK
