@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the 256^3 learned-correction comparison")
     ap.add_argument("--workload", choices=["fpcg128", "batched64", "lobpcg128", "learned256", "bricks", "cg128",
                                            "lobpcg_bricks"],
                     default="fpcg128",
@@ -348,12 +349,10 @@ def run_ours(args):
         handles[prec] = h
     h32 = handles["fp32"]
 
-    # ---- main arm: FP32 cycle, device buffers; level-0 plane-relaxation launches timed ----
+    # ---- main arm: FP32 cycle, device buffers, the device-side solve loop (one CUDA graph) ----
     for _ in range(args.warmup):
         x.zero_()
         smg.krylov_solve(h32, "fpcg", b, x, TOL, 100)
-    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 1)
-    smg.smg_profile_read(h32, 0)
     l0 = smg.smg_launch_count(h32)
     barrier()
     wall0 = time.perf_counter()
@@ -361,10 +360,21 @@ def run_ours(args):
         times, iters, relres = timed_solves(h32, args.steps, 0)
     wall = time.perf_counter() - wall0
     launches = smg.smg_launch_count(h32) - l0
-    pl, pms, pbytes = smg.smg_profile_read(h32, 0)
-    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 0)
     t_step = statistics.mean(times)
     t_max = max_over_ranks(t_step, dist, "cuda")
+    # ---- the finest level's plane-relaxation launches timed with CUDA events on the launching
+    # stream, in solves run right after the timed region (per-launch events cannot sit inside the
+    # graph, so these solves take the host loop) ----
+    kp = max(1, min(args.steps, 3))
+    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 1)
+    smg.smg_profile_read(h32, 0)
+    tprof, _, _ = timed_solves(h32, kp, 0)
+    pl, pms, pbytes = smg.smg_profile_read(h32, 0)
+    smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 0)
+    # ---- host loop without profiling, for comparison with the device-side loop ----
+    smg.smg_set_option(h32, smg.SMG_OPT_GRAPH, 0)
+    thost, _, _ = timed_solves(h32, kp, 1)
+    smg.smg_set_option(h32, smg.SMG_OPT_GRAPH, 1)
 
     # ---- every plane-relaxation launch of one solve timed (all z-levels, the FP64 coarsest plane) ----
     smg.smg_set_option(h32, smg.SMG_OPT_PROFILE, 2)
@@ -383,6 +393,8 @@ def run_ours(args):
 
     for h in handles.values():
         smg.smg_destroy(h)
+    # ---- the learned post-correction at 256^3 against the plain cycles (stored, GPU-trained weights) ----
+    learned256 = None if args.no_learned else learned_comparison(smg, inputs, barrier, flush, stream, k2)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -397,6 +409,9 @@ def run_ours(args):
                 "kernel": "plane_lean_kernel<float,float,4,false> (finest level)",
                 "launches": pl, "avg_launch_us": (pms * 1e3 / pl) if pl else None,
                 "algorithmic_bytes_per_launch": (pbytes / pl) if pl else None,
+                "duration_source": f"CUDA events around every finest-level launch on the launching stream, in {kp} "
+                                   f"solves right after the timed region (the timed solves run as one CUDA graph, "
+                                   f"which cannot hold the events)",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s"}
     # the same ratio over every plane-relaxation launch of a solve (all z-levels, FP32, and the FP64
@@ -426,12 +441,51 @@ def run_ours(args):
                    "fp64_cycle_s": statistics.mean(t64), "fp64_cycle_iters": it64,
                    "bf16_cycle_s": statistics.mean(t16), "bf16_cycle_iters": it16,
                    "speedup_fp32_vs_fp64": statistics.mean(t64) / t_step,
-                   "cycle_classes_profiled_solve": classes},
+                   "host_loop_s": statistics.mean(thost), "profiled_solve_s": statistics.mean(tprof),
+                   "cycle_classes_profiled_solve": classes,
+                   "learned256": learned256},
         "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": statistics.mean(te), "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)
+
+
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_1212_6680_gb300", "weights", "learned_fpcg_seed5000.npz")
+
+
+def learned_comparison(smg, inputs, barrier, flush, stream, steps):
+    """FPCG at 256^3 with the learned post-correction (weights written by learned.train, recipe stored
+    beside them) against the plain FP32 (1,0) and (1,1) cycles and the FP64 (1,0) cycle."""
+    import torch
+
+    from paper_1212_6680_gb300 import learned
+
+    w, recipe = learned.load_weights(LEARNED_WEIGHTS)
+    b = torch.from_numpy(inputs.rhs(LN, LN, LN, seed=0).ravel().copy()).cuda()
+    x = torch.zeros_like(b)
+    out = {"workload": "FPCG to 1e-8 at 256^3 (7-point Dirichlet Laplacian, rhs seed 0), L2 flushed before every "
+                       "timed solve",
+           "weights": {"file": os.path.relpath(LEARNED_WEIGHTS, ROOT),
+                       **{k: recipe.get(k) for k in ("nsys", "sides", "seed", "init_seed", "epochs", "lr", "act", "pairs")}}}
+    for name, npost, prec, use_w in (("learned_10_fp32", 0, "fp32", True), ("plain_10_fp32", 0, "fp32", False),
+                                     ("balanced_11_fp32", 1, "fp32", False), ("plain_10_fp64", 0, "fp64", False)):
+        h = smg.smg_setup(LN, LN, LN, 1, npost)
+        smg.smg_set_precision(h, prec)
+        if use_w:
+            smg.smg_set_learned(h, w)
+
+        def once():
+            x.zero_()
+            rc, it, res = smg.krylov_solve(h, "fpcg", b, x, TOL, 100)
+            assert rc == smg.SMG_OK and res <= TOL, (rc, res)
+            return it
+        times, it = _timed(once, steps, 1, barrier, flush, stream)
+        out[name] = {"s": statistics.mean(times), "iters": it}
+        smg.smg_destroy(h)
+    out["speedup_learned_vs_plain_10"] = out["plain_10_fp32"]["s"] / out["learned_10_fp32"]["s"]
+    out["speedup_learned_vs_fp64"] = out["plain_10_fp64"]["s"] / out["learned_10_fp32"]["s"]
+    return out
 
 
 def run_batched(args):

@@ -58,3 +58,18 @@ def train(nsys=200, lo=64, hi=128, epochs=4, lr=1e-3, seed=5000, init_seed=77, a
     info.update({"collect_s": t1 - t0, "train_s": t2 - t1, "epochs": epochs, "lr": lr, "loss_per_epoch": hist.tolist(),
                  "sides": [lo, hi], "act": act})
     return w, info
+
+
+def save_weights(path: str, w, info: dict) -> None:
+    """Store FP32 weights and their training recipe (the info dict of `train`) in one .npz file."""
+    import json
+
+    np.savez(path, w=np.asarray(w, dtype=np.float32), info=np.array(json.dumps(info)))
+
+
+def load_weights(path: str):
+    """Returns (FP32 weights, recipe dict) stored by `save_weights`."""
+    import json
+
+    with np.load(path) as z:
+        return z["w"].astype(np.float32), json.loads(str(z["info"]))
