@@ -169,11 +169,12 @@ def batched_inputs():
 
 
 def oracle_batched_sample(nsample):
-    """Oracle FPCG-SMG(1,0) solves of the first `nsample` systems; seconds scaled to all 64 by
-    the unknowns they hold."""
+    """Oracle FPCG-SMG(1,0) solves of the first `nsample` systems on every host core; seconds
+    scaled to all 64 by the unknowns they hold (no scaling when nsample = 64)."""
     import oracle
 
     oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
     dims, bs = batched_inputs()
     t0 = time.perf_counter()
     its = []
@@ -228,40 +229,45 @@ def run_reference(args):
                 from oracle import lobpcg as olob
 
                 oracle.build()
+                oracle.set_threads(os.cpu_count() or 1)
                 X0 = _in.initial_block(NX, NY, NZ, LOB_M, seed=7)
                 t0 = time.perf_counter()
                 olob.lobpcg((NZ, NY, NX), np.ascontiguousarray(X0.T), oracle.SMG(NX, NY, NZ, 1, 0), tol=TOL, maxit=1)
                 t1 = time.perf_counter() - t0
-                times.append(t1 * 20)
-                sample = f"oracle LOBPCG set-up + 1 iteration at 128^3, m=16 ({t1:.1f} s) x 20 iterations"
+                times.append(t1 * 37)
+                sample = (f"extrapolated: oracle LOBPCG set-up + 1 iteration at 128^3, m=16 ({t1:.1f} s) x 37 "
+                          f"iterations, {os.cpu_count() or 1} host cores")
             else:
                 v, t1 = oracle_learned_sample(_in.net_init_weights(seed=77), 9)
                 times.append(v)
-                sample = (f"one oracle application of the learned preconditioner at 64^3 ({t1:.1f} s) x 64 points "
-                          f"x 9 iterations")
+                sample = (f"extrapolated: one oracle application of the learned preconditioner at 64^3 ({t1:.1f} s) "
+                          f"x 64 points x 9 iterations, {os.cpu_count() or 1} host cores (OpenMP in the SMG cycle; "
+                          f"the network's convolutions on one core)")
         v = statistics.mean(times)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": (LOB_WORKLOAD if args.workload == "lobpcg128" else LEARNED_WORKLOAD)
                            + " (FP64 CPU oracle, bounded sample)"},
-                "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+                "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                                 "sample": sample},
                 "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
     if args.workload == "batched64":
         times = []
         for _ in range(args.steps):
-            v, its, raw = oracle_batched_sample(4)
+            v, its, raw = oracle_batched_sample(NSYS)
             times.append(v)
         v = statistics.mean(times)
-        sample = (f"oracle FPCG-SMG(1,0) solves of systems 0-3 of the 64 ({raw:.1f} s, iterations {its}), "
-                  "scaled to all 64 by unknowns, single thread")
+        sample = (f"oracle FPCG-SMG(1,0) solves of all 64 systems one after another ({raw:.1f} s), "
+                  f"{os.cpu_count() or 1} host cores (OpenMP)")
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": BATCH_WORKLOAD.replace("V-cycle FP32, Krylov FP64", "FP64 CPU oracle")},
-                "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+                "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                                 "sample": sample},
                 "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -613,10 +619,10 @@ def run_batched(args):
                 "fallback 6.8 TB/s"}
     cpu = None
     if not args.no_cpu_baseline:
-        v, its_o, raw = oracle_batched_sample(4)
-        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle FPCG-SMG(1,0) solves of systems 0-3 ({raw:.1f} s, iterations {its_o}), "
-                         f"scaled to all 64 by unknowns, single thread"}
+        v, its_o, raw = oracle_batched_sample(NSYS)
+        cpu = {"value": v, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"oracle FPCG-SMG(1,0) solves of all 64 systems one after another (iterations "
+                         f"{min(its_o)}-{max(its_o)}), {os.cpu_count() or 1} host cores (OpenMP)"}
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -784,7 +790,7 @@ def run_lobpcg(args):
     achieved = (pbytes / 1e9) / (pms / 1e3) if pms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "plane_relax_kernel<float,float,4> (finest level, 16 vectors per launch)",
+                "kernel": "plane_lean_kernel<float,float,4,false> (finest level, 16 vectors per launch)",
                 "launches": pl, "avg_launch_us": (pms * 1e3 / pl) if pl else None,
                 "algorithmic_bytes_per_launch": (pbytes / pl) if pl else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
@@ -794,13 +800,14 @@ def run_lobpcg(args):
         from oracle import lobpcg as olob
 
         oracle.build()
+        oracle.set_threads(os.cpu_count() or 1)
         T = oracle.SMG(NX, NY, NZ, 1, 0)
         t0 = time.perf_counter()
         olob.lobpcg((NZ, NY, NX), np.ascontiguousarray(X0.T), T, tol=TOL, maxit=1)
         t1 = time.perf_counter() - t0
-        cpu = {"value": t1 * max(main["iters"], 1), "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle LOBPCG set-up + 1 iteration at 128^3, m=16 ({t1:.1f} s), scaled by the GPU's "
-                         f"{main['iters']} iterations, single thread"}
+        cpu = {"value": t1 * max(main["iters"], 1), "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"extrapolated: oracle LOBPCG set-up + 1 iteration at 128^3, m=16 ({t1:.1f} s), scaled by "
+                         f"the GPU's {main['iters']} iterations, {os.cpu_count() or 1} host cores (OpenMP)"}
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -833,6 +840,7 @@ def oracle_learned_sample(w, iters):
     from paper_1212_6680_gb300 import inputs
 
     oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
     T = oracle.SMG(64, 64, 64, 1, 0)
     T.set_learned(np.asarray(w, dtype=np.float64))
     r = inputs.rhs(64, 64, 64, seed=0)
@@ -941,10 +949,11 @@ def run_learned(args):
     cpu = None
     if not args.no_cpu_baseline:
         v, t1 = oracle_learned_sample(w, main["iters"])
-        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle application of the learned preconditioner at 64^3 ({t1:.1f} s), scaled by "
-                         f"64x the points and the GPU's {main['iters']} iterations (Krylov work not included), "
-                         f"single thread"}
+        cpu = {"value": v, "unit": "s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"extrapolated: one oracle application of the learned preconditioner at 64^3 ({t1:.1f} s), "
+                         f"scaled by 64x the points and the GPU's {main['iters']} iterations (Krylov work not "
+                         f"included), {os.cpu_count() or 1} host cores (OpenMP in the SMG cycle; the network's "
+                         f"convolutions on one core)"}
     line = {
         "metric": METRIC, "value": t_max, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": False, "scaling": "weak",
