@@ -285,6 +285,69 @@ __device__ __forceinline__ void lean_restrict_solve(const LeanEnv<C, K> &e, TriF
 // (mode 0: f_z; mode 1: the own plane is zero; mode 2: all terms), stored unless g_0 is f_z
 // itself; even lines are solved at once (into u_0, or into the plane when the plane has a
 // single line).  Lines in pairs (2k, 2k+1), k = rank + R i.
+//
+// d -= Mc (4 c - c_{x-1} - c_{x+1} - up - dn) + Kc c for one plane line c with its y-neighbours up
+// and dn already loaded (the arithmetic of sub_plane_term).
+template <class C, int K>
+__device__ __forceinline__ void lean_plane_term(C (&d)[K], const C (&cv)[K], const C (&up)[K], const C (&dn)[K], C Mc,
+                                                C Kc, int lane) {
+    C vl = __shfl_up_sync(0xffffffffu, cv[K - 1], 1);
+    C vr = __shfl_down_sync(0xffffffffu, cv[0], 1);
+    if (lane == 0) vl = C(0);
+    if (lane == 31) vr = C(0);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const C left = (j == 0) ? vl : cv[j - 1];
+        const C right = (j == K - 1) ? vr : cv[j + 1];
+        d[j] -= Mc * (C(4) * cv[j] - left - right - up[j] - dn[j]) + Kc * cv[j];
+    }
+}
+
+// Lines y0 and y0 + 1 (when `two`) of g_0 = f_z - sum_dz A_{z,z+dz} u_{z+dz} (mode 1: own plane
+// zero; mode 2: all).  Lines y0 - 1 .. y0 + 2 of each plane the pair needs are loaded once for both
+// lines and before any arithmetic, so their latencies overlap; per line the terms are subtracted
+// in the order of rhs_group (plane z-1, z+1, then z).
+template <class C, class S, int K>
+__device__ __forceinline__ void lean_rhs_pair(C (&d)[2][K], const S *fpl, const S *ub, int z, int nz, int y0, bool two,
+                                              int ny, int nx, long long np, const C *zc, int mode, bool vec, int lane) {
+    load_plane_line<C, S, K>(d[0], fpl, y0, nx, vec, lane);
+    if (two) load_plane_line<C, S, K>(d[1], fpl, y0 + 1, nx, vec, lane);
+    auto rows = [&](C (&r)[4][K], const S *pl) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int y = y0 - 1 + t;
+            if (y >= 0 && y < ny && (t < 3 || two)) {
+                load_plane_line<C, S, K>(r[t], pl, y, nx, vec, lane);
+            } else {
+#pragma unroll
+                for (int j = 0; j < K; ++j) r[t][j] = C(0);
+            }
+        }
+    };
+    auto apply = [&](const C (&r)[4][K], C Mc, C Kc) {
+        lean_plane_term<C, K>(d[0], r[1], r[0], r[2], Mc, Kc, lane);
+        if (two) lean_plane_term<C, K>(d[1], r[2], r[1], r[3], Mc, Kc, lane);
+    };
+    const bool lo = mode >= 1 && z > 0, hi = mode >= 1 && z + 1 < nz;
+    if (lo && hi) {
+        C ra[4][K], rb[4][K];
+        rows(ra, ub + (z - 1) * np);
+        rows(rb, ub + (z + 1) * np);
+        apply(ra, zc[0], zc[3]);
+        apply(rb, zc[2], zc[5]);
+    } else if (lo || hi) {
+        C ra[4][K];
+        rows(ra, ub + (lo ? z - 1 : z + 1) * np);
+        if (lo) apply(ra, zc[0], zc[3]);
+        else apply(ra, zc[2], zc[5]);
+    }
+    if (mode == 2) {
+        C ra[4][K];
+        rows(ra, ub + z * np);
+        apply(ra, zc[1], zc[4]);
+    }
+}
+
 template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void lean_rhs_even(const LeanEnv<C, K> &e, TriFac<C, K> &fac, int &key,
                                               const PlaneRelaxArgs &a, int mode, bool g0_is_f, const S *fpl,
@@ -298,17 +361,28 @@ __device__ __forceinline__ void lean_rhs_even(const LeanEnv<C, K> &e, TriFac<C, 
     for (int i = e.warp; i < nown; i += e.nw) {
         const int k = CL ? e.rank + (i << e.lr) : i;
         C d[2][K];
+        if constexpr (sizeof(C) == 4) {
+            // FP32 compute: the pair's plane lines loaded together (in FP64 the extra registers
+            // spill, so the lines are assembled one after the other there)
+            const bool two = 2 * k + 1 < ny;
+            lean_rhs_pair<C, S, K>(d, fpl, ub, z, a.nz, 2 * k, two, ny, nx, np, zc, mode, e.vec, lane);
+            if (!g0_is_f) {
+                store_line<C, K>(lean_line<C, K, CL>(e, L.g, L.gon, 2 * k), d[0], nx, e.vec, lane);
+                if (two) store_line<C, K>(lean_line<C, K, CL>(e, L.g, L.gon, 2 * k + 1), d[1], nx, e.vec, lane);
+            }
+        } else {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int y = 2 * k + t;
-            if (y >= ny) break;
-            load_plane_line<C, S, K>(d[t], fpl, y, nx, e.vec, lane);
-            if (mode >= 1 && z > 0)
-                sub_plane_term<C, S, K>(d[t], ub + (z - 1) * np, y, nx, ny, zc[0], zc[3], e.vec, lane);
-            if (mode >= 1 && z + 1 < a.nz)
-                sub_plane_term<C, S, K>(d[t], ub + (z + 1) * np, y, nx, ny, zc[2], zc[5], e.vec, lane);
-            if (mode == 2) sub_plane_term<C, S, K>(d[t], ub + z * np, y, nx, ny, zc[1], zc[4], e.vec, lane);
-            if (!g0_is_f) store_line<C, K>(lean_line<C, K, CL>(e, L.g, L.gon, y), d[t], nx, e.vec, lane);
+            for (int t = 0; t < 2; ++t) {
+                const int y = 2 * k + t;
+                if (y >= ny) break;
+                load_plane_line<C, S, K>(d[t], fpl, y, nx, e.vec, lane);
+                if (mode >= 1 && z > 0)
+                    sub_plane_term<C, S, K>(d[t], ub + (z - 1) * np, y, nx, ny, zc[0], zc[3], e.vec, lane);
+                if (mode >= 1 && z + 1 < a.nz)
+                    sub_plane_term<C, S, K>(d[t], ub + (z + 1) * np, y, nx, ny, zc[2], zc[5], e.vec, lane);
+                if (mode == 2) sub_plane_term<C, S, K>(d[t], ub + z * np, y, nx, ny, zc[1], zc[4], e.vec, lane);
+                if (!g0_is_f) store_line<C, K>(lean_line<C, K, CL>(e, L.g, L.gon, y), d[t], nx, e.vec, lane);
+            }
         }
         C dv[1][K];
 #pragma unroll
