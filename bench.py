@@ -631,7 +631,7 @@ def run_batched(args):
                    "npre": 1, "npost": 0, "cycle_precision": "fp32", "iters_max": int(its.max()),
                    "iters_mean": float(its.mean()), "true_relres_max": float(rel.max()),
                    "unknowns_per_s": n_all / t_max, "setup_s": setup_s,
-                   "schedule": {k: info0[k] for k in ("threads", "order", "blocks", "tasks")},
+                   "schedule": {k: info0[k] for k in ("rows_per_lane", "threads", "blocks", "order", "tasks")},
                    "sequential_fp32_s": seq["fp32"], "sequential_fp64_s": seq["fp64"],
                    "speedup_vs_sequential_fp32": seq["fp32"] / t_step,
                    "speedup_vs_sequential_fp64": seq["fp64"] / t_step,

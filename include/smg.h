@@ -199,12 +199,15 @@ int smg_batched_apply(smg_batched_handle h, const double *const *r, double *cons
 int smg_batched_destroy(smg_batched_handle h);
 
 /*
- * smg_batched_info -- the chosen schedule: threads per CTA (256 or 512), task order (0 system
- * order, 1 longest plane first), persistent CTAs, tasks per V-cycle, and the kernel launches
- * the handle has issued so far (the persistent V-cycle counts once per launch).  Host outputs.
+ * smg_batched_info -- the schedule the set-up's autotuner chose by timing every candidate
+ * V-cycle: x-line tile (rows_per_lane K: a warp holds 32 K rows of a line, K from the narrowest
+ * that holds every system's lines up to 4), threads per CTA (256 or 512), persistent CTAs
+ * (`blocks`: a multiple of the SM count, 1 up to the occupancy limit per SM) and task order
+ * (0 system order, 1 longest plane first); also the tasks per V-cycle and the kernel launches the
+ * handle has issued so far (the persistent V-cycle counts once per launch).  Host outputs.
  */
 int smg_batched_info(smg_batched_handle h, int *threads, int *order, int *blocks, long long *tasks,
-                     long long *launches);
+                     long long *launches, int *rows_per_lane);
 
 /*
  * smg_batched_set_profile / smg_batched_profile_read -- with profiling on, each iteration's

@@ -490,6 +490,8 @@ int chunk_K(int nx) { return (nx + 31) / 32; }
 struct Tuned {
     int threads = 512;
     int order = 1;  // 1: tasks of a step in decreasing cost, 0: system order
+    int K = 0;      // x-line rows per lane (the line tile: 32 K rows per warp)
+    int bps = 1;    // persistent CTAs per SM
 };
 std::mutex g_tune_mutex;
 std::map<std::vector<int>, Tuned> g_tune_cache;
@@ -741,6 +743,7 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
     };
     std::vector<PlaneRelaxArgs> relax;
     std::vector<int> relax_f64;  // 1: the entry computes in FP64
+    std::vector<int> relax_sys, relax_layd;  // the entry's system; 1: it uses the FP64 layout
     std::vector<BTransfer> xfer;
     std::map<std::vector<int>, int> relax_index;  // (s, l, colour, mode, f64) -> args index
     size_t smem_max = 0;
@@ -786,6 +789,8 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
         a.ws_per_plane = lay.ws_per_plane;  // elements; converted to a common byte stride below
         relax.push_back(a);
         relax_f64.push_back((f64 || P == Prec::F64) ? 1 : 0);
+        relax_sys.push_back(s);
+        relax_layd.push_back(f64 ? 1 : 0);
         relax_index[key] = static_cast<int>(relax.size()) - 1;
         return static_cast<int>(relax.size()) - 1;
     };
@@ -866,13 +871,51 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
     // drop empty steps
     steps.erase(std::remove_if(steps.begin(), steps.end(), [](const StepTasks &x) { return x.t.empty(); }),
                 steps.end());
-    // common workspace stride in bytes for every task; one slot per persistent CTA
-    const long long ws_stride = (ws_bytes + 255) / 256 * 256;
-    for (size_t i = 0; i < relax.size(); ++i)
-        relax[i].ws_per_plane = ws_stride / (relax_f64[i] ? 8 : static_cast<long long>(cb));
-
-    c.smem = std::max<size_t>(smem_max, 1024);
-    if (set_persistent_smem(P, K, c.smem) != 0) {
+    // ---- candidate line tiles: x-line rows per lane from the narrowest that holds every
+    // system's lines (K) up to 4; each has its own layouts, shared memory and workspace stride ----
+    struct KPlan {
+        int K;
+        std::vector<PlaneRelaxArgs> relax;
+        size_t smem;
+        long long ws_stride;  // bytes per persistent CTA
+    };
+    std::vector<KPlan> kplans;
+    for (int kc = K; kc <= 4; ++kc) {
+        KPlan kp;
+        kp.K = kc;
+        kp.relax = relax;
+        std::vector<PlaneLayout> lay(nsys), layd(nsys);
+        for (int s = 0; s < nsys; ++s) {
+            lay[s] = plan_plane_layout(sys[s].H, cb, kBudget, kc);
+            layd[s] = plan_plane_layout(sys[s].H, 8, kBudget, kc);
+        }
+        size_t sm = 0;
+        long long wsb = 0;
+        for (size_t i = 0; i < relax.size(); ++i) {
+            const PlaneLayout &L = relax_layd[i] ? layd[relax_sys[i]] : lay[relax_sys[i]];
+            PlaneRelaxArgs &a = kp.relax[i];
+            for (int m = 0; m < a.P; ++m) {
+                a.off_u[m] = L.off_u[m];
+                a.off_g[m] = L.off_g[m];
+            }
+            a.smem_u_mask = L.smem_u_mask;
+            a.smem_g_mask = L.smem_g_mask;
+            a.MF = L.MF;
+            a.off_fs = L.off_fs;
+            sm = std::max(sm, L.smem_bytes);
+            wsb = std::max<long long>(wsb, L.ws_per_plane * static_cast<long long>(relax_layd[i] ? 8 : cb));
+        }
+        kp.ws_stride = (wsb + 255) / 256 * 256;
+        for (size_t i = 0; i < relax.size(); ++i)
+            kp.relax[i].ws_per_plane = kp.ws_stride / (relax_f64[i] ? 8 : static_cast<long long>(cb));
+        kp.smem = std::max<size_t>(sm, 1024);
+        if (set_persistent_smem(P, kc, kp.smem) != 0) {
+            cudaGetLastError();
+            continue;  // this tile's layout does not fit: not a candidate
+        }
+        kplans.push_back(kp);
+    }
+    if (kplans.empty()) {
         set_last_error("batched solver: shared-memory configuration failed");
         return SMG_ERR_CUDA;
     }
@@ -919,16 +962,30 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
         return SMG_OK;
     };
     // workspace: one slot per CTA of the largest persistent grid any candidate schedule uses
+    size_t ws_total = 0;
     int max_blocks = 0;
-    for (int threads : {256, 512})
-        max_blocks = std::max(max_blocks, nsm * persistent_blocks_per_sm(P, K, threads, c.smem));
+    for (auto &kp : kplans)
+        for (int threads : {256, 512}) {
+            const int b = nsm * persistent_blocks_per_sm(P, kp.K, threads, kp.smem);
+            max_blocks = std::max(max_blocks, b);
+            ws_total = std::max(ws_total, static_cast<size_t>(std::max<long long>(kp.ws_stride, 256)) * std::max(b, 0));
+        }
     if (max_blocks < 1) {
         set_last_error("batched solver: the persistent kernel does not fit on an SM");
         return SMG_ERR_CUDA;
     }
-    BCHK(buf.alloc(&d_ws, static_cast<size_t>(std::max<long long>(ws_stride, 256)) * max_blocks));
-    for (auto &a : relax) a.gws = d_ws;
-    BCHK(cudaMemcpyAsync(d_relax, relax.data(), relax.size() * sizeof(PlaneRelaxArgs), cudaMemcpyHostToDevice, st));
+    BCHK(buf.alloc(&d_ws, ws_total));
+    for (auto &kp : kplans)
+        for (auto &a : kp.relax) a.gws = d_ws;
+    // the persistent kernel reads the relaxation arguments of the line tile in use
+    auto use_tile = [&](const KPlan &kp) -> int {
+        c.K = kp.K;
+        c.smem = kp.smem;
+        BCHK(cudaMemcpyAsync(d_relax, kp.relax.data(), kp.relax.size() * sizeof(PlaneRelaxArgs), cudaMemcpyHostToDevice,
+                             st));
+        BCHK(cudaStreamSynchronize(st));
+        return SMG_OK;
+    };
     BCHK(cudaMemcpyAsync(d_xfer, xfer.data(), xfer.size() * sizeof(BTransfer), cudaMemcpyHostToDevice, st));
 
     // Krylov data
@@ -1017,7 +1074,8 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
     pa.err = c.d_flags + 1;
     pa.spin_limit = 10000000;  // about a second of polling
 
-    // ---- autotuned schedule: threads per CTA and task order within a step ----
+    // ---- autotuned schedule: line tile (rows per lane), threads per CTA, persistent CTAs per SM
+    // and task order within a step ----
     std::vector<int> key{nsys, c.prec, c.npre, c.npost};
     for (int s = 0; s < 3 * nsys; ++s) key.push_back(dims[s]);
     bool tuned = false;
@@ -1033,38 +1091,48 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
         // the cost of a V-cycle does not depend on the values: time each candidate on the
         // zero-initialised level vectors with every system active
         float best = 1e30f;
-        for (int threads : {256, 512}) {
-            const int bps = persistent_blocks_per_sm(P, K, threads, c.smem);
-            if (bps < 1) continue;
-            const int nb = nsm * bps;
-            for (int order : {0, 1}) {
-                if (upload_tasks(order) != SMG_OK) return SMG_ERR_CUDA;
-                BCHK(c.launch_vcycle(st, threads, nb));  // warm-up
-                BCHK(cudaEventRecord(c.ev[0], st));
-                BCHK(c.launch_vcycle(st, threads, nb));
-                BCHK(cudaEventRecord(c.ev[1], st));
-                BCHK(cudaEventSynchronize(c.ev[1]));
-                c.kernel_launches += 2;
-                float ms = 0.0f;
-                BCHK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]));
-                int herr = 0;
-                BCHK(cudaMemcpy(&herr, pa.err, sizeof(int), cudaMemcpyDeviceToHost));
-                if (herr != 0) {
-                    set_last_error("batched solver: a V-cycle barrier wait timed out");
-                    return herr;
-                }
-                if (ms < best) {
-                    best = ms;
-                    c.tune.threads = threads;
-                    c.tune.order = order;
+        for (const auto &kp : kplans) {
+            if (use_tile(kp) != SMG_OK) return SMG_ERR_CUDA;
+            for (int threads : {256, 512}) {
+                const int bmax = persistent_blocks_per_sm(P, kp.K, threads, kp.smem);
+                for (int bps = 1; bps <= bmax; ++bps) {
+                    const int nb = nsm * bps;
+                    for (int order : {0, 1}) {
+                        if (upload_tasks(order) != SMG_OK) return SMG_ERR_CUDA;
+                        BCHK(c.launch_vcycle(st, threads, nb));  // warm-up
+                        BCHK(cudaEventRecord(c.ev[0], st));
+                        BCHK(c.launch_vcycle(st, threads, nb));
+                        BCHK(cudaEventRecord(c.ev[1], st));
+                        BCHK(cudaEventSynchronize(c.ev[1]));
+                        c.kernel_launches += 2;
+                        float ms = 0.0f;
+                        BCHK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]));
+                        int herr = 0;
+                        BCHK(cudaMemcpy(&herr, pa.err, sizeof(int), cudaMemcpyDeviceToHost));
+                        if (herr != 0) {
+                            set_last_error("batched solver: a V-cycle barrier wait timed out");
+                            return herr;
+                        }
+                        if (ms < best) {
+                            best = ms;
+                            c.tune.K = kp.K;
+                            c.tune.threads = threads;
+                            c.tune.bps = bps;
+                            c.tune.order = order;
+                        }
+                    }
                 }
             }
         }
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = c.tune;
     }
+    const KPlan *chosen = &kplans[0];
+    for (const auto &kp : kplans)
+        if (kp.K == c.tune.K) chosen = &kp;
+    if (use_tile(*chosen) != SMG_OK) return SMG_ERR_CUDA;
     if (upload_tasks(c.tune.order) != SMG_OK) return SMG_ERR_CUDA;
-    const int bps = std::max(1, persistent_blocks_per_sm(P, K, c.tune.threads, c.smem));
+    const int bps = std::max(1, std::min(c.tune.bps, persistent_blocks_per_sm(P, c.K, c.tune.threads, c.smem)));
     c.blocks = std::min(max_blocks, nsm * bps);
 
     // ---- capture one iteration into a CUDA graph ----
@@ -1272,13 +1340,14 @@ extern "C" int smg_batched_destroy(smg_batched_handle h) {
 }
 
 extern "C" int smg_batched_info(smg_batched_handle h, int *threads, int *order, int *blocks, long long *tasks,
-                                long long *launches) {
-    if (!h || !threads || !order || !blocks || !tasks || !launches) {
+                                long long *launches, int *rows_per_lane) {
+    if (!h || !threads || !order || !blocks || !tasks || !launches || !rows_per_lane) {
         set_last_error("null pointer");
         return SMG_ERR_ARG;
     }
     *threads = h->tune.threads;
     *order = h->tune.order;
+    *rows_per_lane = h->K;
     *blocks = h->blocks;
     *tasks = h->ntasks;
     *launches = h->kernel_launches;

@@ -76,7 +76,7 @@ def _load():
     L.smg_batched_solve.argtypes = [vp, i, vp, vp, d, i, vp, vp, vp]
     L.smg_batched_destroy.argtypes = [vp]
     L.smg_batched_apply.argtypes = [vp, vp, vp, vp]
-    L.smg_batched_info.argtypes = [vp, ip, ip, ip, ll, ll]
+    L.smg_batched_info.argtypes = [vp, ip, ip, ip, ll, ll, ip]
     L.smg_batched_set_profile.argtypes = [vp, i]
     L.smg_batched_profile_read.argtypes = [vp, i, ll, dp, dp]
     L.smg_set_learned.argtypes = [vp, vp, i]
@@ -283,11 +283,12 @@ def smg_batched_destroy(h) -> None:
 
 
 def smg_batched_info(h) -> dict:
-    t, o, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    t, o, b, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     n, la = ctypes.c_longlong(), ctypes.c_longlong()
     _check(_lib.smg_batched_info(ctypes.c_void_p(h), ctypes.byref(t), ctypes.byref(o), ctypes.byref(b),
-                                 ctypes.byref(n), ctypes.byref(la)))
-    return {"threads": t.value, "order": o.value, "blocks": b.value, "tasks": n.value, "launches": la.value}
+                                 ctypes.byref(n), ctypes.byref(la), ctypes.byref(k)))
+    return {"threads": t.value, "order": o.value, "blocks": b.value, "tasks": n.value, "launches": la.value,
+            "rows_per_lane": k.value}
 
 
 def smg_batched_set_profile(h, on: int) -> None:

@@ -115,8 +115,12 @@ def test_batched_handle_reuse_is_deterministic_and_profiles(smg):
     h = smg.smg_batched_setup(dims)
     try:
         info = smg.smg_batched_info(h)
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
         assert info["threads"] in (256, 512) and info["order"] in (0, 1)
-        assert info["blocks"] >= torch.cuda.get_device_properties(0).multi_processor_count
+        assert info["blocks"] >= nsm and info["blocks"] % nsm == 0
+        # the line tile: from the narrowest that holds the widest system's lines up to 4 rows per lane
+        kmin = (int(max(d[0] for d in dims)) + 31) // 32
+        assert kmin <= info["rows_per_lane"] <= 4
         smg.smg_batched_set_profile(h, 1)
         out = []
         for _ in range(2):
