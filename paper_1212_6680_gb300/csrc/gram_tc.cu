@@ -221,11 +221,13 @@ __device__ __forceinline__ void gt_drain(uint32_t tmem, int q, int cb, int NP, l
 
 // The digit-split Gram of the CTA's row range.  Items (column j, row pair): 8 columns x 4 row
 // pairs per warp access, so a warp's 4-byte digit stores fill 128 contiguous bytes of a K chunk.
-// A thread owns at most GT_ITEMS items; their rows for the next stage are loaded into registers
-// while the current stage's MMAs run.  With two digit buffers (when they fit in shared memory)
-// the digits of stage st are written while the MMAs of stage st-1 read the other buffer.
-constexpr int GT_ITEMS = 8;     // (64 + 64 columns / 8) x 256 items / 512 threads
-constexpr int GT_PREFETCH = 3;  // stages ahead the rows are prefetched into L2
+// A thread owns at most (NP + 64) / 16 items ((k1 <= NP plus k2 <= 64 columns) / 8 x 256 items /
+// 512 threads); their rows
+// are loaded into registers two stages ahead (two register sets, the stage loop unrolled by two so
+// that each set is named statically), so a stage's loads have the whole previous stage to arrive.
+// With two digit buffers (when they fit in shared memory) the digits of stage st are written while
+// the MMAs of stage st-1 read the other buffer.
+constexpr int GT_PREFETCH = 4;  // stages ahead the rows are prefetched into L2
 
 template <int NP>
 __global__ void __launch_bounds__(GT_THREADS, 1)
@@ -276,11 +278,12 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 
     // this thread's items: column jj (U's columns, then V's) and row pair rp; packed jj | rp << 8
     // a symmetric product (V = U) slices U's columns once and stores them on both sides
+    constexpr int GI = (NP + 64) / 16;  // items per thread
     const int ncol = sym ? k1 : k1 + k2, ncg = (ncol + 7) / 8;
-    int pk[GT_ITEMS];
-    const double *cp[GT_ITEMS];
+    int pk[GI];
+    const double *cp[GI];
 #pragma unroll
-    for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+    for (int q2 = 0; q2 < GI; ++q2) {
         const int it = tid + q2 * GT_THREADS;
         const int jj = (it & 7) + 8 * ((it >> 5) % ncg);
         const int rp = ((it >> 3) & 3) + 4 * ((it >> 5) / ncg);
@@ -290,11 +293,11 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         cp[q2] = valid ? (jj < k1 ? U + static_cast<long long>(j) * ldu : V + static_cast<long long>(j) * ldv) + 2 * rp
                        : nullptr;
     }
-    double xa[GT_ITEMS], xb[GT_ITEMS];
-    auto load_stage = [&](long long st) {
+    double xa0[GI], xb0[GI], xa1[GI], xb1[GI];
+    auto load_stage = [&](long long st, double (&xa)[GI], double (&xb)[GI]) {
         const long long r0 = st * GT_ROWS;
 #pragma unroll
-        for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+        for (int q2 = 0; q2 < GI; ++q2) {
             xa[q2] = 0.0;
             xb[q2] = 0.0;
             if (pk[q2] >= 0 && st < st1) {
@@ -309,16 +312,16 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         if (st >= st1) return;
         const long long r0 = st * GT_ROWS;
 #pragma unroll
-        for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+        for (int q2 = 0; q2 < GI; ++q2) {
             // one prefetch per 32-byte sector: the even lanes of a row-pair group
             if (pk[q2] >= 0 && ((pk[q2] >> 8) & 1) == 0 && r0 + 2 * (pk[q2] >> 8) < n)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(cp[q2] + r0));
         }
     };
-    auto slice_stage = [&](int b) {
+    auto slice_stage = [&](int b, const double (&xa)[GI], const double (&xb)[GI]) {
         unsigned char *Vs = sm + b * BUFB, *Us = Vs + GT_VBYTES;
 #pragma unroll
-        for (int q2 = 0; q2 < GT_ITEMS; ++q2) {
+        for (int q2 = 0; q2 < GI; ++q2) {
             if (pk[q2] < 0) continue;
             const int jj = pk[q2] & 0xff, rp = pk[q2] >> 8;
             const bool isu = jj < k1;
@@ -403,24 +406,34 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         GT_TRACE(3);
         return true;
     };
-    for (int d = 1; d < GT_PREFETCH; ++d) prefetch_stage(st0 + d);
-    if (st0 < st1) load_stage(st0);
-    for (long long st = st0; st < st1 && ok; ++st) {
+    // one stage: slice its rows (loaded two stages ago), hand the digits to the tensor cores,
+    // load the rows of stage st + 2 into the registers just consumed
+    auto stage = [&](long long st, double (&xa)[GI], double (&xb)[GI]) -> bool {
         GT_TRACE(0);
         const int b = NBUF == 2 ? static_cast<int>((st - st0) & 1) : 0;
-        slice_stage(b);
+        slice_stage(b, xa, xb);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         GT_TRACE(1);
         // two buffers: the previous stage's MMAs (reading the other buffer) ran during the slicing
-        if (NBUF == 2 && st > st0 && !wait_drain()) {
+        if (NBUF == 2 && st > st0 && !wait_drain()) return false;
+        if (tid == 0) issue_mmas(b, st == st0);
+        load_stage(st + 2, xa, xb);  // in flight during the next stage
+        prefetch_stage(st + GT_PREFETCH);  // into L2, so that the register loads find it there
+        if (NBUF == 1 && !wait_drain()) return false;
+        return true;
+    };
+    for (int d = 2; d < GT_PREFETCH; ++d) prefetch_stage(st0 + d);
+    if (st0 < st1) {
+        load_stage(st0, xa0, xb0);
+        load_stage(st0 + 1, xa1, xb1);
+    }
+    for (long long st = st0; st < st1 && ok; st += 2) {
+        if (!stage(st, xa0, xb0)) {
             ok = false;
             break;
         }
-        if (tid == 0) issue_mmas(b, st == st0);
-        load_stage(st + 1);  // in flight while the MMAs run
-        prefetch_stage(st + GT_PREFETCH);  // into L2, so that the register loads find it there
-        if (NBUF == 1 && !wait_drain()) ok = false;
+        if (st + 1 < st1 && !stage(st + 1, xa1, xb1)) ok = false;
     }
     if (ok && NBUF == 2 && st0 < st1 && !wait_drain()) ok = false;
     if (!ok && lane == 0) atomicExch(&g_gram_tc_err, 1);

@@ -26,6 +26,8 @@ def main() -> None:
     ap.add_argument("--solves", type=int, default=1)
     ap.add_argument("--m", type=int, default=16)
     ap.add_argument("--nsys", type=int, default=16)
+    ap.add_argument("--device-loop", dest="host_loop", action="store_false",
+                    help="run krylov_solve's iterations as one CUDA graph (default: the host loop)")
     a = ap.parse_args()
 
     import torch
@@ -43,6 +45,9 @@ def main() -> None:
         x = torch.zeros_like(b)
         h = S.smg_setup(n, n, n, 1, a.npost)
         S.smg_set_precision(h, a.prec)
+        # the host loop launches every kernel of an iteration itself, so a kernel profiler sees each
+        # launch (the device-side loop runs them inside a conditional graph node)
+        S.smg_set_option(h, S.SMG_OPT_GRAPH, 0 if a.host_loop else 1)
         if a.case == "learned":
             S.smg_set_learned(h, inputs.net_init_weights(seed=77))
         S.krylov_solve(h, "fpcg", b, x, 1e-8, 100)
