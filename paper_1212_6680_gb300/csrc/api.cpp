@@ -92,6 +92,8 @@ struct smg_ctx {
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
+    PlaneLayout lay_lean32[5];      // FP32-compute shortened-step layouts (every factor set on chip)
+    bool lean32_ok[5] = {false, false, false, false, false};
     int cluster_max32 = 0;          // largest cluster for FP32-compute plane relaxations; 0 = chosen
                                     // per size (see relax)
     int num_sms = 0;
@@ -190,7 +192,7 @@ int ensure_levels(smg_ctx *h, int nb) {
         if (set_plane_wide_smem(h->prec, f64c, h->lay_c.smem_bytes) != 0 ||
             set_plane_wide_smem(h->prec, true, h->lay_d.smem_bytes) != 0)
             return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, wide lines) failed");
-        for (int lr = 0; lr <= 4; ++lr) h->cl_ok[lr] = h->cl32_ok[lr] = h->lean64_ok[lr] = false;
+        for (int lr = 0; lr <= 4; ++lr) h->cl_ok[lr] = h->cl32_ok[lr] = h->lean64_ok[lr] = h->lean32_ok[lr] = false;
         if (h->num_sms == 0) {
             int dev = 0;
             SMG_CUDA(cudaGetDevice(&dev));
@@ -250,7 +252,29 @@ int ensure_levels(smg_ctx *h, int nb) {
             cudaGetLastError();
             continue;
         }
-        h->lean64_ok[lr] = (lr == 0) || lean_cluster_resident(h->prec, K, R, h->threads, ly.smem_bytes);
+        h->lean64_ok[lr] = (lr == 0) || lean_cluster_resident(h->prec, true, K, R, h->threads, ly.smem_bytes);
+    }
+    // the same for FP32 compute (FP32 and BF16 cycles): used where the general layout does not keep
+    // every factor set on chip (one CTA) or the plane is spread over a cluster
+    for (int lr = 0; lr <= 4; ++lr) {
+        h->lean32_ok[lr] = false;
+        if (!lean_supported(K) || h->prec == Prec::F64) break;
+        const int R = 1 << lr;
+        PlaneLayout &ly = h->lay_lean32[lr];
+        ly = (lr == 0) ? plan_plane_layout(H, 4, kSmemBudget, 0, true) : plan_plane_layout_cluster(H, 4, kSmemBudget, R, true);
+        if (ly.smem_bytes == 0 || ly.smem_bytes > kSmemBudget || ly.MF != H.P) continue;
+        if (set_plane_lean_smem(h->prec, false, lr > 0, K, ly.smem_bytes) != 0) {
+            cudaGetLastError();
+            continue;
+        }
+        h->lean32_ok[lr] = (lr == 0) || lean_cluster_resident(h->prec, false, K, R, h->threads, ly.smem_bytes);
+    }
+    // a single-CTA lean layout can need more shared memory than the general one
+    {
+        size_t m32 = h->lay_c.smem_bytes;
+        if (h->lean32_ok[0]) m32 = std::max(m32, h->lay_lean32[0].smem_bytes);
+        if (h->prec != Prec::F64 && lean_supported(K) && set_plane_lean_smem(h->prec, false, false, K, m32) != 0)
+            return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, shortened-step cycle) failed");
     }
     return alloc_plane_workspace(h, nb);
 }
@@ -265,8 +289,10 @@ int alloc_plane_workspace(smg_ctx *h, int nb) {
         if (h->cl_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_cl[lr].ws_per_plane) * 8);
         if (h->cl32_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_cl32[lr].ws_per_plane) * 4);
     }
-    for (int lr = 0; lr <= 4; ++lr)
+    for (int lr = 0; lr <= 4; ++lr) {
         if (h->lean64_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_lean64[lr].ws_per_plane) * 8);
+        if (h->lean32_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_lean32[lr].ws_per_plane) * 4);
+    }
     const long long slots = static_cast<long long>((H.nz + 1) / 2) * nb;
     h->ws_bytes = std::max<size_t>(per * slots, 256);
     SMG_CUDA(cudaMalloc(&h->d_ws, h->ws_bytes));
@@ -387,7 +413,12 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     const PlaneLayout *llay = &lay;
     if (W == 1 && h->lean && lean_supported(K) && h->lean_level[l]) {
         if (!f64c) {
-            use_lean = (R == 1 && iters == 1 && lay.MF == H.P);
+            if (iters == 1 && R == 1 && lay.MF == H.P) {
+                use_lean = true;  // the general layout already keeps every factor set on chip
+            } else if (iters == 1 && h->lean32_ok[__builtin_ctz(R)]) {
+                use_lean = true;
+                llay = &h->lay_lean32[__builtin_ctz(R)];
+            }
         } else {
             int lrb = -1;
             for (int lr = 0; lr <= 4; ++lr) {

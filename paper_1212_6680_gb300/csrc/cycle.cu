@@ -74,12 +74,14 @@ bool cluster_resident(Prec storage, bool f64, int K, int R, int threads, size_t 
 #define SMG_DECL_LEAN(k, p)                                                                           \
     cudaError_t launch_plane_lean_k##k##_p##p(bool, int, int, int, const PlaneRelaxArgs &, size_t, cudaStream_t); \
     int set_plane_lean_smem_k##k##_p##p(bool, bool, size_t);                                          \
-    bool lean_cluster_resident_k##k##_p##p(int, int, size_t);
+    bool lean_cluster_resident_k##k##_p##p(bool, int, int, size_t);
 #define SMG_DECL_LEAN_K(k) SMG_DECL_LEAN(k, 0) SMG_DECL_LEAN(k, 1) SMG_DECL_LEAN(k, 2)
 SMG_DECL_LEAN_K(1)
 SMG_DECL_LEAN_K(2)
 SMG_DECL_LEAN_K(3)
 SMG_DECL_LEAN_K(4)
+SMG_DECL_LEAN_K(6)
+SMG_DECL_LEAN_K(8)
 
 #define SMG_LEAN_SWITCH(K, storage, CALL)                                                             \
     switch (K) {                                                                                      \
@@ -87,9 +89,11 @@ SMG_DECL_LEAN_K(4)
     case 2: SMG_SWITCH_P(2, storage, CALL)                                                            \
     case 3: SMG_SWITCH_P(3, storage, CALL)                                                            \
     case 4: SMG_SWITCH_P(4, storage, CALL)                                                            \
+    case 6: SMG_SWITCH_P(6, storage, CALL)                                                            \
+    case 8: SMG_SWITCH_P(8, storage, CALL)                                                            \
     }
 
-bool lean_supported(int K) { return K >= 1 && K <= 4; }
+bool lean_supported(int K) { return K >= 1 && K <= 8; }
 
 cudaError_t launch_plane_lean(Prec storage, bool f64, int K, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
                               size_t smem, cudaStream_t st) {
@@ -104,8 +108,8 @@ int set_plane_lean_smem(Prec storage, bool f64, bool cl, int K, size_t smem) {
     return static_cast<int>(cudaErrorInvalidValue);
 }
 
-bool lean_cluster_resident(Prec storage, int K, int R, int threads, size_t smem) {
-#define SMG_CALL_LEAN_RES(k, p) lean_cluster_resident_k##k##_p##p(R, threads, smem)
+bool lean_cluster_resident(Prec storage, bool f64, int K, int R, int threads, size_t smem) {
+#define SMG_CALL_LEAN_RES(k, p) lean_cluster_resident_k##k##_p##p(f64, R, threads, smem)
     SMG_LEAN_SWITCH(K, storage, SMG_CALL_LEAN_RES)
     return false;
 }

@@ -361,9 +361,10 @@ __device__ __forceinline__ void lean_rhs_even(const LeanEnv<C, K> &e, TriFac<C, 
     for (int i = e.warp; i < nown; i += e.nw) {
         const int k = CL ? e.rank + (i << e.lr) : i;
         C d[2][K];
-        if constexpr (sizeof(C) == 4) {
-            // FP32 compute: the pair's plane lines loaded together (in FP64 the extra registers
-            // spill, so the lines are assembled one after the other there)
+        if constexpr (sizeof(C) == 4 && sizeof(C) * K <= 16) {
+            // FP32 with a lane's share of a line in at most 16 bytes (nx <= 128): the pair's plane lines
+            // loaded together (with wider shares the extra registers spill, so the lines are
+            // assembled one after the other there)
             const bool two = 2 * k + 1 < ny;
             lean_rhs_pair<C, S, K>(d, fpl, ub, z, a.nz, 2 * k, two, ny, nx, np, zc, mode, e.vec, lane);
             if (!g0_is_f) {

@@ -74,9 +74,9 @@ bool SMG_NAME(cluster_resident_k, SMG_K, SMG_PREC)(bool f64, int R, int threads,
     return n > 0;
 }
 
-#if SMG_K <= 4
-// The shortened-step plane cycle (plane_lean.cuh): FP32 compute on one CTA per plane (FP32 and
-// BF16 storage), FP64 compute on one CTA or a cluster (a.R > 1) per plane.
+#if SMG_K <= 8
+// The shortened-step plane cycle (plane_lean.cuh): FP32 or FP64 compute, on one CTA or a cluster
+// (a.R > 1) per plane.
 cudaError_t SMG_NAME(launch_plane_lean_k, SMG_K, SMG_PREC)(bool f64, int nplanes, int nb, int threads,
                                                            const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
     const bool cl = a.R > 1;
@@ -84,20 +84,27 @@ cudaError_t SMG_NAME(launch_plane_lean_k, SMG_K, SMG_PREC)(bool f64, int nplanes
         return cl ? launch_lean<StorageT, double, SMG_K, true>(nplanes, nb, threads, a, smem, st)
                   : launch_lean<StorageT, double, SMG_K, false>(nplanes, nb, threads, a, smem, st);
 #if SMG_PREC != 0
-    if (!cl) return launch_lean<StorageT, float, SMG_K, false>(nplanes, nb, threads, a, smem, st);
-#endif
+    return cl ? launch_lean<StorageT, float, SMG_K, true>(nplanes, nb, threads, a, smem, st)
+              : launch_lean<StorageT, float, SMG_K, false>(nplanes, nb, threads, a, smem, st);
+#else
     return cudaErrorInvalidValue;
+#endif
 }
 int SMG_NAME(set_plane_lean_smem_k, SMG_K, SMG_PREC)(bool f64, bool cl, size_t smem) {
     if (f64 || SMG_PREC == 0)
         return cl ? set_lean_smem_attr<StorageT, double, SMG_K, true>(smem)
                   : set_lean_smem_attr<StorageT, double, SMG_K, false>(smem);
 #if SMG_PREC != 0
-    if (!cl) return set_lean_smem_attr<StorageT, float, SMG_K, false>(smem);
-#endif
+    return cl ? set_lean_smem_attr<StorageT, float, SMG_K, true>(smem)
+              : set_lean_smem_attr<StorageT, float, SMG_K, false>(smem);
+#else
     return static_cast<int>(cudaErrorInvalidValue);
+#endif
 }
-bool SMG_NAME(lean_cluster_resident_k, SMG_K, SMG_PREC)(int R, int threads, size_t smem) {
+bool SMG_NAME(lean_cluster_resident_k, SMG_K, SMG_PREC)(bool f64, int R, int threads, size_t smem) {
+#if SMG_PREC != 0
+    if (!f64) return lean_cluster_resident<StorageT, float, SMG_K>(R, threads, smem);
+#endif
     return lean_cluster_resident<StorageT, double, SMG_K>(R, threads, smem);
 }
 #endif

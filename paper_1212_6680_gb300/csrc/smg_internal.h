@@ -173,15 +173,14 @@ cudaError_t launch_convert_to(Prec storage, long long n, const double *src, void
 cudaError_t launch_convert_from(Prec storage, long long n, const void *src, double *dst, cudaStream_t st);
 cudaError_t launch_apply_A(int nx, int ny, int nz, int nb, const double *u, double *out, cudaStream_t st);
 int set_plane_relax_smem(Prec storage, bool compute_f64, bool cluster, int K, size_t smem);
-// The shortened-step plane cycle (plane_lean.cuh): nx <= 128 (K <= 4), every 2D level's factor
+// The shortened-step plane cycle (plane_lean.cuh): nx <= 256 (K <= 8), every 2D level's factor
 // sets in shared memory, and every line of a 2D level but its last sharing one line matrix
-// (lean_uniform_level); FP32 compute on one CTA per plane, FP64 compute on one CTA or a cluster
-// of a.R CTAs.
+// (lean_uniform_level); FP32 or FP64 compute on one CTA or a cluster of a.R CTAs per plane.
 bool lean_supported(int K);
 cudaError_t launch_plane_lean(Prec storage, bool compute_f64, int K, int nplanes, int nb, int threads,
                               const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
 int set_plane_lean_smem(Prec storage, bool compute_f64, bool cluster, int K, size_t smem);
-bool lean_cluster_resident(Prec storage, int K, int R, int threads, size_t smem);
+bool lean_cluster_resident(Prec storage, bool compute_f64, int K, int R, int threads, size_t smem);
 // True when, on every plane of z-level l and every 2D level, the lines before the last share the
 // line matrix (S(y,y), T(y,y)) of line 0.
 bool lean_uniform_level(const HostHierarchy &H, int l);

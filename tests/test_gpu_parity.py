@@ -114,12 +114,14 @@ def test_apply_mixed_precision_close_to_oracle(smg, orc, prec, tol, shape, npost
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("shape", [(128, 128, 16), (96, 80, 64), (33, 17, 20), (100, 3, 5), (5, 6, 1), (1, 1, 8)])
+@pytest.mark.parametrize("shape", [(128, 128, 16), (96, 80, 64), (33, 17, 20), (100, 3, 5), (5, 6, 1), (1, 1, 8),
+                                   (256, 256, 8), (200, 96, 20), (160, 40, 12), (256, 130, 3)])
 @pytest.mark.parametrize("npost", [1, 0])
 def test_shortened_step_plane_cycle_is_bitwise_the_general_one(smg, orc, prec, shape, npost):
     """The FP32 plane kernel with fewer barrier-separated steps (SMG_OPT_LEAN = 1, the default for
-    nx <= 128) does the same line solves in the same order as the general kernel: bit-identical
-    cycles, and both within the precision's tolerance of the oracle."""
+    nx <= 256; clusters of 2-4 CTAs for 256-wide planes) does the same line solves in the same order
+    as the general kernel: bit-identical cycles, and both within the precision's tolerance of the
+    oracle."""
     nx, ny, nz = shape
     r = inputs.rhs(nx, ny, nz, seed=14)
     out = {}
