@@ -663,7 +663,7 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
     const int nsys = c.nsys;
     const Prec P = c.P;
     const size_t sb = storage_bytes(P), cb = (P == Prec::F64) ? 8 : 4;
-    constexpr size_t kBudget = 227 * 1024 - 1024;  // 1 KB left for static shared memory
+    constexpr size_t kBudget = 227 * 1024 - 3 * 1024;  // static shared memory of the two plane cycles (~2 KB)
     DevBuf &buf = c.buf;
 
     // ---- per-system hierarchies and layouts ----
@@ -744,6 +744,7 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
     std::vector<PlaneRelaxArgs> relax;
     std::vector<int> relax_f64;  // 1: the entry computes in FP64
     std::vector<int> relax_sys, relax_layd;  // the entry's system; 1: it uses the FP64 layout
+    std::vector<int> relax_lvl;              // the entry's z-level
     std::vector<BTransfer> xfer;
     std::map<std::vector<int>, int> relax_index;  // (s, l, colour, mode, f64) -> args index
     size_t smem_max = 0;
@@ -791,6 +792,7 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
         relax_f64.push_back((f64 || P == Prec::F64) ? 1 : 0);
         relax_sys.push_back(s);
         relax_layd.push_back(f64 ? 1 : 0);
+        relax_lvl.push_back(l);
         relax_index[key] = static_cast<int>(relax.size()) - 1;
         return static_cast<int>(relax.size()) - 1;
     };
@@ -884,16 +886,25 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
         KPlan kp;
         kp.K = kc;
         kp.relax = relax;
-        std::vector<PlaneLayout> lay(nsys), layd(nsys);
+        // general layouts, and the shortened-step cycle's (every factor set on chip) where it fits
+        std::vector<PlaneLayout> lay(nsys), layd(nsys), lean(nsys), leand(nsys);
         for (int s = 0; s < nsys; ++s) {
             lay[s] = plan_plane_layout(sys[s].H, cb, kBudget, kc);
             layd[s] = plan_plane_layout(sys[s].H, 8, kBudget, kc);
+            lean[s] = plan_plane_layout(sys[s].H, cb, kBudget, kc, true);
+            leand[s] = plan_plane_layout(sys[s].H, 8, kBudget, kc, true);
         }
         size_t sm = 0;
         long long wsb = 0;
         for (size_t i = 0; i < relax.size(); ++i) {
-            const PlaneLayout &L = relax_layd[i] ? layd[relax_sys[i]] : lay[relax_sys[i]];
+            const int si = relax_sys[i];
+            const PlaneLayout &Lg = relax_layd[i] ? layd[si] : lay[si];
+            const PlaneLayout &Ll = relax_layd[i] ? leand[si] : lean[si];
+            const bool use_lean = lean_supported(kc) && relax[i].iters == 1 && Ll.MF == sys[si].H.P &&
+                                  Ll.smem_bytes <= kBudget && lean_uniform_level(sys[si].H, relax_lvl[i]);
+            const PlaneLayout &L = use_lean ? Ll : Lg;
             PlaneRelaxArgs &a = kp.relax[i];
+            a.lean = use_lean ? 1 : 0;
             for (int m = 0; m < a.P; ++m) {
                 a.off_u[m] = L.off_u[m];
                 a.off_g[m] = L.off_g[m];

@@ -12,6 +12,7 @@
 #include "../../include/smg.h"
 #include "batched.h"
 #include "grid_sync.cuh"
+#include "plane_lean.cuh"
 #include "plane_relax.cuh"
 #include "transfer.cuh"
 
@@ -27,9 +28,13 @@ __global__ void __launch_bounds__(512, 1) persistent_vcycle_kernel(const __grid_
             const BTask tk = p.tasks[t];
             if (!p.active[tk.sys]) continue;
             if (tk.type == TASK_RELAX) {
-                plane_task<S, CL, K, false>(p.relax[tk.arg], tk.idx, 0, blockIdx.x, 0, smem_raw);
+                const PlaneRelaxArgs &a = p.relax[tk.arg];
+                if (a.lean) plane_lean_task<S, CL, K, false>(a, tk.idx, 0, blockIdx.x, 0, smem_raw);
+                else plane_task<S, CL, K, false>(a, tk.idx, 0, blockIdx.x, 0, smem_raw);
             } else if (tk.type == TASK_RELAX_F64) {
-                plane_task<S, double, K, false>(p.relax[tk.arg], tk.idx, 0, blockIdx.x, 0, smem_raw);
+                const PlaneRelaxArgs &a = p.relax[tk.arg];
+                if (a.lean) plane_lean_task<S, double, K, false>(a, tk.idx, 0, blockIdx.x, 0, smem_raw);
+                else plane_task<S, double, K, false>(a, tk.idx, 0, blockIdx.x, 0, smem_raw);
             } else if (tk.type == TASK_RESTRICT) {
                 const BTransfer &x = p.xfer[tk.arg];
                 const CL *zc = coef_table<CL>(x.zc64, x.zc32);

@@ -124,6 +124,8 @@ struct PlaneRelaxArgs {
     int vec;                      // 1: nx == 32 K and f, u, the workspace are 16-byte aligned
                                   // (wide lines: nx % 8 == 0 and the same alignment)
     int W;                        // x-line segments of 512 rows (1 unless nx > 512: plane_wide.cu)
+    int lean;                     // persistent multi-system kernel: 1 runs this entry with the
+                                  // shortened-step cycle (its layout keeps every factor set on chip)
 };
 
 // Placement of the per-plane 2D-cycle arrays: shared memory where they fit, else global.
