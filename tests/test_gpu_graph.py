@@ -24,7 +24,7 @@ def smg():
     return m
 
 
-def solve(smg, shape, variant, prec, graph, maxit=40, npost=0, precond=1, x_new=False, fused=1):
+def solve(smg, shape, variant, prec, graph, maxit=40, npost=0, precond=1, x_new=False, fused=1, tol=1e-8):
     nx, ny, nz = shape
     b = torch.from_numpy(inputs.rhs(nx, ny, nz, seed=3).ravel().copy()).cuda()
     h = smg.smg_setup(nx, ny, nz, 1, npost)
@@ -40,7 +40,7 @@ def solve(smg, shape, variant, prec, graph, maxit=40, npost=0, precond=1, x_new=
                 x = torch.zeros_like(b)
             x.zero_()
             l0 = smg.smg_launch_count(h)
-            rc, it, rr = smg.krylov_solve(h, variant, b, x, 1e-8, maxit, check=False)
+            rc, it, rr = smg.krylov_solve(h, variant, b, x, tol, maxit, check=False)
             out.append((rc, it, rr, x.cpu().numpy().copy(), smg.smg_krylov_history(h), smg.smg_launch_count(h) - l0))
     finally:
         smg.smg_destroy(h)
@@ -103,3 +103,13 @@ def test_fused_krylov_tail_128cube(smg):
     u = solve(smg, (128, 128, 128), "fpcg", "fp32", 1, fused=0)
     same(f, u)
     assert f[0][0] == smg.SMG_OK
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_device_loop_tight_tolerance_with_true_residual_restarts(smg, prec):
+    """At tol = 1e-13 the recurrence residual of a reduced-precision cycle can pass the test while
+    the true residual does not; the host then continues from the true residual (beta = 0) and
+    relaunches the device loop.  Whatever path a solve takes, both loops take the same one."""
+    g = solve(smg, (48, 40, 36), "fpcg", prec, 1, maxit=80, tol=1e-13)
+    h = solve(smg, (48, 40, 36), "fpcg", prec, 0, maxit=80, tol=1e-13)
+    same(g, h)
