@@ -87,7 +87,12 @@ enum {
                                  four kernels chained by programmatic dependent launch, which is
                                  faster on GB300 (the barriers cost more than the kernel
                                  boundaries).  A barrier wait that gives up returns SMG_ERR_TIMEOUT
-                                 from krylov_solve */
+                                 from krylov_solve */,
+    SMG_OPT_SOLO = 10         /* T in [0, 512] (default 8): when the shortened-step plane cycle
+                                 runs on a thread-block cluster, the 2D levels of at most T lines
+                                 are held whole by the cluster's first CTA, whose steps on them
+                                 end in a CTA barrier instead of a cluster barrier; the same
+                                 results as 0 (every level spread over the cluster) */
 };
 
 /*

@@ -89,6 +89,8 @@ struct smg_ctx {
     int cluster_max = 16;           // largest cluster for FP64-compute plane relaxations (1 = none)
     int precond = 1;                // krylov_solve's preconditioner: 1 the SMG cycle, 0 none (T = I)
     int lean = 1;                   // 1: the shortened-step plane cycle where it applies
+    int solo = 8;                   // its cluster layouts give the 2D levels of at most `solo`
+                                    // lines to CTA 0 (0: none)
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
@@ -168,6 +170,23 @@ int instantiated_K(int nx) {
 
 int alloc_plane_workspace(smg_ctx *h, int nb);
 
+// The shortened-step cycle on a cluster: the coarse 2D levels from the first one with at most
+// max_lines lines are held whole by CTA 0, provided the layout still keeps on chip every array
+// the spread layout `base` keeps; else the next coarser level is tried, and `base` is kept when
+// none qualifies (or fewer than two levels would be solo: no barrier would become CTA 0's own).
+PlaneLayout with_solo_levels(const HostHierarchy &H, size_t elem_bytes, int R, int max_lines, const PlaneLayout &base) {
+    for (int s = 1; s + 2 <= H.P; ++s) {
+        if (H.ny_m[s] > max_lines) continue;
+        PlaneLayout ly = plan_plane_layout_cluster(H, elem_bytes, kSmemBudget, R, true, s);
+        if (ly.smem_bytes == 0 || ly.smem_bytes > kSmemBudget || ly.MF != base.MF) continue;
+        if ((ly.smem_u_mask & base.smem_u_mask) != base.smem_u_mask ||
+            (ly.smem_g_mask & base.smem_g_mask) != base.smem_g_mask)
+            continue;
+        return ly;
+    }
+    return base;
+}
+
 // Allocate level vectors for nb right-hand sides in the current precision, and the plane
 // workspace; configure the kernels' dynamic shared memory.
 int ensure_levels(smg_ctx *h, int nb) {
@@ -239,6 +258,26 @@ int ensure_levels(smg_ctx *h, int nb) {
         if (cl_smem > 0 && set_plane_relax_smem(h->prec, cf64, true, K, cl_smem) != 0)
             return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, cluster) failed");
     }
+    // a shortened-step layout is usable when its shared memory can be granted and (cluster) its
+    // CTAs fit on the GPU at once; a cluster layout takes its coarse levels solo where it can
+    auto settle_lean = [&](bool c64, int lr, PlaneLayout &ly) -> bool {
+        const int R = 1 << lr;
+        auto usable = [&](const PlaneLayout &l) {
+            if (set_plane_lean_smem(h->prec, c64, lr > 0, K, l.smem_bytes) != 0) {
+                cudaGetLastError();
+                return false;
+            }
+            return lr == 0 || lean_cluster_resident(h->prec, c64, K, R, h->threads, l.smem_bytes);
+        };
+        if (lr > 0 && h->solo) {
+            const PlaneLayout sl = with_solo_levels(H, c64 ? 8 : 4, R, h->solo, ly);
+            if (sl.solo_from < kMaxPlaneLevels && usable(sl)) {
+                ly = sl;
+                return true;
+            }
+        }
+        return usable(ly);
+    };
     // FP64-compute shortened-step layouts (every 2D level's factor sets on chip), one CTA or a
     // cluster per plane
     for (int lr = 0; lr <= 4; ++lr) {
@@ -248,11 +287,7 @@ int ensure_levels(smg_ctx *h, int nb) {
         PlaneLayout &ly = h->lay_lean64[lr];
         ly = (lr == 0) ? plan_plane_layout(H, 8, kSmemBudget, 0, true) : plan_plane_layout_cluster(H, 8, kSmemBudget, R, true);
         if (ly.smem_bytes == 0 || ly.smem_bytes > kSmemBudget || ly.MF != H.P) continue;
-        if (set_plane_lean_smem(h->prec, true, lr > 0, K, ly.smem_bytes) != 0) {
-            cudaGetLastError();
-            continue;
-        }
-        h->lean64_ok[lr] = (lr == 0) || lean_cluster_resident(h->prec, true, K, R, h->threads, ly.smem_bytes);
+        h->lean64_ok[lr] = settle_lean(true, lr, ly);
     }
     // the same for FP32 compute (FP32 and BF16 cycles): used where the general layout does not keep
     // every factor set on chip (one CTA) or the plane is spread over a cluster
@@ -263,11 +298,7 @@ int ensure_levels(smg_ctx *h, int nb) {
         PlaneLayout &ly = h->lay_lean32[lr];
         ly = (lr == 0) ? plan_plane_layout(H, 4, kSmemBudget, 0, true) : plan_plane_layout_cluster(H, 4, kSmemBudget, R, true);
         if (ly.smem_bytes == 0 || ly.smem_bytes > kSmemBudget || ly.MF != H.P) continue;
-        if (set_plane_lean_smem(h->prec, false, lr > 0, K, ly.smem_bytes) != 0) {
-            cudaGetLastError();
-            continue;
-        }
-        h->lean32_ok[lr] = (lr == 0) || lean_cluster_resident(h->prec, false, K, R, h->threads, ly.smem_bytes);
+        h->lean32_ok[lr] = settle_lean(false, lr, ly);
     }
     // a single-CTA lean layout can need more shared memory than the general one
     {
@@ -364,6 +395,7 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
                                      : ((f64c && h->prec != Prec::F64) ? h->lay_d : h->lay_c);
     PlaneRelaxArgs a;
     std::memset(&a, 0, sizeof(a));
+    a.solo_from = kMaxPlaneLevels;
     a.nx = h->nx;
     a.ny = h->ny;
     a.nz = nzl;
@@ -443,6 +475,7 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
         a.smem_g_mask = llay->smem_g_mask;
         a.MF = llay->MF;
         a.off_fs = llay->off_fs;
+        a.solo_from = llay->solo_from;
     }
     cudaError_t err = (W > 1)  ? launch_plane_wide(h->prec, f64c, nplanes, nb, h->threads, a, lay.smem_bytes, st)
                       : use_lean ? launch_plane_lean(h->prec, f64c, K, nplanes, nb, h->threads, a, llay->smem_bytes, st)
@@ -800,7 +833,13 @@ int smg_set_option(smg_handle h, int option, int value) {
         return SMG_OK;
     case SMG_OPT_THREADS:
         if (value != 256 && value != 512) return fail(SMG_ERR_ARG, "threads must be 256 or 512");
+        if (value != h->threads) free_levels(h);  // the layouts and residency checks depend on it
         h->threads = value;
+        return SMG_OK;
+    case SMG_OPT_SOLO:
+        if (value < 0 || value > kMaxNy) return fail(SMG_ERR_ARG, "solo must be in [0, 512]");
+        if (value != h->solo) free_levels(h);
+        h->solo = value;
         return SMG_OK;
     case SMG_OPT_CLUSTER_MAX:
         if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)

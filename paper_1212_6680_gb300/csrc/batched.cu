@@ -757,6 +757,7 @@ int batched_build(smg_batched_ctx &c, const int *dims, cudaStream_t st) {
         const PlaneLayout &lay = f64 ? p.lay_d : p.lay;
         PlaneRelaxArgs a;
         std::memset(&a, 0, sizeof(a));
+        a.solo_from = kMaxPlaneLevels;
         a.nx = p.nx;
         a.ny = p.ny;
         a.nz = p.H.nz_l[l];

@@ -288,9 +288,10 @@ PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t 
 }
 
 PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R,
-                                      bool all_sets) {
+                                      bool all_sets, int solo_from) {
     PlaneLayout P;
     P.K = chunk_K(H.nx);
+    P.solo_from = solo_from;
     auto align4 = [](size_t v) { return (v + 3) & ~static_cast<size_t>(3); };
     size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
     P.MF = all_sets ? std::min(H.P, kMaxFactorLevels) : factor_levels(H, P.K, elem_bytes, smem_budget);
@@ -307,7 +308,7 @@ PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes,
     for (const auto &o : layout_order(H)) {
         const int m = o.first;
         const int pairs = (H.ny_m[m] + 1) / 2;
-        const size_t nloc = 2 * static_cast<size_t>((pairs + R - 1) / R);
+        const size_t nloc = (m >= solo_from) ? static_cast<size_t>(H.ny_m[m]) : 2 * static_cast<size_t>((pairs + R - 1) / R);
         const size_t sz = align4(static_cast<size_t>(H.nx) * nloc);
         int &off = (o.second == 0) ? P.off_u[m] : P.off_g[m];
         unsigned &mask = (o.second == 0) ? P.smem_u_mask : P.smem_g_mask;

@@ -27,7 +27,10 @@
 // With a cluster of R CTAs (CL = true) line y of a level kept on chip belongs to CTA
 // ((y/2) mod R), stored there at local line ((y/2) div R)*2 + (y mod 2) (the layout of
 // plan_plane_layout_cluster); a CTA relaxes, restricts and assembles only the lines (pairs) it
-// owns and reads the others' lines through distributed shared memory.
+// owns and reads the others' lines through distributed shared memory.  The coarse levels from
+// a.solo_from on belong whole to CTA 0 (line y at local line y): the steps that touch only those
+// levels run on CTA 0 alone and end in a CTA barrier instead of a cluster barrier; the other CTAs
+// wait at the next cluster barrier.
 #pragma once
 
 #include "plane_relax.cuh"
@@ -42,7 +45,9 @@ struct LeanLevel {
     const C *fs;      // the level's two factor sets (interior lines, then the last line)
     int ny;           // lines
     int lb;           // first row of the level in the coefficient table
-    int uon, gon;     // u_m / g_m on chip (cluster addressing applies)
+    int uon, gon;     // u_m / g_m: 0 in the global slot, 1 on chip (cluster addressing applies),
+                      // 2 on chip with every line on CTA 0 (a solo level)
+    int solo;         // the level belongs whole to CTA 0 of the cluster
 };
 
 template <class C, int K>
@@ -62,6 +67,7 @@ __device__ __forceinline__ C *lean_line(const LeanEnv<C, K> &e, C *base, int on_
         return base + y * e.nx;
     } else {
         if (!on_chip) return base + y * e.nx;
+        if (on_chip == 2) return cg::this_cluster().map_shared_rank(base + y * e.nx, 0);
         const int k = y >> 1;
         const int owner = k & ((1 << e.lr) - 1);
         const int local = ((k >> e.lr) << 1) + (y & 1);
@@ -204,9 +210,13 @@ template <class S, class C, int K, bool CL>
 __device__ __forceinline__ void lean_colour(const LeanEnv<C, K> &e, TriFac<C, K> &fac, int &key, int m, int colour,
                                             int nbmode, int out, S *plane, bool acc) {
     const int nl = (e.lv[m].ny - colour + 1) / 2;
+    const bool dist = CL && !e.lv[m].solo;  // lines spread over the cluster
     int nown = nl;
-    if constexpr (CL) nown = (nl > e.rank) ? ((nl - e.rank + (1 << e.lr) - 1) >> e.lr) : 0;
-    auto Y = [&](int i) { return CL ? colour + 2 * (e.rank + (i << e.lr)) : colour + 2 * i; };
+    if constexpr (CL) {
+        if (dist) nown = (nl > e.rank) ? ((nl - e.rank + (1 << e.lr) - 1) >> e.lr) : 0;
+        else if (e.rank != 0) nown = 0;
+    }
+    auto Y = [&](int i) { return dist ? colour + 2 * (e.rank + (i << e.lr)) : colour + 2 * i; };
     int i = e.warp;
     if constexpr (lean_pair<C, K>() == 2) {
         for (; i + e.nw < nown; i += 2 * e.nw) {
@@ -248,14 +258,18 @@ __device__ __forceinline__ void lean_restrict_solve(const LeanEnv<C, K> &e, TriF
     const LeanLevel<C> L = e.lv[m], Lc = e.lv[m + 1];
     const int nx = e.nx, lane = e.lane;
     const int npairs = (Lc.ny + 1) / 2;
+    const bool dist = CL && !Lc.solo;  // coarse line pairs spread over the cluster
     int nown = npairs;
-    if constexpr (CL) nown = (npairs > e.rank) ? ((npairs - e.rank + (1 << e.lr) - 1) >> e.lr) : 0;
+    if constexpr (CL) {
+        if (dist) nown = (npairs > e.rank) ? ((npairs - e.rank + (1 << e.lr) - 1) >> e.lr) : 0;
+        else if (e.rank != 0) nown = 0;
+    }
     const int half = e.nw >> 1;
     if (2 * nown <= e.nw) {
         const bool odd = e.warp >= half;
         const int i = odd ? e.warp - half : e.warp;
         if (i >= nown) return;
-        const int k = CL ? e.rank + (i << e.lr) : i;
+        const int k = dist ? e.rank + (i << e.lr) : i;
         const int j = 2 * k + (odd ? 1 : 0);
         if (j >= Lc.ny) return;
         C g[1][K];
@@ -268,7 +282,7 @@ __device__ __forceinline__ void lean_restrict_solve(const LeanEnv<C, K> &e, TriF
         return;
     }
     for (int i = e.warp; i < nown; i += e.nw) {
-        const int k = CL ? e.rank + (i << e.lr) : i;
+        const int k = dist ? e.rank + (i << e.lr) : i;
         const int j0 = 2 * k, j1 = 2 * k + 1;
         C g0[1][K], g1[K];
         lean_restrict_line<C, K, CL>(e, L, j0, g0[0]);
@@ -424,8 +438,9 @@ __device__ __forceinline__ void plane_lean_task(const PlaneRelaxArgs &a, int pid
         for (int i = tid; i < a.sum_ny * kCoefPerLine; i += nt) sm[i] = pc[i];
         if (tid < P) {
             LeanLevel<C> L;
-            L.uon = static_cast<int>((a.smem_u_mask >> tid) & 1u);
-            L.gon = static_cast<int>((a.smem_g_mask >> tid) & 1u);
+            L.solo = (CL && tid >= a.solo_from) ? 1 : 0;
+            L.uon = static_cast<int>((a.smem_u_mask >> tid) & 1u) * (L.solo ? 2 : 1);
+            L.gon = static_cast<int>((a.smem_g_mask >> tid) & 1u) * (L.solo ? 2 : 1);
             L.u = (L.uon ? sm : gw) + a.off_u[tid];
             L.g = (L.gon ? sm : gw) + a.off_g[tid];
             L.fs = sm + a.off_fs + 2 * tid * trifac_fields<C, K>() * 32;
@@ -473,20 +488,35 @@ __device__ __forceinline__ void plane_lean_task(const PlaneRelaxArgs &a, int pid
         lean_sync<CL>();
         SMG_TRACE(1);
         if (P == 1) continue;
+        // a step runs on CTA 0 alone when the level it writes is solo (odd and even lines of level
+        // m: m >= solo_from; restriction to level m+1: m+1 >= solo_from); the barrier between two
+        // such steps is CTA 0's own
+        const int sf = CL ? a.solo_from : P;
+        auto step_sync = [&](bool solo_pair) {
+            if constexpr (CL) {
+                if (solo_pair) {
+                    if (e.rank == 0) __syncthreads();
+                    return;
+                }
+            }
+            lean_sync<CL>();
+        };
         for (int m = 0; m + 1 < P; ++m) {
             lean_colour<S, C, K, CL>(e, fac, key, m, 1, NB_PLAIN, OUT_U, plane, false);
-            lean_sync<CL>();
+            step_sync(m >= sf);  // odd(m) down -> restrict(m)
             SMG_TRACE(2 + 2 * m);
             lean_restrict_solve<C, K, CL>(e, fac, key, m);
-            lean_sync<CL>();
+            // restrict(m) runs on CTA 0 alone when level m+1 is solo; the next step is odd(m+1)
+            // down, or odd(P-2) up after the last restriction
+            step_sync(m + 1 < P - 1 ? m + 1 >= sf : m >= sf);
             SMG_TRACE(3 + 2 * m);
         }
         for (int m = P - 2; m >= 0; --m) {
             lean_colour<S, C, K, CL>(e, fac, key, m, 1, NB_CORR, m > 0 ? OUT_U : OUT_U_AND_PLANE, plane, acc);
-            lean_sync<CL>();
+            step_sync(m >= sf);  // odd(m) up -> even(m) up
             SMG_TRACE(2 * P + 2 * (P - 2 - m));
             lean_colour<S, C, K, CL>(e, fac, key, m, 0, NB_PLAIN, m > 0 ? OUT_U : OUT_PLANE, plane, acc);
-            lean_sync<CL>();
+            step_sync(m >= sf && m - 1 >= sf);  // even(m) up -> odd(m-1) up
             SMG_TRACE(2 * P + 1 + 2 * (P - 2 - m));
         }
     }

@@ -126,6 +126,8 @@ struct PlaneRelaxArgs {
     int W;                        // x-line segments of 512 rows (1 unless nx > 512: plane_wide.cu)
     int lean;                     // persistent multi-system kernel: 1 runs this entry with the
                                   // shortened-step cycle (its layout keeps every factor set on chip)
+    int solo_from;                // shortened-step cycle on a cluster: 2D levels >= solo_from belong
+                                  // whole to CTA 0 (kMaxPlaneLevels: none)
 };
 
 // Placement of the per-plane 2D-cycle arrays: shared memory where they fit, else global.
@@ -138,6 +140,7 @@ struct PlaneLayout {
     unsigned smem_u_mask = 0, smem_g_mask = 0;
     int MF = 0;                   // factor sets kept in shared memory (2D levels 0..MF-1)
     int off_fs = 0;
+    int solo_from = kMaxPlaneLevels;  // cluster layouts: 2D levels >= solo_from held whole by CTA 0
 };
 
 // Elements of one shared-memory factor set of the x-line solver (fields x 32 lanes).
@@ -151,9 +154,11 @@ PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t 
                               bool all_sets = false, bool no_sets = false);
 // Layout for a cluster of R CTAs per plane: each CTA holds the lines it owns (pairs (y/2) mod R)
 // of the arrays kept on chip; an array that does not fit lives whole in the cluster's global
-// slot.  smem_bytes = 0 when the coefficient table and factor sets alone exceed the budget.
+// slot.  The arrays of 2D levels >= solo_from are held whole (every line) by CTA 0 instead (the
+// same space is reserved on every CTA).  smem_bytes = 0 when the coefficient table and factor
+// sets alone exceed the budget.
 PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R,
-                                      bool all_sets = false);
+                                      bool all_sets = false, int solo_from = kMaxPlaneLevels);
 
 // Kernel launchers (cycle.cu and its instantiation units).
 enum class Prec { F64 = 0, F32 = 1, BF16 = 2 };

@@ -135,6 +135,28 @@ def test_shortened_step_plane_cycle_is_bitwise_the_general_one(smg, orc, prec, s
     assert_close(out[1], orc.SMG(nx, ny, nz, 1, npost).apply(r), 2e-5 if prec == "fp32" else 3e-2, shape, prec)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(128, 128, 16), (256, 256, 2), (200, 96, 20), (96, 80, 64), (64, 64, 4)])
+@pytest.mark.parametrize("threads", [512, 256])
+def test_solo_coarse_levels_are_bitwise_the_spread_ones(smg, orc, prec, shape, threads):
+    """Planes spread over a cluster with the coarse 2D levels held whole by the cluster's first CTA
+    (SMG_OPT_SOLO = T: the levels of at most T lines) give bit-identical cycles to every level
+    spread over the cluster: the same line solves in the same order, only their placement
+    differs."""
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=15)
+    out = {}
+    for solo in (32, 8, 0):
+        with smg.Handle(nx, ny, nz, 1, 1, precision=prec) as h:
+            smg.smg_set_option(h.h, smg.SMG_OPT_THREADS, threads)
+            smg.smg_set_option(h.h, smg.SMG_OPT_SOLO, solo)
+            sd = torch.empty(r.size, dtype=torch.float64, device="cuda")
+            smg.smg_apply(h.h, dev(r), sd)
+            out[solo] = sd.cpu().numpy()
+    assert np.array_equal(out[0], out[8]) and np.array_equal(out[0], out[32])
+    assert_close(out[8], orc.SMG(nx, ny, nz, 1, 1).apply(r), 1e-12 if prec == "fp64" else 2e-5, shape, prec)
+
+
 def test_apply_batched_matches_columns(smg, orc):
     nx, ny, nz, nb = 24, 20, 18, 3
     R = np.stack([inputs.rhs(nx, ny, nz, seed=20 + j).ravel() for j in range(nb)])
