@@ -92,7 +92,14 @@ enum {
                                  runs on a thread-block cluster, the 2D levels of at most T lines
                                  are held whole by the cluster's first CTA, whose steps on them
                                  end in a CTA barrier instead of a cluster barrier; the same
-                                 results as 0 (every level spread over the cluster) */
+                                 results as 0 (every level spread over the cluster) */,
+    SMG_OPT_RESTRICT_COLUMN = 11 /* 1 (default): with FP64 storage, or from 4M coarse points per
+                                 launch, each thread of the residual + restriction walks four
+                                 coarse planes, computing each fine residual (and each plane's
+                                 in-plane stencil) once; smaller FP32 / BF16 launches, and every
+                                 launch with 0, use one coarse plane per thread, recomputing the
+                                 residual of every even fine plane for both coarse planes it
+                                 feeds.  Bit-identical results */
 };
 
 /*

@@ -91,6 +91,7 @@ struct smg_ctx {
     int lean = 1;                   // 1: the shortened-step plane cycle where it applies
     int solo = 8;                   // its cluster layouts give the 2D levels of at most `solo`
                                     // lines to CTA 0 (0: none)
+    int restrict_column = 1;        // 1: the restriction walks columns of coarse planes
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
@@ -512,7 +513,7 @@ int run_cycle(smg_ctx *h, int nb, const void *f0, void *u0, cudaStream_t st) {
         cudaError_t e = launch_restrict(h->prec, h->nx, h->ny, H.nz_l[l], nb, F(l), U(l), h->d_f[l + 1],
                                         h->d_zcoef + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
                                         h->d_zcoef32 + static_cast<size_t>(H.plane_base[l]) * kCoefPerPlane,
-                                        h->Nl(l), h->Nl(l + 1), st);
+                                        h->Nl(l), h->Nl(l + 1), st, h->restrict_column != 0);
         if (e != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("restriction launch: ") + cudaGetErrorString(e));
         h->launches += 1;
     }
@@ -835,6 +836,10 @@ int smg_set_option(smg_handle h, int option, int value) {
         if (value != 256 && value != 512) return fail(SMG_ERR_ARG, "threads must be 256 or 512");
         if (value != h->threads) free_levels(h);  // the layouts and residency checks depend on it
         h->threads = value;
+        return SMG_OK;
+    case SMG_OPT_RESTRICT_COLUMN:
+        if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "restrict_column must be 0 or 1");
+        h->restrict_column = value;
         return SMG_OK;
     case SMG_OPT_SOLO:
         if (value < 0 || value > kMaxNy) return fail(SMG_ERR_ARG, "solo must be in [0, 512]");

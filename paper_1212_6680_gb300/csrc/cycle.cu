@@ -8,8 +8,9 @@
 // planes:
 //   f_c[j] = r[2j+1] + wp(2j) r[2j] + wm(2j+2) r[2j+2],   r = f - A_l u      (R = P^T)
 //   u[2j+1] += e[j],  u[2j] += wm(2j) e[j-1] + wp(2j) e[j]                   (P)
-// Both are bandwidth-bound stencils; one thread per output point, x fastest (coalesced), the
-// 15-point residual reads its five planes through L1/L2.
+// Both are bandwidth-bound stencils, x fastest (coalesced).  The restriction walks a column of
+// kRestrictJ coarse planes per thread, computing each fine residual once; the prolongation has one
+// thread per fine point.
 #include <cstdlib>
 #include "plane_relax.cuh"
 #include "transfer.cuh"
@@ -115,18 +116,25 @@ bool lean_cluster_resident(Prec storage, bool f64, int K, int R, int threads, si
 }
 
 // ---- residual + restriction -------------------------------------------------------------------
+constexpr int kRestrictJ = 4;  // coarse planes per thread (restrict_column)
 template <class S, class C>
 __global__ void restrict_kernel(int nx, int ny, int nzf, int nzc, long long total, const S *__restrict__ f,
                                 const S *__restrict__ u, S *__restrict__ fc, const double *__restrict__ zcoef64,
-                                const float *__restrict__ zcoef32, long long vsf, long long vsc) {
-    // blockIdx.y: one coarse plane, blockIdx.z: one batch entry; x covers the plane
+                                const float *__restrict__ zcoef32, long long vsf, long long vsc, int jper) {
+    // blockIdx.y: jper consecutive coarse planes, blockIdx.z: one batch entry; x covers the plane
     pdl_trigger();
     pdl_wait();
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= nx * ny) return;
     const int b = blockIdx.z;
-    restrict_point<S, C>(nx, ny, nzf, f + b * vsf, u + b * vsf, fc + b * vsc, coef_table<C>(zcoef64, zcoef32),
-                         blockIdx.y, ip);
+    if (jper == 1) {  // one coarse plane per thread
+        restrict_point<S, C>(nx, ny, nzf, f + b * vsf, u + b * vsf, fc + b * vsc, coef_table<C>(zcoef64, zcoef32),
+                             blockIdx.y, ip);
+        return;
+    }
+    const int j0 = blockIdx.y * jper, j1 = min(j0 + jper, nzc);
+    restrict_column<S, C>(nx, ny, nzf, f + b * vsf, u + b * vsf, fc + b * vsc, coef_table<C>(zcoef64, zcoef32), j0,
+                          j1, ip);
 }
 
 // ---- prolongation + correction ----------------------------------------------------------------
@@ -157,28 +165,36 @@ bool &pdl_enabled() {
 }
 
 cudaError_t launch_restrict(Prec storage, int nx, int ny, int nzf, int nb, const void *f, const void *u, void *fc,
-                            const double *zcoef, const float *zcoef32, long long vsf, long long vsc, cudaStream_t st) {
+                            const double *zcoef, const float *zcoef32, long long vsf, long long vsc, cudaStream_t st,
+                            bool column) {
     const int nzc = nzf / 2;
     const long long total = static_cast<long long>(nx) * ny * nzc * nb;
     if (total == 0) return cudaSuccess;
     const int T = 256;
-    const dim3 grid(nblocks(static_cast<long long>(nx) * ny, T), nzc, nb);
+    // column walks of kRestrictJ coarse planes per thread where they pay (measured on GB300): with
+    // FP64 storage, whose residual arithmetic runs on the slow FP64 pipe, and for launches of at
+    // least 4M coarse points; smaller FP32 / BF16 launches are latency-bound and keep one coarse
+    // plane per thread (one round of independent loads instead of a walk up nine planes)
+    const bool walk = column && (storage == Prec::F64 || total >= (1ll << 22));
+    const int jper = walk ? kRestrictJ : 1;
+    const int gy = (nzc + jper - 1) / jper;
+    const dim3 grid(nblocks(static_cast<long long>(nx) * ny, T), gy, nb);
     cudaError_t e = cudaSuccess;
     switch (storage) {
     case Prec::F64:
         e = launch_pdl(restrict_kernel<double, double>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<const double *>(f), static_cast<const double *>(u),
-            static_cast<double *>(fc), zcoef, zcoef32, vsf, vsc);
+            static_cast<double *>(fc), zcoef, zcoef32, vsf, vsc, jper);
         break;
     case Prec::F32:
         e = launch_pdl(restrict_kernel<float, float>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<const float *>(f), static_cast<const float *>(u),
-            static_cast<float *>(fc), zcoef, zcoef32, vsf, vsc);
+            static_cast<float *>(fc), zcoef, zcoef32, vsf, vsc, jper);
         break;
     case Prec::BF16:
         e = launch_pdl(restrict_kernel<__nv_bfloat16, float>, grid, dim3(T), 0, st,
             nx, ny, nzf, nzc, total, static_cast<const __nv_bfloat16 *>(f), static_cast<const __nv_bfloat16 *>(u),
-            static_cast<__nv_bfloat16 *>(fc), zcoef, zcoef32, vsf, vsc);
+            static_cast<__nv_bfloat16 *>(fc), zcoef, zcoef32, vsf, vsc, jper);
         break;
     }
     return e != cudaSuccess ? e : cudaGetLastError();

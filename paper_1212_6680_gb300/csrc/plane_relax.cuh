@@ -300,8 +300,13 @@ __device__ __forceinline__ void tri_apply(const TriFac<C, K> &f, C (&d)[NL][K], 
 }
 
 // ---- one plane: in-plane 5-point term M*L2D u + K*u of a neighbouring plane -----------------
+// (L2D u, u) at (x, y) of one plane, and the term M*L2D u + K*u from them.
+template <class C>
+struct PlanePoint {
+    C s, c;
+};
 template <class C, class S>
-__device__ __forceinline__ C plane_term(const S *u, int x, int y, int nx, int ny, C Mc, C Kc) {
+__device__ __forceinline__ PlanePoint<C> plane_point(const S *u, int x, int y, int nx, int ny) {
     const long long i = static_cast<long long>(y) * nx + x;
     const C c = ldv<C>(u + i);
     C s = C(4) * c;
@@ -309,7 +314,17 @@ __device__ __forceinline__ C plane_term(const S *u, int x, int y, int nx, int ny
     if (x < nx - 1) s -= ldv<C>(u + i + 1);
     if (y > 0) s -= ldv<C>(u + i - nx);
     if (y < ny - 1) s -= ldv<C>(u + i + nx);
-    return Mc * s + Kc * c;
+    return PlanePoint<C>{s, c};
+}
+// the rounding is spelled out (one product, then one fused multiply-add) so that every caller
+// gets the same bits whatever the compiler would contract
+template <class C>
+__device__ __forceinline__ C plane_term_of(const PlanePoint<C> &v, C Mc, C Kc) {
+    return fma(Mc, v.s, Kc * v.c);
+}
+template <class C, class S>
+__device__ __forceinline__ C plane_term(const S *u, int x, int y, int nx, int ny, C Mc, C Kc) {
+    return plane_term_of<C>(plane_point<C, S>(u, x, y, nx, ny), Mc, Kc);
 }
 
 enum : int { NB_NONE = 0, NB_PLAIN = 1, NB_CORR = 2 };

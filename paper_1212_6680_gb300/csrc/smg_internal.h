@@ -167,9 +167,11 @@ size_t storage_bytes(Prec p);
 // Plane relaxation: S = storage type, compute in double (F64 / coarsest) or float.
 cudaError_t launch_plane_relax(Prec storage, bool compute_f64, int K, int nplanes, int nb,
                                int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
+// column: each thread walks several coarse planes and computes each fine residual once (else one
+// coarse plane per thread); the results are bit-identical.
 cudaError_t launch_restrict(Prec storage, int nx, int ny, int nzf, int nb, const void *f,
                             const void *u, void *fc, const double *zcoef, const float *zcoef32,
-                            long long vstride_f, long long vstride_c, cudaStream_t st);
+                            long long vstride_f, long long vstride_c, cudaStream_t st, bool column = true);
 cudaError_t launch_prolong(Prec storage, int nx, int ny, int nzf, int nb, void *u, const void *uc,
                            const double *zcoef, const float *zcoef32, long long vstride_f,
                            long long vstride_c, cudaStream_t st);

@@ -157,6 +157,47 @@ def test_solo_coarse_levels_are_bitwise_the_spread_ones(smg, orc, prec, shape, t
     assert_close(out[8], orc.SMG(nx, ny, nz, 1, 1).apply(r), 1e-12 if prec == "fp64" else 2e-5, shape, prec)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 20), (7, 5, 3), (1, 1, 8), (5, 6, 1), (64, 48, 41),
+                                   (24, 20, 127), (9, 7, 18), (16, 8, 10)])
+@pytest.mark.parametrize("npost", [0, 1])
+def test_column_restriction_is_bitwise_the_per_point_one(smg, orc, prec, shape, npost):
+    """The residual + restriction walking four coarse planes per thread (each fine residual computed
+    once, SMG_OPT_RESTRICT_COLUMN = 1, the default) gives the same cycle, bit for bit, as one coarse
+    plane per thread, for one and for several right-hand sides, and both match the oracle."""
+    nx, ny, nz = shape
+    nb = 2
+    R = np.stack([inputs.rhs(nx, ny, nz, seed=50 + j).ravel() for j in range(nb)])
+    out = {}
+    for col in (1, 0):
+        with smg.Handle(nx, ny, nz, 1, npost, precision=prec) as h:
+            smg.smg_set_option(h.h, smg.SMG_OPT_RESTRICT_COLUMN, col)
+            Sd = torch.empty((nb, nx * ny * nz), dtype=torch.float64, device="cuda")
+            smg.smg_apply_batched(h.h, nb, dev(R), Sd)
+            out[col] = Sd.cpu().numpy()
+    assert np.array_equal(out[0], out[1])
+    tol = {"fp64": 1e-12, "fp32": 2e-5, "bf16": 3e-2}[prec]
+    ref = orc.SMG(nx, ny, nz, 1, npost).apply(R[1].reshape(nz, ny, nx)).ravel()
+    assert_close(out[1][1], ref, tol, shape, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_column_restriction_large_launch_is_bitwise(smg, prec):
+    """FP32 and BF16 storage walk columns only from 4M coarse points per launch (128 x 128 x 512:
+    the finest restriction has 4M): bit-identical to one coarse plane per thread there too."""
+    nx, ny, nz = 128, 128, 512
+    r = inputs.rhs(nx, ny, nz, seed=51).ravel()
+    out = {}
+    for col in (1, 0):
+        with smg.Handle(nx, ny, nz, 1, 0, precision=prec) as h:
+            smg.smg_set_option(h.h, smg.SMG_OPT_RESTRICT_COLUMN, col)
+            sd = torch.empty(r.size, dtype=torch.float64, device="cuda")
+            smg.smg_apply(h.h, dev(r), sd)
+            out[col] = sd.cpu().numpy()
+    assert np.isfinite(out[1]).all() and np.abs(out[1]).max() > 0
+    assert np.array_equal(out[0], out[1])
+
+
 def test_apply_batched_matches_columns(smg, orc):
     nx, ny, nz, nb = 24, 20, 18, 3
     R = np.stack([inputs.rhs(nx, ny, nz, seed=20 + j).ravel() for j in range(nb)])
