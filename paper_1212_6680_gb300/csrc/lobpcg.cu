@@ -31,6 +31,7 @@ namespace {
 constexpr int kGT = 16;          // Gram output tile (kGT x kGT per CTA of kGT * kGT threads)
 constexpr int kGRows = 64;       // rows staged per step
 constexpr int kGChunk = 8192;    // rows per CTA (split-K; fewer for small products)
+constexpr int kNormChunks = 256; // row chunks per column of the residual norms
 constexpr int kMulCols = 16;     // output columns per block_mul thread
 
 // ---- double-float arithmetic -------------------------------------------------------------------
@@ -241,10 +242,11 @@ __global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int nti
 // Y = alpha * U C + beta * Y  (U: n x k, C: k x m2 row-major, Y: n x m2, column stride n), the
 // products in double-float arithmetic.  A CTA covers NC output columns (NC a power of two, the
 // smallest that holds the product's columns, at most kMulCols), so narrow products do no work on
-// padding.
+// padding.  Y may overlap U when the product has a single column block (m2 <= NC, beta = 0):
+// each thread reads all k entries of its row before it writes the row.
 template <int NC>
-__global__ void block_mul_kernel(long long n, int k, int m2, const double *__restrict__ U,
-                                 const double *__restrict__ C, double alpha, double beta, double *__restrict__ Y) {
+__global__ void block_mul_kernel(long long n, int k, int m2, const double *U, const double *__restrict__ C,
+                                 double alpha, double beta, double *Y) {
     extern __shared__ __align__(16) float2 cs[];  // [k][NC] (hi, lo) pairs of C's column block
     const int j0 = blockIdx.y * NC;
     const int nc = min(NC, m2 - j0);
@@ -288,13 +290,52 @@ __global__ void block_mul_kernel(long long n, int k, int m2, const double *__res
     }
 }
 
-// R = AX - X diag(lambda)
-__global__ void residual_kernel(long long n, int m, const double *__restrict__ X, const double *__restrict__ AX,
-                                const double *__restrict__ lam, double *__restrict__ R) {
-    const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= n * m) return;
-    const int j = static_cast<int>(t / n);
-    R[t] = fma(-lam[j], X[t], AX[t]);
+// R = AX - X diag(lambda) for column blockIdx.y over one chunk of `rows` rows, and the chunk's sum of
+// squares of that column of R in partial[column * gridDim.x + chunk]: the convergence test needs
+// only the residual norms, not the whole Gram matrix R^T R.
+constexpr int kNormThreads = 256;
+__global__ void __launch_bounds__(kNormThreads) residual_norm_kernel(long long n, long long rows,
+                                                                     const double *__restrict__ X,
+                                                                     const double *__restrict__ AX,
+                                                                     const double *__restrict__ lam,
+                                                                     double *__restrict__ R,
+                                                                     double *__restrict__ partial) {
+    const int j = blockIdx.y;
+    const long long r0 = static_cast<long long>(blockIdx.x) * rows, r1 = min(n, r0 + rows);
+    const long long off = static_cast<long long>(j) * n;
+    const double l = lam[j];
+    double acc = 0.0;
+    for (long long i = r0 + threadIdx.x; i < r1; i += kNormThreads) {
+        const double v = fma(-l, X[off + i], AX[off + i]);
+        R[off + i] = v;
+        acc = fma(v, v, acc);
+    }
+    __shared__ double sh[kNormThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = (threadIdx.x < kNormThreads / 32) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) partial[static_cast<long long>(j) * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+// out[j] = the sum of column j's nch partials (one CTA per column, a fixed summation order)
+__global__ void __launch_bounds__(kNormThreads) column_sum_kernel(int nch, const double *__restrict__ partial,
+                                                                  double *__restrict__ out) {
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nch; i += kNormThreads) acc += partial[static_cast<long long>(j) * nch + i];
+    __shared__ double sh[kNormThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = (threadIdx.x < kNormThreads / 32) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) out[j] = acc;
+    }
 }
 
 int cdiv(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
@@ -555,7 +596,8 @@ int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<d
     return SMG_OK;
 }
 
-// Y = alpha U C + beta Y with C (k x m2, host row-major)
+// Y = alpha U C + beta Y with C (k x m2, host row-major).  Y may overlap U (the product written
+// in place) when m2 <= kMulCols and beta = 0 (block_mul_kernel).
 int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, double alpha, double beta, double *Y) {
     LCHK(cudaMemcpyAsync(c.w.coef, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, c.st));
     const int nc = (m2 <= 1) ? 1 : (m2 <= 2) ? 2 : (m2 <= 4) ? 4 : (m2 <= 8) ? 8 : kMulCols;
@@ -585,6 +627,11 @@ int ortho(Ctx &c, int q, double *Y, double *AY, double *tmp, bool &ok) {
     ok = cholesky(q, G.data(), L.data());
     if (!ok) return SMG_OK;
     lower_inverse_transpose(q, L.data(), Z.data());
+    if (q <= kMulCols) {  // one column block: in place
+        if ((rc = bmul(c, q, Y, q, Z, 1.0, 0.0, Y))) return rc;
+        if (AY && (rc = bmul(c, q, AY, q, Z, 1.0, 0.0, AY))) return rc;
+        return SMG_OK;
+    }
     const size_t bytes = sizeof(double) * static_cast<size_t>(q) * c.n;
     if ((rc = bmul(c, q, Y, q, Z, 1.0, 0.0, tmp))) return rc;
     LCHK(cudaMemcpyAsync(Y, tmp, bytes, cudaMemcpyDeviceToDevice, c.st));
@@ -706,16 +753,27 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
     int it = 0, status = SMG_ERR_NOCONV;
     double *d_lam = w.coef;  // reused for lambda right before the residual kernel
     for (it = 0;; ++it) {
-        // residuals R = AX - X Lambda into T1[:, 0:m]
+        // residuals R = AX - X Lambda into T1[:, 0:m], with their squared norms (the diagonal of
+        // R^T R, all the convergence test uses)
         double *R = w.T1;
         LCHK(cudaMemcpyAsync(d_lam, lam.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-        residual_kernel<<<cdiv(n * m, 256), 256, 0, st>>>(n, m, X, AX, d_lam, R);
-        LCHK(cudaGetLastError());
-        std::vector<double> GR;
-        if ((rc = gram(c, m, R, m, R, GR, true))) return rc;
+        {
+            const long long cap = w.part_tiles * kGT * kGT / m;  // partials the Gram buffer holds per column
+            const int nch = static_cast<int>(std::max<long long>(1, std::min<long long>(
+                std::min<long long>(kNormChunks, cdiv(n, kNormThreads)), cap)));
+            const long long rows = (n + nch - 1) / nch;
+            residual_norm_kernel<<<dim3(nch, m), kNormThreads, 0, st>>>(n, rows, X, AX, d_lam, R, w.part);
+            LCHK(cudaGetLastError());
+            column_sum_kernel<<<m, kNormThreads, 0, st>>>(nch, w.part, w.gram);
+            LCHK(cudaGetLastError());
+        }
+        std::vector<double> rn2(m);
+        LCHK(cudaMemcpyAsync(w.h_buf, w.gram, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        LCHK(cudaStreamSynchronize(st));
+        std::memcpy(rn2.data(), w.h_buf, sizeof(double) * m);
         std::vector<int> active;
         for (int j = 0; j < m; ++j) {
-            const double rn = std::sqrt(std::max(0.0, GR[j * m + j]));
+            const double rn = std::sqrt(std::max(0.0, rn2[j]));
             if (!std::isfinite(rn)) {
                 msg = "lobpcg: NaN in a residual";
                 return SMG_ERR_NAN;
@@ -729,11 +787,15 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         if (it >= maxit) break;
         const int na = static_cast<int>(active.size());
         double *W = w.S + static_cast<size_t>(n) * m, *AW = w.AS + static_cast<size_t>(n) * m;
-        // gather the active residuals and precondition them: W = T R_active
-        for (int a = 0; a < na; ++a)
-            LCHK(cudaMemcpyAsync(AW + static_cast<size_t>(n) * a, R + static_cast<size_t>(n) * active[a], col,
-                                 cudaMemcpyDeviceToDevice, st));
-        if ((rc = ops.apply_T(na, AW, W, st))) return rc;
+        // precondition the active residuals: W = T R_active (gathered first unless all are active)
+        if (na == m) {
+            if ((rc = ops.apply_T(na, R, W, st))) return rc;
+        } else {
+            for (int a = 0; a < na; ++a)
+                LCHK(cudaMemcpyAsync(AW + static_cast<size_t>(n) * a, R + static_cast<size_t>(n) * active[a], col,
+                                     cudaMemcpyDeviceToDevice, st));
+            if ((rc = ops.apply_T(na, AW, W, st))) return rc;
+        }
         // W -= X (X^T W)
         std::vector<double> XW;
         if ((rc = gram(c, m, X, na, W, XW))) return rc;
@@ -788,14 +850,21 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
                 Cm[i * m + j] = C[i * k + j];
                 if (i >= m) Cwp[(i - m) * m + j] = C[i * k + j];
             }
-        double *Xn = w.T1;  // T1 is free again (R no longer needed)
-        double *AXn = w.T1 + static_cast<size_t>(n) * m;
-        if ((rc = bmul(c, k, w.S, m, Cm, 1.0, 0.0, Xn))) return rc;
-        if ((rc = bmul(c, k, w.AS, m, Cm, 1.0, 0.0, AXn))) return rc;
+        // P, AP first: they read the W and P columns of S, AS; X, AX then overwrite the first m
+        // columns (in place when m <= kMulCols, else through T1, which is free again)
         if ((rc = bmul(c, k - m, W, m, Cwp, 1.0, 0.0, Pf))) return rc;
         if ((rc = bmul(c, k - m, AW, m, Cwp, 1.0, 0.0, APf))) return rc;
-        LCHK(cudaMemcpyAsync(X, Xn, col * m, cudaMemcpyDeviceToDevice, st));
-        LCHK(cudaMemcpyAsync(AX, AXn, col * m, cudaMemcpyDeviceToDevice, st));
+        if (m <= kMulCols) {
+            if ((rc = bmul(c, k, w.S, m, Cm, 1.0, 0.0, X))) return rc;
+            if ((rc = bmul(c, k, w.AS, m, Cm, 1.0, 0.0, AX))) return rc;
+        } else {
+            double *Xn = w.T1;
+            double *AXn = w.T1 + static_cast<size_t>(n) * m;
+            if ((rc = bmul(c, k, w.S, m, Cm, 1.0, 0.0, Xn))) return rc;
+            if ((rc = bmul(c, k, w.AS, m, Cm, 1.0, 0.0, AXn))) return rc;
+            LCHK(cudaMemcpyAsync(X, Xn, col * m, cudaMemcpyDeviceToDevice, st));
+            LCHK(cudaMemcpyAsync(AX, AXn, col * m, cudaMemcpyDeviceToDevice, st));
+        }
         haveP = true;
         for (int j = 0; j < m; ++j) lam[j] = theta[j];
     }
