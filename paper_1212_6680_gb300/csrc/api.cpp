@@ -89,9 +89,10 @@ struct smg_ctx {
     int cluster_max = 16;           // largest cluster for FP64-compute plane relaxations (1 = none)
     int precond = 1;                // krylov_solve's preconditioner: 1 the SMG cycle, 0 none (T = I)
     int lean = 1;                   // 1: the shortened-step plane cycle where it applies
-    int solo = 8;                   // its cluster layouts give the 2D levels of at most `solo`
-                                    // lines to CTA 0 (0: none)
-    int restrict_column = 1;        // 1: the restriction walks columns of coarse planes
+    int solo = 8;                   // shortened-step cluster layouts give the 2D levels of at most
+                                    // `solo` lines to CTA 0 (0: none)
+    int restrict_column = 1;        // 1: the restriction walks columns of coarse planes where it
+                                    // pays (launch_restrict)
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
