@@ -711,7 +711,7 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         LCHK(cudaMalloc(&w.S, blk));
         LCHK(cudaMalloc(&w.AS, blk));
         LCHK(cudaMalloc(&w.T1, blk));
-        LCHK(cudaMalloc(&w.T2, blk));
+        if (m > kMulCols) LCHK(cudaMalloc(&w.T2, blk));  // P, AP outside S (see below)
         const int k = 3 * m, nt = cdiv(k, kGT);
         w.part_tiles = static_cast<long long>(cdiv(n, kGChunk)) * nt * nt;
         int dev = 0;
@@ -725,8 +725,12 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
     }
     const size_t col = sizeof(double) * static_cast<size_t>(n);
     double *X = w.S, *AX = w.AS;
-    // P and AP for all m columns live in T2 (columns [0, m) and [m, 2m))
-    double *Pf = w.T2, *APf = w.T2 + static_cast<size_t>(n) * m;
+    // P and AP for all m columns: with m <= kMulCols in S, AS themselves, columns [2m, 3m) (the
+    // block products that form them are written in place, and W never reaches column 2m); else in
+    // T2 (columns [0, m) and [m, 2m))
+    const bool p_in_s = m <= kMulCols;
+    double *Pf = p_in_s ? w.S + static_cast<size_t>(n) * 2 * m : w.T2;
+    double *APf = p_in_s ? w.AS + static_cast<size_t>(n) * 2 * m : w.T2 + static_cast<size_t>(n) * m;
     int rc;
     LCHK(cudaMemcpyAsync(X, Xuser, col * m, cudaMemcpyDeviceToDevice, st));
     bool ok = false;
@@ -810,11 +814,14 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         int np = 0;
         double *Pa = w.S + static_cast<size_t>(n) * (m + na), *APa = w.AS + static_cast<size_t>(n) * (m + na);
         if (haveP) {
+            // gather the active columns; in S the target column m + na + a never lies after its
+            // source 2m + active[a] and never on a source still to be read, so column copies in
+            // increasing a are safe, and with every column active nothing moves
             for (int a = 0; a < na; ++a) {
-                LCHK(cudaMemcpyAsync(Pa + static_cast<size_t>(n) * a, Pf + static_cast<size_t>(n) * active[a], col,
-                                     cudaMemcpyDeviceToDevice, st));
-                LCHK(cudaMemcpyAsync(APa + static_cast<size_t>(n) * a, APf + static_cast<size_t>(n) * active[a], col,
-                                     cudaMemcpyDeviceToDevice, st));
+                const double *ps = Pf + static_cast<size_t>(n) * active[a], *aps = APf + static_cast<size_t>(n) * active[a];
+                double *pd = Pa + static_cast<size_t>(n) * a, *apd = APa + static_cast<size_t>(n) * a;
+                if (pd != ps) LCHK(cudaMemcpyAsync(pd, ps, col, cudaMemcpyDeviceToDevice, st));
+                if (apd != aps) LCHK(cudaMemcpyAsync(apd, aps, col, cudaMemcpyDeviceToDevice, st));
             }
             if ((rc = ortho(c, na, Pa, APa, R, ok))) return rc;
             np = ok ? na : 0;
@@ -850,14 +857,18 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
                 Cm[i * m + j] = C[i * k + j];
                 if (i >= m) Cwp[(i - m) * m + j] = C[i * k + j];
             }
-        // P, AP first: they read the W and P columns of S, AS; X, AX then overwrite the first m
-        // columns (in place when m <= kMulCols, else through T1, which is free again)
-        if ((rc = bmul(c, k - m, W, m, Cwp, 1.0, 0.0, Pf))) return rc;
-        if ((rc = bmul(c, k - m, AW, m, Cwp, 1.0, 0.0, APf))) return rc;
-        if (m <= kMulCols) {
+        if (p_in_s) {
+            // X, AX first, in place: they read every column of S, AS and write the first m; then
+            // P, AP, in place into columns [2m, 3m): they read the W and P columns [m, k), which the
+            // X update left alone (one column block each, so every thread reads its row first)
             if ((rc = bmul(c, k, w.S, m, Cm, 1.0, 0.0, X))) return rc;
             if ((rc = bmul(c, k, w.AS, m, Cm, 1.0, 0.0, AX))) return rc;
+            if ((rc = bmul(c, k - m, W, m, Cwp, 1.0, 0.0, Pf))) return rc;
+            if ((rc = bmul(c, k - m, AW, m, Cwp, 1.0, 0.0, APf))) return rc;
         } else {
+            // P, AP into T2 first (they read the W and P columns of S, AS), then X, AX through T1
+            if ((rc = bmul(c, k - m, W, m, Cwp, 1.0, 0.0, Pf))) return rc;
+            if ((rc = bmul(c, k - m, AW, m, Cwp, 1.0, 0.0, APf))) return rc;
             double *Xn = w.T1;
             double *AXn = w.T1 + static_cast<size_t>(n) * m;
             if ((rc = bmul(c, k, w.S, m, Cm, 1.0, 0.0, Xn))) return rc;
