@@ -504,16 +504,17 @@ size_t gram_tc_workspace_bytes(long long n) {
 }
 
 cudaError_t gram_tc(long long n, int k1, const double *U, long long ldu, int k2, const double *V, long long ldv,
-                    double *G, void *work, int num_sms, cudaStream_t st) {
+                    double *G, void *work, int num_sms, cudaStream_t st, bool reuse_u_cmax) {
     if (k1 < 1 || k2 < 1 || k1 > 64 || k2 > 64 || n < 1) return cudaErrorInvalidValue;
     unsigned long long *cmax = static_cast<unsigned long long *>(work);
     double *part = reinterpret_cast<double *>(cmax + 128);
-    cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * 128, st);
+    cudaError_t e = cudaMemsetAsync(cmax + (reuse_u_cmax ? 64 : 0), 0, sizeof(unsigned long long) * (reuse_u_cmax ? 64 : 128),
+                                    st);
     if (e != cudaSuccess) return e;
     {
         // about 16 CTAs per SM over all columns
         const int bx = static_cast<int>(std::min<long long>((n + 255) / 256, std::max(1, 16 * num_sms / std::max(1, k1))));
-        gram_colmax_kernel<<<dim3(std::max(1, bx), k1), 256, 0, st>>>(n, k1, U, ldu, cmax);
+        if (!reuse_u_cmax) gram_colmax_kernel<<<dim3(std::max(1, bx), k1), 256, 0, st>>>(n, k1, U, ldu, cmax);
         if (V != U || ldv != ldu || k2 != k1) {
             const int by = static_cast<int>(std::min<long long>((n + 255) / 256, std::max(1, 16 * num_sms / std::max(1, k2))));
             gram_colmax_kernel<<<dim3(std::max(1, by), k2), 256, 0, st>>>(n, k2, V, ldv, cmax + 64);

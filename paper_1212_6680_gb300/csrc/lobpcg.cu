@@ -539,12 +539,14 @@ struct Ctx {
     } while (0)
 
 // G (k1 x k2, host row-major) = U^T V; sym: the product is symmetric (k1 = k2 and U^T V = V^T U,
-// e.g. V = U or V = A U), so only its upper tiles are computed
-int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G, bool sym = false) {
+// e.g. V = U or V = A U), so only its upper tiles are computed.  same_u: the previous call had the
+// same U, unchanged since (the tensor-core path then reuses U's column maxima).
+int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<double> &G, bool sym = false,
+         bool same_u = false) {
     const int nti = cdiv(k1, kGT), ntj = cdiv(k2, kGT);
     if (c.w.gram_tc_min > 0 && k1 >= c.w.gram_tc_min && k2 >= c.w.gram_tc_min && k1 <= 64 && k2 <= 64) {
         // FP64-accurate digit-split products on the tensor cores
-        LCHK(gram_tc(c.n, k1, U, c.n, k2, V, c.n, c.w.gram, c.w.tc_work, c.w.num_sms, c.st));
+        LCHK(gram_tc(c.n, k1, U, c.n, k2, V, c.n, c.w.gram, c.w.tc_work, c.w.num_sms, c.st, same_u));
         G.resize(static_cast<size_t>(k1) * k2);
         LCHK(cudaMemcpyAsync(c.w.h_buf, c.w.gram, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c.st));
         LCHK(cudaStreamSynchronize(c.st));
@@ -829,7 +831,7 @@ int lobpcg_run(const LobpcgOps &ops, LobpcgWork &w, int m, double *Xuser, double
         // Rayleigh-Ritz on S = [X W P]
         int k = m + na + np;
         if ((rc = gram(c, k, w.S, k, w.AS, GA, true))) return rc;
-        if ((rc = gram(c, k, w.S, k, w.S, GB, true))) return rc;
+        if ((rc = gram(c, k, w.S, k, w.S, GB, true, true))) return rc;  // S's column maxima from GA
         if (!rayleigh_ritz(k, GA, GB, theta, C)) {
             if (np == 0) {
                 msg = "lobpcg: Gram matrix of [X W] is not positive definite";
