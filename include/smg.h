@@ -99,7 +99,13 @@ enum {
                                  in-plane stencil) once; smaller FP32 / BF16 launches, and every
                                  launch with 0, use one coarse plane per thread, recomputing the
                                  residual of every even fine plane for both coarse planes it
-                                 feeds.  Bit-identical results */
+                                 feeds.  Bit-identical results */,
+    SMG_OPT_WIDE_FACTORS = 12 /* 1 (default): planes with x-lines longer than 512 rows that are
+                                 relaxed in FP64 (the coarsest plane; every plane of an FP64 cycle
+                                 while the tables take at most 512 MB) read the line solver's
+                                 segment factors and reduced-system rows from tables formed once
+                                 when the level vectors are allocated; 0: formed inside the plane
+                                 cycle at every change of line matrix.  Bit-identical results */
 };
 
 /*

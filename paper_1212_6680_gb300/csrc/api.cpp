@@ -93,6 +93,10 @@ struct smg_ctx {
                                     // `solo` lines to CTA 0 (0: none)
     int restrict_column = 1;        // 1: the restriction walks columns of coarse planes where it
                                     // pays (launch_restrict)
+    int wide_factors = 1;           // 1: FP64 wide-line planes read their line-solver data from
+                                    // tables formed at set-up (d_wftab)
+    double *d_wftab = nullptr;      // those tables, all levels that have one
+    std::vector<long long> wftab_off;  // [L] offset of level l's table in d_wftab, -1: none
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
@@ -150,6 +154,9 @@ namespace {
 
 void free_levels(smg_ctx *h) {
     h->gen += 1;
+    cudaFree(h->d_wftab);
+    h->d_wftab = nullptr;
+    h->wftab_off.clear();
     for (void *p : h->d_f) cudaFree(p);
     for (void *p : h->d_u) cudaFree(p);
     h->d_f.clear();
@@ -218,6 +225,29 @@ int ensure_levels(smg_ctx *h, int nb) {
             int dev = 0;
             SMG_CUDA(cudaGetDevice(&dev));
             SMG_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        // line-solver tables for the planes relaxed in FP64: the coarsest level always, every level
+        // of an FP64 cycle while all of them take at most 512 MB
+        h->wftab_off.assign(H.L, -1);
+        if (h->wide_factors) {
+            const int W = wide_segments(h->nx);
+            const long long per = wide_factor_values(H.P, W);
+            long long all = 0;
+            for (int l = 0; l < H.L; ++l) all += per * H.nz_l[l];
+            const bool every = f64c && all * 8 <= (512ll << 20);
+            long long off = 0;
+            for (int l = every ? 0 : H.L - 1; l < H.L; ++l) {
+                h->wftab_off[l] = off;
+                off += per * H.nz_l[l];
+            }
+            SMG_CUDA(cudaMalloc(&h->d_wftab, static_cast<size_t>(off) * sizeof(double)));
+            for (int l = 0; l < H.L; ++l) {
+                if (h->wftab_off[l] < 0) continue;
+                SMG_CUDA(launch_wide_factor_table(h->nx, W, H.P, H.sum_ny, H.ny_m.data(), H.line_base.data(), H.nz_l[l],
+                                                  h->d_pcoef + static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine,
+                                                  h->d_wftab + h->wftab_off[l], 0));
+            }
+            SMG_CUDA(cudaStreamSynchronize(0));
         }
         return alloc_plane_workspace(h, nb);
     }
@@ -398,6 +428,8 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     PlaneRelaxArgs a;
     std::memset(&a, 0, sizeof(a));
     a.solo_from = kMaxPlaneLevels;
+    if (W > 1 && f64c && h->d_wftab != nullptr && l < static_cast<int>(h->wftab_off.size()) && h->wftab_off[l] >= 0)
+        a.wftab = h->d_wftab + h->wftab_off[l];
     a.nx = h->nx;
     a.ny = h->ny;
     a.nz = nzl;
@@ -837,6 +869,11 @@ int smg_set_option(smg_handle h, int option, int value) {
         if (value != 256 && value != 512) return fail(SMG_ERR_ARG, "threads must be 256 or 512");
         if (value != h->threads) free_levels(h);  // the layouts and residency checks depend on it
         h->threads = value;
+        return SMG_OK;
+    case SMG_OPT_WIDE_FACTORS:
+        if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "wide_factors must be 0 or 1");
+        if (value != h->wide_factors) free_levels(h);
+        h->wide_factors = value;
         return SMG_OK;
     case SMG_OPT_RESTRICT_COLUMN:
         if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "restrict_column must be 0 or 1");

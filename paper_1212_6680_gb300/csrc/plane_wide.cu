@@ -22,7 +22,9 @@
 // exact line solve; it differs from a one-warp solve only by rounding.
 // The x-halo of a segment (the neighbouring segments' edge values, read by the couplings) is
 // read from the line in memory.  One CTA per plane; the shortened-step cycle and clusters are
-// not used for these planes.
+// not used for these planes.  With FP64 compute the solver data of every 2D level's two line
+// matrices can come from a table formed once per set-up (wide_factor_kernel): at about two FP64
+// FMAs per clock per SM, forming them costs a one-CTA plane tens of microseconds per step.
 #include "plane_relax.cuh"
 
 namespace smg {
@@ -48,6 +50,7 @@ struct WideCtx {
     C *const *ub;
     C *const *gb;
     C *xb;        // exchange buffers: two of [warps][kXchg]
+    const C *ftab; // this plane's precomputed solver data ([m][set][segment] entries), or null
 };
 
 // The line solver's data for one line matrix (dg, of) on this warp's segment.
@@ -200,11 +203,68 @@ __device__ __forceinline__ const C *exchange(const WideCtx<C> &c, int &xp, const
     return b + (c.warp - c.seg) * kXchg;  // the team's first warp
 }
 
-// Make wf hold the solver data of (dg, of): the segment factors, eL, eR and the two rows of the
-// reduced system's inverse.  Every warp of the team calls this with the same (dg, of).
+// One table entry per (plane, 2D level, line set, segment): the factor fields of trifac_store,
+// then eL and eR (kWK x 32 each, field-major like the factors), then mv and mu.
+constexpr int kWEntry = trifac_fields<double, kWK>() * 32 + 2 * kWK * 32 + 4 * kMaxSeg;
+
 template <class C>
-__device__ __forceinline__ void ensure_wfac(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane) {
+__device__ __forceinline__ void wfac_store(C *e, const WideFac<C> &wf, int lane) {
+    trifac_store<C, kWK>(e, wf.f, lane);
+    C *p = e + trifac_fields<C, kWK>() * 32;
+#pragma unroll
+    for (int j = 0; j < kWK; ++j) {
+        p[j * 32 + lane] = wf.eL[j];
+        p[(kWK + j) * 32 + lane] = wf.eR[j];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 2 * kMaxSeg; ++q) {
+            p[2 * kWK * 32 + q] = wf.mv[q];
+            p[2 * kWK * 32 + 2 * kMaxSeg + q] = wf.mu[q];
+        }
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void wfac_load(WideFac<C> &wf, const C *e, int lane) {
+    trifac_load<C, kWK>(wf.f, e, lane);
+    const C *p = e + trifac_fields<C, kWK>() * 32;
+#pragma unroll
+    for (int j = 0; j < kWK; ++j) {
+        wf.eL[j] = p[j * 32 + lane];
+        wf.eR[j] = p[(kWK + j) * 32 + lane];
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * kMaxSeg; ++q) {
+        wf.mv[q] = p[2 * kWK * 32 + q];
+        wf.mu[q] = p[2 * kWK * 32 + 2 * kMaxSeg + q];
+    }
+}
+
+// The line matrix (diagonal, off-diagonal) of a line with coefficient row cr.
+template <class C>
+__device__ __forceinline__ void line_matrix(const CoefRow<C> &cr, C &dg, C &of) {
+    dg = C(2) * cr.s[1] + cr.t[1];
+    of = -cr.s[1];
+}
+
+// Make wf hold the solver data of (dg, of): the segment factors, eL, eR and the two rows of the
+// reduced system's inverse.  Every warp of the team calls this with the same (dg, of), so every
+// warp takes the same branch below (the table's entries of one (level, set) share (dg, of)).
+template <class C>
+__device__ __forceinline__ void ensure_wfac(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane,
+                                            int m = -1) {
     if (wf.f.dg == dg && wf.f.of == of) return;
+    if (c.ftab != nullptr && m >= 0) {
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            const C *e = c.ftab + (static_cast<long long>(2 * m + set) * c.W + c.seg) * kWEntry;
+            if (e[0] == dg && e[32] == of) {  // fields 0 and 1 hold the matrix (lane 0's copy)
+                wfac_load<C>(wf, e, lane);
+                return;
+            }
+        }
+    }
     tri_factor<C, kWK>(wf.f, dg, of, c.ns, lane);
     const int il = c.ns - 1;
     {
@@ -329,7 +389,9 @@ __device__ __forceinline__ void wide_relax_line(const WideCtx<C> &c, WideFac<C> 
                 if (lane * kWK + j >= c.ns) d[0][j] = C(0);
         }
     }
-    ensure_wfac(c, wf, C(2) * cr.s[1] + cr.t[1], -cr.s[1], xp, lane);
+    C dg, of;
+    line_matrix<C>(cr, dg, of);
+    ensure_wfac(c, wf, dg, of, xp, lane, m);
     wide_solve(c, wf, d, xp, lane);
     if (out != OUT_PLANE) wstore(wline_u(c, m, y), d[0], c, lane);
     if (out != OUT_U) {
@@ -456,6 +518,13 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     c.ns = min(kSeg, a.nx - c.x0);
     c.vec = a.vec != 0 && c.ns == kSeg;
     c.xb = s_xb;
+    c.ftab = nullptr;
+    if constexpr (sizeof(C) == 8) {
+        if (a.wftab != nullptr) {
+            const int zp = a.colour + 2 * pidx;  // the plane's index in its z-level
+            c.ftab = static_cast<const C *>(a.wftab) + static_cast<long long>(zp) * 2 * a.P * a.W * kWEntry;
+        }
+    }
     const bool active = c.team < c.nteam;
     if (tid < a.P) {
         s_ny[tid] = a.ny_m[tid];
@@ -534,6 +603,52 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     }
 }
 
+// The solver data of one (plane, 2D level m, line set) for all W segments: one warp per segment,
+// the same ensure_wfac as inside the plane cycle.  Grid (planes, 2P), W warps per CTA.
+struct WideFactorArgs {
+    int nx, W, P, sum_ny;
+    int ny_m[kMaxPlaneLevels];
+    int line_base[kMaxPlaneLevels];
+    const double *pcoef;  // the planes' coefficient tables (sum_ny lines x kCoefPerLine each)
+    double *tab;          // out: 2P W kWEntry doubles per plane
+};
+
+__global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
+    __shared__ __align__(16) double s_xb[2 * 16 * kXchg];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = blockIdx.x, pair = blockIdx.y, m = pair >> 1, set = pair & 1;
+    WideCtx<double> c;
+    c.sm = nullptr;
+    c.gw = nullptr;
+    c.g0 = nullptr;
+    c.nx = a.nx;
+    c.W = a.W;
+    c.warp = warp;
+    c.seg = warp;
+    c.team = 0;
+    c.nteam = 1;
+    c.x0 = c.seg * kSeg;
+    c.ns = min(kSeg, a.nx - c.x0);
+    c.vec = false;
+    c.ny = nullptr;
+    c.lb = nullptr;
+    c.ub = nullptr;
+    c.gb = nullptr;
+    c.xb = s_xb;
+    c.ftab = nullptr;
+    const int y = set ? a.ny_m[m] - 1 : 0;
+    const CoefRow<double> cr =
+        coef_row<double>(a.pcoef + (static_cast<long long>(p) * a.sum_ny + a.line_base[m] + y) * kCoefPerLine);
+    double dg, of;
+    line_matrix<double>(cr, dg, of);
+    WideFac<double> wf;
+    wf.f.dg = 0.0;
+    wf.f.of = 0.0;
+    int xp = 0;
+    ensure_wfac<double>(c, wf, dg, of, xp, lane);
+    wfac_store<double>(a.tab + ((static_cast<long long>(p) * 2 * a.P + pair) * a.W + c.seg) * kWEntry, wf, lane);
+}
+
 template <class S, class C>
 cudaError_t launch_wide(int nplanes, int nb, int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
     return launch_pdl(plane_wide_kernel<S, C>, dim3(nplanes, nb), dim3(threads), smem, st, a);
@@ -547,6 +662,26 @@ int wide_smem_attr(size_t smem) {
 }  // namespace
 
 int wide_segments(int nx) { return (nx + kSeg - 1) / kSeg; }
+
+long long wide_factor_values(int P, int W) { return 2LL * P * W * kWEntry; }
+
+cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
+                                     int nplanes, const double *pcoef, double *tab, cudaStream_t st) {
+    if (W < 2 || W > kMaxSeg || P < 1 || P > kMaxPlaneLevels || nplanes < 1) return cudaErrorInvalidValue;
+    WideFactorArgs a;
+    a.nx = nx;
+    a.W = W;
+    a.P = P;
+    a.sum_ny = sum_ny;
+    for (int m = 0; m < kMaxPlaneLevels; ++m) {
+        a.ny_m[m] = m < P ? ny_m[m] : 0;
+        a.line_base[m] = m < P ? line_base[m] : 0;
+    }
+    a.pcoef = pcoef;
+    a.tab = tab;
+    wide_factor_kernel<<<dim3(nplanes, 2 * P), 32 * W, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_plane_wide(Prec storage, bool f64, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
                               size_t smem, cudaStream_t st) {

@@ -56,6 +56,31 @@ def test_wide_lines_apply_matches_oracle(smg, orc, shape, prec, npre, npost):
     assert_close(s, ref, TOL[prec], shape, f"{prec} wide lines {shape} ({npre},{npost})")
 
 
+@pytest.mark.parametrize("shape", [(600, 20, 10), (1100, 12, 7), (2048, 8, 4), (1290, 9, 5), (777, 1, 6),
+                                   (1536, 5, 1)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_wide_factor_tables_are_bitwise_the_on_the_fly_ones(smg, orc, shape, prec):
+    """FP64 wide-line planes (the coarsest plane; every plane of the FP64 cycle) reading their
+    line-solver data from tables formed once (SMG_OPT_WIDE_FACTORS = 1, the default) give the cycle
+    bit for bit that forming the data inside the plane cycle gives."""
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=19)
+    out = {}
+    for wf in (1, 0):
+        h = smg.smg_setup(nx, ny, nz, 1, 1)
+        try:
+            smg.smg_set_precision(h, prec)
+            smg.smg_set_option(h, smg.SMG_OPT_WIDE_FACTORS, wf)
+            rd, sd = dev(r), torch.empty(nz * ny * nx, dtype=torch.float64, device="cuda")
+            smg.smg_apply(h, rd, sd)
+            torch.cuda.synchronize()
+            out[wf] = sd.cpu().numpy()
+        finally:
+            smg.smg_destroy(h)
+    assert np.array_equal(out[0], out[1])
+    assert_close(out[1], orc.SMG(nx, ny, nz, 1, 1).apply(r), TOL[prec], shape, prec)
+
+
 def test_wide_lines_batched_apply_matches_single(smg, orc):
     """Several right-hand sides per launch (LOBPCG's block preconditioner) on wide lines."""
     nx, ny, nz, m = 700, 6, 5, 3
