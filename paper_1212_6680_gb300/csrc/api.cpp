@@ -101,6 +101,8 @@ struct smg_ctx {
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
     PlaneLayout lay_lean32[5];      // FP32-compute shortened-step layouts (every factor set on chip)
+    PlaneLayout lay_wcl[2][5];      // wide-line cluster layouts: [FP64 compute][log2 R]
+    bool wcl_ok[2][5] = {{false, false, false, false, false}, {false, false, false, false, false}};
     bool lean32_ok[5] = {false, false, false, false, false};
     int cluster_max32 = 0;          // largest cluster for FP32-compute plane relaxations; 0 = chosen
                                     // per size (see relax)
@@ -217,9 +219,25 @@ int ensure_levels(smg_ctx *h, int nb) {
         // the fly, no cluster and no shortened-step layouts
         h->lay_c = plan_plane_layout(H, compute_bytes(h->prec), kWideSmemBudget, 16, false, true);
         h->lay_d = plan_plane_layout(H, 8, kWideSmemBudget, 16, false, true);
-        if (set_plane_wide_smem(h->prec, f64c, h->lay_c.smem_bytes) != 0 ||
-            set_plane_wide_smem(h->prec, true, h->lay_d.smem_bytes) != 0)
+        if (set_plane_wide_smem(h->prec, f64c, false, h->lay_c.smem_bytes) != 0 ||
+            set_plane_wide_smem(h->prec, true, false, h->lay_d.smem_bytes) != 0)
             return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, wide lines) failed");
+        // a plane spread over a cluster of R CTAs, each relaxing the lines it owns
+        for (int c64 = 0; c64 < 2; ++c64) {
+            for (int lr = 0; lr <= 4; ++lr) h->wcl_ok[c64][lr] = false;
+            if (!c64 && f64c) continue;  // an FP64 cycle has no FP32-compute planes
+            for (int lr = 1; lr <= 4; ++lr) {
+                const int R = 1 << lr;
+                PlaneLayout &ly = h->lay_wcl[c64][lr];
+                ly = plan_plane_layout_cluster(H, c64 ? 8 : 4, kWideSmemBudget, R, false, kMaxPlaneLevels, true);
+                if (ly.smem_bytes == 0 || ly.smem_bytes > kWideSmemBudget) continue;
+                if (set_plane_wide_smem(h->prec, c64 != 0, true, ly.smem_bytes) != 0) {
+                    cudaGetLastError();
+                    continue;
+                }
+                h->wcl_ok[c64][lr] = wide_cluster_resident(h->prec, c64 != 0, R, h->threads, ly.smem_bytes);
+            }
+        }
         for (int lr = 0; lr <= 4; ++lr) h->cl_ok[lr] = h->cl32_ok[lr] = h->lean64_ok[lr] = h->lean32_ok[lr] = false;
         if (h->num_sms == 0) {
             int dev = 0;
@@ -355,6 +373,8 @@ int alloc_plane_workspace(smg_ctx *h, int nb) {
     for (int lr = 0; lr <= 4; ++lr) {
         if (h->lean64_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_lean64[lr].ws_per_plane) * 8);
         if (h->lean32_ok[lr]) per = std::max(per, static_cast<size_t>(h->lay_lean32[lr].ws_per_plane) * 4);
+        if (h->wcl_ok[1][lr]) per = std::max(per, static_cast<size_t>(h->lay_wcl[1][lr].ws_per_plane) * 8);
+        if (h->wcl_ok[0][lr]) per = std::max(per, static_cast<size_t>(h->lay_wcl[0][lr].ws_per_plane) * 4);
     }
     const long long slots = static_cast<long long>((H.nz + 1) / 2) * nb;
     h->ws_bytes = std::max<size_t>(per * slots, 256);
@@ -411,20 +431,23 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     // coarsest level and up to 8 elsewhere (beyond 8 the cluster barrier costs more than the
     // FP64 work it spreads); FP32 planes stay on one CTA while its 2D-cycle iterate u_0 fits in
     // shared memory (the cycle is then latency-bound and a cluster only adds barrier cost), and
-    // use up to 4 CTAs when it does not (256-wide planes).
-    // Planes with x-lines longer than 512 rows run on one CTA each (plane_wide.cu).
+    // use up to 4 CTAs when it does not (256-wide planes).  Planes with x-lines longer than 512
+    // rows (plane_wide.cu) hold several lines per team of warps and are spread the same way, FP32
+    // ones over up to 8 CTAs (the paper's 16n x n x n bricks: 1280 x 80 x 80 FPCG 116 -> 57 ms).
     int R = 1;
     const int W = wide_segments(h->nx);
-    const bool *ok = f64c ? h->cl_ok : h->cl32_ok;
+    const bool *ok = (W > 1) ? h->wcl_ok[f64c ? 1 : 0] : (f64c ? h->cl_ok : h->cl32_ok);
     int rmax;
     if (f64c) rmax = coarsest ? h->cluster_max : std::min(h->cluster_max, 8);
     else if (h->cluster_max32 > 0) rmax = h->cluster_max32;
+    else if (W > 1) rmax = 8;
     else rmax = (h->lay_c.smem_u_mask & 1u) ? 1 : 4;
-    if (W > 1) rmax = 1;
     for (int cand = 2; cand <= rmax && cand <= 16; cand *= 2)
         if (ok[__builtin_ctz(cand)] && static_cast<long long>(nplanes) * nb * cand <= h->num_sms) R = cand;
-    const PlaneLayout &lay = (R > 1) ? (f64c ? h->lay_cl[__builtin_ctz(R)] : h->lay_cl32[__builtin_ctz(R)])
-                                     : ((f64c && h->prec != Prec::F64) ? h->lay_d : h->lay_c);
+    const PlaneLayout &lay =
+        (R > 1) ? (W > 1 ? h->lay_wcl[f64c ? 1 : 0][__builtin_ctz(R)]
+                         : (f64c ? h->lay_cl[__builtin_ctz(R)] : h->lay_cl32[__builtin_ctz(R)]))
+                : ((f64c && h->prec != Prec::F64) ? h->lay_d : h->lay_c);
     PlaneRelaxArgs a;
     std::memset(&a, 0, sizeof(a));
     a.solo_from = kMaxPlaneLevels;

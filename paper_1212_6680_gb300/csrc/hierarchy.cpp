@@ -288,13 +288,14 @@ PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t 
 }
 
 PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R,
-                                      bool all_sets, int solo_from) {
+                                      bool all_sets, int solo_from, bool no_sets) {
     PlaneLayout P;
     P.K = chunk_K(H.nx);
     P.solo_from = solo_from;
     auto align4 = [](size_t v) { return (v + 3) & ~static_cast<size_t>(3); };
     size_t smem_elems = align4(static_cast<size_t>(H.sum_ny) * kCoefPerLine);
-    P.MF = all_sets ? std::min(H.P, kMaxFactorLevels) : factor_levels(H, P.K, elem_bytes, smem_budget);
+    P.MF = no_sets ? 0
+                   : (all_sets ? std::min(H.P, kMaxFactorLevels) : factor_levels(H, P.K, elem_bytes, smem_budget));
     P.off_fs = static_cast<int>(smem_elems);
     smem_elems += 2 * static_cast<size_t>(P.MF) * trifac_set_elems(P.K);
     const size_t budget_elems = smem_budget / elem_bytes;

@@ -21,8 +21,11 @@
 // correction x_s = y_s - of v_{s-1} eL_s - of u_{s+1} eR_s.  In real arithmetic this is the
 // exact line solve; it differs from a one-warp solve only by rounding.
 // The x-halo of a segment (the neighbouring segments' edge values, read by the couplings) is
-// read from the line in memory.  One CTA per plane; the shortened-step cycle and clusters are
-// not used for these planes.  With FP64 compute the solver data of every 2D level's two line
+// read from the line in memory.  One CTA per plane, or a thread-block cluster of R CTAs per
+// plane: line y of an array kept on chip then belongs to CTA (y/2) mod R (local line
+// ((y/2) div R)*2 + y mod 2, the layout of plan_plane_layout_cluster), which relaxes, restricts
+// and assembles it, reading other CTAs' lines through distributed shared memory; the team of a
+// line is always inside one CTA.  The shortened-step cycle is not used for these planes.  With FP64 compute the solver data of every 2D level's two line
 // matrices can come from a table formed once per set-up (wide_factor_kernel): at about two FP64
 // FMAs per clock per SM, forming them costs a one-CTA plane tens of microseconds per step.
 #include "plane_relax.cuh"
@@ -49,6 +52,8 @@ struct WideCtx {
     const int *ny, *lb;
     C *const *ub;
     C *const *gb;
+    const int *uon, *gon;  // [m]: the level's u / g is on chip (spread over the cluster when R > 1)
+    int R, lr, rank;       // CTAs per plane (2^lr) and this CTA's rank
     C *xb;        // exchange buffers: two of [warps][kXchg]
     const C *ftab; // this plane's precomputed solver data ([m][set][segment] entries), or null
 };
@@ -66,14 +71,33 @@ __device__ __forceinline__ void team_sync(const WideCtx<C> &c) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + c.team), "r"(32 * c.W) : "memory");
 }
 
+// Line y of an array at `base`: in this CTA's slot or shared memory, or (a cluster's on-chip
+// array) in the shared memory of the CTA that owns it.
+template <class C>
+__device__ __forceinline__ C *wline(const WideCtx<C> &c, C *base, int on, int y) {
+    if (c.R > 1 && on) {
+        const int k = y >> 1;
+        const int local = ((k >> c.lr) << 1) + (y & 1);
+        return cg::this_cluster().map_shared_rank(base + static_cast<long long>(local) * c.nx, k & (c.R - 1));
+    }
+    return base + static_cast<long long>(y) * c.nx;
+}
 template <class C>
 __device__ __forceinline__ C *wline_u(const WideCtx<C> &c, int m, int y) {
-    return c.ub[m] + static_cast<long long>(y) * c.nx;
+    return wline(c, c.ub[m], c.uon[m], y);
 }
 template <class C>
 __device__ __forceinline__ C *wline_g(const WideCtx<C> &c, int m, int y) {
     if (m == 0 && c.g0 != nullptr) return c.g0 + static_cast<long long>(y) * c.nx;
-    return c.gb[m] + static_cast<long long>(y) * c.nx;
+    return wline(c, c.gb[m], c.gon[m], y);
+}
+
+// The j-th line this CTA owns of a level with n lines (the pairs (2i, 2i+1) with i mod R equal to
+// its rank; every line with one CTA), or n past the last: increasing in j.
+template <class C>
+__device__ __forceinline__ int owned_line(const WideCtx<C> &c, int j, int n) {
+    const int y = 2 * (c.rank + ((j >> 1) << c.lr)) + (j & 1);
+    return y < n ? y : n;
 }
 
 // Row x of a line, 0 outside 0 .. nx-1.
@@ -493,17 +517,32 @@ __device__ __forceinline__ void wide_rhs_line(const PlaneRelaxArgs &a, const Wid
     wstore(wline_g(c, 0, y), d, c, lane);
 }
 
-template <class S, class C>
+// One CTA (CL = false) or one cluster of a.R CTAs (CL = true) per plane of the colour; blockIdx.y
+// is the batch entry.
+template <class S, class C, bool CL>
 __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constant__ PlaneRelaxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) C s_xb[2 * 16 * kXchg];
-    __shared__ int s_ny[kMaxPlaneLevels], s_lb[kMaxPlaneLevels];
+    __shared__ int s_ny[kMaxPlaneLevels], s_lb[kMaxPlaneLevels], s_uon[kMaxPlaneLevels], s_gon[kMaxPlaneLevels];
     __shared__ C *s_ub[kMaxPlaneLevels], *s_gb[kMaxPlaneLevels];
     pdl_trigger();
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int pidx = static_cast<int>(blockIdx.x), b = static_cast<int>(blockIdx.y);
-    const long long slot = static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
+    int pidx, rank;
+    if constexpr (CL) {
+        rank = static_cast<int>(cg::this_cluster().block_rank());
+        pidx = static_cast<int>(blockIdx.x) / a.R;
+    } else {
+        rank = 0;
+        pidx = static_cast<int>(blockIdx.x);
+    }
+    const int b = static_cast<int>(blockIdx.y);
+    const long long slot = CL ? static_cast<long long>(blockIdx.y) * (gridDim.x / a.R) + pidx
+                              : static_cast<long long>(blockIdx.y) * gridDim.x + blockIdx.x;
+    auto step_sync = [&]() {
+        if constexpr (CL) cg::this_cluster().sync();
+        else __syncthreads();
+    };
     WideCtx<C> c;
     c.sm = reinterpret_cast<C *>(smem_raw);
     c.gw = reinterpret_cast<C *>(a.gws) + slot * a.ws_per_plane;
@@ -518,6 +557,9 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     c.ns = min(kSeg, a.nx - c.x0);
     c.vec = a.vec != 0 && c.ns == kSeg;
     c.xb = s_xb;
+    c.R = CL ? a.R : 1;
+    c.lr = CL ? __ffs(a.R) - 1 : 0;
+    c.rank = rank;
     c.ftab = nullptr;
     if constexpr (sizeof(C) == 8) {
         if (a.wftab != nullptr) {
@@ -529,13 +571,17 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     if (tid < a.P) {
         s_ny[tid] = a.ny_m[tid];
         s_lb[tid] = a.line_base[tid];
-        s_ub[tid] = (((a.smem_u_mask >> tid) & 1u) ? c.sm : c.gw) + a.off_u[tid];
-        s_gb[tid] = (((a.smem_g_mask >> tid) & 1u) ? c.sm : c.gw) + a.off_g[tid];
+        s_uon[tid] = static_cast<int>((a.smem_u_mask >> tid) & 1u);
+        s_gon[tid] = static_cast<int>((a.smem_g_mask >> tid) & 1u);
+        s_ub[tid] = (s_uon[tid] ? c.sm : c.gw) + a.off_u[tid];
+        s_gb[tid] = (s_gon[tid] ? c.sm : c.gw) + a.off_g[tid];
     }
     c.ny = s_ny;
     c.lb = s_lb;
     c.ub = s_ub;
     c.gb = s_gb;
+    c.uon = s_uon;
+    c.gon = s_gon;
     const int nx = a.nx, ny = a.ny;
     const long long np = static_cast<long long>(nx) * ny;
     const int z = a.colour + 2 * pidx;
@@ -549,6 +595,7 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     }
     __syncthreads();
     pdl_wait();
+    step_sync();  // (cluster) every CTA's level table and shared memory are set up
     WideFac<C> wf;
     wf.f.dg = C(0);  // no real line matrix has a zero diagonal: the first line always factors
     wf.f.of = C(0);
@@ -562,8 +609,12 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
             if (mode == 0) c.g0 = const_cast<C *>(reinterpret_cast<const C *>(fpl));
         }
         if (c.g0 == nullptr && active)
-            for (int y = c.team; y < ny; y += c.nteam) wide_rhs_line<S, C>(a, c, y, mode, fpl, ub, z, zc, lane);
-        __syncthreads();
+            for (int j = c.team;; j += c.nteam) {
+                const int y = owned_line(c, j, ny);
+                if (y >= ny) break;
+                wide_rhs_line<S, C>(a, c, y, mode, fpl, ub, z, zc, lane);
+            }
+        step_sync();
         const bool acc = (mode == 2);
         // the 2D cycle's steps in the order of plane_task (plane_relax.cuh)
         const int nsteps = (P == 1) ? 1 : 5 * P - 4;
@@ -591,14 +642,23 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
             }
             if (active) {
                 if (is_restrict) {
-                    for (int jc = c.team; jc < c.ny[m + 1]; jc += c.nteam) wide_restrict_line<C>(c, m, jc, lane);
+                    const int nc = c.ny[m + 1];
+                    for (int j = c.team;; j += c.nteam) {
+                        const int jc = owned_line(c, j, nc);
+                        if (jc >= nc) break;
+                        wide_restrict_line<C>(c, m, jc, lane);
+                    }
                 } else {
+                    // line colour + 2i belongs to CTA i mod R
                     const int nl = (c.ny[m] - colour + 1) / 2;
-                    for (int i = c.team; i < nl; i += c.nteam)
+                    for (int k = c.team;; k += c.nteam) {
+                        const int i = c.rank + (k << c.lr);
+                        if (i >= nl) break;
                         wide_relax_line<S, C>(c, wf, m, colour + 2 * i, plane, accu, nbmode, out, xp, lane);
+                    }
                 }
             }
-            __syncthreads();
+            step_sync();
         }
     }
 }
@@ -634,6 +694,11 @@ __global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
     c.lb = nullptr;
     c.ub = nullptr;
     c.gb = nullptr;
+    c.uon = nullptr;
+    c.gon = nullptr;
+    c.R = 1;
+    c.lr = 0;
+    c.rank = 0;
     c.xb = s_xb;
     c.ftab = nullptr;
     const int y = set ? a.ny_m[m] - 1 : 0;
@@ -651,12 +716,52 @@ __global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
 
 template <class S, class C>
 cudaError_t launch_wide(int nplanes, int nb, int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
-    return launch_pdl(plane_wide_kernel<S, C>, dim3(nplanes, nb), dim3(threads), smem, st, a);
+    if (a.R <= 1) return launch_pdl(plane_wide_kernel<S, C, false>, dim3(nplanes, nb), dim3(threads), smem, st, a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nplanes * a.R, nb, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = a.R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, plane_wide_kernel<S, C, true>, a);
 }
 
 template <class S, class C>
-int wide_smem_attr(size_t smem) {
-    return static_cast<int>(raise_smem_attr(reinterpret_cast<const void *>(&plane_wide_kernel<S, C>), smem));
+int wide_smem_attr(bool cl, size_t smem) {
+    if (!cl)
+        return static_cast<int>(raise_smem_attr(reinterpret_cast<const void *>(&plane_wide_kernel<S, C, false>), smem));
+    cudaError_t e = raise_smem_attr(reinterpret_cast<const void *>(&plane_wide_kernel<S, C, true>), smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(plane_wide_kernel<S, C, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return static_cast<int>(e);
+}
+
+template <class S, class C>
+bool wide_resident(int R, int threads, size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(R, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, plane_wide_kernel<S, C, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
 }
 
 }  // namespace
@@ -685,7 +790,8 @@ cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int
 
 cudaError_t launch_plane_wide(Prec storage, bool f64, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
                               size_t smem, cudaStream_t st) {
-    if (a.W < 2 || a.W > kMaxSeg || threads / 32 < a.W || threads > 512) return cudaErrorInvalidValue;
+    if (a.W < 2 || a.W > kMaxSeg || threads / 32 < a.W || threads > 512 || a.R < 1 || a.R > 16 || (a.R & (a.R - 1)))
+        return cudaErrorInvalidValue;
     switch (storage) {
     case Prec::F64: return launch_wide<double, double>(nplanes, nb, threads, a, smem, st);
     case Prec::F32:
@@ -698,14 +804,25 @@ cudaError_t launch_plane_wide(Prec storage, bool f64, int nplanes, int nb, int t
     return cudaErrorInvalidValue;
 }
 
-int set_plane_wide_smem(Prec storage, bool f64, size_t smem) {
+int set_plane_wide_smem(Prec storage, bool f64, bool cl, size_t smem) {
     switch (storage) {
-    case Prec::F64: return wide_smem_attr<double, double>(smem);
-    case Prec::F32: return f64 ? wide_smem_attr<float, double>(smem) : wide_smem_attr<float, float>(smem);
+    case Prec::F64: return wide_smem_attr<double, double>(cl, smem);
+    case Prec::F32: return f64 ? wide_smem_attr<float, double>(cl, smem) : wide_smem_attr<float, float>(cl, smem);
     case Prec::BF16:
-        return f64 ? wide_smem_attr<__nv_bfloat16, double>(smem) : wide_smem_attr<__nv_bfloat16, float>(smem);
+        return f64 ? wide_smem_attr<__nv_bfloat16, double>(cl, smem) : wide_smem_attr<__nv_bfloat16, float>(cl, smem);
     }
     return static_cast<int>(cudaErrorInvalidValue);
+}
+
+bool wide_cluster_resident(Prec storage, bool f64, int R, int threads, size_t smem) {
+    switch (storage) {
+    case Prec::F64: return wide_resident<double, double>(R, threads, smem);
+    case Prec::F32: return f64 ? wide_resident<float, double>(R, threads, smem) : wide_resident<float, float>(R, threads, smem);
+    case Prec::BF16:
+        return f64 ? wide_resident<__nv_bfloat16, double>(R, threads, smem)
+                   : wide_resident<__nv_bfloat16, float>(R, threads, smem);
+    }
+    return false;
 }
 
 }  // namespace smg

@@ -160,7 +160,7 @@ PlaneLayout plan_plane_layout(const HostHierarchy &H, size_t elem_bytes, size_t 
 // same space is reserved on every CTA).  smem_bytes = 0 when the coefficient table and factor
 // sets alone exceed the budget.
 PlaneLayout plan_plane_layout_cluster(const HostHierarchy &H, size_t elem_bytes, size_t smem_budget, int R,
-                                      bool all_sets = false, int solo_from = kMaxPlaneLevels);
+                                      bool all_sets = false, int solo_from = kMaxPlaneLevels, bool no_sets = false);
 
 // Kernel launchers (cycle.cu and its instantiation units).
 enum class Prec { F64 = 0, F32 = 1, BF16 = 2 };
@@ -209,7 +209,9 @@ cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int
                                      int nplanes, const double *pcoef, double *tab, cudaStream_t st);
 cudaError_t launch_plane_wide(Prec storage, bool compute_f64, int nplanes, int nb, int threads,
                               const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
-int set_plane_wide_smem(Prec storage, bool compute_f64, size_t smem);
+int set_plane_wide_smem(Prec storage, bool compute_f64, bool cluster, size_t smem);
+// Whether a cluster of R wide-line CTAs with `smem` bytes each fits on the GPU at once.
+bool wide_cluster_resident(Prec storage, bool compute_f64, int R, int threads, size_t smem);
 // True when a cluster of R CTAs of the plane kernel (FP64 or FP32 compute) can be resident.
 bool cluster_resident(Prec storage, bool compute_f64, int K, int R, int threads, size_t smem);
 

@@ -81,6 +81,33 @@ def test_wide_factor_tables_are_bitwise_the_on_the_fly_ones(smg, orc, shape, pre
     assert_close(out[1], orc.SMG(nx, ny, nz, 1, 1).apply(r), TOL[prec], shape, prec)
 
 
+@pytest.mark.parametrize("shape", [(600, 20, 10), (1100, 12, 7), (2048, 8, 4), (1290, 9, 5), (777, 1, 6),
+                                   (1536, 5, 1), (1280, 40, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_wide_planes_on_clusters_are_bitwise_one_cta(smg, orc, shape, prec):
+    """Wide-line planes spread over thread-block clusters (each CTA relaxing the lines it owns,
+    reading the others' through distributed shared memory) give the cycle of one CTA per plane bit
+    for bit: every line is solved by the same code on the same data."""
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=23)
+    out = {}
+    for one in (False, True):
+        h = smg.smg_setup(nx, ny, nz, 1, 1)
+        try:
+            smg.smg_set_precision(h, prec)
+            if one:
+                smg.smg_set_option(h, smg.SMG_OPT_CLUSTER_MAX, 1)
+                smg.smg_set_option(h, smg.SMG_OPT_CLUSTER_MAX32, 1)
+            rd, sd = dev(r), torch.empty(nz * ny * nx, dtype=torch.float64, device="cuda")
+            smg.smg_apply(h, rd, sd)
+            torch.cuda.synchronize()
+            out[one] = sd.cpu().numpy()
+        finally:
+            smg.smg_destroy(h)
+    assert np.array_equal(out[False], out[True])
+    assert_close(out[False], orc.SMG(nx, ny, nz, 1, 1).apply(r), TOL[prec], shape, prec)
+
+
 def test_wide_lines_batched_apply_matches_single(smg, orc):
     """Several right-hand sides per launch (LOBPCG's block preconditioner) on wide lines."""
     nx, ny, nz, m = 700, 6, 5, 3
