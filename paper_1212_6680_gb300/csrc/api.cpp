@@ -93,10 +93,10 @@ struct smg_ctx {
                                     // `solo` lines to CTA 0 (0: none)
     int restrict_column = 1;        // 1: the restriction walks columns of coarse planes where it
                                     // pays (launch_restrict)
-    int wide_factors = 1;           // 1: FP64 wide-line planes read their line-solver data from
-                                    // tables formed at set-up (d_wftab)
-    double *d_wftab = nullptr;      // those tables, all levels that have one
-    std::vector<long long> wftab_off;  // [L] offset of level l's table in d_wftab, -1: none
+    int wide_factors = 1;           // 1: wide-line planes read their line-solver data from tables
+                                    // formed with the level vectors (d_wftab)
+    unsigned char *d_wftab = nullptr;  // those tables (each level's in its compute type)
+    std::vector<long long> wftab_off;  // [L] byte offset of level l's table in d_wftab, -1: none
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
@@ -244,25 +244,31 @@ int ensure_levels(smg_ctx *h, int nb) {
             SMG_CUDA(cudaGetDevice(&dev));
             SMG_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
         }
-        // line-solver tables for the planes relaxed in FP64: the coarsest level always, every level
-        // of an FP64 cycle while all of them take at most 512 MB
+        // line-solver tables, each level's in its compute type (FP64 on the coarsest level and in an
+        // FP64 cycle, else FP32): the coarsest level always, the others while all tables take at
+        // most 512 MB
         h->wftab_off.assign(H.L, -1);
         if (h->wide_factors) {
             const int W = wide_segments(h->nx);
             const long long per = wide_factor_values(H.P, W);
+            auto bytes_of = [&](int l) -> long long {
+                const bool c64 = f64c || l == H.L - 1;
+                return per * H.nz_l[l] * (c64 ? 8 : 4);
+            };
             long long all = 0;
-            for (int l = 0; l < H.L; ++l) all += per * H.nz_l[l];
-            const bool every = f64c && all * 8 <= (512ll << 20);
+            for (int l = 0; l < H.L; ++l) all += bytes_of(l);
+            const bool every = all <= (512ll << 20);
             long long off = 0;
             for (int l = every ? 0 : H.L - 1; l < H.L; ++l) {
                 h->wftab_off[l] = off;
-                off += per * H.nz_l[l];
+                off += (bytes_of(l) + 255) / 256 * 256;
             }
-            SMG_CUDA(cudaMalloc(&h->d_wftab, static_cast<size_t>(off) * sizeof(double)));
+            SMG_CUDA(cudaMalloc(&h->d_wftab, static_cast<size_t>(off)));
             for (int l = 0; l < H.L; ++l) {
                 if (h->wftab_off[l] < 0) continue;
+                const size_t pb = static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine;
                 SMG_CUDA(launch_wide_factor_table(h->nx, W, H.P, H.sum_ny, H.ny_m.data(), H.line_base.data(), H.nz_l[l],
-                                                  h->d_pcoef + static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine,
+                                                  h->d_pcoef + pb, h->d_pcoef32 + pb, f64c || l == H.L - 1,
                                                   h->d_wftab + h->wftab_off[l], 0));
             }
             SMG_CUDA(cudaStreamSynchronize(0));
@@ -451,7 +457,9 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     PlaneRelaxArgs a;
     std::memset(&a, 0, sizeof(a));
     a.solo_from = kMaxPlaneLevels;
-    if (W > 1 && f64c && h->d_wftab != nullptr && l < static_cast<int>(h->wftab_off.size()) && h->wftab_off[l] >= 0)
+    // the level's table was formed in its compute type: FP64 exactly when f64c (the coarsest level
+    // or an FP64 cycle)
+    if (W > 1 && h->d_wftab != nullptr && l < static_cast<int>(h->wftab_off.size()) && h->wftab_off[l] >= 0)
         a.wftab = h->d_wftab + h->wftab_off[l];
     a.nx = h->nx;
     a.ny = h->ny;

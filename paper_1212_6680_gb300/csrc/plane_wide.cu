@@ -561,11 +561,9 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     c.lr = CL ? __ffs(a.R) - 1 : 0;
     c.rank = rank;
     c.ftab = nullptr;
-    if constexpr (sizeof(C) == 8) {
-        if (a.wftab != nullptr) {
-            const int zp = a.colour + 2 * pidx;  // the plane's index in its z-level
-            c.ftab = static_cast<const C *>(a.wftab) + static_cast<long long>(zp) * 2 * a.P * a.W * kWEntry;
-        }
+    if (a.wftab != nullptr) {  // a table of the compute type C (the host passes the matching one)
+        const int zp = a.colour + 2 * pidx;  // the plane's index in its z-level
+        c.ftab = static_cast<const C *>(a.wftab) + static_cast<long long>(zp) * 2 * a.P * a.W * kWEntry;
     }
     const bool active = c.team < c.nteam;
     if (tid < a.P) {
@@ -670,14 +668,16 @@ struct WideFactorArgs {
     int ny_m[kMaxPlaneLevels];
     int line_base[kMaxPlaneLevels];
     const double *pcoef;  // the planes' coefficient tables (sum_ny lines x kCoefPerLine each)
-    double *tab;          // out: 2P W kWEntry doubles per plane
+    const float *pcoef32; // the same rounded to FP32
+    void *tab;            // out: 2P W kWEntry values of the compute type per plane
 };
 
+template <class C>
 __global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
-    __shared__ __align__(16) double s_xb[2 * 16 * kXchg];
+    __shared__ __align__(16) C s_xb[2 * 16 * kXchg];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = blockIdx.x, pair = blockIdx.y, m = pair >> 1, set = pair & 1;
-    WideCtx<double> c;
+    WideCtx<C> c;
     c.sm = nullptr;
     c.gw = nullptr;
     c.g0 = nullptr;
@@ -702,16 +702,17 @@ __global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
     c.xb = s_xb;
     c.ftab = nullptr;
     const int y = set ? a.ny_m[m] - 1 : 0;
-    const CoefRow<double> cr =
-        coef_row<double>(a.pcoef + (static_cast<long long>(p) * a.sum_ny + a.line_base[m] + y) * kCoefPerLine);
-    double dg, of;
-    line_matrix<double>(cr, dg, of);
-    WideFac<double> wf;
-    wf.f.dg = 0.0;
-    wf.f.of = 0.0;
+    const CoefRow<C> cr = coef_row<C>(coef_table<C>(a.pcoef, a.pcoef32) +
+                                      (static_cast<long long>(p) * a.sum_ny + a.line_base[m] + y) * kCoefPerLine);
+    C dg, of;
+    line_matrix<C>(cr, dg, of);
+    WideFac<C> wf;
+    wf.f.dg = C(0);
+    wf.f.of = C(0);
     int xp = 0;
-    ensure_wfac<double>(c, wf, dg, of, xp, lane);
-    wfac_store<double>(a.tab + ((static_cast<long long>(p) * 2 * a.P + pair) * a.W + c.seg) * kWEntry, wf, lane);
+    ensure_wfac<C>(c, wf, dg, of, xp, lane);
+    wfac_store<C>(static_cast<C *>(a.tab) + ((static_cast<long long>(p) * 2 * a.P + pair) * a.W + c.seg) * kWEntry, wf,
+                  lane);
 }
 
 template <class S, class C>
@@ -771,7 +772,8 @@ int wide_segments(int nx) { return (nx + kSeg - 1) / kSeg; }
 long long wide_factor_values(int P, int W) { return 2LL * P * W * kWEntry; }
 
 cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
-                                     int nplanes, const double *pcoef, double *tab, cudaStream_t st) {
+                                     int nplanes, const double *pcoef, const float *pcoef32, bool f64, void *tab,
+                                     cudaStream_t st) {
     if (W < 2 || W > kMaxSeg || P < 1 || P > kMaxPlaneLevels || nplanes < 1) return cudaErrorInvalidValue;
     WideFactorArgs a;
     a.nx = nx;
@@ -783,8 +785,10 @@ cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int
         a.line_base[m] = m < P ? line_base[m] : 0;
     }
     a.pcoef = pcoef;
+    a.pcoef32 = pcoef32;
     a.tab = tab;
-    wide_factor_kernel<<<dim3(nplanes, 2 * P), 32 * W, 0, st>>>(a);
+    if (f64) wide_factor_kernel<double><<<dim3(nplanes, 2 * P), 32 * W, 0, st>>>(a);
+    else wide_factor_kernel<float><<<dim3(nplanes, 2 * P), 32 * W, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -198,15 +198,16 @@ bool lean_uniform_level(const HostHierarchy &H, int l);
 // Plane relaxation for nx > 512 (plane_wide.cu): x-lines cut into wide_segments(nx) segments of
 // 512 rows, one warp each, coupled through a reduced system; one CTA per plane (a.W segments).
 int wide_segments(int nx);
-// Line-solver data of FP64 wide-line planes, formed once instead of at every change of line
-// matrix inside the plane cycle: for nplanes consecutive planes of one z-level (pcoef: their
+// Line-solver data of wide-line planes, formed once instead of at every change of line matrix
+// inside the plane cycle: for nplanes consecutive planes of one z-level (pcoef / pcoef32: their
 // coefficient tables) and every 2D level m and line set (0: the first line's matrix, 1: the
 // last line's), the segment factors, T_s^{-1} e_first, T_s^{-1} e_last and the reduced system's
-// inverse rows of every segment, computed by the same code as on the fly (bit-identical).
-// wide_factor_values(P, W): doubles per plane.
+// inverse rows of every segment, in the compute type (FP64 when f64, else FP32), computed by the
+// same code as on the fly (bit-identical).  wide_factor_values(P, W): values per plane.
 long long wide_factor_values(int P, int W);
 cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
-                                     int nplanes, const double *pcoef, double *tab, cudaStream_t st);
+                                     int nplanes, const double *pcoef, const float *pcoef32, bool f64, void *tab,
+                                     cudaStream_t st);
 cudaError_t launch_plane_wide(Prec storage, bool compute_f64, int nplanes, int nb, int threads,
                               const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
 int set_plane_wide_smem(Prec storage, bool compute_f64, bool cluster, size_t smem);
