@@ -1,6 +1,7 @@
 """Run one small case of the solver path, for profiling under a kernel profiler.
 
     python -m paper_1212_6680_gb300.profile_case fpcg    --n 128 --prec fp32 --solves 2
+    python -m paper_1212_6680_gb300.profile_case brick   --n 80 --prec fp32 --solves 1
     python -m paper_1212_6680_gb300.profile_case learned --n 128 --solves 1
     python -m paper_1212_6680_gb300.profile_case lobpcg  --n 48 --m 16
     python -m paper_1212_6680_gb300.profile_case batched --nsys 16
@@ -19,7 +20,7 @@ import numpy as np
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fpcg", "learned", "lobpcg", "batched"])
+    ap.add_argument("case", choices=["fpcg", "brick", "learned", "lobpcg", "batched"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--prec", default="fp32")
     ap.add_argument("--npost", type=int, default=0)
@@ -39,11 +40,12 @@ def main() -> None:
     from . import smg as S
 
     out = {"case": a.case}
-    if a.case in ("fpcg", "learned"):
-        n = a.n
-        b = torch.from_numpy(inputs.rhs(n, n, n, seed=0).ravel().copy()).cuda()
+    if a.case in ("fpcg", "brick", "learned"):
+        # the n^3 cube, or the paper's 16n x n x n brick (long in x)
+        nx, ny, nz = (16 * a.n, a.n, a.n) if a.case == "brick" else (a.n, a.n, a.n)
+        b = torch.from_numpy(inputs.rhs(nx, ny, nz, seed=0).ravel().copy()).cuda()
         x = torch.zeros_like(b)
-        h = S.smg_setup(n, n, n, 1, a.npost)
+        h = S.smg_setup(nx, ny, nz, 1, a.npost)
         S.smg_set_precision(h, a.prec)
         # the host loop launches every kernel of an iteration itself, so a kernel profiler sees each
         # launch (the device-side loop runs them inside a conditional graph node)
