@@ -433,6 +433,23 @@ int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, dou
  */
 int smg_plane_layout(int nx, int ny, int elem_bytes, int R, long long *out);
 
+/*
+ * smg_plane_layout_kind -- smg_plane_layout for each plane-cycle kernel's own layout (host only):
+ *   kind 0: the general cycle (smg_plane_layout's plan);
+ *   kind 1: the shortened-step cycle, nx <= 256: every 2D level's factor sets on chip (MF = P);
+ *           on a cluster (R > 1) the 2D levels of at most `solo` lines from the first such level
+ *           on are held whole by the cluster's first CTA where that keeps on chip every array the
+ *           spread plan keeps (solo = 0: none);
+ *   kind 2: the wide-line cycle, 513 <= nx <= 2048: no factor sets on chip (MF = 0), 2 KB of the
+ *           shared memory left to the kernel's static arrays.
+ * out as smg_plane_layout's, plus [11] the first 2D level held whole by the first CTA (P when
+ * none).  A level held whole keeps all ny_m lines on every CTA's plan (CTA 0 uses them); a spread
+ * level keeps 2 ceil(ceil(ny_m / 2) / R) lines.  Residency of the cluster on the GPU is not
+ * checked here (the library falls back to the spread plan, or a smaller cluster, at run time).
+ * Arguments outside these ranges (and those smg_plane_layout refuses) return SMG_ERR_ARG.
+ */
+int smg_plane_layout_kind(int nx, int ny, int elem_bytes, int R, int kind, int solo, long long *out);
+
 #ifdef __cplusplus
 }
 #endif

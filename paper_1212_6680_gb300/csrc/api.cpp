@@ -1203,6 +1203,51 @@ int smg_plane_layout(int nx, int ny, int elem_bytes, int R, long long *out) {
     return SMG_OK;
 }
 
+int smg_plane_layout_kind(int nx, int ny, int elem_bytes, int R, int kind, int solo, long long *out) {
+    using namespace smg;
+    if (out == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    if (kind < 0 || kind > 2) return fail(SMG_ERR_ARG, "kind must be 0, 1 or 2");
+    const int nx_lo = (kind == 2) ? kMaxNx + 1 : 1;
+    const int nx_hi = (kind == 2) ? kMaxNxWide : (kind == 1 ? 256 : kMaxNx);
+    if (nx < nx_lo || nx > nx_hi || ny < 1 || ny > kMaxNy)
+        return fail(SMG_ERR_ARG, "nx outside the kind's range or ny outside 1..512");
+    if (elem_bytes != 4 && elem_bytes != 8) return fail(SMG_ERR_ARG, "elem_bytes must be 4 or 8");
+    if (R != 1 && R != 2 && R != 4 && R != 8 && R != 16) return fail(SMG_ERR_ARG, "R must be 1, 2, 4, 8 or 16");
+    if (solo < 0 || solo > kMaxNy) return fail(SMG_ERR_ARG, "solo must be in [0, 512]");
+    HostHierarchy H;
+    build_hierarchy(nx, ny, 1, H);
+    const size_t eb = static_cast<size_t>(elem_bytes);
+    PlaneLayout P;
+    if (kind == 0) {
+        P = (R == 1) ? plan_plane_layout(H, eb, kSmemBudget) : plan_plane_layout_cluster(H, eb, kSmemBudget, R);
+    } else if (kind == 1) {
+        P = (R == 1) ? plan_plane_layout(H, eb, kSmemBudget, 0, true) : plan_plane_layout_cluster(H, eb, kSmemBudget, R, true);
+        if (R > 1 && solo > 0 && P.smem_bytes > 0) P = with_solo_levels(H, eb, R, solo, P);
+    } else {
+        P = (R == 1) ? plan_plane_layout(H, eb, kWideSmemBudget, 16, false, true)
+                     : plan_plane_layout_cluster(H, eb, kWideSmemBudget, R, false, kMaxPlaneLevels, true);
+    }
+    for (int i = 0; i < 64; ++i) out[i] = 0;
+    out[0] = H.P;
+    out[1] = P.K;
+    out[2] = P.MF;
+    out[3] = static_cast<long long>(P.smem_bytes);
+    out[4] = P.ws_per_plane;
+    out[5] = P.off_fs;
+    out[6] = P.smem_u_mask;
+    out[7] = P.smem_g_mask;
+    out[8] = H.sum_ny;
+    out[9] = kCoefPerLine;
+    out[10] = trifac_set_elems(P.K);
+    out[11] = std::min(P.solo_from, H.P);
+    for (int m = 0; m < H.P && m < 16; ++m) {
+        out[16 + m] = P.off_u[m];
+        out[32 + m] = P.off_g[m];
+        out[48 + m] = H.ny_m[m];
+    }
+    return SMG_OK;
+}
+
 int smg_destroy(smg_handle h) {
     if (h == nullptr) return SMG_OK;
     free_levels(h);

@@ -41,7 +41,7 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "smg_batched_destroy", "smg_batched_apply", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
            "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs",
-           "smg_plane_layout", "smg_gram", "smg_krylov_history")
+           "smg_plane_layout", "smg_plane_layout_kind", "smg_gram", "smg_krylov_history")
 NET_WEIGHTS = 7776
 
 
@@ -67,6 +67,7 @@ def _load():
     L.smg_destroy.argtypes = [vp]
     L.smg_setup_coefs.argtypes = [i, i, i, i, i, i, dp, dp, ip, ip]
     L.smg_plane_layout.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_longlong)]
+    L.smg_plane_layout_kind.argtypes = [i, i, i, i, i, i, ctypes.POINTER(ctypes.c_longlong)]
     L.smg_last_error.restype = ctypes.c_char_p
     L.smg_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp]
     L.smg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -224,6 +225,17 @@ def smg_plane_layout(nx: int, ny: int, elem_bytes: int, R: int = 1) -> dict:
     return {"P": P, "K": v[1], "MF": v[2], "smem_bytes": v[3], "ws_elems": v[4], "off_fs": v[5],
             "u_mask": v[6], "g_mask": v[7], "sum_ny": v[8], "coef_per_line": v[9], "set_elems": v[10],
             "off_u": v[16:16 + P], "off_g": v[32:32 + P], "ny_m": v[48:48 + P]}
+
+
+def smg_plane_layout_kind(nx: int, ny: int, elem_bytes: int, R: int, kind: int, solo: int = 8) -> dict:
+    """The layout of one plane-cycle kernel (0 general, 1 shortened-step, 2 wide lines), host only."""
+    out = (ctypes.c_longlong * 64)()
+    _check(_lib.smg_plane_layout_kind(nx, ny, elem_bytes, R, kind, solo, out))
+    v = list(out)
+    P = v[0]
+    return {"P": P, "K": v[1], "MF": v[2], "smem_bytes": v[3], "ws_elems": v[4], "off_fs": v[5],
+            "u_mask": v[6], "g_mask": v[7], "sum_ny": v[8], "coef_per_line": v[9], "set_elems": v[10],
+            "solo_from": v[11], "off_u": v[16:16 + P], "off_g": v[32:32 + P], "ny_m": v[48:48 + P]}
 
 
 def smg_apply_A_dot_static(nx: int, ny: int, nz: int, u, out, dot, stream=None) -> None:
