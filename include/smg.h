@@ -105,7 +105,12 @@ enum {
                                  while the tables take at most 512 MB) read the line solver's
                                  segment factors and reduced-system rows from tables formed once
                                  when the level vectors are allocated; 0: formed inside the plane
-                                 cycle at every change of line matrix.  Bit-identical results */
+                                 cycle at every change of line matrix.  Bit-identical results */,
+    SMG_OPT_WIDE_MIN_ROWS = 13 /* 257 (default) or 513: x-lines of at least this many rows (and at
+                                 most 512) are split over two warps of 8 rows per lane (the
+                                 wide-line kernel, with its clusters and tables) instead of one
+                                 warp of 16 (the general plane cycle); lines longer than 512 rows
+                                 always take the wide-line kernel.  The two differ by rounding */
 };
 
 /*
@@ -440,8 +445,9 @@ int smg_plane_layout(int nx, int ny, int elem_bytes, int R, long long *out);
  *           on a cluster (R > 1) the 2D levels of at most `solo` lines from the first such level
  *           on are held whole by the cluster's first CTA where that keeps on chip every array the
  *           spread plan keeps (solo = 0: none);
- *   kind 2: the wide-line cycle, 513 <= nx <= 2048: no factor sets on chip (MF = 0), 2 KB of the
- *           shared memory left to the kernel's static arrays.
+ *   kind 2: the wide-line cycle, 257 <= nx <= 2048 (K = 8 rows per lane up to 512 rows, else 16):
+ *           no factor sets on chip (MF = 0), 2 KB of the shared memory left to the kernel's
+ *           static arrays.
  * out as smg_plane_layout's, plus [11] the first 2D level held whole by the first CTA (P when
  * none).  A level held whole keeps all ny_m lines on every CTA's plan (CTA 0 uses them); a spread
  * level keeps 2 ceil(ceil(ny_m / 2) / R) lines.  Residency of the cluster on the GPU is not

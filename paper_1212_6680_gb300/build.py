@@ -20,7 +20,8 @@ LIB = os.path.join(HERE, "libsmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 KS = (1, 2, 3, 4, 6, 8, 16)
 SOURCES = ["api.cpp", "hierarchy.cpp", "cycle.cu", "krylov_kernels.cu", "lobpcg.cu", "noalloc.cu", "batched.cu", "net.cu",
-           "net_api.cpp", "conv_tc.cu", "gram_tc.cu", "plane_wide.cu"]
+           "net_api.cpp", "conv_tc.cu", "gram_tc.cu"]
+WKS = (8, 16)  # rows per lane of the wide-line kernel's segments (plane_wide.cu, one unit each)
 
 
 def nvcc() -> str:
@@ -42,6 +43,9 @@ def _units():
         obj = os.path.join(BUILD, os.path.splitext(s)[0] + ".o")
         lang = ["-x", "cu"] if s.endswith(".cu") else ["-x", "c++"]
         units.append((src, obj, lang, []))
+    for w in WKS:
+        units.append((os.path.join(CSRC, "plane_wide.cu"), os.path.join(BUILD, f"plane_wide_w{w}.o"), ["-x", "cu"],
+                      [f"-DSMG_WK={w}"]))
     for k in (1, 2, 3, 4):
         src = os.path.join(CSRC, "batched_inst.cu")
         units.append((src, os.path.join(BUILD, f"batched_k{k}.o"), ["-x", "cu"], [f"-DSMG_K={k}"]))

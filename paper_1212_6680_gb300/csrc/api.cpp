@@ -93,6 +93,7 @@ struct smg_ctx {
                                     // `solo` lines to CTA 0 (0: none)
     int restrict_column = 1;        // 1: the restriction walks columns of coarse planes where it
                                     // pays (launch_restrict)
+    int wide_min = 257;             // lines of at least this many rows run the wide-line kernel
     int wide_factors = 1;           // 1: wide-line planes read their line-solver data from tables
                                     // formed with the level vectors (d_wftab)
     unsigned char *d_wftab = nullptr;  // those tables (each level's in its compute type)
@@ -181,6 +182,13 @@ int instantiated_K(int nx) {
 
 int alloc_plane_workspace(smg_ctx *h, int nb);
 
+// Rows per lane of the wide-line kernel's segments for this handle's lines, 0 when the lines go
+// to the one-warp kernels: 16 beyond 512 rows (always), 8 from wide_min (257 by default) to 512.
+int wide_rows(const smg_ctx *h) {
+    if (h->nx > kMaxNx) return 16;
+    return (h->nx > 256 && h->nx >= h->wide_min) ? 8 : 0;
+}
+
 // The shortened-step cycle on a cluster: the coarse 2D levels from the first one with at most
 // max_lines lines are held whole by CTA 0, provided the layout still keeps on chip every array
 // the spread layout `base` keeps; else the next coarser level is tried, and `base` is kept when
@@ -213,14 +221,15 @@ int ensure_levels(smg_ctx *h, int nb) {
         SMG_CUDA(cudaMalloc(&h->d_u[l], bytes));
     }
     const bool f64c = (h->prec == Prec::F64);
-    const bool wide = wide_segments(h->nx) > 1;
+    const int wk = wide_rows(h);
+    const bool wide = wk > 0;
     if (wide) {
         // x-lines over several warps (plane_wide.cu): one CTA per plane, segment factors formed on
         // the fly, no cluster and no shortened-step layouts
-        h->lay_c = plan_plane_layout(H, compute_bytes(h->prec), kWideSmemBudget, 16, false, true);
-        h->lay_d = plan_plane_layout(H, 8, kWideSmemBudget, 16, false, true);
-        if (set_plane_wide_smem(h->prec, f64c, false, h->lay_c.smem_bytes) != 0 ||
-            set_plane_wide_smem(h->prec, true, false, h->lay_d.smem_bytes) != 0)
+        h->lay_c = plan_plane_layout(H, compute_bytes(h->prec), kWideSmemBudget, wk, false, true);
+        h->lay_d = plan_plane_layout(H, 8, kWideSmemBudget, wk, false, true);
+        if (set_plane_wide_smem(wk, h->prec, f64c, false, h->lay_c.smem_bytes) != 0 ||
+            set_plane_wide_smem(wk, h->prec, true, false, h->lay_d.smem_bytes) != 0)
             return fail(SMG_ERR_CUDA, "cudaFuncSetAttribute (plane relaxation, wide lines) failed");
         // a plane spread over a cluster of R CTAs, each relaxing the lines it owns
         for (int c64 = 0; c64 < 2; ++c64) {
@@ -231,11 +240,11 @@ int ensure_levels(smg_ctx *h, int nb) {
                 PlaneLayout &ly = h->lay_wcl[c64][lr];
                 ly = plan_plane_layout_cluster(H, c64 ? 8 : 4, kWideSmemBudget, R, false, kMaxPlaneLevels, true);
                 if (ly.smem_bytes == 0 || ly.smem_bytes > kWideSmemBudget) continue;
-                if (set_plane_wide_smem(h->prec, c64 != 0, true, ly.smem_bytes) != 0) {
+                if (set_plane_wide_smem(wk, h->prec, c64 != 0, true, ly.smem_bytes) != 0) {
                     cudaGetLastError();
                     continue;
                 }
-                h->wcl_ok[c64][lr] = wide_cluster_resident(h->prec, c64 != 0, R, h->threads, ly.smem_bytes);
+                h->wcl_ok[c64][lr] = wide_cluster_resident(wk, h->prec, c64 != 0, R, h->threads, ly.smem_bytes);
             }
         }
         for (int lr = 0; lr <= 4; ++lr) h->cl_ok[lr] = h->cl32_ok[lr] = h->lean64_ok[lr] = h->lean32_ok[lr] = false;
@@ -249,8 +258,8 @@ int ensure_levels(smg_ctx *h, int nb) {
         // most 512 MB
         h->wftab_off.assign(H.L, -1);
         if (h->wide_factors) {
-            const int W = wide_segments(h->nx);
-            const long long per = wide_factor_values(H.P, W);
+            const int W = wide_segments(wk, h->nx);
+            const long long per = wide_factor_values(wk, H.P, W);
             auto bytes_of = [&](int l) -> long long {
                 const bool c64 = f64c || l == H.L - 1;
                 return per * H.nz_l[l] * (c64 ? 8 : 4);
@@ -267,7 +276,7 @@ int ensure_levels(smg_ctx *h, int nb) {
             for (int l = 0; l < H.L; ++l) {
                 if (h->wftab_off[l] < 0) continue;
                 const size_t pb = static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine;
-                SMG_CUDA(launch_wide_factor_table(h->nx, W, H.P, H.sum_ny, H.ny_m.data(), H.line_base.data(), H.nz_l[l],
+                SMG_CUDA(launch_wide_factor_table(wk, h->nx, W, H.P, H.sum_ny, H.ny_m.data(), H.line_base.data(), H.nz_l[l],
                                                   h->d_pcoef + pb, h->d_pcoef32 + pb, f64c || l == H.L - 1,
                                                   h->d_wftab + h->wftab_off[l], 0));
             }
@@ -441,7 +450,8 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     // rows (plane_wide.cu) hold several lines per team of warps and are spread the same way, FP32
     // ones over up to 8 CTAs (the paper's 16n x n x n bricks: 1280 x 80 x 80 FPCG 116 -> 57 ms).
     int R = 1;
-    const int W = wide_segments(h->nx);
+    const int wk = wide_rows(h);
+    const int W = wide_segments(wk, h->nx);
     const bool *ok = (W > 1) ? h->wcl_ok[f64c ? 1 : 0] : (f64c ? h->cl_ok : h->cl32_ok);
     int rmax;
     if (f64c) rmax = coarsest ? h->cluster_max : std::min(h->cluster_max, 8);
@@ -542,7 +552,7 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
         a.off_fs = llay->off_fs;
         a.solo_from = llay->solo_from;
     }
-    cudaError_t err = (W > 1)  ? launch_plane_wide(h->prec, f64c, nplanes, nb, h->threads, a, lay.smem_bytes, st)
+    cudaError_t err = (W > 1)  ? launch_plane_wide(wk, h->prec, f64c, nplanes, nb, h->threads, a, lay.smem_bytes, st)
                       : use_lean ? launch_plane_lean(h->prec, f64c, K, nplanes, nb, h->threads, a, llay->smem_bytes, st)
                                  : launch_plane_relax(h->prec, f64c, K, nplanes, nb, h->threads, a, lay.smem_bytes, st);
     if (err != cudaSuccess) return fail(SMG_ERR_CUDA, std::string("plane relaxation launch: ") + cudaGetErrorString(err));
@@ -901,6 +911,11 @@ int smg_set_option(smg_handle h, int option, int value) {
         if (value != h->threads) free_levels(h);  // the layouts and residency checks depend on it
         h->threads = value;
         return SMG_OK;
+    case SMG_OPT_WIDE_MIN_ROWS:
+        if (value != 257 && value != 513) return fail(SMG_ERR_ARG, "wide_min_rows must be 257 or 513");
+        if (value != h->wide_min) free_levels(h);
+        h->wide_min = value;
+        return SMG_OK;
     case SMG_OPT_WIDE_FACTORS:
         if (value != 0 && value != 1) return fail(SMG_ERR_ARG, "wide_factors must be 0 or 1");
         if (value != h->wide_factors) free_levels(h);
@@ -1207,7 +1222,7 @@ int smg_plane_layout_kind(int nx, int ny, int elem_bytes, int R, int kind, int s
     using namespace smg;
     if (out == nullptr) return fail(SMG_ERR_ARG, "null pointer");
     if (kind < 0 || kind > 2) return fail(SMG_ERR_ARG, "kind must be 0, 1 or 2");
-    const int nx_lo = (kind == 2) ? kMaxNx + 1 : 1;
+    const int nx_lo = (kind == 2) ? 257 : 1;
     const int nx_hi = (kind == 2) ? kMaxNxWide : (kind == 1 ? 256 : kMaxNx);
     if (nx < nx_lo || nx > nx_hi || ny < 1 || ny > kMaxNy)
         return fail(SMG_ERR_ARG, "nx outside the kind's range or ny outside 1..512");
@@ -1224,8 +1239,10 @@ int smg_plane_layout_kind(int nx, int ny, int elem_bytes, int R, int kind, int s
         P = (R == 1) ? plan_plane_layout(H, eb, kSmemBudget, 0, true) : plan_plane_layout_cluster(H, eb, kSmemBudget, R, true);
         if (R > 1 && solo > 0 && P.smem_bytes > 0) P = with_solo_levels(H, eb, R, solo, P);
     } else {
-        P = (R == 1) ? plan_plane_layout(H, eb, kWideSmemBudget, 16, false, true)
+        const int wk = nx > kMaxNx ? 16 : 8;
+        P = (R == 1) ? plan_plane_layout(H, eb, kWideSmemBudget, wk, false, true)
                      : plan_plane_layout_cluster(H, eb, kWideSmemBudget, R, false, kMaxPlaneLevels, true);
+        P.K = wk;
     }
     for (int i = 0; i < 64; ++i) out[i] = 0;
     out[0] = H.P;

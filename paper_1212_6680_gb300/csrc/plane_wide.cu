@@ -1,4 +1,7 @@
-// plane_wide.cu -- SMG plane relaxation for x-lines longer than one warp holds (nx > 512).
+// plane_wide.cu -- SMG plane relaxation for x-lines split over several warps: segments of
+// 32 SMG_WK rows (SMG_WK rows per lane), compiled once with SMG_WK = 16 (lines of 513-2048 rows,
+// longer than one warp holds) and once with SMG_WK = 8 (lines of 257-512 rows, two warps of 8
+// rows per lane instead of one of 16).
 //
 // The plane cycle is the one of plane_relax.cuh (section "Preconditioning with SMG" of
 // arXiv:1212.6680: plane relaxation as the SMG smoother, each plane by a 2D y-semicoarsening
@@ -34,9 +37,12 @@ namespace smg {
 
 namespace {
 
-constexpr int kWK = 16;              // rows per lane in a segment
+#ifndef SMG_WK
+#error "compile with -DSMG_WK=<rows per lane in a segment: 8 or 16>"
+#endif
+constexpr int kWK = SMG_WK;          // rows per lane in a segment
 constexpr int kSeg = 32 * kWK;       // rows per segment (one warp)
-constexpr int kMaxSeg = 4;           // segments per line: nx <= 2048
+constexpr int kMaxSeg = 4;           // segments per line: nx <= 4 kSeg
 constexpr int kXchg = 4;             // values a warp publishes per exchange
 
 template <class C>
@@ -276,6 +282,9 @@ __device__ __forceinline__ void line_matrix(const CoefRow<C> &cr, C &dg, C &of) 
 // reduced system's inverse.  Every warp of the team calls this with the same (dg, of), so every
 // warp takes the same branch below (the table's entries of one (level, set) share (dg, of)).
 template <class C>
+__device__ __noinline__ void wfac_form(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane);
+
+template <class C>
 __device__ __forceinline__ void ensure_wfac(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane,
                                             int m = -1) {
     if (wf.f.dg == dg && wf.f.of == of) return;
@@ -289,6 +298,14 @@ __device__ __forceinline__ void ensure_wfac(const WideCtx<C> &c, WideFac<C> &wf,
             }
         }
     }
+    wfac_form<C>(c, wf, dg, of, xp, lane);
+}
+
+// Form the solver data of (dg, of) in wf (a team-wide exchange inside).  One out-of-line body, so
+// that the table kernel and the plane cycle run the same instructions on the same inputs and the
+// table holds the bits the cycle would form.
+template <class C>
+__device__ __noinline__ void wfac_form(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane) {
     tri_factor<C, kWK>(wf.f, dg, of, c.ns, lane);
     const int il = c.ns - 1;
     {
@@ -767,11 +784,13 @@ bool wide_resident(int R, int threads, size_t smem) {
 
 }  // namespace
 
-int wide_segments(int nx) { return (nx + kSeg - 1) / kSeg; }
+#define SMG_WCAT(a, b) a##b
+#define SMG_WCAT2(a, b) SMG_WCAT(a, b)
+#define SMG_WNAME(base) SMG_WCAT2(base##_w, SMG_WK)
 
-long long wide_factor_values(int P, int W) { return 2LL * P * W * kWEntry; }
+long long SMG_WNAME(wide_factor_values)(int P, int W) { return 2LL * P * W * kWEntry; }
 
-cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
+cudaError_t SMG_WNAME(launch_wide_factor_table)(int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
                                      int nplanes, const double *pcoef, const float *pcoef32, bool f64, void *tab,
                                      cudaStream_t st) {
     if (W < 2 || W > kMaxSeg || P < 1 || P > kMaxPlaneLevels || nplanes < 1) return cudaErrorInvalidValue;
@@ -792,7 +811,7 @@ cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int
     return cudaGetLastError();
 }
 
-cudaError_t launch_plane_wide(Prec storage, bool f64, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
+cudaError_t SMG_WNAME(launch_plane_wide)(Prec storage, bool f64, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
                               size_t smem, cudaStream_t st) {
     if (a.W < 2 || a.W > kMaxSeg || threads / 32 < a.W || threads > 512 || a.R < 1 || a.R > 16 || (a.R & (a.R - 1)))
         return cudaErrorInvalidValue;
@@ -808,7 +827,7 @@ cudaError_t launch_plane_wide(Prec storage, bool f64, int nplanes, int nb, int t
     return cudaErrorInvalidValue;
 }
 
-int set_plane_wide_smem(Prec storage, bool f64, bool cl, size_t smem) {
+int SMG_WNAME(set_plane_wide_smem)(Prec storage, bool f64, bool cl, size_t smem) {
     switch (storage) {
     case Prec::F64: return wide_smem_attr<double, double>(cl, smem);
     case Prec::F32: return f64 ? wide_smem_attr<float, double>(cl, smem) : wide_smem_attr<float, float>(cl, smem);
@@ -818,7 +837,7 @@ int set_plane_wide_smem(Prec storage, bool f64, bool cl, size_t smem) {
     return static_cast<int>(cudaErrorInvalidValue);
 }
 
-bool wide_cluster_resident(Prec storage, bool f64, int R, int threads, size_t smem) {
+bool SMG_WNAME(wide_cluster_resident)(Prec storage, bool f64, int R, int threads, size_t smem) {
     switch (storage) {
     case Prec::F64: return wide_resident<double, double>(R, threads, smem);
     case Prec::F32: return f64 ? wide_resident<float, double>(R, threads, smem) : wide_resident<float, float>(R, threads, smem);

@@ -195,24 +195,24 @@ bool lean_cluster_resident(Prec storage, bool compute_f64, int K, int R, int thr
 // True when, on every plane of z-level l and every 2D level, the lines before the last share the
 // line matrix (S(y,y), T(y,y)) of line 0.
 bool lean_uniform_level(const HostHierarchy &H, int l);
-// Plane relaxation for nx > 512 (plane_wide.cu): x-lines cut into wide_segments(nx) segments of
-// 512 rows, one warp each, coupled through a reduced system; one CTA per plane (a.W segments).
-int wide_segments(int nx);
+// Plane relaxation with x-lines split over the warps of a team (plane_wide.cu): segments of
+// 32 wk rows, wk = 16 (lines of 513-2048 rows) or 8 (257-512 rows), one warp each.
+inline int wide_segments(int wk, int nx) { return wk > 0 ? (nx + 32 * wk - 1) / (32 * wk) : 1; }
 // Line-solver data of wide-line planes, formed once instead of at every change of line matrix
 // inside the plane cycle: for nplanes consecutive planes of one z-level (pcoef / pcoef32: their
 // coefficient tables) and every 2D level m and line set (0: the first line's matrix, 1: the
 // last line's), the segment factors, T_s^{-1} e_first, T_s^{-1} e_last and the reduced system's
 // inverse rows of every segment, in the compute type (FP64 when f64, else FP32), computed by the
-// same code as on the fly (bit-identical).  wide_factor_values(P, W): values per plane.
-long long wide_factor_values(int P, int W);
-cudaError_t launch_wide_factor_table(int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
+// same code as on the fly (bit-identical).  wide_factor_values(wk, P, W): values per plane.
+long long wide_factor_values(int wk, int P, int W);
+cudaError_t launch_wide_factor_table(int wk, int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
                                      int nplanes, const double *pcoef, const float *pcoef32, bool f64, void *tab,
                                      cudaStream_t st);
-cudaError_t launch_plane_wide(Prec storage, bool compute_f64, int nplanes, int nb, int threads,
+cudaError_t launch_plane_wide(int wk, Prec storage, bool compute_f64, int nplanes, int nb, int threads,
                               const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
-int set_plane_wide_smem(Prec storage, bool compute_f64, bool cluster, size_t smem);
+int set_plane_wide_smem(int wk, Prec storage, bool compute_f64, bool cluster, size_t smem);
 // Whether a cluster of R wide-line CTAs with `smem` bytes each fits on the GPU at once.
-bool wide_cluster_resident(Prec storage, bool compute_f64, int R, int threads, size_t smem);
+bool wide_cluster_resident(int wk, Prec storage, bool compute_f64, int R, int threads, size_t smem);
 // True when a cluster of R CTAs of the plane kernel (FP64 or FP32 compute) can be resident.
 bool cluster_resident(Prec storage, bool compute_f64, int K, int R, int threads, size_t smem);
 

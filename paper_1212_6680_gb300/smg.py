@@ -29,6 +29,7 @@ SMG_OPT_FUSED_TAIL = 9
 SMG_OPT_SOLO = 10
 SMG_OPT_RESTRICT_COLUMN = 11
 SMG_OPT_WIDE_FACTORS = 12
+SMG_OPT_WIDE_MIN_ROWS = 13
 
 VARIANTS = {"pcg": SMG_PCG, "fpcg": SMG_FPCG, "psd": SMG_PSD}
 PRECISIONS = {"fp64": SMG_FP64, "fp32": SMG_FP32, "bf16": SMG_BF16}

@@ -1,5 +1,6 @@
-"""x-lines longer than one warp holds (513 <= nx <= 2048): the plane relaxation cuts each line into
-512-row segments, one warp each, coupled exactly through a reduced system (plane_wide.cu).
+"""x-lines split over the warps of a team (plane_wide.cu): 513 <= nx <= 2048 in 512-row segments
+(16 rows per lane), 257 <= nx <= 512 in 256-row segments (8 rows per lane), one warp each,
+coupled exactly through a reduced system.
 Checked element by element against the oracle's Thomas-algorithm line solves at the tolerances
 of the other apply tests, and at the paper's brick 1280 x 80 x 80 (n = 80 of the 16n x n x n
 family, section 3, figures 5-7): apply parity and the figure 5 residual histories."""
@@ -31,7 +32,8 @@ def dev(a):
 
 # two, three and four segments; ragged last segments (600, 1100, 1290) and full ones (1024, 2048,
 # with vector access); a single line per plane (ny = 1) and a single plane (nz = 1)
-SHAPES = [(600, 20, 10), (1100, 12, 7), (1024, 16, 6), (2048, 8, 4), (1290, 9, 5), (777, 1, 6), (1536, 5, 1)]
+SHAPES = [(600, 20, 10), (1100, 12, 7), (1024, 16, 6), (2048, 8, 4), (1290, 9, 5), (777, 1, 6), (1536, 5, 1),
+          (300, 7, 3), (512, 32, 12), (257, 9, 5), (480, 20, 6)]
 TOL = {"fp64": 1e-12, "fp32": 2e-5, "bf16": 3e-2}
 
 
@@ -57,7 +59,7 @@ def test_wide_lines_apply_matches_oracle(smg, orc, shape, prec, npre, npost):
 
 
 @pytest.mark.parametrize("shape", [(600, 20, 10), (1100, 12, 7), (2048, 8, 4), (1290, 9, 5), (777, 1, 6),
-                                   (1536, 5, 1)])
+                                   (1536, 5, 1), (320, 20, 20), (512, 32, 12)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_wide_factor_tables_are_bitwise_the_on_the_fly_ones(smg, orc, shape, prec):
     """FP64 wide-line planes (the coarsest plane; every plane of the FP64 cycle) reading their
@@ -82,7 +84,7 @@ def test_wide_factor_tables_are_bitwise_the_on_the_fly_ones(smg, orc, shape, pre
 
 
 @pytest.mark.parametrize("shape", [(600, 20, 10), (1100, 12, 7), (2048, 8, 4), (1290, 9, 5), (777, 1, 6),
-                                   (1536, 5, 1), (1280, 40, 3)])
+                                   (1536, 5, 1), (1280, 40, 3), (320, 20, 20), (512, 32, 12)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_wide_planes_on_clusters_are_bitwise_one_cta(smg, orc, shape, prec):
     """Wide-line planes spread over thread-block clusters (each CTA relaxing the lines it owns,
@@ -106,6 +108,29 @@ def test_wide_planes_on_clusters_are_bitwise_one_cta(smg, orc, shape, prec):
             smg.smg_destroy(h)
     assert np.array_equal(out[False], out[True])
     assert_close(out[False], orc.SMG(nx, ny, nz, 1, 1).apply(r), TOL[prec], shape, prec)
+
+
+@pytest.mark.parametrize("shape", [(320, 20, 20), (512, 32, 12), (300, 7, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_two_warp_lines_and_one_warp_lines_both_match_oracle(smg, orc, shape, prec):
+    """Lines of 257-512 rows: two warps of 8 rows per lane (the wide-line kernel, the default) and
+    one warp of 16 (SMG_OPT_WIDE_MIN_ROWS = 513: the general plane cycle) solve the same line
+    systems exactly; both cycles match the oracle at the precision's tolerance."""
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=29)
+    ref = orc.SMG(nx, ny, nz, 1, 0).apply(r)
+    for wmin in (257, 513):
+        h = smg.smg_setup(nx, ny, nz, 1, 0)
+        try:
+            smg.smg_set_precision(h, prec)
+            smg.smg_set_option(h, smg.SMG_OPT_WIDE_MIN_ROWS, wmin)
+            rd, sd = dev(r), torch.empty(nz * ny * nx, dtype=torch.float64, device="cuda")
+            smg.smg_apply(h, rd, sd)
+            torch.cuda.synchronize()
+            s = sd.cpu().numpy()
+        finally:
+            smg.smg_destroy(h)
+        assert_close(s, ref, TOL[prec], shape, f"{prec} lines of {nx} rows, wide from {wmin}")
 
 
 def test_wide_lines_batched_apply_matches_single(smg, orc):

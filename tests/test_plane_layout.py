@@ -114,12 +114,13 @@ def test_shortened_step_layout_fits_and_does_not_overlap(smg, nx, ny, elem, R, s
 
 @pytest.mark.parametrize("elem", [4, 8])
 @pytest.mark.parametrize("R", [1, 2, 8, 16])
-@pytest.mark.parametrize("nx,ny", [(513, 1), (600, 20), (1280, 80), (2048, 512), (777, 33), (1536, 5)])
+@pytest.mark.parametrize("nx,ny", [(513, 1), (600, 20), (1280, 80), (2048, 512), (777, 33), (1536, 5), (257, 3),
+                                   (320, 20), (512, 32), (480, 240), (300, 512)])
 def test_wide_line_layout_fits_and_does_not_overlap(smg, nx, ny, elem, R):
-    """Kind 2 (lines of 513-2048 rows): no factor sets on chip, 2 KB left for the kernel's own
-    shared arrays."""
+    """Kind 2 (lines of 257-2048 rows in segments of 8 or 16 rows per lane): no factor sets on
+    chip, 2 KB left for the kernel's own shared arrays."""
     L = smg.smg_plane_layout_kind(nx, ny, elem, R, 2)
-    assert L["MF"] == 0 and L["K"] == 16 and L["solo_from"] == L["P"]
+    assert L["MF"] == 0 and L["K"] == (16 if nx > 512 else 8) and L["solo_from"] == L["P"]
     if L["smem_bytes"] == 0:
         assert R > 1
         return
@@ -127,7 +128,7 @@ def test_wide_line_layout_fits_and_does_not_overlap(smg, nx, ny, elem, R):
 
 
 def test_plane_layout_kind_rejects_bad_arguments(smg):
-    for args in ((300, 8, 4, 1, 1, 8), (512, 8, 4, 1, 2, 8), (2049, 8, 4, 1, 2, 8), (8, 8, 4, 1, 3, 8),
+    for args in ((300, 8, 4, 1, 1, 8), (256, 8, 4, 1, 2, 8), (2049, 8, 4, 1, 2, 8), (8, 8, 4, 1, 3, 8),
                  (8, 8, 4, 3, 1, 8), (8, 8, 4, 2, 1, -1)):
         with pytest.raises(Exception):
             smg.smg_plane_layout_kind(*args)
