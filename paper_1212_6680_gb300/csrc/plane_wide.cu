@@ -282,9 +282,6 @@ __device__ __forceinline__ void line_matrix(const CoefRow<C> &cr, C &dg, C &of) 
 // reduced system's inverse.  Every warp of the team calls this with the same (dg, of), so every
 // warp takes the same branch below (the table's entries of one (level, set) share (dg, of)).
 template <class C>
-__device__ __noinline__ void wfac_form(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane);
-
-template <class C>
 __device__ __forceinline__ void ensure_wfac(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane,
                                             int m = -1) {
     if (wf.f.dg == dg && wf.f.of == of) return;
@@ -298,15 +295,10 @@ __device__ __forceinline__ void ensure_wfac(const WideCtx<C> &c, WideFac<C> &wf,
             }
         }
     }
-    wfac_form<C>(c, wf, dg, of, xp, lane);
-}
-
-// Form the solver data of (dg, of) in wf (a team-wide exchange inside).  One out-of-line body, so
-// that the table kernel and the plane cycle run the same instructions on the same inputs and the
-// table holds the bits the cycle would form.
-template <class C>
-__device__ __noinline__ void wfac_form(const WideCtx<C> &c, WideFac<C> &wf, C dg, C of, int &xp, int lane) {
-    tri_factor<C, kWK>(wf.f, dg, of, c.ns, lane);
+    // the factors through the one out-of-line body (also for 8 FP32 rows per lane, which the
+    // inlined form would compile differently inside the table kernel and inside the cycle), so
+    // that a table entry holds the bits the cycle would form
+    tri_factor_call<C, kWK>(wf.f, dg, of, c.ns, lane);
     const int il = c.ns - 1;
     {
         C e[1][kWK];
