@@ -59,15 +59,18 @@ enum {
                                  plane relaxations: 1, 2, 4, 8 or 16 (default 16; levels other
                                  than the one-plane coarsest use at most 8) */
     SMG_OPT_CLUSTER_MAX32 = 4, /* the same for the FP32-compute plane relaxations of the FP32 and
-                                 BF16 cycles: 1, 2, 4, 8 or 16, or 0 (default) for 1 while a plane's
-                                 2D-cycle iterate fits in one CTA's shared memory, else 4 */
+                                 BF16 cycles: 1, 2, 4, 8 or 16, or 0 (default) for 8 with x-lines
+                                 split over several warps, else 1 while a plane's 2D-cycle iterate
+                                 fits in one CTA's shared memory and 4 when it does not */
     SMG_OPT_PRECOND = 5,      /* the preconditioner krylov_solve applies: 1 (default) the SMG cycle,
                                  0 none (T = I: plain CG by eq. (1) or (2), steepest descent for PSD;
                                  section 2, figures 1-2); lobpcg_solve always uses the cycle */
-    SMG_OPT_LEAN = 6,         /* 1 (default): FP32-compute plane relaxations on one CTA per plane
-                                 with nx <= 128 run the 2D cycle with fewer barrier-separated
-                                 steps (the restriction fused with the next level's even lines;
-                                 the same line solves in the same order); 0: the general kernel */
+    SMG_OPT_LEAN = 6,         /* 1 (default): plane relaxations with x-lines of at most 256 rows
+                                 whose layout keeps every 2D level's factor sets on chip (FP32 or
+                                 FP64 compute, one CTA or a cluster per plane) run the 2D cycle
+                                 with fewer barrier-separated steps (the restriction fused with the
+                                 next level's even lines; the same line solves in the same order,
+                                 bit-identical); 0: the general kernel */
     SMG_OPT_GRAM_TC = 7,      /* lobpcg_solve's Gram products with both block widths >= value (and
                                  <= 64) run on the tensor cores (smg_gram's digit splitting); the
                                  others, and all of them with value 0, on the CUDA cores in
@@ -100,11 +103,13 @@ enum {
                                  launch with 0, use one coarse plane per thread, recomputing the
                                  residual of every even fine plane for both coarse planes it
                                  feeds.  Bit-identical results */,
-    SMG_OPT_WIDE_FACTORS = 12 /* 1 (default): planes with x-lines longer than 512 rows that are
-                                 relaxed in FP64 (the coarsest plane; every plane of an FP64 cycle
-                                 while the tables take at most 512 MB) read the line solver's
-                                 segment factors and reduced-system rows from tables formed once
-                                 when the level vectors are allocated; 0: formed inside the plane
+    SMG_OPT_WIDE_FACTORS = 12 /* 1 (default): planes whose x-lines run on the wide-line kernel
+                                 (see SMG_OPT_WIDE_MIN_ROWS) read the line solver's data of every
+                                 2D level's two line matrices (segment factors, the segments'
+                                 responses to their end values, the reduced system's rows) from
+                                 tables formed once, in the compute precision, when the level
+                                 vectors are allocated (the coarsest level always, the others
+                                 while the tables take at most 512 MB); 0: formed inside the plane
                                  cycle at every change of line matrix.  Bit-identical results */,
     SMG_OPT_WIDE_MIN_ROWS = 13 /* 257 (default) or 513: x-lines of at least this many rows (and at
                                  most 512) are split over two warps of 8 rows per lane (the
@@ -119,11 +124,13 @@ enum {
  * sweeps (npost = 0 is the paper's nonsymmetric "no post-relaxation" cycle).  The hierarchy
  * is computed on the host in FP64 (z-semicoarsening, Galerkin coarse operators, per-plane
  * y-hierarchies) and copied to the current device; work vectors for one right-hand side are
- * allocated.  Sizes: 1 <= nx <= 2048, 1 <= ny <= 512, 1 <= nz <= 4096.  x-lines of up to 512
+ * allocated.  Sizes: 1 <= nx <= 2048, 1 <= ny <= 512, 1 <= nz <= 4096.  x-lines of up to 256
  * rows are solved by one warp; longer ones (the paper's 16n x n x n bricks up to n = 128) are cut
- * into 512-row segments, one warp each, joined exactly through a reduced system of the segment
- * ends, on one CTA per plane (the cluster and shortened-step options then do not apply).  *out
- * receives the handle.  The cycle precision starts as SMG_FP64.
+ * into segments of 256 rows (lines of 257-512 rows) or 512 rows (longer lines), one warp each,
+ * joined exactly through a reduced system of the segment ends (SMG_OPT_WIDE_MIN_ROWS = 513 keeps
+ * lines of up to 512 rows on one warp); a plane of such lines runs on one CTA or on a cluster of
+ * CTAs that own its lines in pairs, without the shortened-step cycle.  *out receives the handle.
+ * The cycle precision starts as SMG_FP64.
  */
 int smg_setup(int nx, int ny, int nz, int npre, int npost, smg_handle *out);
 

@@ -27,7 +27,8 @@ namespace smg {
 constexpr int kMaxPlaneLevels = 16;
 constexpr int kCoefPerLine = 8;
 constexpr int kCoefPerPlane = 8;
-constexpr int kMaxNx = 512;     // one warp per x-line (16 rows per lane)
+constexpr int kMaxNx = 512;     // longest x-line one warp can hold (16 rows per lane); lines of
+                                // 257-512 rows run on two warps by default (plane_wide.cu)
 constexpr int kMaxNxWide = 2048; // x-lines split over up to 4 warps (plane_wide.cu)
 constexpr int kMaxNy = 512;    // the plane's coefficient table (8 values per line of every 2D level) sits in shared memory
 constexpr int kMaxNz = 4096;
