@@ -70,7 +70,9 @@ enum {
                                  FP64 compute, one CTA or a cluster per plane) run the 2D cycle
                                  with fewer barrier-separated steps (the restriction fused with the
                                  next level's even lines; the same line solves in the same order,
-                                 bit-identical); 0: the general kernel */
+                                 bit-identical), and the wide-line kernel (longer x-lines) runs its
+                                 cycle in the same shortened step order (bit-identical); 0: the
+                                 general kernel and the general step order */
     SMG_OPT_GRAM_TC = 7,      /* lobpcg_solve's Gram products with both block widths >= value (and
                                  <= 64) run on the tensor cores (smg_gram's digit splitting); the
                                  others, and all of them with value 0, on the CUDA cores in

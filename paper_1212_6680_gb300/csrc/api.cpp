@@ -467,6 +467,7 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     PlaneRelaxArgs a;
     std::memset(&a, 0, sizeof(a));
     a.solo_from = kMaxPlaneLevels;
+    a.lean = (W > 1 && h->lean) ? 1 : 0;  // wide lines: the shortened step order
     // the level's table was formed in its compute type: FP64 exactly when f64c (the coarsest level
     // or an FP64 cycle)
     if (W > 1 && h->d_wftab != nullptr && l < static_cast<int>(h->wftab_off.size()) && h->wftab_off[l] >= 0)

@@ -106,6 +106,18 @@ __device__ __forceinline__ int owned_line(const WideCtx<C> &c, int j, int n) {
     return y < n ? y : n;
 }
 
+// The i-th item of a fused step's work list over a level of n lines: the owned even lines first
+// (each carrying a line solve besides its right-hand side), then the owned odd lines, so that the
+// teams share the solves evenly; n past the last.
+template <class C>
+__device__ __forceinline__ int fused_line(const WideCtx<C> &c, int i, int n, bool &even) {
+    const int pe = (n + 1) >> 1;  // even lines of the level
+    const int ne = pe > c.rank ? (pe - c.rank + c.R - 1) >> c.lr : 0;
+    even = i < ne;
+    const int y = even ? 2 * (c.rank + (i << c.lr)) : 2 * (c.rank + ((i - ne) << c.lr)) + 1;
+    return y < n ? y : n;
+}
+
 // Row x of a line, 0 outside 0 .. nx-1.
 template <class T>
 __device__ __forceinline__ T wat(const T *line, int nx, int x) {
@@ -608,6 +620,7 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     wf.f.of = C(0);
     int xp = 0;
     const int P = a.P;
+    const bool fuse = a.lean != 0 && P > 1;  // the shortened step order (4P - 3 steps)
     for (int it = 0; it < a.iters; ++it) {
         const int mode = (it == 0) ? a.mode : 2;
         const S *fpl = fb + static_cast<long long>(z) * np;
@@ -615,54 +628,63 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
         if constexpr (std::is_same<S, C>::value) {
             if (mode == 0) c.g0 = const_cast<C *>(reinterpret_cast<const C *>(fpl));
         }
-        if (c.g0 == nullptr && active)
-            for (int j = c.team;; j += c.nteam) {
-                const int y = owned_line(c, j, ny);
-                if (y >= ny) break;
-                wide_rhs_line<S, C>(a, c, y, mode, fpl, ub, z, zc, lane);
-            }
-        step_sync();
         const bool acc = (mode == 2);
-        // the 2D cycle's steps in the order of plane_task (plane_relax.cuh)
-        const int nsteps = (P == 1) ? 1 : 5 * P - 4;
-        for (int st = 0; st < nsteps; ++st) {
-            int m, colour, nbmode, out;
-            bool accu = false, is_restrict = false;
-            if (P == 1) {
-                m = 0, colour = 0, nbmode = NB_NONE, out = OUT_PLANE, accu = acc;
-            } else if (st < 3 * (P - 1)) {
-                m = st / 3;
-                const int k = st - 3 * m;
-                is_restrict = (k == 2);
-                colour = k;
-                nbmode = (k == 0) ? NB_NONE : NB_PLAIN;
-                out = OUT_U;
-            } else if (st == 3 * (P - 1)) {
-                m = P - 1, colour = 0, nbmode = NB_NONE, out = OUT_U;
+        const bool rhs = (c.g0 == nullptr);
+        // step -1 forms the right-hand side of level 0 (where the plane of f is not used
+        // directly); then the 2D cycle's steps in the order of plane_task (plane_relax.cuh):
+        // down-sweep steps (even lines, odd lines, restriction per level, then the coarsest
+        // level's lines) and up-sweep steps (odd lines with the coarse correction, even lines per
+        // level).  In the shortened order every step that fills a level's right-hand side (step
+        // -1, each restriction) also solves that level's even lines, which start from zero and
+        // read no coupling.
+        const int down = fuse ? 2 * (P - 1) : 3 * (P - 1) + 1;
+        const int nsteps = (P == 1) ? 1 : down + 2 * (P - 1);
+        for (int st = -1; st < nsteps; ++st) {
+            int m = 0, colour = 0, nbmode = NB_NONE, out = OUT_U;
+            bool accu = false, solve = true;
+            int pre = 0;  // 1: the right-hand side of each listed line, 2: its restriction
+            if (st < 0) {
+                pre = rhs ? 1 : 0;
+                solve = fuse;
+            } else if (P == 1) {
+                out = OUT_PLANE, accu = acc;
+            } else if (st < down) {
+                if (fuse) {
+                    m = (st >> 1) + (st & 1);
+                    if (st & 1) pre = 2;
+                    else colour = 1, nbmode = NB_PLAIN;
+                } else if (st < 3 * (P - 1)) {
+                    m = st / 3;
+                    const int k = st - 3 * m;
+                    if (k == 2) {
+                        m += 1, pre = 2, solve = false;
+                    } else {
+                        colour = k;
+                        nbmode = (k == 0) ? NB_NONE : NB_PLAIN;
+                    }
+                } else {
+                    m = P - 1;
+                }
             } else {
-                const int u = st - 3 * (P - 1) - 1;
+                const int u = st - down;
                 m = P - 2 - u / 2;
                 colour = (u & 1) ? 0 : 1;
                 nbmode = colour ? NB_CORR : NB_PLAIN;
                 out = (m > 0) ? OUT_U : (colour ? OUT_U_AND_PLANE : OUT_PLANE);
                 accu = acc;
             }
-            if (active) {
-                if (is_restrict) {
-                    const int nc = c.ny[m + 1];
-                    for (int j = c.team;; j += c.nteam) {
-                        const int jc = owned_line(c, j, nc);
-                        if (jc >= nc) break;
-                        wide_restrict_line<C>(c, m, jc, lane);
-                    }
-                } else {
-                    // line colour + 2i belongs to CTA i mod R
-                    const int nl = (c.ny[m] - colour + 1) / 2;
-                    for (int k = c.team;; k += c.nteam) {
-                        const int i = c.rank + (k << c.lr);
-                        if (i >= nl) break;
-                        wide_relax_line<S, C>(c, wf, m, colour + 2 * i, plane, accu, nbmode, out, xp, lane);
-                    }
+            if (active && (pre != 0 || solve)) {
+                // a filling step lists every owned line of level m (even ones first) and solves
+                // the even ones; a relaxation lists the owned lines of its colour (line
+                // colour + 2i belongs to CTA i mod R)
+                const int n = c.ny[m];
+                for (int i = c.team;; i += c.nteam) {
+                    bool even = true;
+                    const int y = pre ? fused_line(c, i, n, even) : colour + 2 * (c.rank + (i << c.lr));
+                    if (y >= n) break;
+                    if (pre == 1) wide_rhs_line<S, C>(a, c, y, mode, fpl, ub, z, zc, lane);
+                    else if (pre == 2) wide_restrict_line<C>(c, m - 1, y, lane);
+                    if (solve && even) wide_relax_line<S, C>(c, wf, m, y, plane, accu, nbmode, out, xp, lane);
                 }
             }
             step_sync();

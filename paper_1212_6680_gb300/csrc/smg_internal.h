@@ -125,12 +125,13 @@ struct PlaneRelaxArgs {
     int vec;                      // 1: nx == 32 K and f, u, the workspace are 16-byte aligned
                                   // (wide lines: nx % 8 == 0 and the same alignment)
     int W;                        // x-line segments of 512 rows (1 unless nx > 512: plane_wide.cu)
-    int lean;                     // persistent multi-system kernel: 1 runs this entry with the
-                                  // shortened-step cycle (its layout keeps every factor set on chip)
+    int lean;                     // 1: the shortened step order (the persistent multi-system
+                                  // kernel, whose layout then keeps every factor set on chip; the
+                                  // wide-line kernel)
     int solo_from;                // shortened-step cycle on a cluster: 2D levels >= solo_from belong
                                   // whole to CTA 0 (kMaxPlaneLevels: none)
-    const void *wftab;            // wide lines with FP64 compute: the precomputed line-solver data of
-                                  // this level's planes (wide_factor_table), or null
+    const void *wftab;            // wide lines: the precomputed line-solver data of this level's
+                                  // planes in its compute type (wide_factor_table), or null
 };
 
 // Placement of the per-plane 2D-cycle arrays: shared memory where they fit, else global.

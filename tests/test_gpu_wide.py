@@ -110,6 +110,33 @@ def test_wide_planes_on_clusters_are_bitwise_one_cta(smg, orc, shape, prec):
     assert_close(out[False], orc.SMG(nx, ny, nz, 1, 1).apply(r), TOL[prec], shape, prec)
 
 
+@pytest.mark.parametrize("shape", [(600, 20, 10), (1100, 12, 7), (2048, 8, 4), (1290, 9, 5), (777, 1, 6),
+                                   (1536, 5, 1), (1280, 40, 3), (320, 20, 20), (512, 32, 12), (257, 9, 5)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("npre,npost", [(1, 0), (1, 1)])
+def test_wide_shortened_step_order_is_bitwise_the_general_one(smg, orc, shape, prec, npre, npost):
+    """The wide-line kernel's shortened step order (SMG_OPT_LEAN = 1, the default: each step that
+    fills a 2D level's right-hand side also solves that level's even lines) performs the same line
+    solves on the same data as the general order (SMG_OPT_LEAN = 0): the cycle is bit for bit the
+    same, on one CTA or a cluster per plane."""
+    nx, ny, nz = shape
+    r = inputs.rhs(nx, ny, nz, seed=31)
+    out = {}
+    for lean in (1, 0):
+        h = smg.smg_setup(nx, ny, nz, npre, npost)
+        try:
+            smg.smg_set_precision(h, prec)
+            smg.smg_set_option(h, smg.SMG_OPT_LEAN, lean)
+            rd, sd = dev(r), torch.empty(nz * ny * nx, dtype=torch.float64, device="cuda")
+            smg.smg_apply(h, rd, sd)
+            torch.cuda.synchronize()
+            out[lean] = sd.cpu().numpy()
+        finally:
+            smg.smg_destroy(h)
+    assert np.array_equal(out[0], out[1])
+    assert_close(out[1], orc.SMG(nx, ny, nz, npre, npost).apply(r), TOL[prec], shape, prec)
+
+
 @pytest.mark.parametrize("shape", [(320, 20, 20), (512, 32, 12), (300, 7, 3)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_two_warp_lines_and_one_warp_lines_both_match_oracle(smg, orc, shape, prec):
