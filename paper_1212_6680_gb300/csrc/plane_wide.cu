@@ -65,6 +65,14 @@ struct WideCtx {
 };
 
 // The line solver's data for one line matrix (dg, of) on this warp's segment.
+// Threads of a wide-line CTA: 512 for FP64 compute; 384 for FP32 compute, which leaves 168
+// registers a thread (128 at 512) for the line-solver data (fewer teams of warps per CTA, but
+// measured faster on the paper's bricks).
+template <class C>
+constexpr int wide_threads() { return sizeof(C) == 8 ? 512 : 384; }
+template <class C>
+constexpr bool kWfRegs() { return sizeof(C) == 8 || kWK == 8; }
+
 template <class C>
 struct WideFac {
     TriFac<C, kWK> f;                    // factors of T_s (rows >= ns are identity rows)
@@ -309,8 +317,16 @@ __device__ __forceinline__ void ensure_wfac(const WideCtx<C> &c, WideFac<C> &wf,
     }
     // the factors through the one out-of-line body (also for 8 FP32 rows per lane, which the
     // inlined form would compile differently inside the table kernel and inside the cycle), so
-    // that a table entry holds the bits the cycle would form
-    tri_factor_call<C, kWK>(wf.f, dg, of, c.ns, lane);
+    // that a table entry holds the bits the cycle would form.  Formed into a copy where wf then
+    // stays in registers (FP64; 8 FP32 rows per lane); with 16 FP32 rows per lane wf is left
+    // in local memory, which measured faster than the spills of a register-resident copy.
+    if constexpr (kWfRegs<C>()) {
+        TriFac<C, kWK> tf;
+        tri_factor_call<C, kWK>(tf, dg, of, c.ns, lane);
+        wf.f = tf;
+    } else {
+        tri_factor_call<C, kWK>(wf.f, dg, of, c.ns, lane);
+    }
     const int il = c.ns - 1;
     {
         C e[1][kWK];
@@ -541,7 +557,7 @@ __device__ __forceinline__ void wide_rhs_line(const PlaneRelaxArgs &a, const Wid
 // One CTA (CL = false) or one cluster of a.R CTAs (CL = true) per plane of the colour; blockIdx.y
 // is the batch entry.
 template <class S, class C, bool CL>
-__global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constant__ PlaneRelaxArgs a) {
+__global__ void __launch_bounds__(wide_threads<C>(), 1) plane_wide_kernel(const __grid_constant__ PlaneRelaxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) C s_xb[2 * 16 * kXchg];
     __shared__ int s_ny[kMaxPlaneLevels], s_lb[kMaxPlaneLevels], s_uon[kMaxPlaneLevels], s_gon[kMaxPlaneLevels];
@@ -615,6 +631,7 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
     __syncthreads();
     pdl_wait();
     step_sync();  // (cluster) every CTA's level table and shared memory are set up
+    SMG_TRACE(0);
     WideFac<C> wf;
     wf.f.dg = C(0);  // no real line matrix has a zero diagonal: the first line always factors
     wf.f.of = C(0);
@@ -688,6 +705,7 @@ __global__ void __launch_bounds__(512, 1) plane_wide_kernel(const __grid_constan
                 }
             }
             step_sync();
+            SMG_TRACE(st + 2);
         }
     }
 }
@@ -748,6 +766,7 @@ __global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
 
 template <class S, class C>
 cudaError_t launch_wide(int nplanes, int nb, int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
+    threads = std::min(threads, wide_threads<C>());
     if (a.R <= 1) return launch_pdl(plane_wide_kernel<S, C, false>, dim3(nplanes, nb), dim3(threads), smem, st, a);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nplanes * a.R, nb, 1);
@@ -777,6 +796,7 @@ int wide_smem_attr(bool cl, size_t smem) {
 
 template <class S, class C>
 bool wide_resident(int R, int threads, size_t smem) {
+    threads = std::min(threads, wide_threads<C>());
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(R, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);
