@@ -524,8 +524,14 @@ __device__ __forceinline__ void plane_lean_task(const PlaneRelaxArgs &a, int pid
 
 // One CTA (CL = false) or one cluster of R CTAs (CL = true) per plane of the colour; blockIdx.y
 // is the batch entry.
+// Threads of a shortened-step CTA: 512 for FP32 compute; 384 for FP64 compute, which leaves 168
+// registers a thread for the FP64 line factors instead of spilling them (measured faster on the
+// FP64 cycle and the FP64 coarsest plane; the cycle is bit-identical for any warp count).
+template <class C>
+constexpr int lean_threads() { return sizeof(C) == 8 ? 384 : 512; }
+
 template <class S, class C, int K, bool CL>
-__global__ void __launch_bounds__(512, 1) plane_lean_kernel(const __grid_constant__ PlaneRelaxArgs a) {
+__global__ void __launch_bounds__(lean_threads<C>(), 1) plane_lean_kernel(const __grid_constant__ PlaneRelaxArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_trigger();
     int pidx, rank;
@@ -543,6 +549,7 @@ __global__ void __launch_bounds__(512, 1) plane_lean_kernel(const __grid_constan
 
 template <class S, class C, int K, bool CL>
 cudaError_t launch_lean(int nplanes, int nb, int threads, const PlaneRelaxArgs &a, size_t smem, cudaStream_t st) {
+    threads = std::min(threads, lean_threads<C>());
     if constexpr (!CL) {
         return launch_pdl(plane_lean_kernel<S, C, K, false>, dim3(nplanes, nb), dim3(threads), smem, st, a);
     } else {
@@ -574,6 +581,7 @@ int set_lean_smem_attr(size_t smem) {
 
 template <class S, class C, int K>
 bool lean_cluster_resident(int R, int threads, size_t smem) {
+    threads = std::min(threads, lean_threads<C>());
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(R, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);
