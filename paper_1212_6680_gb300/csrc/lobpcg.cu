@@ -243,10 +243,12 @@ __global__ void gram_reduce_kernel(int nchunks, int k1, int k2, int ntj, int nti
 // products in double-float arithmetic.  A CTA covers NC output columns (NC a power of two, the
 // smallest that holds the product's columns, at most kMulCols), so narrow products do no work on
 // padding.  Y may overlap U when the product has a single column block (m2 <= NC, beta = 0):
-// each thread reads all k entries of its row before it writes the row.
+// each thread reads all k entries of its row before it writes the row.  With `tri` set, C is
+// upper triangular (the Cholesky QR transform) and the multiply-adds with its zeros below the
+// diagonal are skipped (adding them would leave every sum unchanged).
 template <int NC>
 __global__ void block_mul_kernel(long long n, int k, int m2, const double *U, const double *__restrict__ C,
-                                 double alpha, double beta, double *Y) {
+                                 double alpha, double beta, double *Y, int tri) {
     extern __shared__ __align__(16) float2 cs[];  // [k][NC] (hi, lo) pairs of C's column block
     const int j0 = blockIdx.y * NC;
     const int nc = min(NC, m2 - j0);
@@ -263,17 +265,20 @@ __global__ void block_mul_kernel(long long n, int k, int m2, const double *U, co
 #pragma unroll
     for (int j = 0; j < NC; ++j) S[j] = sl[j] = 0.0f;
     double un = U[r];  // the next row's operand is loaded before the current row's multiply-adds
-    for (int i = 0; i < k; ++i) {
+    const int kend = tri ? min(k, j0 + NC) : k;  // rows of C below the block's last column are zero
+    for (int i = 0; i < kend; ++i) {
         float uh, ul;
         df_split(un, uh, ul);
-        if (i + 1 < k) un = U[static_cast<long long>(i + 1) * n + r];
+        if (i + 1 < kend) un = U[static_cast<long long>(i + 1) * n + r];
         if constexpr (NC == 1) {
+            if (tri && i > j0) continue;
             const float2 cc = cs[i];
             df_mac(S[0], sl[0], uh, ul, cc.x, cc.y);
         } else {
             const float4 *c4 = reinterpret_cast<const float4 *>(cs + i * NC);  // two (hi, lo) pairs per load
 #pragma unroll
             for (int j = 0; j < NC; j += 2) {
+                if (tri && i > j0 + j + 1) continue;  // C[i][j0 + j] = C[i][j0 + j + 1] = 0
                 const float4 cc = c4[j / 2];
                 df_mac(S[j], sl[j], uh, ul, cc.x, cc.y);
                 df_mac(S[j + 1], sl[j + 1], uh, ul, cc.z, cc.w);
@@ -600,17 +605,19 @@ int gram(Ctx &c, int k1, const double *U, int k2, const double *V, std::vector<d
 
 // Y = alpha U C + beta Y with C (k x m2, host row-major).  Y may overlap U (the product written
 // in place) when m2 <= kMulCols and beta = 0 (block_mul_kernel).
-int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, double alpha, double beta, double *Y) {
+int bmul(Ctx &c, int k, const double *U, int m2, const std::vector<double> &C, double alpha, double beta, double *Y,
+         bool tri = false) {
     LCHK(cudaMemcpyAsync(c.w.coef, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, c.st));
     const int nc = (m2 <= 1) ? 1 : (m2 <= 2) ? 2 : (m2 <= 4) ? 4 : (m2 <= 8) ? 8 : kMulCols;
     dim3 grid(cdiv(c.n, 256), cdiv(m2, nc));
     const size_t smem = sizeof(float2) * k * nc;
+    const int t = tri ? 1 : 0;
     switch (nc) {
-    case 1: block_mul_kernel<1><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
-    case 2: block_mul_kernel<2><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
-    case 4: block_mul_kernel<4><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
-    case 8: block_mul_kernel<8><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
-    default: block_mul_kernel<kMulCols><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y); break;
+    case 1: block_mul_kernel<1><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y, t); break;
+    case 2: block_mul_kernel<2><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y, t); break;
+    case 4: block_mul_kernel<4><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y, t); break;
+    case 8: block_mul_kernel<8><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y, t); break;
+    default: block_mul_kernel<kMulCols><<<grid, 256, smem, c.st>>>(c.n, k, m2, U, c.w.coef, alpha, beta, Y, t); break;
     }
     LCHK(cudaGetLastError());
     // the host vector C may be reused right after; the copy above is stream-ordered but reads
@@ -630,15 +637,15 @@ int ortho(Ctx &c, int q, double *Y, double *AY, double *tmp, bool &ok) {
     if (!ok) return SMG_OK;
     lower_inverse_transpose(q, L.data(), Z.data());
     if (q <= kMulCols) {  // one column block: in place
-        if ((rc = bmul(c, q, Y, q, Z, 1.0, 0.0, Y))) return rc;
-        if (AY && (rc = bmul(c, q, AY, q, Z, 1.0, 0.0, AY))) return rc;
+        if ((rc = bmul(c, q, Y, q, Z, 1.0, 0.0, Y, true))) return rc;
+        if (AY && (rc = bmul(c, q, AY, q, Z, 1.0, 0.0, AY, true))) return rc;
         return SMG_OK;
     }
     const size_t bytes = sizeof(double) * static_cast<size_t>(q) * c.n;
-    if ((rc = bmul(c, q, Y, q, Z, 1.0, 0.0, tmp))) return rc;
+    if ((rc = bmul(c, q, Y, q, Z, 1.0, 0.0, tmp, true))) return rc;
     LCHK(cudaMemcpyAsync(Y, tmp, bytes, cudaMemcpyDeviceToDevice, c.st));
     if (AY) {
-        if ((rc = bmul(c, q, AY, q, Z, 1.0, 0.0, tmp))) return rc;
+        if ((rc = bmul(c, q, AY, q, Z, 1.0, 0.0, tmp, true))) return rc;
         LCHK(cudaMemcpyAsync(AY, tmp, bytes, cudaMemcpyDeviceToDevice, c.st));
     }
     return SMG_OK;
