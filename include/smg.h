@@ -52,7 +52,9 @@ enum { SMG_FP64 = 0, SMG_FP32 = 1, SMG_BF16 = 2 };     /* V-cycle storage precis
 /* Options for smg_set_option. */
 enum {
     SMG_OPT_COARSE_ITERS = 0, /* plane-cycle steps on the one-plane coarsest level (>= 1, default 1) */
-    SMG_OPT_THREADS = 1,      /* threads per CTA of the plane-relaxation kernel: 256 or 512 */
+    SMG_OPT_THREADS = 1,      /* threads per CTA of the plane-relaxation kernels: 256 or 512
+                                 (default 512; the shortened-step kernel with FP64 compute and the
+                                 wide-line kernel with FP32 compute use at most 384, for registers) */
     SMG_OPT_PROFILE = 2,      /* time plane-relaxation launches with CUDA events: 0 off,
                                  1 the finest level's launches only, 2 every launch */
     SMG_OPT_CLUSTER_MAX = 3,  /* largest thread-block cluster (CTAs per plane) for the FP64
