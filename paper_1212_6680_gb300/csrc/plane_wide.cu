@@ -6,8 +6,8 @@
 // The plane cycle is the one of plane_relax.cuh (section "Preconditioning with SMG" of
 // arXiv:1212.6680: plane relaxation as the SMG smoother, each plane by a 2D y-semicoarsening
 // V-cycle with exact x-line solves); only the x-line solve changes.  A line of nx rows is cut
-// into W = ceil(nx / 512) segments of 512 rows (the last one shorter), and a team of W warps
-// owns the line, warp s holding segment s (16 rows per lane).  The exact solve of the Toeplitz
+// into W = ceil(nx / (32 SMG_WK)) segments of 32 SMG_WK rows (the last one shorter), and a team
+// of W warps owns the line, warp s holding segment s.  The exact solve of the Toeplitz
 // tridiagonal system T x = d (diagonal dg, off-diagonal of, Dirichlet ends) is split as follows.
 // With T_s the segment's own block and x_s its part of x,
 //     T_s x_s = d_s - of v_{s-1} e_first - of u_{s+1} e_last,
@@ -28,9 +28,12 @@
 // plane: line y of an array kept on chip then belongs to CTA (y/2) mod R (local line
 // ((y/2) div R)*2 + y mod 2, the layout of plan_plane_layout_cluster), which relaxes, restricts
 // and assembles it, reading other CTAs' lines through distributed shared memory; the team of a
-// line is always inside one CTA.  The shortened-step cycle is not used for these planes.  With FP64 compute the solver data of every 2D level's two line
-// matrices can come from a table formed once per set-up (wide_factor_kernel): at about two FP64
-// FMAs per clock per SM, forming them costs a one-CTA plane tens of microseconds per step.
+// line is always inside one CTA.  The 2D cycle runs in the general step order or in the
+// shortened one of plane_lean.cuh (each step that fills a level's right-hand side also solves
+// that level's even lines; the same solves on the same data, bit-identical).  The solver data of
+// every 2D level's two line matrices can come from a table formed once per allocation of the
+// level vectors (wide_factor_kernel), in the level's compute type: at about two FP64 FMAs per
+// clock per SM, forming them costs a one-CTA FP64 plane tens of microseconds per step.
 #include "plane_relax.cuh"
 
 namespace smg {
@@ -231,7 +234,7 @@ __device__ __forceinline__ void wload_nb(C (&v)[kWK], C &hl, C &hr, const WideCt
     }
 }
 
-// Value of row i of the segment (held by lane i / 16, register i % 16), broadcast to the warp.
+// Value of row i of the segment (held by lane i / kWK, register i % kWK), broadcast to the warp.
 template <class C>
 __device__ __forceinline__ C seg_value(const C (&v)[kWK], int i) {
     const int l = i / kWK, j = i - l * kWK;
