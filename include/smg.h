@@ -431,6 +431,19 @@ int smg_apply_A_dot_static(int nx, int ny, int nz, const double *u, double *out,
 int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, double *lines, int *nz_l, int *ny_m);
 
 /*
+ * smg_plane_classes -- the planes of z-level l that share one set of line-solver data, on the
+ * host only (no device, no handle).  Planes whose 2D hierarchies (the `lines` of
+ * smg_setup_coefs, every 2D level) are bit for bit equal form one class; the wide-line plane
+ * relaxation (x-lines of more than 256 rows) forms its line-solver table once per class.
+ *   cls: nz_l ints (host, caller-owned): the class of each plane of level l, numbered in order
+ *        of first appearance (so cls[0] = 0).
+ * Returns the number of classes (>= 1), or SMG_ERR_ARG (a grid smg_setup refuses, l out of
+ * range, cls NULL; nothing written) or SMG_ERR_HOST (host allocation).  Builds the whole host
+ * hierarchy like smg_setup_coefs: for inspection and tests.
+ */
+int smg_plane_classes(int nx, int ny, int nz, int l, int *cls);
+
+/*
  * smg_plane_layout -- where the plane-relaxation kernel keeps the arrays of a plane's 2D cycle
  * (host only, no device): the layout the library plans for an nx x ny plane computed in
  * elem_bytes-byte arithmetic (4 or 8) by one CTA (R = 1) or by a cluster of R = 2, 4, 8 or 16

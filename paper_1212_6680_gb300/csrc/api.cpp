@@ -98,6 +98,9 @@ struct smg_ctx {
                                     // formed with the level vectors (d_wftab)
     unsigned char *d_wftab = nullptr;  // those tables (each level's in its compute type)
     std::vector<long long> wftab_off;  // [L] byte offset of level l's table in d_wftab, -1: none
+    int *d_wfslot = nullptr;           // per level with a table: the slot of each plane (nz_l ints),
+                                       // then the plane of each slot (one slot per plane class)
+    std::vector<long long> wfslot_off; // [L] int offset of level l's slots in d_wfslot
     std::vector<char> lean_level;   // [L] the level's line matrices allow it (lean_uniform_level)
     PlaneLayout lay_lean64[5];      // FP64-compute shortened-step layouts: one CTA, clusters of 2..16
     bool lean64_ok[5] = {false, false, false, false, false};
@@ -160,6 +163,9 @@ void free_levels(smg_ctx *h) {
     cudaFree(h->d_wftab);
     h->d_wftab = nullptr;
     h->wftab_off.clear();
+    cudaFree(h->d_wfslot);
+    h->d_wfslot = nullptr;
+    h->wfslot_off.clear();
     for (void *p : h->d_f) cudaFree(p);
     for (void *p : h->d_u) cudaFree(p);
     h->d_f.clear();
@@ -254,30 +260,49 @@ int ensure_levels(smg_ctx *h, int nb) {
             SMG_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
         }
         // line-solver tables, each level's in its compute type (FP64 on the coarsest level and in an
-        // FP64 cycle, else FP32): the coarsest level always, the others while all tables take at
-        // most 512 MB
+        // FP64 cycle, else FP32), one slot per class of planes with bit-identical coefficient
+        // tables (the data depend on nothing else): the coarsest level always, the others while
+        // all tables take at most 512 MB
         h->wftab_off.assign(H.L, -1);
+        h->wfslot_off.assign(H.L, -1);
         if (h->wide_factors) {
             const int W = wide_segments(wk, h->nx);
             const long long per = wide_factor_values(wk, H.P, W);
+            std::vector<std::vector<int>> slot(H.L), rep(H.L);
+            for (int l = 0; l < H.L; ++l) plane_classes(H, l, slot[l], rep[l]);
             auto bytes_of = [&](int l) -> long long {
                 const bool c64 = f64c || l == H.L - 1;
-                return per * H.nz_l[l] * (c64 ? 8 : 4);
+                return per * static_cast<long long>(rep[l].size()) * (c64 ? 8 : 4);
             };
             long long all = 0;
             for (int l = 0; l < H.L; ++l) all += bytes_of(l);
             const bool every = all <= (512ll << 20);
             long long off = 0;
+            std::vector<int> ints;
             for (int l = every ? 0 : H.L - 1; l < H.L; ++l) {
                 h->wftab_off[l] = off;
                 off += (bytes_of(l) + 255) / 256 * 256;
+                // slots of the planes, then the plane of each slot; every index checked here
+                // bounds a device read (a table slot, a coefficient table)
+                const int nc = static_cast<int>(rep[l].size());
+                for (int z = 0; z < H.nz_l[l]; ++z)
+                    if (slot[l][z] < 0 || slot[l][z] >= nc) return fail(SMG_ERR_HOST, "plane class out of range");
+                for (int c = 0; c < nc; ++c)
+                    if (rep[l][c] < 0 || rep[l][c] >= H.nz_l[l]) return fail(SMG_ERR_HOST, "plane class out of range");
+                h->wfslot_off[l] = static_cast<long long>(ints.size());
+                ints.insert(ints.end(), slot[l].begin(), slot[l].end());
+                ints.insert(ints.end(), rep[l].begin(), rep[l].end());
             }
             SMG_CUDA(cudaMalloc(&h->d_wftab, static_cast<size_t>(off)));
+            SMG_CUDA(cudaMalloc(&h->d_wfslot, sizeof(int) * ints.size()));
+            SMG_CUDA(cudaMemcpy(h->d_wfslot, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice));
             for (int l = 0; l < H.L; ++l) {
                 if (h->wftab_off[l] < 0) continue;
                 const size_t pb = static_cast<size_t>(H.plane_base[l]) * H.sum_ny * kCoefPerLine;
-                SMG_CUDA(launch_wide_factor_table(wk, h->nx, W, H.P, H.sum_ny, H.ny_m.data(), H.line_base.data(), H.nz_l[l],
-                                                  h->d_pcoef + pb, h->d_pcoef32 + pb, f64c || l == H.L - 1,
+                const int nc = static_cast<int>(rep[l].size());
+                SMG_CUDA(launch_wide_factor_table(wk, h->nx, W, H.P, H.sum_ny, H.ny_m.data(), H.line_base.data(), nc,
+                                                  h->d_wfslot + h->wfslot_off[l] + H.nz_l[l], h->d_pcoef + pb,
+                                                  h->d_pcoef32 + pb, f64c || l == H.L - 1,
                                                   h->d_wftab + h->wftab_off[l], 0));
             }
             SMG_CUDA(cudaStreamSynchronize(0));
@@ -470,8 +495,10 @@ int relax(smg_ctx *h, int l, int colour, int mode, int iters, bool coarsest, con
     a.lean = (W > 1 && h->lean) ? 1 : 0;  // wide lines: the shortened step order
     // the level's table was formed in its compute type: FP64 exactly when f64c (the coarsest level
     // or an FP64 cycle)
-    if (W > 1 && h->d_wftab != nullptr && l < static_cast<int>(h->wftab_off.size()) && h->wftab_off[l] >= 0)
+    if (W > 1 && h->d_wftab != nullptr && l < static_cast<int>(h->wftab_off.size()) && h->wftab_off[l] >= 0) {
         a.wftab = h->d_wftab + h->wftab_off[l];
+        a.wfslot = h->d_wfslot + h->wfslot_off[l];
+    }
     a.nx = h->nx;
     a.ny = h->ny;
     a.nz = nzl;
@@ -1187,6 +1214,23 @@ int smg_setup_coefs(int nx, int ny, int nz, int l, int z, int m, double *zc, dou
     if (nz_l) *nz_l = H.nz_l[l];
     if (ny_m) *ny_m = H.ny_m[m];
     return SMG_OK;
+}
+
+int smg_plane_classes(int nx, int ny, int nz, int l, int *cls) {
+    using namespace smg;
+    if (const char *e = grid_size_error(nx, ny, nz)) return fail(SMG_ERR_ARG, e);
+    if (cls == nullptr) return fail(SMG_ERR_ARG, "null pointer");
+    if (l < 0 || l >= hierarchy_levels(nz)) return fail(SMG_ERR_ARG, "level out of range");
+    HostHierarchy H;
+    std::vector<int> slot, rep;
+    try {
+        build_hierarchy(nx, ny, nz, H);
+        plane_classes(H, l, slot, rep);
+    } catch (const std::exception &ex) {
+        return fail(SMG_ERR_HOST, std::string("building the hierarchy failed: ") + ex.what());
+    }
+    for (int z = 0; z < H.nz_l[l]; ++z) cls[z] = slot[z];
+    return static_cast<int>(rep.size());
 }
 
 int smg_plane_layout(int nx, int ny, int elem_bytes, int R, long long *out) {

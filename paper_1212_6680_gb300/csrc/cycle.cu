@@ -56,7 +56,8 @@ SMG_DECL_K(16)
 #define SMG_DECL_W(w)                                                                                 \
     long long wide_factor_values_w##w(int, int);                                                      \
     cudaError_t launch_wide_factor_table_w##w(int, int, int, int, const int *, const int *, int,       \
-                                              const double *, const float *, bool, void *, cudaStream_t); \
+                                              const int *, const double *, const float *, bool, void *, \
+                                              cudaStream_t);                                            \
     cudaError_t launch_plane_wide_w##w(Prec, bool, int, int, int, const PlaneRelaxArgs &, size_t,      \
                                        cudaStream_t);                                                 \
     int set_plane_wide_smem_w##w(Prec, bool, bool, size_t);                                           \
@@ -68,10 +69,12 @@ long long wide_factor_values(int wk, int P, int W) {
     return wk == 8 ? wide_factor_values_w8(P, W) : wide_factor_values_w16(P, W);
 }
 cudaError_t launch_wide_factor_table(int wk, int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
-                                     int nplanes, const double *pcoef, const float *pcoef32, bool f64, void *tab,
-                                     cudaStream_t st) {
-    return wk == 8 ? launch_wide_factor_table_w8(nx, W, P, sum_ny, ny_m, line_base, nplanes, pcoef, pcoef32, f64, tab, st)
-                   : launch_wide_factor_table_w16(nx, W, P, sum_ny, ny_m, line_base, nplanes, pcoef, pcoef32, f64, tab, st);
+                                     int nslots, const int *planes, const double *pcoef, const float *pcoef32,
+                                     bool f64, void *tab, cudaStream_t st) {
+    return wk == 8 ? launch_wide_factor_table_w8(nx, W, P, sum_ny, ny_m, line_base, nslots, planes, pcoef, pcoef32, f64,
+                                                 tab, st)
+                   : launch_wide_factor_table_w16(nx, W, P, sum_ny, ny_m, line_base, nslots, planes, pcoef, pcoef32,
+                                                  f64, tab, st);
 }
 cudaError_t launch_plane_wide(int wk, Prec storage, bool f64, int nplanes, int nb, int threads, const PlaneRelaxArgs &a,
                               size_t smem, cudaStream_t st) {

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <array>
 #include <cstdio>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -206,6 +207,23 @@ bool lean_uniform_level(const HostHierarchy &H, int l) {
         }
     }
     return true;
+}
+
+int plane_classes(const HostHierarchy &H, int l, std::vector<int> &slot, std::vector<int> &rep) {
+    const size_t per = static_cast<size_t>(H.sum_ny) * kCoefPerLine;
+    const double *base = &H.pcoef[static_cast<size_t>(H.plane_base[l]) * per];
+    slot.assign(H.nz_l[l], -1);
+    rep.clear();
+    for (int z = 0; z < H.nz_l[l]; ++z) {
+        for (size_t c = 0; c < rep.size() && slot[z] < 0; ++c)
+            if (std::memcmp(base + z * per, base + static_cast<size_t>(rep[c]) * per, per * sizeof(double)) == 0)
+                slot[z] = static_cast<int>(c);
+        if (slot[z] < 0) {
+            slot[z] = static_cast<int>(rep.size());
+            rep.push_back(z);
+        }
+    }
+    return static_cast<int>(rep.size());
 }
 
 // Greedy placement of the 2D-cycle arrays: the coefficient table first, then the coarsest

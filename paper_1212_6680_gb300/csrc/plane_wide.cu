@@ -603,7 +603,8 @@ __global__ void __launch_bounds__(wide_threads<C>(), 1) plane_wide_kernel(const 
     c.ftab = nullptr;
     if (a.wftab != nullptr) {  // a table of the compute type C (the host passes the matching one)
         const int zp = a.colour + 2 * pidx;  // the plane's index in its z-level
-        c.ftab = static_cast<const C *>(a.wftab) + static_cast<long long>(zp) * 2 * a.P * a.W * kWEntry;
+        const int slot = (a.wfslot != nullptr) ? a.wfslot[zp] : zp;
+        c.ftab = static_cast<const C *>(a.wftab) + static_cast<long long>(slot) * 2 * a.P * a.W * kWEntry;
     }
     const bool active = c.team < c.nteam;
     if (tid < a.P) {
@@ -714,21 +715,23 @@ __global__ void __launch_bounds__(wide_threads<C>(), 1) plane_wide_kernel(const 
 }
 
 // The solver data of one (plane, 2D level m, line set) for all W segments: one warp per segment,
-// the same ensure_wfac as inside the plane cycle.  Grid (planes, 2P), W warps per CTA.
+// the same ensure_wfac as inside the plane cycle.  Grid (slots, 2P), W warps per CTA.
 struct WideFactorArgs {
     int nx, W, P, sum_ny;
     int ny_m[kMaxPlaneLevels];
     int line_base[kMaxPlaneLevels];
+    const int *planes;    // the plane of each slot (null: slot s is plane s)
     const double *pcoef;  // the planes' coefficient tables (sum_ny lines x kCoefPerLine each)
     const float *pcoef32; // the same rounded to FP32
-    void *tab;            // out: 2P W kWEntry values of the compute type per plane
+    void *tab;            // out: 2P W kWEntry values of the compute type per slot
 };
 
 template <class C>
 __global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
     __shared__ __align__(16) C s_xb[2 * 16 * kXchg];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p = blockIdx.x, pair = blockIdx.y, m = pair >> 1, set = pair & 1;
+    const int slot = blockIdx.x, pair = blockIdx.y, m = pair >> 1, set = pair & 1;
+    const int p = (a.planes != nullptr) ? a.planes[slot] : slot;
     WideCtx<C> c;
     c.sm = nullptr;
     c.gw = nullptr;
@@ -763,8 +766,8 @@ __global__ void wide_factor_kernel(const __grid_constant__ WideFactorArgs a) {
     wf.f.of = C(0);
     int xp = 0;
     ensure_wfac<C>(c, wf, dg, of, xp, lane);
-    wfac_store<C>(static_cast<C *>(a.tab) + ((static_cast<long long>(p) * 2 * a.P + pair) * a.W + c.seg) * kWEntry, wf,
-                  lane);
+    wfac_store<C>(static_cast<C *>(a.tab) + ((static_cast<long long>(slot) * 2 * a.P + pair) * a.W + c.seg) * kWEntry,
+                  wf, lane);
 }
 
 template <class S, class C>
@@ -828,9 +831,9 @@ bool wide_resident(int R, int threads, size_t smem) {
 long long SMG_WNAME(wide_factor_values)(int P, int W) { return 2LL * P * W * kWEntry; }
 
 cudaError_t SMG_WNAME(launch_wide_factor_table)(int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
-                                     int nplanes, const double *pcoef, const float *pcoef32, bool f64, void *tab,
-                                     cudaStream_t st) {
-    if (W < 2 || W > kMaxSeg || P < 1 || P > kMaxPlaneLevels || nplanes < 1) return cudaErrorInvalidValue;
+                                     int nslots, const int *planes, const double *pcoef, const float *pcoef32,
+                                     bool f64, void *tab, cudaStream_t st) {
+    if (W < 2 || W > kMaxSeg || P < 1 || P > kMaxPlaneLevels || nslots < 1) return cudaErrorInvalidValue;
     WideFactorArgs a;
     a.nx = nx;
     a.W = W;
@@ -840,11 +843,12 @@ cudaError_t SMG_WNAME(launch_wide_factor_table)(int nx, int W, int P, int sum_ny
         a.ny_m[m] = m < P ? ny_m[m] : 0;
         a.line_base[m] = m < P ? line_base[m] : 0;
     }
+    a.planes = planes;
     a.pcoef = pcoef;
     a.pcoef32 = pcoef32;
     a.tab = tab;
-    if (f64) wide_factor_kernel<double><<<dim3(nplanes, 2 * P), 32 * W, 0, st>>>(a);
-    else wide_factor_kernel<float><<<dim3(nplanes, 2 * P), 32 * W, 0, st>>>(a);
+    if (f64) wide_factor_kernel<double><<<dim3(nslots, 2 * P), 32 * W, 0, st>>>(a);
+    else wide_factor_kernel<float><<<dim3(nslots, 2 * P), 32 * W, 0, st>>>(a);
     return cudaGetLastError();
 }
 

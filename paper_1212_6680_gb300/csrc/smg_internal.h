@@ -132,6 +132,8 @@ struct PlaneRelaxArgs {
                                   // whole to CTA 0 (kMaxPlaneLevels: none)
     const void *wftab;            // wide lines: the precomputed line-solver data of this level's
                                   // planes in its compute type (wide_factor_table), or null
+    const int *wfslot;            // with wftab: the table slot of each plane of the level (planes
+                                  // with equal coefficient tables share one), or null: slot = plane
 };
 
 // Placement of the per-plane 2D-cycle arrays: shared memory where they fit, else global.
@@ -197,6 +199,10 @@ bool lean_cluster_resident(Prec storage, bool compute_f64, int K, int R, int thr
 // True when, on every plane of z-level l and every 2D level, the lines before the last share the
 // line matrix (S(y,y), T(y,y)) of line 0.
 bool lean_uniform_level(const HostHierarchy &H, int l);
+// Classes of the planes of z-level l with bit-identical coefficient tables (pcoef): slot[z] is
+// the class of plane z (numbered in order of first appearance), rep[c] the first plane of class
+// c; returns the number of classes.
+int plane_classes(const HostHierarchy &H, int l, std::vector<int> &slot, std::vector<int> &rep);
 // Plane relaxation with x-lines split over the warps of a team (plane_wide.cu): segments of
 // 32 wk rows, wk = 16 (lines of 513-2048 rows) or 8 (257-512 rows), one warp each.
 inline int wide_segments(int wk, int nx) { return wk > 0 ? (nx + 32 * wk - 1) / (32 * wk) : 1; }
@@ -206,10 +212,12 @@ inline int wide_segments(int wk, int nx) { return wk > 0 ? (nx + 32 * wk - 1) / 
 // last line's), the segment factors, T_s^{-1} e_first, T_s^{-1} e_last and the reduced system's
 // inverse rows of every segment, in the compute type (FP64 when f64, else FP32), computed by the
 // same code as on the fly (bit-identical).  wide_factor_values(wk, P, W): values per plane.
+// The table has nslots entries of that size; slot s holds the data of plane planes[s] (device
+// array; null: plane s).
 long long wide_factor_values(int wk, int P, int W);
 cudaError_t launch_wide_factor_table(int wk, int nx, int W, int P, int sum_ny, const int *ny_m, const int *line_base,
-                                     int nplanes, const double *pcoef, const float *pcoef32, bool f64, void *tab,
-                                     cudaStream_t st);
+                                     int nslots, const int *planes, const double *pcoef, const float *pcoef32,
+                                     bool f64, void *tab, cudaStream_t st);
 cudaError_t launch_plane_wide(int wk, Prec storage, bool compute_f64, int nplanes, int nb, int threads,
                               const PlaneRelaxArgs &a, size_t smem, cudaStream_t st);
 int set_plane_wide_smem(int wk, Prec storage, bool compute_f64, bool cluster, size_t smem);

@@ -42,7 +42,7 @@ EXPORTS = ("smg_setup", "smg_set_precision", "smg_set_option", "smg_apply", "smg
            "smg_batched_destroy", "smg_batched_apply", "smg_batched_info", "smg_batched_set_profile", "smg_batched_profile_read",
            "smg_set_learned", "smg_learned_stats", "smg_collect_pairs", "smg_net_forward", "smg_net_loss_grad",
            "smg_net_train", "smg_net_set_tensor_cores", "smg_net_tc_status", "smg_setup_coefs",
-           "smg_plane_layout", "smg_plane_layout_kind", "smg_gram", "smg_krylov_history")
+           "smg_plane_layout", "smg_plane_layout_kind", "smg_gram", "smg_krylov_history", "smg_plane_classes")
 NET_WEIGHTS = 7776
 
 
@@ -67,6 +67,7 @@ def _load():
     L.lobpcg_solve.argtypes = [vp, i, vp, dp, d, i, ip, vp]
     L.smg_destroy.argtypes = [vp]
     L.smg_setup_coefs.argtypes = [i, i, i, i, i, i, dp, dp, ip, ip]
+    L.smg_plane_classes.argtypes = [i, i, i, i, ip]
     L.smg_plane_layout.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_longlong)]
     L.smg_plane_layout_kind.argtypes = [i, i, i, i, i, i, ctypes.POINTER(ctypes.c_longlong)]
     L.smg_last_error.restype = ctypes.c_char_p
@@ -215,6 +216,17 @@ def smg_setup_coefs(nx: int, ny: int, nz: int, l: int, z: int, m: int):
     _check(_lib.smg_setup_coefs(nx, ny, nz, l, z, m, zc.ctypes.data_as(dp_), lines.ctypes.data_as(dp_),
                                 ctypes.byref(nzl), ctypes.byref(nym)))
     return zc, lines[: nym.value].copy()
+
+
+def smg_plane_classes(nx: int, ny: int, nz: int, l: int):
+    """Classes of the planes of z-level l with equal 2D hierarchies (host only): (count, cls)."""
+    cls = np.full(max(nz, 1), -1, dtype=np.int32)  # level l holds at most nz planes
+    rc = _lib.smg_plane_classes(nx, ny, nz, l, cls.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    _check(min(rc, 0))
+    nzl = nz
+    for _ in range(l):
+        nzl //= 2
+    return rc, cls[:nzl].copy()
 
 
 def smg_plane_layout(nx: int, ny: int, elem_bytes: int, R: int = 1) -> dict:
