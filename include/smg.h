@@ -112,8 +112,9 @@ enum {
                                  2D level's two line matrices (segment factors, the segments'
                                  responses to their end values, the reduced system's rows) from
                                  tables formed once, in the compute precision, when the level
-                                 vectors are allocated (the coarsest level always, the others
-                                 while the tables take at most 512 MB); 0: formed inside the plane
+                                 vectors are allocated, one per class of planes with equal
+                                 coefficients (smg_plane_classes; the coarsest level always, the
+                                 others while the tables take at most 512 MB); 0: formed inside the plane
                                  cycle at every change of line matrix.  Bit-identical results */,
     SMG_OPT_WIDE_MIN_ROWS = 13 /* 257 (default) or 513: x-lines of at least this many rows (and at
                                  most 512) are split over two warps of 8 rows per lane (the
