@@ -33,6 +33,17 @@ def test_header_declarations_are_exported(smg):
     assert set(names) == set(smg.EXPORTS)
 
 
+def test_binding_constants_match_the_header(smg):
+    """The Python binding passes status codes, variants, precisions and option ids as plain
+    integers: each must be the value include/smg.h gives it."""
+    text = open(os.path.join(ROOT, "include", "smg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\b(SMG_\w+)\s*=\s*(-?\d+)", text)}
+    assert "SMG_OPT_WIDE_MIN_ROWS" in consts and "SMG_ERR_HOST" in consts
+    for name, value in consts.items():
+        assert getattr(smg, name) == value, name
+
+
 def test_library_is_built_for_sm_103a():
     from paper_1212_6680_gb300 import build
 
